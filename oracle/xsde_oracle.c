@@ -1,0 +1,501 @@
+/*
+ * xsde_oracle.c -- plain FP64 CPU oracle for the RK4IP method-of-lines step of
+ * XMDS2 (Dennis, Hope & Johnsson, arXiv:1204.4255).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
+ * reference that the CUDA path is checked against.  Only the tests, the
+ * smoke check and the CPU-baseline leg of the benchmark may load it.  It
+ * shares no code, header, table or helper with the GPU library.
+ *
+ * What it computes (one function per paper item):
+ *   - separable complex FFT on a periodic tensor-product lattice: Sec. 2.2
+ *     (fast spatial-to-spectral transforms) and the Fourier basis of Sec. 2.1;
+ *     textbook iterative radix-2 Cooley-Tukey with bit reversal.  Forward is
+ *     unnormalised (sign -1), inverse is scaled by 1/N (sign +1).
+ *   - Philox4x32-10 counter-based generator (Salmon, Moraes, Dror & Shaw,
+ *     SC'11) and Box-Muller normals: the Wiener increments of Sec. 2.5.
+ *   - RK4 in the interaction picture: Sec. 2.5 (method of lines, classical RK4)
+ *     combined with Sec. 2.6 (Eqs. PDEBeforeIPTransform/PDEAfterIPTransform),
+ *     with the picture re-centred every step so that only exp(L dt/2) is needed.
+ *   - norm and energy by equal-weight quadrature (Sec. 2.4, Fourier case) and
+ *     per-point ensemble moments over paths (Sec. 2.5, multiple paths).
+ *
+ * Conventions (the readings where the paper is silent):
+ *   - lattice x_j = xmin + j*dx on [xmin, xmax), dx = (xmax-xmin)/N;
+ *     k_j = 2*pi/(xmax-xmin) * (j < N/2 ? j : j-N);
+ *   - array layout [path][n0][n1][n2], the last grid dimension contiguous;
+ *   - L(k) = c0 + c2*|k|^2;
+ *     g(x,t,psi) = -i*(V(x,t) + gnl*|psi|^2 + alpha*xi_r)*psi + sigma*xi_a,
+ *     with xi_r a real and xi_a a real or complex spatial white noise,
+ *     <xi(x) xi(x')> = delta/(dt*dV) per step, held fixed over the 4 stages
+ *     (Stratonovich limit, Sec. 2.5);
+ *   - noise of global step n, point j, path p: Philox counter
+ *     (j, p, n+1, 0), key (seed & 0xffffffff, seed >> 32); uniforms
+ *     u = (x + 0.5) * 2^-32; z0 = sqrt(-2 ln u0) cos(2 pi u1),
+ *     z1 = sqrt(-2 ln u0) sin(2 pi u1).  Real noise uses z0, complex noise
+ *     (z0 + i z1)/sqrt(2).
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double complex cplx;
+
+#define TWO_PI 6.283185307179586476925286766559
+
+typedef struct {
+    int32_t ndim;      /* 0 (a single point: an ordinary SDE) .. 3 */
+    int32_t n[3];      /* points per dimension, powers of two */
+    double xmin[3];
+    double xmax[3];
+} oracle_grid;
+
+typedef struct {
+    double c0_re, c0_im;   /* L(k) = c0 + c2 |k|^2 */
+    double c2_re, c2_im;
+    double gnl;            /* nonlinear coefficient g */
+    double noise_amp;      /* sigma (additive) or alpha (multiplicative) */
+    double omega[3];       /* harmonic trap V = 1/2 sum omega_i^2 x_i^2 */
+    const double *V;       /* potential table [V_nt][npts] */
+    int64_t V_nt;          /* rows of the table: 1 = static, else one per step */
+    uint64_t seed;
+    int32_t pot_kind;      /* 0 none, 1 harmonic, 2 table */
+    int32_t noise_kind;    /* 0 none, 1 additive real, 2 additive complex,
+                              3 multiplicative real */
+} oracle_ops;
+
+enum { POT_NONE = 0, POT_HARMONIC = 1, POT_TABLE = 2 };
+enum { NOISE_NONE = 0, NOISE_ADD_REAL = 1, NOISE_ADD_COMPLEX = 2, NOISE_MUL_REAL = 3 };
+
+/* ------------------------------------------------------------------------- */
+/* Lattice                                                                   */
+/* ------------------------------------------------------------------------- */
+
+static int64_t grid_points(const oracle_grid *g)
+{
+    int64_t n = 1;
+    for (int d = 0; d < g->ndim; d++) n *= g->n[d];
+    return n;
+}
+
+static double grid_dx(const oracle_grid *g, int d)
+{
+    return (g->xmax[d] - g->xmin[d]) / g->n[d];
+}
+
+static double grid_dV(const oracle_grid *g)
+{
+    double v = 1.0;
+    for (int d = 0; d < g->ndim; d++) v *= grid_dx(g, d);
+    return v;
+}
+
+/* multi-index of flat point index j (last dimension fastest) */
+static void unflatten(const oracle_grid *g, int64_t j, int idx[3])
+{
+    for (int d = g->ndim - 1; d >= 0; d--) {
+        idx[d] = (int)(j % g->n[d]);
+        j /= g->n[d];
+    }
+}
+
+static double coord_x(const oracle_grid *g, int d, int i)
+{
+    return g->xmin[d] + i * grid_dx(g, d);
+}
+
+static double coord_k(const oracle_grid *g, int d, int i)
+{
+    int n = g->n[d];
+    int m = (i < n / 2) ? i : i - n;
+    return TWO_PI / (g->xmax[d] - g->xmin[d]) * m;
+}
+
+static double ksq_at(const oracle_grid *g, int64_t j)
+{
+    int idx[3];
+    unflatten(g, j, idx);
+    double s = 0.0;
+    for (int d = 0; d < g->ndim; d++) {
+        double k = coord_k(g, d, idx[d]);
+        s += k * k;
+    }
+    return s;
+}
+
+/* ------------------------------------------------------------------------- */
+/* FFT: iterative radix-2 Cooley-Tukey on one contiguous line                */
+/* ------------------------------------------------------------------------- */
+
+static void fft_line(cplx *x, int n, int sign)
+{
+    /* bit-reversal reordering */
+    for (int i = 1, j = 0; i < n; i++) {
+        int bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) {
+            cplx t = x[i];
+            x[i] = x[j];
+            x[j] = t;
+        }
+    }
+    /* butterflies of doubling length; each twiddle evaluated directly */
+    for (int len = 2; len <= n; len <<= 1) {
+        int half = len / 2;
+        for (int k = 0; k < half; k++) {
+            double ang = sign * TWO_PI * k / len;
+            cplx w = cos(ang) + I * sin(ang);
+            for (int i = 0; i < n; i += len) {
+                cplx u = x[i + k];
+                cplx v = x[i + k + half] * w;
+                x[i + k] = u + v;
+                x[i + k + half] = u - v;
+            }
+        }
+    }
+    if (sign > 0) {
+        for (int i = 0; i < n; i++) x[i] /= n;
+    }
+}
+
+/* Transform every line of every dimension of nbatch stacked arrays. */
+static void fft_nd(cplx *data, const oracle_grid *g, int64_t nbatch, int sign)
+{
+    int64_t npts = grid_points(g);
+    for (int d = 0; d < g->ndim; d++) {
+        int n = g->n[d];
+        int64_t stride = 1;
+        for (int e = d + 1; e < g->ndim; e++) stride *= g->n[e];
+        int64_t outer = npts / (stride * n);
+        int64_t nlines = nbatch * outer * stride;
+        #pragma omp parallel for schedule(static)
+        for (int64_t line = 0; line < nlines; line++) {
+            int64_t b = line / (outer * stride);
+            int64_t r = line % (outer * stride);
+            int64_t o = r / stride, s = r % stride;
+            cplx *base = data + b * npts + o * stride * n + s;
+            cplx *tmp = malloc(sizeof(cplx) * n);
+            for (int i = 0; i < n; i++) tmp[i] = base[i * stride];
+            fft_line(tmp, n, sign);
+            for (int i = 0; i < n; i++) base[i * stride] = tmp[i];
+            free(tmp);
+        }
+    }
+}
+
+void oracle_fft(double *data, const oracle_grid *g, int64_t nbatch, int32_t sign)
+{
+    fft_nd((cplx *)data, g, nbatch, sign);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 and Box-Muller                                              */
+/* ------------------------------------------------------------------------- */
+
+static void philox_round(uint32_t c[4], const uint32_t k[2])
+{
+    uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t r0 = hi1 ^ c[1] ^ k[0];
+    uint32_t r1 = lo1;
+    uint32_t r2 = hi0 ^ c[3] ^ k[1];
+    uint32_t r3 = lo0;
+    c[0] = r0; c[1] = r1; c[2] = r2; c[3] = r3;
+}
+
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+    uint32_t k[2] = {key[0], key[1]};
+    for (int round = 0; round < 10; round++) {
+        if (round > 0) {           /* Weyl-sequence key schedule */
+            k[0] += 0x9E3779B9u;
+            k[1] += 0xBB67AE85u;
+        }
+        philox_round(c, k);
+    }
+    for (int i = 0; i < 4; i++) out[i] = c[i];
+}
+
+void oracle_philox_batch(const uint32_t *ctr, const uint32_t *key, int64_t m, uint32_t *out)
+{
+    for (int64_t i = 0; i < m; i++) oracle_philox4x32_10(ctr + 4 * i, key, out + 4 * i);
+}
+
+static double uniform_open(uint32_t x)
+{
+    return ((double)x + 0.5) * (1.0 / 4294967296.0);
+}
+
+/* the normal pair (z0, z1) that step `step` draws at (point j, path p) */
+static void wiener_pair(uint64_t seed, int64_t j, int64_t p, int64_t step, double z[2])
+{
+    uint32_t ctr[4] = {(uint32_t)j, (uint32_t)p, (uint32_t)(step + 1), 0u};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t x[4];
+    oracle_philox4x32_10(ctr, key, x);
+    double u0 = uniform_open(x[0]), u1 = uniform_open(x[1]);
+    double r = sqrt(-2.0 * log(u0));
+    z[0] = r * cos(TWO_PI * u1);
+    z[1] = r * sin(TWO_PI * u1);
+}
+
+void oracle_wiener_normals(uint64_t seed, int64_t npts, int64_t npaths, int64_t path0,
+                           int64_t step, double *z)
+{
+    for (int64_t p = 0; p < npaths; p++)
+        for (int64_t j = 0; j < npts; j++)
+            wiener_pair(seed, j, path0 + p, step, z + 2 * (p * npts + j));
+}
+
+/* ------------------------------------------------------------------------- */
+/* The equation: L(k) in Fourier space, g(x, t, psi) in real space           */
+/* ------------------------------------------------------------------------- */
+
+static double potential_at(const oracle_grid *g, const oracle_ops *ops, int64_t j, int64_t step)
+{
+    if (ops->pot_kind == POT_HARMONIC) {
+        int idx[3];
+        unflatten(g, j, idx);
+        double v = 0.0;
+        for (int d = 0; d < g->ndim; d++) {
+            double x = coord_x(g, d, idx[d]);
+            v += 0.5 * ops->omega[d] * ops->omega[d] * x * x;
+        }
+        return v;
+    }
+    if (ops->pot_kind == POT_TABLE) {
+        int64_t row = (ops->V_nt > 1) ? step : 0;
+        if (row >= ops->V_nt) row = ops->V_nt - 1;
+        return ops->V[row * grid_points(g) + j];
+    }
+    return 0.0;
+}
+
+/* exp(L(k) dt/2) on every point of the lattice */
+static void half_step_factors(const oracle_grid *g, const oracle_ops *ops, double dt, cplx *E)
+{
+    cplx c0 = ops->c0_re + I * ops->c0_im;
+    cplx c2 = ops->c2_re + I * ops->c2_im;
+    int64_t npts = grid_points(g);
+    for (int64_t j = 0; j < npts; j++) E[j] = cexp((c0 + c2 * ksq_at(g, j)) * (0.5 * dt));
+}
+
+/* D(u) = iFFT( exp(L dt/2) FFT(u) ), applied to every path */
+static void apply_D(cplx *u, const cplx *E, const oracle_grid *g, int64_t npaths)
+{
+    int64_t npts = grid_points(g);
+    fft_nd(u, g, npaths, -1);
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < npaths * npts; i++) u[i] *= E[i % npts];
+    fft_nd(u, g, npaths, +1);
+}
+
+typedef struct {
+    double *Vrow;   /* potential of this step [npts] */
+    cplx *xi_a;     /* additive noise of this step [npaths][npts] (or NULL) */
+    double *xi_m;   /* multiplicative noise of this step [npaths][npts] (or NULL) */
+} step_inputs;
+
+/* out = N(u) = dt * g(x, t_n, u) for every path */
+static void nonlinear(cplx *out, const cplx *u, const oracle_ops *ops, const step_inputs *in,
+                      int64_t npts, int64_t npaths, double dt)
+{
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < npaths * npts; i++) {
+        int64_t j = i % npts;
+        double mod2 = creal(u[i]) * creal(u[i]) + cimag(u[i]) * cimag(u[i]);
+        double pot = in->Vrow[j] + ops->gnl * mod2;
+        if (in->xi_m) pot += ops->noise_amp * in->xi_m[i];
+        cplx gval = -I * pot * u[i];
+        if (in->xi_a) gval += ops->noise_amp * in->xi_a[i];
+        out[i] = dt * gval;
+    }
+}
+
+static void fill_step_inputs(step_inputs *in, const oracle_grid *g, const oracle_ops *ops,
+                             int64_t npaths, int64_t path0, int64_t step, double dt)
+{
+    int64_t npts = grid_points(g);
+    for (int64_t j = 0; j < npts; j++) in->Vrow[j] = potential_at(g, ops, j, step);
+    if (ops->noise_kind == NOISE_NONE) return;
+    double scale = 1.0 / sqrt(dt * grid_dV(g));   /* white noise per step: var 1/(dt dV) */
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < npaths * npts; i++) {
+        int64_t p = i / npts, j = i % npts;
+        double z[2];
+        wiener_pair(ops->seed, j, path0 + p, step, z);
+        if (ops->noise_kind == NOISE_ADD_REAL) in->xi_a[i] = scale * z[0];
+        else if (ops->noise_kind == NOISE_ADD_COMPLEX) in->xi_a[i] = scale * (z[0] + I * z[1]) / sqrt(2.0);
+        else in->xi_m[i] = scale * z[0];
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Observables                                                               */
+/* ------------------------------------------------------------------------- */
+
+/* per path: norm = sum |psi|^2 dV and
+ * energy = sum_k Re(i L(k)) |psi_k|^2 dV / N + sum_x (V |psi|^2 + g/2 |psi|^4) dV */
+void oracle_observables(const oracle_grid *g, const oracle_ops *ops, const double *psi_in,
+                        int64_t npaths, int64_t step, double *out)
+{
+    const cplx *psi = (const cplx *)psi_in;
+    int64_t npts = grid_points(g);
+    double dV = grid_dV(g);
+    cplx *spec = malloc(sizeof(cplx) * npaths * npts);
+    memcpy(spec, psi, sizeof(cplx) * npaths * npts);
+    fft_nd(spec, g, npaths, -1);
+    for (int64_t p = 0; p < npaths; p++) {
+        double norm = 0.0, e_lin = 0.0, e_loc = 0.0;
+        for (int64_t j = 0; j < npts; j++) {
+            cplx u = psi[p * npts + j];
+            double m2 = creal(u) * creal(u) + cimag(u) * cimag(u);
+            norm += m2 * dV;
+            e_loc += (potential_at(g, ops, j, step) * m2 + 0.5 * ops->gnl * m2 * m2) * dV;
+            cplx s = spec[p * npts + j];
+            double s2 = creal(s) * creal(s) + cimag(s) * cimag(s);
+            double hk = -ops->c0_im - ops->c2_im * ksq_at(g, j);    /* Re(i L(k)) */
+            e_lin += hk * s2 * dV / npts;
+        }
+        out[2 * p] = norm;
+        out[2 * p + 1] = e_lin + e_loc;
+    }
+    free(spec);
+}
+
+/* ------------------------------------------------------------------------- */
+/* RK4 in the interaction picture                                            */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * RK4IP, one step from t_n to t_n + dt for all paths (a is real-space psi, updated):
+ *   a_I = D(a)
+ *   k1  = D(N(a))
+ *   k2  = N(a_I + k1/2)
+ *   k3  = N(a_I + k2/2)
+ *   k4  = N(D(a_I + k3))
+ *   a  <- D(a_I + k1/6 + k2/3 + k3/3) + k4/6
+ * with D = exp(L dt/2) applied in Fourier space and N = dt*g in real space.
+ */
+
+/*
+ * Integrate nsteps RK4IP steps.  psi: [npaths][npts] complex (in/out).
+ * Paths are the global paths path0 .. path0+npaths-1; steps are the global
+ * steps step0 .. step0+nsteps-1 (the noise and the potential table row follow
+ * the global indices).  If sample_every > 0, samples are taken at local steps
+ * 0, S, 2S, ... <= nsteps:
+ *   per_path  [nsamp][npaths][2] = (norm, energy)
+ *   per_point [nsamp][npts][2]   = (mean |psi|^2, mean |psi|^4) over the paths
+ * Returns 0, or -1 on an invalid argument.
+ */
+int oracle_rk4ip(const oracle_grid *g, const oracle_ops *ops, double *psi_in, int64_t npaths,
+                 int64_t path0, double dt, int64_t nsteps, int64_t step0, int32_t sample_every,
+                 double *per_path, double *per_point)
+{
+    if (g->ndim < 0 || g->ndim > 3 || npaths < 1 || nsteps < 0) return -1;
+    for (int d = 0; d < g->ndim; d++)
+        if (g->n[d] < 1 || (g->n[d] & (g->n[d] - 1))) return -1;
+    if (ops->pot_kind == POT_TABLE && ops->V_nt > 1 && step0 + nsteps > ops->V_nt) return -1;
+
+    cplx *a = (cplx *)psi_in;
+    int64_t npts = grid_points(g), m = npaths * npts;
+    cplx *E = malloc(sizeof(cplx) * npts);
+    cplx *aI = malloc(sizeof(cplx) * m), *k1 = malloc(sizeof(cplx) * m);
+    cplx *k2 = malloc(sizeof(cplx) * m), *k3 = malloc(sizeof(cplx) * m);
+    cplx *k4 = malloc(sizeof(cplx) * m), *tmp = malloc(sizeof(cplx) * m);
+    step_inputs in;
+    in.Vrow = malloc(sizeof(double) * npts);
+    in.xi_a = (ops->noise_kind == NOISE_ADD_REAL || ops->noise_kind == NOISE_ADD_COMPLEX)
+                  ? malloc(sizeof(cplx) * m) : NULL;
+    in.xi_m = (ops->noise_kind == NOISE_MUL_REAL) ? malloc(sizeof(double) * m) : NULL;
+    double *obs = malloc(sizeof(double) * 2 * npaths);
+
+    half_step_factors(g, ops, dt, E);
+
+    int64_t sample = 0;
+    for (int64_t n = 0; n <= nsteps; n++) {
+        if (sample_every > 0 && n % sample_every == 0) {
+            if (per_path) {
+                oracle_observables(g, ops, psi_in, npaths, step0 + n, obs);
+                memcpy(per_path + sample * npaths * 2, obs, sizeof(double) * 2 * npaths);
+            }
+            if (per_point) {
+                double *pp = per_point + sample * npts * 2;
+                for (int64_t j = 0; j < npts; j++) {
+                    double s2 = 0.0, s4 = 0.0;
+                    for (int64_t p = 0; p < npaths; p++) {
+                        cplx u = a[p * npts + j];
+                        double m2 = creal(u) * creal(u) + cimag(u) * cimag(u);
+                        s2 += m2;
+                        s4 += m2 * m2;
+                    }
+                    pp[2 * j] = s2 / npaths;
+                    pp[2 * j + 1] = s4 / npaths;
+                }
+            }
+            sample++;
+        }
+        if (n == nsteps) break;
+
+        fill_step_inputs(&in, g, ops, npaths, path0, step0 + n, dt);
+
+        /* a_I = D(a) */
+        memcpy(aI, a, sizeof(cplx) * m);
+        apply_D(aI, E, g, npaths);
+        /* k1 = D(N(a)) */
+        nonlinear(k1, a, ops, &in, npts, npaths, dt);
+        apply_D(k1, E, g, npaths);
+        /* k2 = N(a_I + k1/2) */
+        for (int64_t i = 0; i < m; i++) tmp[i] = aI[i] + 0.5 * k1[i];
+        nonlinear(k2, tmp, ops, &in, npts, npaths, dt);
+        /* k3 = N(a_I + k2/2) */
+        for (int64_t i = 0; i < m; i++) tmp[i] = aI[i] + 0.5 * k2[i];
+        nonlinear(k3, tmp, ops, &in, npts, npaths, dt);
+        /* k4 = N(D(a_I + k3)) */
+        for (int64_t i = 0; i < m; i++) tmp[i] = aI[i] + k3[i];
+        apply_D(tmp, E, g, npaths);
+        nonlinear(k4, tmp, ops, &in, npts, npaths, dt);
+        /* a <- D(a_I + k1/6 + k2/3 + k3/3) + k4/6 */
+        for (int64_t i = 0; i < m; i++) tmp[i] = aI[i] + k1[i] / 6.0 + k2[i] / 3.0 + k3[i] / 3.0;
+        apply_D(tmp, E, g, npaths);
+        for (int64_t i = 0; i < m; i++) a[i] = tmp[i] + k4[i] / 6.0;
+    }
+
+    free(E); free(aI); free(k1); free(k2); free(k3); free(k4); free(tmp);
+    free(in.Vrow); free(in.xi_a); free(in.xi_m); free(obs);
+    return 0;
+}
+
+/* number of samples oracle_rk4ip writes for (nsteps, sample_every) */
+int64_t oracle_num_samples(int64_t nsteps, int32_t sample_every)
+{
+    return sample_every > 0 ? nsteps / sample_every + 1 : 0;
+}
+
+/* threads used by the OpenMP loops over lines and points (1 = serial) */
+void oracle_set_threads(int32_t n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int32_t oracle_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

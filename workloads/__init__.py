@@ -1,0 +1,223 @@
+"""Seeded synthetic inputs for the RK4IP workloads.
+
+This module only builds inputs (lattices, equation parameters, initial fields,
+space-time potentials).  It holds none of the method's arithmetic: no
+transforms, no time stepping, no noise of the integrator.  Both the CPU oracle
+and the GPU library consume what it returns, each through its own code.
+
+The workloads follow the problems of XMDS2 (arXiv:1204.4255):
+  * the 1D nonlinear Schroedinger equation (Sec. 2.6, Eq. NonlinearSchrodingerEquation)
+    with its exact bright soliton as initial state;
+  * the dimensionless trapped GPE (Sec. 3.1, Eq. NonlinearSchrodingerEquationDimensionless)
+    in 2D (Sec. 3.2) with a Thomas-Fermi initial state, and in 3D;
+  * a truncated-Wigner stochastic GPE ensemble (Sec. 3.6, many paths);
+  * Ornstein-Uhlenbeck and Kubo-oscillator SDEs (Sec. 2.5, Wiener noise in
+    Stratonovich form) as zero-dimensional problems;
+  * the harmonic ground state of Eq. InitialCondition (Sec. 3.1) driven by a
+    space-time potential, for the adjoint.
+
+Equation family shared by every workload (the reading used throughout):
+    d psi/dt = L[psi] + g(x, t, psi),   L(k) = c0 + c2 |k|^2,
+    g = -i (V(x,t) + gnl |psi|^2 + alpha xi_r) psi + sigma xi_a.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+POT_NONE, POT_HARMONIC, POT_TABLE = 0, 1, 2
+NOISE_NONE, NOISE_ADD_REAL, NOISE_ADD_COMPLEX, NOISE_MUL_REAL = 0, 1, 2, 3
+
+
+@dataclass
+class Workload:
+    """One seeded problem instance (or a batch of paths of one problem)."""
+    name: str
+    n: tuple                      # points per dimension (last contiguous); () = 0-D
+    xmin: tuple
+    xmax: tuple
+    c0: complex
+    c2: complex
+    gnl: float
+    pot_kind: int
+    omega: tuple
+    V: np.ndarray | None          # [nt][npts] float64 table, or None
+    noise_kind: int
+    noise_amp: float
+    seed: int
+    dt: float
+    nsteps: int
+    psi0: np.ndarray              # [npaths, *n] complex128
+    sample_every: int = 0
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def npaths(self) -> int:
+        return self.psi0.shape[0]
+
+    @property
+    def npts(self) -> int:
+        return int(np.prod(self.n)) if self.n else 1
+
+    def dx(self, d: int) -> float:
+        return (self.xmax[d] - self.xmin[d]) / self.n[d]
+
+    def coords(self, d: int) -> np.ndarray:
+        return self.xmin[d] + np.arange(self.n[d]) * self.dx(d)
+
+
+def _mesh(n, xmin, xmax):
+    axes = [xmin[d] + np.arange(n[d]) * (xmax[d] - xmin[d]) / n[d] for d in range(len(n))]
+    return np.meshgrid(*axes, indexing="ij")
+
+
+def harmonic_potential(n, xmin, xmax, omega) -> np.ndarray:
+    grids = _mesh(n, xmin, xmax)
+    v = np.zeros(n)
+    for d, x in enumerate(grids):
+        v += 0.5 * omega[d] ** 2 * x ** 2
+    return v
+
+
+def thomas_fermi(n, xmin, xmax, omega, g, norm=1.0) -> np.ndarray:
+    """psi = sqrt(max(mu - V, 0)/g) with mu fixed by bisection so that
+    sum |psi|^2 dV = norm on the discrete lattice, then renormalised exactly."""
+    V = harmonic_potential(n, xmin, xmax, omega)
+    dV = float(np.prod([(xmax[d] - xmin[d]) / n[d] for d in range(len(n))]))
+    lo, hi = 0.0, float(V.max()) + 10.0 * norm * g
+    for _ in range(200):
+        mu = 0.5 * (lo + hi)
+        nrm = np.maximum(mu - V, 0.0).sum() / g * dV
+        lo, hi = (mu, hi) if nrm < norm else (lo, mu)
+    dens = np.maximum(0.5 * (lo + hi) - V, 0.0) / g
+    psi = np.sqrt(dens)
+    psi *= math.sqrt(norm / (np.sum(psi ** 2) * dV))
+    return psi
+
+
+# --------------------------------------------------------------------------- #
+# The five workloads                                                          #
+# --------------------------------------------------------------------------- #
+
+def nls_soliton(n: int = 256, dt: float = 1e-3, nsteps: int = 1000, L: float = 20.0) -> Workload:
+    """1D cubic NLS i psi_t = -1/2 psi_xx - |psi|^2 psi on [-L, L) with the exact
+    bright soliton psi(x, t) = sech(x) exp(i t/2) (L = -i k^2/2, gnl = -1)."""
+    x = -L + np.arange(n) * (2 * L / n)
+    psi0 = (1.0 / np.cosh(x)).astype(np.complex128)[None, :]
+    return Workload("nls_soliton_1d", (n,), (-L,), (L,), 0j, -0.5j, -1.0, POT_NONE, (0.0,), None,
+                    NOISE_NONE, 0.0, 0, dt, nsteps, psi0)
+
+
+def gpe_2d(n: int = 512, dt: float = 1e-4, nsteps: int = 2000, g: float = 500.0, box: float = 12.0,
+           seed: int = 2, npaths: int = 1) -> Workload:
+    """2D GPE i psi_t = [-1/2 lap + 1/2 r^2 + g|psi|^2] psi on [-box, box)^2 with a
+    Thomas-Fermi state (norm 1) times exp(i 0.01 N(0,1)) seeded phase noise.
+    npaths > 1 stacks independent instances, each with its own phase noise."""
+    shape = (n, n)
+    tf = thomas_fermi(shape, (-box, -box), (box, box), (1.0, 1.0), g)
+    rng = np.random.default_rng(seed)
+    phase = 0.01 * rng.standard_normal((npaths, n, n))
+    psi0 = tf[None] * np.exp(1j * phase)
+    return Workload("gpe_2d", shape, (-box, -box), (box, box), 0j, -0.5j, g, POT_HARMONIC, (1.0, 1.0),
+                    None, NOISE_NONE, 0.0, 0, dt, nsteps, psi0.astype(np.complex128))
+
+
+def gpe_3d(n: int = 128, dt: float = 1e-4, nsteps: int = 500, g: float = 200.0, box: float = 10.0,
+           seed: int = 4) -> Workload:
+    """3D GPE on [-box, box)^3, V = r^2/2, Thomas-Fermi state (norm 1) with
+    exp(i 0.01 N(0,1)) phase noise."""
+    shape = (n, n, n)
+    tf = thomas_fermi(shape, (-box,) * 3, (box,) * 3, (1.0, 1.0, 1.0), g)
+    rng = np.random.default_rng(seed)
+    psi0 = tf[None] * np.exp(1j * 0.01 * rng.standard_normal((1,) + shape))
+    return Workload("gpe_3d", shape, (-box,) * 3, (box,) * 3, 0j, -0.5j, g, POT_HARMONIC,
+                    (1.0, 1.0, 1.0), None, NOISE_NONE, 0.0, 0, dt, nsteps, psi0.astype(np.complex128))
+
+
+def truncated_wigner(npaths: int = 4096, n: int = 1024, dt: float = 5e-4, nsteps: int = 4000,
+                     g: float = 0.1, sigma: float = 0.01, box: float = 50.0, amp2: float = 100.0,
+                     seed: int = 3, sample_every: int = 100) -> Workload:
+    """Truncated-Wigner 1D GPE ensemble on [-box, box): psi_j = sqrt(amp2) + eta_j
+    with complex Gaussian vacuum noise E|eta_j|^2 = 1/(2 dx) (each quadrature of
+    variance 1/(4 dx)), additive complex Wiener noise of strength sigma."""
+    dx = 2 * box / n
+    rng = np.random.default_rng(seed)
+    s = math.sqrt(1.0 / (4.0 * dx))
+    eta = s * (rng.standard_normal((npaths, n)) + 1j * rng.standard_normal((npaths, n)))
+    psi0 = (math.sqrt(amp2) + eta).astype(np.complex128)
+    return Workload("truncated_wigner_1d", (n,), (-box,), (box,), 0j, -0.5j, g, POT_NONE, (0.0,), None,
+                    NOISE_ADD_COMPLEX, sigma, seed, dt, nsteps, psi0, sample_every,
+                    extra={"amp2": amp2})
+
+
+def ornstein_uhlenbeck(npaths: int = 65536, theta: float = 1.0, sigma: float = 0.5, x0: float = 1.0,
+                       dt: float = 1e-3, nsteps: int = 5000, seed: int = 31,
+                       sample_every: int = 100) -> Workload:
+    """dx = -theta x dt + sigma dW as a 0-D problem (L = -theta, additive real noise)."""
+    psi0 = np.full((npaths,), x0, dtype=np.complex128)
+    return Workload("ornstein_uhlenbeck", (), (), (), complex(-theta, 0.0), 0j, 0.0, POT_NONE, (),
+                    None, NOISE_ADD_REAL, sigma, seed, dt, nsteps, psi0, sample_every,
+                    extra={"theta": theta, "sigma": sigma, "x0": x0})
+
+
+def kubo_oscillator(npaths: int = 65536, omega: float = 1.0, beta: float = 0.5, z0: float = 1.0,
+                    dt: float = 1e-3, nsteps: int = 5000, seed: int = 32,
+                    sample_every: int = 100) -> Workload:
+    """dz = i omega z dt + i beta z o dW (Stratonovich) as a 0-D problem:
+    L = i omega, multiplicative real noise with alpha = -beta in -i alpha xi z."""
+    psi0 = np.full((npaths,), z0, dtype=np.complex128)
+    return Workload("kubo_oscillator", (), (), (), complex(0.0, omega), 0j, 0.0, POT_NONE, (), None,
+                    NOISE_MUL_REAL, -beta, seed, dt, nsteps, psi0, sample_every,
+                    extra={"omega": omega, "beta": beta, "z0": z0})
+
+
+def smooth_potential(n: int, nt: int, L: float, seed: int, kmax: int = 8) -> np.ndarray:
+    """V(x, t) = x^2/2 + 0.1 * w(x, t) on an [nt][n] space-time grid, with w white
+    N(0,1) noise low-passed to |k_x|, |omega| <= kmax Fourier modes and rescaled to
+    unit RMS (time-major: row t is the potential of step t)."""
+    rng = np.random.default_rng(seed)
+    w = rng.standard_normal((nt, n))
+    W = np.fft.fft2(w)
+    it = np.fft.fftfreq(nt, d=1.0 / nt)
+    ix = np.fft.fftfreq(n, d=1.0 / n)
+    mask = (np.abs(it)[:, None] <= kmax) & (np.abs(ix)[None, :] <= kmax)
+    w = np.real(np.fft.ifft2(W * mask))
+    w /= math.sqrt(np.mean(w ** 2))
+    x = -L + np.arange(n) * (2 * L / n)
+    return 0.5 * x[None, :] ** 2 + 0.1 * w
+
+
+def adjoint_control(n: int = 1024, nsteps: int = 500, dt: float = 1e-3, g: float = 1.0,
+                    L: float = 20.0, seed: int = 5, ckpt_every: int = 50) -> Workload:
+    """1D GPE driven by a space-time potential V(x, t_n) (piecewise constant per
+    step); psi0 = pi^-1/4 exp(-x^2/2) (Eq. InitialCondition, N = 1) and the
+    target a displaced Gaussian pi^-1/4 exp(-(x-2)^2/2)."""
+    x = -L + np.arange(n) * (2 * L / n)
+    psi0 = (math.pi ** -0.25 * np.exp(-x ** 2 / 2)).astype(np.complex128)[None, :]
+    target = (math.pi ** -0.25 * np.exp(-(x - 2.0) ** 2 / 2)).astype(np.complex128)
+    V = smooth_potential(n, nsteps, L, seed)
+    return Workload("adjoint_control_1d", (n,), (-L,), (L,), 0j, -0.5j, g, POT_TABLE, (0.0,), V,
+                    NOISE_NONE, 0.0, 0, dt, nsteps, psi0, extra={"target": target, "ckpt_every": ckpt_every})
+
+
+def batched_1d_instances(count_per_size: int = 256, sizes=(256, 512, 1024, 2048), L: float = 20.0,
+                         seed: int = 4, dt: float = 1e-4, nsteps: int = 500) -> list:
+    """1D NLS instances on [-L, L): half A sech(A(x-x0)) e^{i v x}, half Gaussian
+    exp(-(x-x0)^2/(2 w^2)), with A in [0.5,1.5], x0 in [-5,5], v in [-1,1], w in [1,3]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for n in sizes:
+        x = -L + np.arange(n) * (2 * L / n)
+        for i in range(count_per_size):
+            x0 = rng.uniform(-5, 5)
+            if i % 2 == 0:
+                A, v = rng.uniform(0.5, 1.5), rng.uniform(-1, 1)
+                psi = A / np.cosh(A * (x - x0)) * np.exp(1j * v * x)
+            else:
+                w = rng.uniform(1, 3)
+                psi = np.exp(-(x - x0) ** 2 / (2 * w * w)).astype(np.complex128)
+            out.append(Workload(f"nls_1d_{n}_{i}", (n,), (-L,), (L,), 0j, -0.5j, -1.0, POT_NONE, (0.0,),
+                                None, NOISE_NONE, 0.0, 0, dt, nsteps, psi.astype(np.complex128)[None, :]))
+    return out
