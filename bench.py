@@ -1,0 +1,307 @@
+"""Benchmark of the RK4IP hot path: grid-point-steps per second.
+
+Workload (the 2D GPE of XMDS2 Sec. 3.2 at 512x512): i psi_t = [-1/2 lap +
+1/2 r^2 + 500 |psi|^2] psi on [-12,12)^2, Thomas-Fermi state (norm 1) times
+exp(i 0.01 N(0,1)) phase noise, dt = 1e-4, complex64 arithmetic.  A batch of P
+independent instances (different phase-noise draws) is integrated per GPU so
+that the fields (2 x P x 2 MiB) are larger than the 129 MB L2.  One bench step
+is one xsde_integrate call of 100 RK4IP steps with its sampling group (norm and
+energy per instance at the first and last step of the call) -- every row of
+the hot path: the FFT passes, exp(L dt/2), the real-space stages and the FP64
+reductions.
+
+value       = instances x points x RK4IP steps / device time (CUDA events), whole job
+e2e         = same metric with the fields copied host->device and back every step
+roofline    = dominant kernel: algorithmic bytes per launch / mean launch time
+cpu_baseline= the FP64 oracle on a bounded sample of the same workload
+
+--impl reference times the FP64 CPU oracle on the same workload (bounded
+samples per step); it is the comparison arm, not the target.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GRID = 512
+STEPS_PER_CALL = 100
+METRIC = "RK4IP grid-point-steps/s"
+UNIT = "pt-steps/s"
+BYTES_PER_PT_PASS = {"c64": 32, "c128": 64}   # 2 fields in + 2 out per pass
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(npaths: int, seed_offset: int = 0):
+    import workloads as W
+    return W.gpe_2d(n=N_GRID, npaths=npaths, seed=2 + seed_offset)
+
+
+def cpu_baseline(budget_s: float = 12.0) -> dict:
+    """The FP64 oracle as it stands on one instance of the workload, for as many
+    whole RK4IP steps as fit in about budget_s seconds (at least one)."""
+    from oracle import oracle as O
+    w = workload(1)
+    grid, ops = O.from_workload(w)
+    O.set_threads(os.cpu_count() or 1)
+    psi = w.psi0
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        psi, _, _ = O.rk4ip(psi, grid, ops, w.dt, 1, step0=steps)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or steps >= 50:
+            break
+    pts = w.npts * steps
+    return {"value": pts / el, "unit": UNIT, "cores": O.get_threads(), "kind": "oracle",
+            "sample": f"1 instance of 512x512, {steps} RK4IP steps, FP64, {el:.1f} s"}
+
+
+def run_reference(args) -> None:
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    w = workload(1)
+    grid, ops = O.from_workload(w)
+    O.set_threads(os.cpu_count() or 1)
+    psi = w.psi0
+    for i in range(args.warmup):
+        psi, _, _ = O.rk4ip(psi, grid, ops, w.dt, 1, step0=i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        psi, _, _ = O.rk4ip(psi, grid, ops, w.dt, 1, step0=args.warmup + i)
+    el = time.perf_counter() - t0
+    value = w.npts * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "2D GPE 512x512 (TF + phase noise, g=500, dt=1e-4)",
+                   "sample": "1 instance, 1 RK4IP step per bench step", "implementation": "FP64 CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.get_threads(), "kind": "oracle",
+                         "sample": f"1 instance of 512x512, {args.steps} RK4IP steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args) -> None:
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1204_4255_gb300 import build, xsde
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    xsde.load()
+
+    dtype = args.dtype
+    P = args.paths
+    w = workload(P, seed_offset=rank)
+    tdt = torch.complex64 if dtype == "c64" else torch.complex128
+    stream = torch.cuda.current_stream()
+
+    prob = xsde.Problem(w.n, w.xmin, w.xmax, dtype)
+    prob.set_operators(c0=w.c0, c2=w.c2, g=w.gnl, pot_kind=w.pot_kind, omega=(1.0, 1.0, 0.0))
+    nsamp = STEPS_PER_CALL // STEPS_PER_CALL + 1
+    per_path = torch.zeros((nsamp, P, 2), dtype=torch.float64, device="cuda")
+    prob.moments(STEPS_PER_CALL, xsde.XSDE_MOM_NORM | xsde.XSDE_MOM_ENERGY, per_path, None)
+    host_psi = torch.from_numpy(w.psi0).to(tdt).pin_memory()
+    psi = host_psi.to("cuda", non_blocking=True)
+    torch.cuda.synchronize()
+
+    path_offset = rank * P
+    step = [0]
+
+    def one_step():
+        prob.integrate(psi, w.dt, STEPS_PER_CALL, path_offset=path_offset, step_offset=0)
+        step[0] += 1
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    prob.synchronize()
+
+    # ---- timed region: device time with CUDA events on the launch stream ----
+    xsde.xsde_profile(prob.prob, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            one_step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    prof = xsde.xsde_profile_report(prob.prob)
+    xsde.xsde_profile(prob.prob, False)
+    prob.synchronize()
+    norms = per_path[-1, :, 0].cpu().numpy()
+    ok = bool(np.all(np.isfinite(norms)) and np.max(np.abs(norms - 1.0)) < 1e-3)
+
+    # max over ranks
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+
+    pts_per_step = P * w.npts * STEPS_PER_CALL
+    value = pts_per_step * args.steps * world / (ms_max / 1e3)
+    launches = int(sum(n for _, n in prof.values()))
+
+    # ---- dominant kernel roofline -------------------------------------------
+    peak, peak_kind = _peaks()
+    dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
+    dom_ms, dom_n = prof[dom]
+    alg_bytes = BYTES_PER_PT_PASS[dtype] * P * w.npts
+    if dom in ("row_prologue", "row_epilogue", "row_fft_only", "col_spectral"):
+        alg_bytes //= 2
+    achieved = alg_bytes / (dom_ms / dom_n / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": dom, "peak_source": f"hbm_gbs of {peak_kind}",
+                "launch_ms": dom_ms / dom_n, "algorithmic_bytes_per_launch": alg_bytes,
+                "kernel_share": dom_ms / sum(v[0] for v in prof.values())}
+
+    # ---- end to end through the public API with host buffers ----------------
+    e2e = None
+    if rank == 0 or world > 1:
+        host_out = torch.empty_like(host_psi).pin_memory()
+        host_mom = torch.empty_like(per_path, device="cpu").pin_memory()
+        k_e2e = max(2, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            psi.copy_(host_psi, non_blocking=True)
+            prob.integrate(psi, w.dt, STEPS_PER_CALL, path_offset=path_offset)
+            host_out.copy_(psi, non_blocking=True)
+            host_mom.copy_(per_path, non_blocking=True)
+            torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        h2d = host_psi.numel() * host_psi.element_size()
+        d2h = h2d + per_path.numel() * 8
+        e2e = {"value": pts_per_step * k_e2e * world / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": k_e2e}
+
+    if rank == 0:
+        cpu = cpu_baseline() if world == 1 and not args.no_cpu_baseline else None
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": f"2D GPE {N_GRID}x{N_GRID} (Thomas-Fermi + phase noise, g=500, V=r^2/2, dt=1e-4)",
+                       "instances_per_gpu": P, "rk4ip_steps_per_bench_step": STEPS_PER_CALL,
+                       "sampling": "norm+energy per instance, FP64", "l2": "inputs larger than L2",
+                       "parallelism": f"paths sharded over {world} GPU(s), no collective"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary(), "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]},
+            "norm_check": ok,
+        }
+        print(json.dumps(line), flush=True)
+    prob.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="xsde", choices=["xsde", "reference"])
+    ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--paths", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,233 @@
+/*
+ * xsde.h -- C-ABI of the GB300 (sm_103a) RK4IP library.
+ *
+ * The library integrates (stochastic) PDEs of the form of XMDS2's
+ * Eq. PDEBeforeIPTransform (Dennis, Hope & Johnsson, arXiv:1204.4255, Sec. 2.6),
+ *
+ *     d psi / dt = L[psi] + g(x, t, psi),
+ *
+ * on a periodic tensor-product Fourier lattice (Secs. 2.1-2.2) by the method of
+ * lines (Sec. 2.5) with fourth-order Runge-Kutta in the interaction picture
+ * (RK4IP, Sec. 2.6): the linear part L is solved exactly in Fourier space as
+ * exp(L(k) dt/2) and g is evaluated in real space.  The closed equation family
+ * accepted here covers the paper's NLS/GPE examples (Eq. NonlinearSchrodingerEquation,
+ * Eq. NonlinearSchrodingerEquationDimensionless), the noisy trap of Example 6
+ * (Sec. 3.6) and scalar SDEs:
+ *
+ *     L(k) = c0 + c2 |k|^2
+ *     g    = -i (V(x, t) + g_nl |psi|^2 + alpha xi_r) psi + sigma xi_a
+ *
+ * with xi_r / xi_a real or complex spatial white Wiener noise (Sec. 2.5, in
+ * Stratonovich form: one draw per step, point and path, fixed over the four
+ * RK stages; variance 1/(dt dV) per step).
+ *
+ * Conventions
+ *   - Lattice: x_j = xmin + j dx on [xmin, xmax), dx = (xmax - xmin)/N;
+ *     k_j = 2 pi/(xmax - xmin) * (j < N/2 ? j : j - N).
+ *   - Field layout: [path][n0][n1][n2] interleaved complex (re, im), the last
+ *     grid dimension contiguous, paths outermost.  C64 = 2 x float,
+ *     C128 = 2 x double.
+ *   - Noise: Philox4x32-10 (Salmon et al., SC'11); the normal pair of global
+ *     step n at point j of global path p comes from counter (j, p, n+1, 0) and
+ *     key (seed_lo, seed_hi) through u = (x + 0.5) 2^-32 and Box-Muller:
+ *     z0 = sqrt(-2 ln u0) cos(2 pi u1), z1 = sqrt(-2 ln u0) sin(2 pi u1).
+ *     Real noise uses z0, complex noise (z0 + i z1)/sqrt(2).  Results are
+ *     therefore independent of launch shape and of how paths are split.
+ *
+ * Errors: every call returns an xsde_status; on failure xsde_last_error()
+ * returns a thread-local message.  No C++ exception crosses this boundary.
+ * Device pointers are CUDA device (or managed) addresses on the current device;
+ * `stream` arguments are cudaStream_t values passed as void*.
+ */
+#ifndef XSDE_H
+#define XSDE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    XSDE_OK = 0,
+    XSDE_EINVAL = 1,        /* invalid argument (checked on the host) */
+    XSDE_ENOMEM = 2,        /* device allocation failed */
+    XSDE_ECUDA = 3,         /* a CUDA runtime call failed */
+    XSDE_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
+    XSDE_ENONFINITE = 5,    /* the field became NaN/Inf */
+    XSDE_EUNSUPPORTED = 6   /* valid but not implemented (size, dtype, combination) */
+} xsde_status;
+
+typedef enum { XSDE_C64 = 1, XSDE_C128 = 2 } xsde_dtype;
+
+typedef enum {
+    XSDE_POT_NONE = 0,
+    XSDE_POT_HARMONIC = 1,  /* V = 1/2 sum_d omega_d^2 x_d^2 */
+    XSDE_POT_TABLE = 2      /* V from a device table [V_nt][npts] */
+} xsde_pot_kind;
+
+typedef enum {
+    XSDE_NOISE_NONE = 0,
+    XSDE_NOISE_WIENER_REAL = 1,
+    XSDE_NOISE_WIENER_COMPLEX = 2
+} xsde_noise_kind;
+
+typedef enum {
+    XSDE_COUPLE_ADDITIVE = 0,        /* + sigma xi_a            (real or complex xi) */
+    XSDE_COUPLE_MULTIPLICATIVE = 1   /* -i alpha xi_r psi       (real xi only) */
+} xsde_noise_coupling;
+
+enum {
+    XSDE_MOM_NORM = 1,     /* per path: sum |psi|^2 dV */
+    XSDE_MOM_ENERGY = 2,   /* per path: sum_k Re(i L(k)) |psi_k|^2 dV/N + sum_x (V|psi|^2 + g/2 |psi|^4) dV */
+    XSDE_MOM_MOD2 = 4,     /* per point: mean over paths of |psi|^2 */
+    XSDE_MOM_MOD4 = 8      /* per point: mean over paths of |psi|^4 */
+};
+
+typedef struct xsde_grid xsde_grid;
+typedef struct xsde_vector xsde_vector;
+typedef struct xsde_noise xsde_noise;
+typedef struct xsde_problem xsde_problem;
+
+/* Linear operator in Fourier space (Sec. 2.6): L(k) = c0 + c2 |k|^2. */
+typedef struct {
+    double c0_re, c0_im;
+    double c2_re, c2_im;
+} xsde_linear_op;
+
+/* Local term in real space (Sec. 2.6, Eq. NonlinearSchrodingerEquation; noise
+ * as in Example 6, Sec. 3.6).  V is a device pointer to a table of the
+ * problem's real type (float for XSDE_C64, double for XSDE_C128) laid out
+ * [V_nt][npts]: V_nt == 1 is a static table, otherwise row n is the potential
+ * of global step n (piecewise constant over the step).  The table is borrowed:
+ * the caller keeps it alive while integrations that use it are in flight. */
+typedef struct {
+    int32_t pot_kind;            /* xsde_pot_kind */
+    double omega[3];             /* harmonic frequencies per dimension */
+    const void *V;               /* device table, or NULL */
+    int64_t V_nt;                /* rows of V */
+    double g;                    /* g_nl */
+    const xsde_noise *noise;     /* NULL: deterministic */
+    int32_t coupling;            /* xsde_noise_coupling */
+    double amplitude;            /* sigma (additive) or alpha (multiplicative) */
+} xsde_nonlinear_op;
+
+/* Sampling group (Sec. 3.1 "sampling", Sec. 3.6 averaged outputs): samples at
+ * local steps 0, every, 2*every, ... <= nsteps of each xsde_integrate call. */
+typedef struct {
+    int32_t every;               /* 0: no sampling */
+    int32_t which;               /* OR of XSDE_MOM_* */
+} xsde_sampling;
+
+/* ---- lattice (Secs. 2.1-2.2; dimensions of Example 2, Sec. 3.2) --------- */
+
+/* ndim in 0..3 (0 = a single point: an ordinary SDE, dV = 1).  npts[d] is a
+ * power of two in [16, 2048]; xmin[d] < xmax[d].  Arrays are read, not kept.
+ * 3D lattices are accepted here but xsde_integrate reports XSDE_EUNSUPPORTED
+ * for them.  *out is owned by the caller (xsde_grid_destroy). */
+int xsde_grid_create(int ndim, const int32_t *npts, const double *xmin, const double *xmax,
+                     xsde_grid **out);
+void xsde_grid_destroy(xsde_grid *grid);
+/* number of lattice points (product of npts; 1 for ndim = 0) */
+int64_t xsde_grid_points(const xsde_grid *grid);
+
+/* ---- fields (Sec. 3.1 "vectors") ---------------------------------------- */
+
+/* Allocate a device field of npaths x npts complex values (ncomp must be 1).
+ * The library owns the memory (xsde_vector_free releases it). */
+int xsde_vector_alloc(const xsde_grid *grid, xsde_dtype dtype, int ncomp, int64_t npaths,
+                      xsde_vector **out);
+/* Describe caller-owned device memory (e.g. a torch tensor) as a field.  The
+ * memory is borrowed: it must stay alive and must not be used on other streams
+ * while a call that uses it is in flight.  xsde_vector_free only frees the
+ * descriptor. */
+int xsde_vector_wrap(const xsde_grid *grid, xsde_dtype dtype, int ncomp, int64_t npaths,
+                     void *dev_ptr, xsde_vector **out);
+void *xsde_vector_data(const xsde_vector *vec);
+void xsde_vector_free(xsde_vector *vec);
+
+/* ---- noise (Sec. 2.5; noise_vector of Example 6, Sec. 3.6) -------------- */
+
+/* A noise vector is not stored: it is (kind, seed) and regenerated from
+ * Philox counters wherever it is needed. */
+int xsde_noise_alloc(const xsde_grid *grid, xsde_noise_kind kind, uint64_t seed, xsde_noise **out);
+void xsde_noise_free(xsde_noise *noise);
+
+/* Raw generator words: out[i] = Philox4x32-10(counters[i], key = (seed_lo,
+ * seed_hi)) for i < n.  counters and out are device arrays of n x 4 uint32,
+ * 16-byte aligned, caller-owned.  Asynchronous on `stream`. */
+int xsde_noise_philox(const uint32_t *counters, uint64_t seed, int64_t n, uint32_t *out, void *stream);
+
+/* The standard normal pairs (z0, z1) that global step `step` draws for paths
+ * path_offset .. path_offset+npaths-1 at points 0 .. npts-1, written to the
+ * device array out[npaths][npts] of complex (z0, z1) in `dtype` (C64: FP32
+ * Box-Muller, C128: FP64).  Asynchronous on `stream`. */
+int xsde_noise_normals(const xsde_noise *noise, xsde_dtype dtype, int64_t npts, int64_t npaths,
+                       int64_t path_offset, uint64_t step, void *out, void *stream);
+
+/* ---- problem -------------------------------------------------------------- */
+
+/* A problem binds a lattice, a precision and the operators; it owns the
+ * device workspace (Fourier tables, one scratch field) that integration needs. */
+int xsde_problem_create(const xsde_grid *grid, xsde_dtype dtype, xsde_problem **out);
+void xsde_problem_destroy(xsde_problem *prob);
+
+/* Set L (Fourier space) and g (real space).  Both structs are copied; the noise
+ * handle and the V table are borrowed.  Multiplicative coupling needs real
+ * noise; a potential table needs V != NULL and V_nt >= 1. */
+int xsde_set_operators(xsde_problem *prob, const xsde_linear_op *L, const xsde_nonlinear_op *N);
+
+/* Register a sampling group for the following xsde_integrate calls.
+ * per_path  (device, FP64): [nsamp][npaths][2] = (norm, energy)  if NORM|ENERGY
+ * per_point (device, FP64): [nsamp][npts][2]  = (mean |psi|^2, mean |psi|^4)
+ *                                               if MOD2|MOD4
+ * with nsamp = nsteps/every + 1.  Either pointer may be NULL when not needed;
+ * entries that were not requested are left untouched.  Passing spec == NULL
+ * or spec->every == 0 removes the sampling group. */
+int xsde_moments(xsde_problem *prob, const xsde_sampling *spec, double *per_path, double *per_point);
+
+/* Advance psi (all npaths paths, in place) by nsteps RK4IP steps of size dt on
+ * `stream`, asynchronously.  Global path p of the noise counter is
+ * path_offset + local path; the global step index is step_offset + local step
+ * (this also selects the row of a time-dependent potential table).  Resuming
+ * with step_offset = steps already taken reproduces an uninterrupted run.
+ * npaths must equal the field's npaths.  Errors detected on the device are
+ * reported by the next xsde_synchronize. */
+int xsde_integrate(xsde_problem *prob, xsde_vector *psi, double dt, int64_t nsteps, int64_t npaths,
+                   int64_t path_offset, uint64_t step_offset, void *stream);
+
+/* Wait for `stream`, then report device-side errors of this problem's calls:
+ * XSDE_ENONFINITE if a sampled field held NaN/Inf, XSDE_ETIMEOUT if a bounded
+ * wait gave up.  Clears the device error word. */
+int xsde_synchronize(xsde_problem *prob, void *stream);
+
+/* ---- launch profiling ------------------------------------------------------ */
+
+/* Kernel kinds reported by xsde_profile_report, in this order:
+ * rk4ip_0d, rk4ip_1d, row_prologue, row_stage2, row_steady, row_epilogue,
+ * row_fft_only, col_propagate, col_spectral (see xsde_kernel_name). */
+#define XSDE_KERNEL_KINDS 9
+
+/* Start (enable != 0) or stop recording a CUDA event pair around every kernel
+ * launch of this problem, on the launch stream; resets the totals. */
+int xsde_profile(xsde_problem *prob, int enable);
+/* Wait for the recorded events and return, per kernel kind, the summed device
+ * time in ms and the number of launches since xsde_profile (host arrays of
+ * XSDE_KERNEL_KINDS entries). */
+int xsde_profile_report(xsde_problem *prob, double *total_ms, int64_t *launches);
+/* Name of kernel kind `kind` ("" if out of range). */
+const char *xsde_kernel_name(int kind);
+
+/* ---- errors --------------------------------------------------------------- */
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *xsde_last_error(void);
+/* Library version string. */
+const char *xsde_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XSDE_H */

@@ -1,0 +1,647 @@
+// api.cu -- the C-ABI of include/xsde.h: handles, host-side validation, the
+// Fourier-space tables, and the pass schedule of one xsde_integrate call.
+//
+// Tables (XMDS2 Sec. 2.6: only exp(+-L dt) factors are needed for fixed steps)
+// are evaluated in FP64 on the host and rounded once to the working precision;
+// for FP32 each complex entry takes, among the neighbouring floats of its real
+// and imaginary parts, the pair whose modulus is closest to the exact one, so
+// that repeated application does not drift the norm.
+#include <cfloat>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/xsde.h"
+#include "kernels.h"
+
+using namespace xsde;
+
+struct xsde_grid {
+    int ndim;
+    int n[3];
+    double xmin[3], xmax[3];
+    int64_t npts;
+};
+
+struct xsde_vector {
+    xsde_grid grid;
+    xsde_dtype dtype;
+    int ncomp;
+    int64_t npaths;
+    void *data;
+    bool owned;
+};
+
+struct xsde_noise {
+    xsde_noise_kind kind;
+    uint64_t seed;
+};
+
+struct xsde_problem {
+    xsde_grid grid;
+    xsde_dtype dtype;
+    int device;
+    bool have_ops = false;
+    xsde_linear_op L{};
+    xsde_nonlinear_op N{};
+    xsde_noise noise{XSDE_NOISE_NONE, 0};
+    xsde_sampling samp{0, 0};
+    double *per_path = nullptr, *per_point = nullptr;
+    double table_dt = -1.0;
+    void *d_tw[3] = {nullptr, nullptr, nullptr};
+    void *d_E[3] = {nullptr, nullptr, nullptr};
+    void *d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int *d_status = nullptr;
+    // launch profiling: CUDA events around every kernel launch of this problem
+    bool profiling = false;
+    struct Mark {
+        int kind;
+        cudaEvent_t start, stop;
+    };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> event_pool;
+    double prof_ms[XSDE_KERNEL_KINDS] = {};
+    int64_t prof_launches[XSDE_KERNEL_KINDS] = {};
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(e == cudaErrorMemoryAllocation ? XSDE_ENOMEM : XSDE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define XSDE_CUDA(call, what)                        \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+bool pow2_in_range(int n) { return n >= 16 && n <= 2048 && (n & (n - 1)) == 0; }
+
+const char *const kKernelNames[XSDE_KERNEL_KINDS] = {
+    "rk4ip_0d",      "rk4ip_1d",      "row_prologue", "row_stage2", "row_steady",
+    "row_epilogue",  "row_fft_only",  "col_propagate", "col_spectral"};
+
+cudaEvent_t take_event(xsde_problem *p) {
+    if (!p->event_pool.empty()) {
+        cudaEvent_t e = p->event_pool.back();
+        p->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Launch through `fn` and, when profiling, bracket it with events on stream s.
+template <typename F> cudaError_t timed(xsde_problem *p, int kind, cudaStream_t s, F &&fn) {
+    if (!p->profiling) return fn();
+    cudaEvent_t a = take_event(p), b = take_event(p);
+    if (a) cudaEventRecord(a, s);
+    cudaError_t e = fn();
+    if (b) cudaEventRecord(b, s);
+    if (a && b) p->marks.push_back({kind, a, b});
+    return e;
+}
+
+// Fold finished event pairs into the per-kind totals (after a synchronize).
+void collect_marks(xsde_problem *p) {
+    for (auto &m : p->marks) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, m.start, m.stop) == cudaSuccess) {
+            p->prof_ms[m.kind] += ms;
+            p->prof_launches[m.kind] += 1;
+        }
+        p->event_pool.push_back(m.start);
+        p->event_pool.push_back(m.stop);
+    }
+    p->marks.clear();
+}
+
+size_t elem_bytes(xsde_dtype d) { return d == XSDE_C64 ? 8 : 16; }
+
+double grid_dx(const xsde_grid &g, int d) { return (g.xmax[d] - g.xmin[d]) / g.n[d]; }
+double grid_dV(const xsde_grid &g) {
+    double v = 1.0;
+    for (int d = 0; d < g.ndim; ++d) v *= grid_dx(g, d);
+    return v;
+}
+double kval(const xsde_grid &g, int d, int i) {
+    const int n = g.n[d];
+    return 2.0 * M_PI / (g.xmax[d] - g.xmin[d]) * (i < n / 2 ? i : i - n);
+}
+
+// complex double -> working precision, rounded once (see file comment)
+void round_to(const std::complex<double> &z, float2 *out) {
+    const double r = std::abs(z);
+    const float re = (float)z.real(), im = (float)z.imag();
+    float best_re = re, best_im = im;
+    double best = std::fabs(std::hypot((double)re, (double)im) - r);
+    for (int a = -1; a <= 1; ++a) {
+        for (int b = -1; b <= 1; ++b) {
+            float cr = a == 0 ? re : std::nextafterf(re, a < 0 ? -FLT_MAX : FLT_MAX);
+            float ci = b == 0 ? im : std::nextafterf(im, b < 0 ? -FLT_MAX : FLT_MAX);
+            double err = std::fabs(std::hypot((double)cr, (double)ci) - r);
+            if (err < best) {
+                best = err;
+                best_re = cr;
+                best_im = ci;
+            }
+        }
+    }
+    *out = make_float2(best_re, best_im);
+}
+void round_to(const std::complex<double> &z, double2 *out) { *out = make_double2(z.real(), z.imag()); }
+
+template <typename V> int upload(const std::vector<std::complex<double>> &h, void **dptr, cudaStream_t s) {
+    std::vector<V> tmp(h.size());
+    for (size_t i = 0; i < h.size(); ++i) round_to(h[i], &tmp[i]);
+    if (!*dptr) XSDE_CUDA(cudaMalloc(dptr, tmp.size() * sizeof(V)), "cudaMalloc(table)");
+    XSDE_CUDA(cudaMemcpyAsync(*dptr, tmp.data(), tmp.size() * sizeof(V), cudaMemcpyHostToDevice, s),
+              "cudaMemcpyAsync(table)");
+    XSDE_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize(table)");
+    return XSDE_OK;
+}
+
+// twiddles exp(-2 pi i m/n) and the exp(L dt/2) factors for this dt
+template <typename V> int ensure_tables(xsde_problem *p, double dt, cudaStream_t s) {
+    if (p->table_dt == dt) return XSDE_OK;
+    const xsde_grid &g = p->grid;
+    const std::complex<double> c0(p->L.c0_re, p->L.c0_im), c2(p->L.c2_re, p->L.c2_im);
+    int rc;
+    for (int d = 0; d < g.ndim; ++d) {
+        std::vector<std::complex<double>> tw(g.n[d]);
+        for (int m = 0; m < g.n[d]; ++m) tw[m] = std::polar(1.0, -2.0 * M_PI * m / g.n[d]);
+        if ((rc = upload<V>(tw, &p->d_tw[d], s)) != XSDE_OK) return rc;
+    }
+    if (g.ndim == 1) {
+        std::vector<std::complex<double>> e(g.n[0]);
+        for (int i = 0; i < g.n[0]; ++i) {
+            const double k = kval(g, 0, i);
+            e[i] = std::exp((c0 + c2 * (k * k)) * (0.5 * dt)) / (double)g.n[0];
+        }
+        if ((rc = upload<V>(e, &p->d_E[0], s)) != XSDE_OK) return rc;
+    } else if (g.ndim == 2) {
+        std::vector<std::complex<double>> e0(g.n[0]), e1(g.n[1]);
+        for (int i = 0; i < g.n[0]; ++i) {
+            const double k = kval(g, 0, i);
+            e0[i] = std::exp((c0 + c2 * (k * k)) * (0.5 * dt)) / ((double)g.n[0] * g.n[1]);
+        }
+        for (int i = 0; i < g.n[1]; ++i) {
+            const double k = kval(g, 1, i);
+            e1[i] = std::exp(c2 * (k * k) * (0.5 * dt));
+        }
+        if ((rc = upload<V>(e0, &p->d_E[0], s)) != XSDE_OK) return rc;
+        if ((rc = upload<V>(e1, &p->d_E[1], s)) != XSDE_OK) return rc;
+    }
+    p->table_dt = dt;
+    return XSDE_OK;
+}
+
+template <typename R>
+void fill_terms(const xsde_problem *p, double dt, int64_t npaths, int64_t path_offset, LocalTerm<R> &lt,
+                Sampling &sm) {
+    const xsde_grid &g = p->grid;
+    const double dV = grid_dV(g);
+    lt.dt = (R)dt;
+    lt.gdt = (R)(p->N.g * dt);
+    lt.pot = p->N.pot_kind;
+    for (int d = 0; d < 3; ++d) {
+        lt.hw2[d] = (R)(d < g.ndim ? 0.5 * p->N.omega[d] * p->N.omega[d] : 0.0);
+        lt.xmin[d] = d < g.ndim ? g.xmin[d] : 0.0;
+        lt.dx[d] = d < g.ndim ? grid_dx(g, d) : 0.0;
+    }
+    lt.V = static_cast<const R *>(p->N.V);
+    lt.V_nt = p->N.V_nt;
+    lt.npts = g.npts;
+    lt.noise = NM_NONE;
+    lt.nscale = 0;
+    if (p->noise.kind != XSDE_NOISE_NONE) {
+        const double base = p->N.amplitude * std::sqrt(dt / dV);
+        if (p->N.coupling == XSDE_COUPLE_MULTIPLICATIVE) {
+            lt.noise = NM_MUL_REAL;
+            lt.nscale = (R)base;
+        } else if (p->noise.kind == XSDE_NOISE_WIENER_REAL) {
+            lt.noise = NM_ADD_REAL;
+            lt.nscale = (R)base;
+        } else {
+            lt.noise = NM_ADD_COMPLEX;
+            lt.nscale = (R)(base / std::sqrt(2.0));
+        }
+    }
+    lt.key = make_uint2((uint32_t)(p->noise.seed & 0xffffffffu), (uint32_t)(p->noise.seed >> 32));
+    lt.path_offset = path_offset;
+
+    sm.every = p->samp.every;
+    sm.which = p->samp.which;
+    sm.per_path = p->per_path;
+    sm.per_point = p->per_point;
+    sm.dV = dV;
+    sm.inv_paths = 1.0 / (double)npaths;
+    sm.h0 = -p->L.c0_im;
+    sm.h2 = -p->L.c2_im;
+    for (int d = 0; d < 3; ++d) sm.kscale[d] = d < g.ndim ? 2.0 * M_PI / (g.xmax[d] - g.xmin[d]) : 0.0;
+    sm.g = p->N.g;
+}
+
+template <typename R>
+int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t npaths, int64_t path_offset,
+                  uint64_t step0, cudaStream_t s) {
+    using V = cx<R>;
+    int rc = ensure_tables<V>(p, dt, s);
+    if (rc != XSDE_OK) return rc;
+    LocalTerm<R> lt;
+    Sampling sm;
+    fill_terms<R>(p, dt, npaths, path_offset, lt, sm);
+    const xsde_grid &g = p->grid;
+    const bool sampling = sm.every > 0;
+    if (sampling) {
+        const int64_t nsamp = nsteps / sm.every + 1;
+        if (sm.per_path && (sm.which & (MOM_NORM | MOM_ENERGY)))
+            XSDE_CUDA(cudaMemsetAsync(sm.per_path, 0, (size_t)nsamp * npaths * 2 * sizeof(double), s), "memset");
+        if (sm.per_point && (sm.which & (MOM_MOD2 | MOM_MOD4)))
+            XSDE_CUDA(cudaMemsetAsync(sm.per_point, 0, (size_t)nsamp * g.npts * 2 * sizeof(double), s), "memset");
+    }
+
+    if (g.ndim == 0) {
+        Params0D<R> q;
+        q.psi = static_cast<V *>(psi);
+        q.npaths = npaths;
+        q.nsteps = nsteps;
+        q.step0 = step0;
+        const std::complex<double> eh = std::exp(std::complex<double>(p->L.c0_re, p->L.c0_im) * (0.5 * dt));
+        q.Ehalf.x = (R)eh.real();
+        q.Ehalf.y = (R)eh.imag();
+        q.lt = lt;
+        q.sm = sm;
+        q.status = p->d_status;
+        XSDE_CUDA(timed(p, 0, s, [&] { return launch_rk4ip_0d<R>(q, s); }), "rk4ip_0d launch");
+        return XSDE_OK;
+    }
+    if (g.ndim == 1) {
+        Params1D<R> q;
+        q.psi = static_cast<V *>(psi);
+        q.npaths = npaths;
+        q.nsteps = nsteps;
+        q.step0 = step0;
+        q.Etab = static_cast<const V *>(p->d_E[0]);
+        q.tw = static_cast<const V *>(p->d_tw[0]);
+        q.lt = lt;
+        q.sm = sm;
+        q.status = p->d_status;
+        XSDE_CUDA(timed(p, 1, s, [&] { return launch_rk4ip_1d<R>(g.n[0], q, s); }), "rk4ip_1d launch");
+        return XSDE_OK;
+    }
+    // 2D: scratch field B (same shape as psi)
+    const size_t need = (size_t)npaths * g.npts * sizeof(V);
+    if (p->scratch_bytes < need) {
+        if (p->d_scratch) {
+            XSDE_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize(scratch)");
+            cudaFree(p->d_scratch);
+            p->d_scratch = nullptr;
+            p->scratch_bytes = 0;
+        }
+        XSDE_CUDA(cudaMalloc(&p->d_scratch, need), "cudaMalloc(scratch)");
+        p->scratch_bytes = need;
+    }
+    Params2D<R> q;
+    q.A = static_cast<V *>(psi);
+    q.B = static_cast<V *>(p->d_scratch);
+    q.npaths = npaths;
+    q.n0 = g.n[0];
+    q.n1 = g.n[1];
+    q.tw0 = static_cast<const V *>(p->d_tw[0]);
+    q.tw1 = static_cast<const V *>(p->d_tw[1]);
+    q.E0 = static_cast<const V *>(p->d_E[0]);
+    q.E1 = static_cast<const V *>(p->d_E[1]);
+    q.lt = lt;
+    q.sm = sm;
+    q.status = p->d_status;
+    const int S = sm.every;
+    auto row = [&](int mode, uint64_t sg, int slot) -> cudaError_t {
+        q.sg = sg;
+        q.sample_slot = slot;
+        return timed(p, 2 + mode, s, [&] { return launch_row_pass<R>(mode, q, s); });
+    };
+    auto col = [&](int mode, int slot) -> cudaError_t {
+        q.sample_slot = slot;
+        return timed(p, 7 + mode, s, [&] { return launch_col_pass<R>(mode, q, s); });
+    };
+    if (nsteps > 0) {
+        XSDE_CUDA(row(ROW_PROLOGUE, step0, sampling ? 0 : -1), "row pass");
+        for (int64_t n = 0; n < nsteps; ++n) {
+            const uint64_t sg = step0 + n;
+            XSDE_CUDA(col(COL_PROPAGATE, (sampling && n % S == 0) ? (int)(n / S) : -1), "col pass");
+            XSDE_CUDA(row(ROW_STAGE2, sg, -1), "row pass");
+            XSDE_CUDA(col(COL_PROPAGATE, -1), "col pass");
+            if (n + 1 < nsteps) {
+                const int slot = (sampling && (n + 1) % S == 0) ? (int)((n + 1) / S) : -1;
+                XSDE_CUDA(row(ROW_STEADY, sg, slot), "row pass");
+            } else {
+                XSDE_CUDA(row(ROW_EPILOGUE, sg, -1), "row pass");
+            }
+        }
+    }
+    if (sampling && nsteps % S == 0) {
+        const int slot = (int)(nsteps / S);
+        XSDE_CUDA(row(ROW_FFT_ONLY, step0 + nsteps, slot), "row pass");
+        XSDE_CUDA(col(COL_SPECTRAL, slot), "col pass");
+    }
+    return XSDE_OK;
+}
+
+bool same_lattice(const xsde_grid &a, const xsde_grid &b) {
+    if (a.ndim != b.ndim) return false;
+    for (int d = 0; d < a.ndim; ++d)
+        if (a.n[d] != b.n[d] || a.xmin[d] != b.xmin[d] || a.xmax[d] != b.xmax[d]) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *xsde_last_error(void) { return g_err.c_str(); }
+const char *xsde_version(void) { return "xsde 0.1 (sm_103a)"; }
+
+int xsde_grid_create(int ndim, const int32_t *npts, const double *xmin, const double *xmax, xsde_grid **out) {
+    if (!out) return fail(XSDE_EINVAL, "xsde_grid_create: out is NULL");
+    *out = nullptr;
+    if (ndim < 0 || ndim > 3) return fail(XSDE_EINVAL, "xsde_grid_create: ndim %d not in 0..3", ndim);
+    if (ndim > 0 && (!npts || !xmin || !xmax)) return fail(XSDE_EINVAL, "xsde_grid_create: NULL array");
+    xsde_grid g{};
+    g.ndim = ndim;
+    g.npts = 1;
+    for (int d = 0; d < ndim; ++d) {
+        if (!pow2_in_range(npts[d]))
+            return fail(XSDE_EINVAL, "xsde_grid_create: npts[%d] = %d is not a power of two in [16, 2048]", d, npts[d]);
+        if (!(xmin[d] < xmax[d]) || !std::isfinite(xmin[d]) || !std::isfinite(xmax[d]))
+            return fail(XSDE_EINVAL, "xsde_grid_create: domain [%g, %g) of dimension %d is empty", xmin[d], xmax[d], d);
+        g.n[d] = npts[d];
+        g.xmin[d] = xmin[d];
+        g.xmax[d] = xmax[d];
+        g.npts *= npts[d];
+    }
+    xsde_grid *p = new (std::nothrow) xsde_grid(g);
+    if (!p) return fail(XSDE_ENOMEM, "xsde_grid_create: out of host memory");
+    *out = p;
+    return XSDE_OK;
+}
+
+void xsde_grid_destroy(xsde_grid *grid) { delete grid; }
+
+int64_t xsde_grid_points(const xsde_grid *grid) { return grid ? grid->npts : 0; }
+
+static int vector_check(const xsde_grid *grid, xsde_dtype dtype, int ncomp, int64_t npaths, xsde_vector **out) {
+    if (!out) return fail(XSDE_EINVAL, "vector: out is NULL");
+    *out = nullptr;
+    if (!grid) return fail(XSDE_EINVAL, "vector: grid is NULL");
+    if (dtype != XSDE_C64 && dtype != XSDE_C128) return fail(XSDE_EINVAL, "vector: unknown dtype %d", (int)dtype);
+    if (ncomp != 1) return fail(XSDE_EUNSUPPORTED, "vector: ncomp = %d (only 1 component is supported)", ncomp);
+    if (npaths < 1 || npaths > (int64_t)UINT32_MAX) return fail(XSDE_EINVAL, "vector: npaths = %lld", (long long)npaths);
+    return XSDE_OK;
+}
+
+int xsde_vector_alloc(const xsde_grid *grid, xsde_dtype dtype, int ncomp, int64_t npaths, xsde_vector **out) {
+    int rc = vector_check(grid, dtype, ncomp, npaths, out);
+    if (rc != XSDE_OK) return rc;
+    const size_t bytes = (size_t)npaths * grid->npts * elem_bytes(dtype);
+    void *d = nullptr;
+    XSDE_CUDA(cudaMalloc(&d, bytes), "xsde_vector_alloc");
+    cudaError_t e = cudaMemset(d, 0, bytes);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "xsde_vector_alloc: memset");
+    }
+    *out = new xsde_vector{*grid, dtype, ncomp, npaths, d, true};
+    return XSDE_OK;
+}
+
+int xsde_vector_wrap(const xsde_grid *grid, xsde_dtype dtype, int ncomp, int64_t npaths, void *dev_ptr,
+                     xsde_vector **out) {
+    int rc = vector_check(grid, dtype, ncomp, npaths, out);
+    if (rc != XSDE_OK) return rc;
+    if (!dev_ptr) return fail(XSDE_EINVAL, "xsde_vector_wrap: dev_ptr is NULL");
+    if ((uintptr_t)dev_ptr % elem_bytes(dtype))
+        return fail(XSDE_EINVAL, "xsde_vector_wrap: dev_ptr not aligned to %zu bytes", elem_bytes(dtype));
+    *out = new xsde_vector{*grid, dtype, ncomp, npaths, dev_ptr, false};
+    return XSDE_OK;
+}
+
+void *xsde_vector_data(const xsde_vector *vec) { return vec ? vec->data : nullptr; }
+
+void xsde_vector_free(xsde_vector *vec) {
+    if (!vec) return;
+    if (vec->owned) cudaFree(vec->data);
+    delete vec;
+}
+
+int xsde_noise_alloc(const xsde_grid *grid, xsde_noise_kind kind, uint64_t seed, xsde_noise **out) {
+    if (!out) return fail(XSDE_EINVAL, "xsde_noise_alloc: out is NULL");
+    *out = nullptr;
+    if (!grid) return fail(XSDE_EINVAL, "xsde_noise_alloc: grid is NULL");
+    if (kind != XSDE_NOISE_WIENER_REAL && kind != XSDE_NOISE_WIENER_COMPLEX)
+        return fail(XSDE_EINVAL, "xsde_noise_alloc: unknown kind %d", (int)kind);
+    *out = new xsde_noise{kind, seed};
+    return XSDE_OK;
+}
+
+void xsde_noise_free(xsde_noise *noise) { delete noise; }
+
+int xsde_problem_create(const xsde_grid *grid, xsde_dtype dtype, xsde_problem **out) {
+    if (!out) return fail(XSDE_EINVAL, "xsde_problem_create: out is NULL");
+    *out = nullptr;
+    if (!grid) return fail(XSDE_EINVAL, "xsde_problem_create: grid is NULL");
+    if (dtype != XSDE_C64 && dtype != XSDE_C128) return fail(XSDE_EINVAL, "xsde_problem_create: unknown dtype");
+    xsde_problem *p = new (std::nothrow) xsde_problem();
+    if (!p) return fail(XSDE_ENOMEM, "xsde_problem_create: out of host memory");
+    p->grid = *grid;
+    p->dtype = dtype;
+    cudaGetDevice(&p->device);
+    cudaError_t e = cudaMalloc(&p->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "xsde_problem_create");
+    }
+    *out = p;
+    return XSDE_OK;
+}
+
+void xsde_problem_destroy(xsde_problem *p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    for (auto &m : p->marks) {
+        cudaEventDestroy(m.start);
+        cudaEventDestroy(m.stop);
+    }
+    for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
+    for (int d = 0; d < 3; ++d) {
+        cudaFree(p->d_tw[d]);
+        cudaFree(p->d_E[d]);
+    }
+    cudaFree(p->d_scratch);
+    cudaFree(p->d_status);
+    delete p;
+}
+
+int xsde_set_operators(xsde_problem *p, const xsde_linear_op *L, const xsde_nonlinear_op *N) {
+    if (!p || !L || !N) return fail(XSDE_EINVAL, "xsde_set_operators: NULL argument");
+    const double vals[] = {L->c0_re, L->c0_im, L->c2_re, L->c2_im, N->g, N->amplitude,
+                           N->omega[0], N->omega[1], N->omega[2]};
+    for (double v : vals)
+        if (!std::isfinite(v)) return fail(XSDE_EINVAL, "xsde_set_operators: non-finite coefficient");
+    if (N->pot_kind < XSDE_POT_NONE || N->pot_kind > XSDE_POT_TABLE)
+        return fail(XSDE_EINVAL, "xsde_set_operators: unknown pot_kind %d", N->pot_kind);
+    if (N->pot_kind == XSDE_POT_TABLE && (!N->V || N->V_nt < 1))
+        return fail(XSDE_EINVAL, "xsde_set_operators: potential table needs V != NULL and V_nt >= 1");
+    if (N->coupling != XSDE_COUPLE_ADDITIVE && N->coupling != XSDE_COUPLE_MULTIPLICATIVE)
+        return fail(XSDE_EINVAL, "xsde_set_operators: unknown coupling %d", N->coupling);
+    if (N->noise && N->coupling == XSDE_COUPLE_MULTIPLICATIVE && N->noise->kind != XSDE_NOISE_WIENER_REAL)
+        return fail(XSDE_EINVAL, "xsde_set_operators: multiplicative coupling needs real noise");
+    p->L = *L;
+    p->N = *N;
+    p->noise = N->noise ? *N->noise : xsde_noise{XSDE_NOISE_NONE, 0};
+    p->N.noise = nullptr;
+    p->have_ops = true;
+    p->table_dt = -1.0;
+    return XSDE_OK;
+}
+
+int xsde_moments(xsde_problem *p, const xsde_sampling *spec, double *per_path, double *per_point) {
+    if (!p) return fail(XSDE_EINVAL, "xsde_moments: problem is NULL");
+    if (!spec || spec->every == 0) {
+        p->samp = xsde_sampling{0, 0};
+        p->per_path = p->per_point = nullptr;
+        return XSDE_OK;
+    }
+    if (spec->every < 0) return fail(XSDE_EINVAL, "xsde_moments: every = %d", spec->every);
+    if (spec->which & ~(XSDE_MOM_NORM | XSDE_MOM_ENERGY | XSDE_MOM_MOD2 | XSDE_MOM_MOD4))
+        return fail(XSDE_EINVAL, "xsde_moments: unknown moment bits 0x%x", spec->which);
+    if ((spec->which & (XSDE_MOM_NORM | XSDE_MOM_ENERGY)) && !per_path)
+        return fail(XSDE_EINVAL, "xsde_moments: NORM/ENERGY requested without per_path buffer");
+    if ((spec->which & (XSDE_MOM_MOD2 | XSDE_MOM_MOD4)) && !per_point)
+        return fail(XSDE_EINVAL, "xsde_moments: MOD2/MOD4 requested without per_point buffer");
+    p->samp = *spec;
+    p->per_path = per_path;
+    p->per_point = per_point;
+    return XSDE_OK;
+}
+
+int xsde_integrate(xsde_problem *p, xsde_vector *psi, double dt, int64_t nsteps, int64_t npaths,
+                   int64_t path_offset, uint64_t step_offset, void *stream) {
+    if (!p || !psi) return fail(XSDE_EINVAL, "xsde_integrate: NULL problem or field");
+    if (!p->have_ops) return fail(XSDE_EINVAL, "xsde_integrate: operators not set");
+    if (psi->dtype != p->dtype) return fail(XSDE_EINVAL, "xsde_integrate: field dtype differs from the problem's");
+    if (!same_lattice(psi->grid, p->grid)) return fail(XSDE_EINVAL, "xsde_integrate: field lattice differs");
+    if (npaths != psi->npaths)
+        return fail(XSDE_EINVAL, "xsde_integrate: npaths %lld != field npaths %lld", (long long)npaths,
+                    (long long)psi->npaths);
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(XSDE_EINVAL, "xsde_integrate: dt must be positive and finite");
+    if (nsteps < 0) return fail(XSDE_EINVAL, "xsde_integrate: nsteps < 0");
+    if (path_offset < 0 || path_offset + npaths > (int64_t)UINT32_MAX + 1)
+        return fail(XSDE_EINVAL, "xsde_integrate: global path indices exceed 32 bits");
+    if (step_offset + (uint64_t)nsteps + 1 > (uint64_t)UINT32_MAX)
+        return fail(XSDE_EINVAL, "xsde_integrate: global step indices exceed 32 bits");
+    if (p->N.pot_kind == XSDE_POT_TABLE && p->N.V_nt > 1 && step_offset + (uint64_t)nsteps > (uint64_t)p->N.V_nt)
+        return fail(XSDE_EINVAL, "xsde_integrate: potential table has %lld rows, steps up to %llu needed",
+                    (long long)p->N.V_nt, (unsigned long long)(step_offset + nsteps));
+    if (p->grid.ndim == 3) return fail(XSDE_EUNSUPPORTED, "xsde_integrate: 3D lattices are not implemented");
+    if (p->grid.ndim == 2 && npaths > 65535)
+        return fail(XSDE_EUNSUPPORTED, "xsde_integrate: at most 65535 paths per call on a 2D lattice");
+    if (p->samp.every > 0 && nsteps / p->samp.every + 1 > (int64_t)INT32_MAX)
+        return fail(XSDE_EINVAL, "xsde_integrate: too many samples");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != p->device) return fail(XSDE_EINVAL, "xsde_integrate: current device %d is not the problem's %d", dev, p->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return p->dtype == XSDE_C64
+               ? run_integrate<float>(p, psi->data, dt, nsteps, npaths, path_offset, step_offset, s)
+               : run_integrate<double>(p, psi->data, dt, nsteps, npaths, path_offset, step_offset, s);
+}
+
+int xsde_profile(xsde_problem *p, int enable) {
+    if (!p) return fail(XSDE_EINVAL, "xsde_profile: problem is NULL");
+    if (!p->marks.empty()) {
+        XSDE_CUDA(cudaDeviceSynchronize(), "xsde_profile");
+        collect_marks(p);
+    }
+    p->profiling = enable != 0;
+    for (int k = 0; k < XSDE_KERNEL_KINDS; ++k) {
+        p->prof_ms[k] = 0.0;
+        p->prof_launches[k] = 0;
+    }
+    return XSDE_OK;
+}
+
+int xsde_profile_report(xsde_problem *p, double *total_ms, int64_t *launches) {
+    if (!p || !total_ms || !launches) return fail(XSDE_EINVAL, "xsde_profile_report: NULL argument");
+    if (!p->marks.empty()) {
+        for (auto &m : p->marks) XSDE_CUDA(cudaEventSynchronize(m.stop), "xsde_profile_report");
+        collect_marks(p);
+    }
+    for (int k = 0; k < XSDE_KERNEL_KINDS; ++k) {
+        total_ms[k] = p->prof_ms[k];
+        launches[k] = p->prof_launches[k];
+    }
+    return XSDE_OK;
+}
+
+const char *xsde_kernel_name(int kind) {
+    return (kind >= 0 && kind < XSDE_KERNEL_KINDS) ? kKernelNames[kind] : "";
+}
+
+int xsde_noise_philox(const uint32_t *counters, uint64_t seed, int64_t n, uint32_t *out, void *stream) {
+    if (n < 0) return fail(XSDE_EINVAL, "xsde_noise_philox: n < 0");
+    if (n > 0 && (!counters || !out)) return fail(XSDE_EINVAL, "xsde_noise_philox: NULL buffer");
+    if (((uintptr_t)counters | (uintptr_t)out) % 16)
+        return fail(XSDE_EINVAL, "xsde_noise_philox: buffers must be 16-byte aligned");
+    XSDE_CUDA(launch_philox(counters, seed, n, out, static_cast<cudaStream_t>(stream)), "xsde_noise_philox");
+    return XSDE_OK;
+}
+
+int xsde_noise_normals(const xsde_noise *noise, xsde_dtype dtype, int64_t npts, int64_t npaths,
+                       int64_t path_offset, uint64_t step, void *out, void *stream) {
+    if (!noise || !out) return fail(XSDE_EINVAL, "xsde_noise_normals: NULL argument");
+    if (dtype != XSDE_C64 && dtype != XSDE_C128) return fail(XSDE_EINVAL, "xsde_noise_normals: unknown dtype");
+    if (npts < 1 || npaths < 1 || path_offset < 0 || path_offset + npaths > (int64_t)UINT32_MAX + 1 ||
+        npts > (int64_t)UINT32_MAX + 1 || step + 1 > (uint64_t)UINT32_MAX)
+        return fail(XSDE_EINVAL, "xsde_noise_normals: indices out of the 32-bit counter range");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = dtype == XSDE_C64
+                        ? launch_normals<float>(noise->seed, npts, npaths, path_offset, (uint32_t)step, out, s)
+                        : launch_normals<double>(noise->seed, npts, npaths, path_offset, (uint32_t)step, out, s);
+    XSDE_CUDA(e, "xsde_noise_normals");
+    return XSDE_OK;
+}
+
+int xsde_synchronize(xsde_problem *p, void *stream) {
+    if (!p) return fail(XSDE_EINVAL, "xsde_synchronize: problem is NULL");
+    XSDE_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)), "xsde_synchronize");
+    int st = 0;
+    XSDE_CUDA(cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost), "xsde_synchronize: status");
+    if (st) XSDE_CUDA(cudaMemset(p->d_status, 0, sizeof(int)), "xsde_synchronize: reset");
+    if (st & ST_TIMEOUT) return fail(XSDE_ETIMEOUT, "a bounded device-side wait gave up");
+    if (st & ST_NONFINITE) return fail(XSDE_ENONFINITE, "the field became non-finite");
+    return XSDE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,201 @@
+// fft.cuh -- register-distributed Stockham FFTs for the RK4IP kernels.
+//
+// A length-N transform is carried by T = N/E threads.  Thread t holds the E
+// elements x[t + m*T], m = 0..E-1, in registers, both on entry and on exit (the
+// Stockham autosort keeps natural order).  Stages have radix R in {2, 4, 8}
+// (the first stage takes the remainder of log2 N, the others the largest radix
+// that divides E), each thread doing E/R butterflies per stage; between stages
+// the values cross threads through a shared-memory buffer whose index map is
+// supplied by the caller (padded rows, or column tiles).  The last stage ends
+// in registers, so a transform costs (stages - 1) shared-memory exchanges.
+//
+// Stage with radix R after Ns = product of earlier radices (Ns*R <= N):
+//   butterfly j in [0, N/R): inputs x[j + r*N/R]; k = j mod Ns;
+//   u_r = x[j + r*N/R] * w^(r*k) with w = exp(S 2 pi i / (Ns R));
+//   U = DFT_R(u) with sign S;  y[(j - k) R + k + r Ns] = U_r.
+// Forward transforms (S = -1) are unnormalised; inverse ones (S = +1) are the
+// plain sum with conjugate roots (callers fold 1/N into other factors).
+// This is the spectral-to-spatial transform of XMDS2 Sec. 2.2 for the Fourier
+// basis of Sec. 2.1, written for sm_103a register files and shared memory.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace xsde {
+
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
+
+// radix of the stage that starts when `rem` points remain to be combined
+template <int E> __host__ __device__ constexpr int stage_radix(int rem) {
+    constexpr int rmax = E >= 8 ? 8 : E;
+    constexpr int lr = ilog2c(rmax);
+    return (ilog2c(rem) % lr) ? (1 << (ilog2c(rem) % lr)) : rmax;
+}
+
+// ---------------------------------------------------------------------------
+// small DFTs in registers, natural-order output
+// ---------------------------------------------------------------------------
+template <int S, typename V> __device__ __forceinline__ void dft2(V *u) {
+    V a = u[0];
+    u[0] = cadd(a, u[1]);
+    u[1] = csub(a, u[1]);
+}
+
+template <int S, typename V> __device__ __forceinline__ void dft4(V *u) {
+    V s02 = cadd(u[0], u[2]), d02 = csub(u[0], u[2]);
+    V s13 = cadd(u[1], u[3]), d13 = csub(u[1], u[3]);
+    V r = (S < 0) ? cmul_mi(d13) : cmul_i(d13);    // S*i*(u1 - u3)
+    u[0] = cadd(s02, s13);
+    u[2] = csub(s02, s13);
+    u[1] = cadd(d02, r);
+    u[3] = csub(d02, r);
+}
+
+template <int S, typename V> __device__ __forceinline__ void dft8(V *u) {
+    using R = decltype(V::x);
+    const R h = R(0.70710678118654752440084436210485);
+    V e[4] = {u[0], u[2], u[4], u[6]};
+    V o[4] = {u[1], u[3], u[5], u[7]};
+    dft4<S>(e);
+    dft4<S>(o);
+    // o[k] *= exp(S 2 pi i k / 8)
+    if (S < 0) {
+        o[1] = mk<V>(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));
+        o[2] = cmul_mi(o[2]);
+        o[3] = mk<V>(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));
+    } else {
+        o[1] = mk<V>(h * (o[1].x - o[1].y), h * (o[1].x + o[1].y));
+        o[2] = cmul_i(o[2]);
+        o[3] = mk<V>(-h * (o[3].x + o[3].y), h * (o[3].x - o[3].y));
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        u[k] = cadd(e[k], o[k]);
+        u[k + 4] = csub(e[k], o[k]);
+    }
+}
+
+template <int R, int S, typename V> __device__ __forceinline__ void dft(V *u) {
+    if constexpr (R == 2) dft2<S>(u);
+    else if constexpr (R == 4) dft4<S>(u);
+    else dft8<S>(u);
+}
+
+// ---------------------------------------------------------------------------
+// one stage on NV vectors held by this thread
+// ---------------------------------------------------------------------------
+template <int N, int E, int R, int Ns, int S, int NV, typename V, typename Tw>
+__device__ __forceinline__ void fft_stage(V (&v)[NV][E], int t, const Tw &tw) {
+    constexpr int B = E / R, T = N / E;
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        V w[R];
+        if constexpr (Ns > 1) {
+            const int k = (t + q * T) & (Ns - 1);
+#pragma unroll
+            for (int r = 1; r < R; ++r) w[r] = tw(r * k * (N / (Ns * R)));
+        }
+#pragma unroll
+        for (int iv = 0; iv < NV; ++iv) {
+            V u[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) u[r] = v[iv][q + r * B];
+            if constexpr (Ns > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) u[r] = (S < 0) ? cmul(u[r], w[r]) : cmulconj(u[r], w[r]);
+            }
+            dft<R, S>(u);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[iv][q + r * B] = u[r];
+        }
+    }
+}
+
+// Move stage outputs to their Stockham positions and fetch the next inputs.
+// sm[iv] is the exchange buffer of vector iv; L maps logical index -> slot.
+template <int N, int E, int R, int Ns, int NV, typename V, typename Layout, typename Sync>
+__device__ __forceinline__ void fft_exchange(V (&v)[NV][E], int t, V *const (&sm)[NV], const Layout &L,
+                                             const Sync &sync) {
+    constexpr int B = E / R, T = N / E;
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        const int j = t + q * T;
+        const int k = j & (Ns - 1);
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int slot = L(base + r * Ns);
+#pragma unroll
+            for (int iv = 0; iv < NV; ++iv) sm[iv][slot] = v[iv][q + r * B];
+        }
+    }
+    sync();
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        const int slot = L(t + m * T);
+#pragma unroll
+        for (int iv = 0; iv < NV; ++iv) v[iv][m] = sm[iv][slot];
+    }
+    sync();
+}
+
+template <int N, int E, int S, int Ns, int NV, typename V, typename Layout, typename Sync, typename Tw>
+__device__ __forceinline__ void fft_from(V (&v)[NV][E], int t, V *const (&sm)[NV], const Layout &L,
+                                         const Sync &sync, const Tw &tw) {
+    constexpr int R = stage_radix<E>(N / Ns);
+    static_assert(E % R == 0, "radix must divide the elements per thread");
+    fft_stage<N, E, R, Ns, S, NV>(v, t, tw);
+    if constexpr (Ns * R < N) {
+        fft_exchange<N, E, R, Ns, NV>(v, t, sm, L, sync);
+        fft_from<N, E, S, Ns * R, NV>(v, t, sm, L, sync, tw);
+    }
+}
+
+// Transform NV vectors in lockstep (sign S; see the header comment).
+template <int N, int E, int S, int NV, typename V, typename Layout, typename Sync, typename Tw>
+__device__ __forceinline__ void fft(V (&v)[NV][E], int t, V *const (&sm)[NV], const Layout &L,
+                                    const Sync &sync, const Tw &tw) {
+    static_assert((N & (N - 1)) == 0 && N >= E, "N must be a power of two, at least E");
+    static_assert(N % E == 0, "E must divide N");
+    fft_from<N, E, S, 1, NV>(v, t, sm, L, sync, tw);
+}
+
+// --- index maps and barriers ------------------------------------------------
+
+// contiguous line padded by one slot every 8 (conflict-free 64/128-bit access)
+struct PaddedLine {
+    __device__ __forceinline__ int operator()(int i) const { return i + (i >> 3); }
+};
+template <int N> __host__ __device__ constexpr int padded_len() { return N + N / 8; }
+
+// tile of C lines interleaved element by element (slot = i*C + c)
+template <int C> struct ColumnTile {
+    int c;
+    __device__ __forceinline__ int operator()(int i) const { return i * C + c; }
+};
+
+struct SyncBlock {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct SyncWarp {
+    __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
+// named barrier `id` shared by `count` threads (count a multiple of 32)
+struct SyncNamed {
+    int id, count;
+    __device__ __forceinline__ void operator()() const {
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+    }
+};
+
+// twiddles exp(-2 pi i m / N) from a table
+template <typename V> struct TwiddleTable {
+    const V *p;
+    __device__ __forceinline__ V operator()(int m) const { return p[m]; }
+};
+template <typename V> struct TwiddleLdg {
+    const V *p;
+    __device__ __forceinline__ V operator()(int m) const { return __ldg(p + m); }
+};
+
+}  // namespace xsde

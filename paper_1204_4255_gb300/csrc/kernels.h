@@ -1,0 +1,178 @@
+// kernels.h -- parameter blocks and launchers of the RK4IP kernels (internal).
+//
+// Equation family (XMDS2 Sec. 2.6, Eq. PDEBeforeIPTransform):
+//   d psi/dt = L psi + g,  L(k) = c0 + c2|k|^2  (applied as exp(L dt/2) in Fourier space)
+//   N(u) = dt g = dt * [-i (V(x,t) + g_nl |u|^2 + alpha xi_r) u + sigma xi_a]  (real space)
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+
+namespace xsde {
+
+enum PotMode { PM_NONE = 0, PM_HARMONIC = 1, PM_TABLE = 2 };
+enum NoiseMode { NM_NONE = 0, NM_ADD_REAL = 1, NM_ADD_COMPLEX = 2, NM_MUL_REAL = 3 };
+
+// status bits written by kernels into the problem's device error word
+enum { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
+
+// The real-space term: potential, nonlinearity and noise of one step.
+template <typename R> struct LocalTerm {
+    R dt;                 // time step
+    R gdt;                // g_nl * dt
+    int pot;              // PotMode
+    R hw2[3];             // omega_d^2 / 2
+    double xmin[3], dx[3];
+    const R *V;           // [V_nt][npts] raw potential (PM_TABLE)
+    int64_t V_nt;
+    int64_t npts;
+    int noise;            // NoiseMode
+    R nscale;             // amplitude * sqrt(dt/dV)   (complex noise: / sqrt 2)
+    uint2 key;            // Philox key (seed_lo, seed_hi)
+    int64_t path_offset;  // global index of local path 0
+};
+
+// Sampling group: FP64 per-path (norm, energy) and per-point (mean |psi|^2, |psi|^4).
+struct Sampling {
+    int every;             // 0: off
+    int which;             // XSDE_MOM_* bits
+    double *per_path;      // [nsamp][npaths][2]
+    double *per_point;     // [nsamp][npts][2]
+    double dV;
+    double inv_paths;      // 1/npaths (means over paths)
+    double h0, h2;         // Re(i L(k)) = h0 + h2 |k|^2 (kinetic energy density)
+    double kscale[3];      // 2 pi / (xmax - xmin) per dimension
+    double g;              // g_nl (interaction energy g/2 |psi|^4)
+};
+
+enum { MOM_NORM = 1, MOM_ENERGY = 2, MOM_MOD2 = 4, MOM_MOD4 = 8 };
+
+// --------------------------------------------------------------------------
+// 1D: one CTA slot per path runs every step with the field in registers.
+// --------------------------------------------------------------------------
+template <typename R> struct Params1D {
+    cx<R> *psi;            // [npaths][N] real space, in/out
+    int64_t npaths;
+    int64_t nsteps;
+    uint64_t step0;        // global index of local step 0
+    const cx<R> *Etab;     // exp(L(k) dt/2)/N in FFT order [N]
+    const cx<R> *tw;       // exp(-2 pi i m/N) [N]
+    LocalTerm<R> lt;
+    Sampling sm;
+    int *status;
+};
+template <typename R> cudaError_t launch_rk4ip_1d(int n, const Params1D<R> &p, cudaStream_t s);
+
+// --------------------------------------------------------------------------
+// 2D: row passes (contiguous dimension 1, real-space work) and column passes
+// (dimension 0, exp(L dt/2)); fields between passes are FFT'd along dim 1.
+// --------------------------------------------------------------------------
+enum RowMode {
+    ROW_PROLOGUE = 0,   // psi (real) -> A = F1 psi, B = F1 N(psi)
+    ROW_STAGE2 = 1,     // A = a_I, B = k1 -> A = u1 = a_I + k3, B = a_I + k1/6 + k2/3 + k3/3
+    ROW_STEADY = 2,     // A = D u1, B = D acc -> a' = D acc + N(D u1)/6; A = F1 a', B = F1 N(a')
+    ROW_EPILOGUE = 3,   // as STEADY but writes a' in real space to A only
+    ROW_FFT_ONLY = 4    // A (real) -> B = F1 A (for the spectral part of the energy)
+};
+enum ColMode {
+    COL_PROPAGATE = 0,  // A, B -> F0^-1 exp(L dt/2)/N F0 (A, B)
+    COL_SPECTRAL = 1    // B: accumulate the kinetic energy only (no write)
+};
+
+template <typename R> struct Params2D {
+    cx<R> *A;              // [npaths][N0][N1]
+    cx<R> *B;              // scratch, same shape
+    int64_t npaths;
+    int n0, n1;
+    const cx<R> *tw0, *tw1;   // twiddles per dimension
+    const cx<R> *E0, *E1;     // separable exp(L dt/2) factors; E0 carries exp(c0 dt/2)/(n0 n1)
+    LocalTerm<R> lt;
+    Sampling sm;
+    int sample_slot;       // sample written by this pass (-1: none)
+    uint64_t sg;           // global step index of the step this pass belongs to
+    int *status;
+};
+template <typename R> cudaError_t launch_row_pass(int mode, const Params2D<R> &p, cudaStream_t s);
+template <typename R> cudaError_t launch_col_pass(int mode, const Params2D<R> &p, cudaStream_t s);
+
+// --------------------------------------------------------------------------
+// 0D: one thread per path (an ordinary SDE; D is a scalar factor).
+// --------------------------------------------------------------------------
+template <typename R> struct Params0D {
+    cx<R> *psi;            // [npaths]
+    int64_t npaths;
+    int64_t nsteps;
+    uint64_t step0;
+    cx<R> Ehalf;           // exp(c0 dt/2)
+    LocalTerm<R> lt;
+    Sampling sm;
+    int *status;
+};
+template <typename R> cudaError_t launch_rk4ip_0d(const Params0D<R> &p, cudaStream_t s);
+
+// Generator entry points (noise.cu).
+cudaError_t launch_philox(const uint32_t *ctr, uint64_t seed, int64_t n, uint32_t *out, cudaStream_t s);
+template <typename R>
+cudaError_t launch_normals(uint64_t seed, int64_t npts, int64_t npaths, int64_t path_offset, uint32_t step,
+                           void *out, cudaStream_t s);
+
+// --------------------------------------------------------------------------
+// Device helpers for the real-space term.
+// --------------------------------------------------------------------------
+
+// Per point and step: dt*(V + alpha xi_r) and the additive increment dt*sigma*xi_a.
+template <typename R> struct PointTerm {
+    R dtV;
+    cx<R> na;
+};
+
+template <typename R>
+__device__ __forceinline__ PointTerm<R> point_term(const LocalTerm<R> &lt, R Vraw, uint32_t j, uint32_t gpath,
+                                                   uint32_t gstep) {
+    PointTerm<R> pt;
+    pt.dtV = lt.dt * Vraw;
+    pt.na = mk<cx<R>>(R(0), R(0));
+    if (lt.noise != NM_NONE) {
+        cx<R> z = wiener_pair<R>(lt.key, j, gpath, gstep);
+        if (lt.noise == NM_MUL_REAL) pt.dtV += lt.nscale * z.x;
+        else if (lt.noise == NM_ADD_REAL) pt.na = mk<cx<R>>(lt.nscale * z.x, R(0));
+        else pt.na = mk<cx<R>>(lt.nscale * z.x, lt.nscale * z.y);
+    }
+    return pt;
+}
+
+// N(u) = dt * (-i (V + alpha xi + g|u|^2) u + sigma xi_a)
+template <typename R> __device__ __forceinline__ cx<R> apply_N(cx<R> u, const PointTerm<R> &pt, R gdt) {
+    R dtpot = pt.dtV + gdt * cabs2(u);
+    return mk<cx<R>>(dtpot * u.y + pt.na.x, -dtpot * u.x + pt.na.y);
+}
+
+// raw potential at flat point j (multi-index given) for global step gstep
+template <typename R>
+__device__ __forceinline__ R potential(const LocalTerm<R> &lt, int ndim, const int (&idx)[3], int64_t j,
+                                       uint64_t gstep) {
+    if (lt.pot == PM_HARMONIC) {
+        R v = R(0);
+        for (int d = 0; d < ndim; ++d) {
+            R x = R(lt.xmin[d] + idx[d] * lt.dx[d]);
+            v += lt.hw2[d] * x * x;
+        }
+        return v;
+    }
+    if (lt.pot == PM_TABLE) {
+        int64_t row = lt.V_nt > 1 ? (int64_t)gstep : 0;
+        if (row >= lt.V_nt) row = lt.V_nt - 1;
+        return lt.V[row * lt.npts + j];
+    }
+    return R(0);
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+}  // namespace xsde

@@ -1,0 +1,221 @@
+// rk4ip_1d.cu -- whole-run RK4IP for 1D lattices (N <= 2048), one CTA slot per path.
+//
+// XMDS2 (arXiv:1204.4255) Sec. 2.5 (method of lines, RK4) with Sec. 2.6 (the
+// interaction picture, re-centred each step so only exp(L dt/2) is needed).
+// Per step, with D(u) = F^-1 exp(L dt/2) F u and N(u) = dt g(u):
+//   a_I = D a,  k1 = D N(a),  k2 = N(a_I + k1/2),  k3 = N(a_I + k2/2),
+//   k4 = N(D(a_I + k3)),  a <- D(a_I + k1/6 + k2/3 + k3/3) + k4/6.
+// The field never leaves the SM during the run: each thread keeps the points
+// t + m*T (m < 8) of its path in registers, the eight FFTs of a step exchange
+// through shared memory, and D is applied to two vectors in lockstep.  Only the
+// initial load, the final store, time-dependent potential rows and the FP64
+// samples touch global memory.
+#include "fft.cuh"
+#include "kernels.h"
+
+namespace xsde {
+namespace {
+
+// barrier of the T threads that carry one path
+template <int T, int PPC> struct SlotSync {
+    int slot;
+    __device__ __forceinline__ void operator()() const {
+        if constexpr (T <= 32) __syncwarp();
+        else if constexpr (PPC == 1) __syncthreads();
+        else asm volatile("bar.sync %0, %1;" ::"r"(slot + 1), "r"(T) : "memory");
+    }
+};
+
+// sum three doubles over the T threads of a slot (result in every thread)
+template <int T, typename Sync>
+__device__ __forceinline__ void slot_sum3(double (&v)[3], int t, double *scratch, const Sync &sync) {
+    if constexpr (T <= 32) {
+#pragma unroll
+        for (int o = T / 2; o > 0; o >>= 1)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    } else {
+        constexpr int W = T / 32;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) v[i] = warp_sum(v[i]);
+        sync();
+        if ((t & 31) == 0)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) scratch[(t >> 5) * 3 + i] = v[i];
+        sync();
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) s += scratch[w * 3 + i];
+            v[i] = s;
+        }
+        sync();
+    }
+}
+
+template <typename R, int N, int E, int PPC>
+__global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R> p) {
+    using V = cx<R>;
+    constexpr int T = N / E;
+    constexpr int BUF = padded_len<N>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *tws = reinterpret_cast<V *>(smem_raw);
+    const int slot = threadIdx.x / T;
+    const int t = threadIdx.x - slot * T;
+    V *bufA = tws + N + slot * 2 * BUF;
+    V *bufB = bufA + BUF;
+    V *const sm2[2] = {bufA, bufB};
+    V *const sm1[1] = {bufA};
+    const SlotSync<T, PPC> sync{slot};
+    const TwiddleTable<V> tw{tws};
+    const PaddedLine L{};
+
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = p.tw[i];
+    __syncthreads();
+
+    const int64_t lp = (int64_t)blockIdx.x * PPC + slot;
+    const bool active = lp < p.npaths;
+    const uint32_t gp = (uint32_t)(p.lt.path_offset + lp);
+    V *psi = p.psi + lp * N;
+    const bool vtime = p.lt.pot == PM_TABLE && p.lt.V_nt > 1;
+
+    V x[2][E];
+    V Ek[E];
+    R Vs[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        const int j = t + m * T;
+        x[0][m] = active ? psi[j] : mk<V>(R(0), R(0));
+        Ek[m] = p.Etab[j];
+        const int idx[3] = {j, 0, 0};
+        Vs[m] = vtime ? R(0) : potential(p.lt, 1, idx, j, 0);
+    }
+    const R gdt = p.lt.gdt;
+    const R sixth = R(1) / R(6), third = R(1) / R(3), half = R(0.5);
+
+    for (int64_t n = 0;; ++n) {
+        // ---- sampling group (XMDS2 Sec. 2.5 moments over paths) ----------
+        if (p.sm.every > 0 && n % p.sm.every == 0) {
+            const int64_t s = n / p.sm.every;
+            const uint64_t gs = p.step0 + n;
+            double acc[3] = {0.0, 0.0, 0.0};   // norm, local energy, kinetic energy
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int j = t + m * T;
+                const int idx[3] = {j, 0, 0};
+                const double m2 = (double)cabs2(x[0][m]);
+                const double vv = (double)potential(p.lt, 1, idx, j, gs);
+                acc[0] += m2;
+                acc[1] += vv * m2 + 0.5 * p.sm.g * m2 * m2;
+                if (active && (p.sm.which & (MOM_MOD2 | MOM_MOD4)) && p.sm.per_point) {
+                    double *pp = p.sm.per_point + 2 * (s * N + j);
+                    atomicAdd(pp, m2 * p.sm.inv_paths);
+                    atomicAdd(pp + 1, m2 * m2 * p.sm.inv_paths);
+                }
+            }
+            V y[1][E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) y[0][m] = x[0][m];
+            fft<N, E, -1, 1>(y, t, sm1, L, sync, tw);
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int kj = t + m * T;
+                const double k = p.sm.kscale[0] * (kj < N / 2 ? kj : kj - N);
+                acc[2] += (p.sm.h0 + p.sm.h2 * k * k) * (double)cabs2(y[0][m]);
+            }
+            slot_sum3<T>(acc, t, reinterpret_cast<double *>(bufB), sync);
+            if (t == 0 && active) {
+                const double norm = acc[0] * p.sm.dV;
+                if ((p.sm.which & (MOM_NORM | MOM_ENERGY)) && p.sm.per_path) {
+                    double *pq = p.sm.per_path + 2 * (s * p.npaths + lp);
+                    pq[0] = norm;
+                    pq[1] = (acc[1] + acc[2] / N) * p.sm.dV;
+                }
+                if (!isfinite(norm)) atomicOr(p.status, ST_NONFINITE);
+            }
+        }
+        if (n == p.nsteps) break;
+
+        // ---- one RK4IP step ----------------------------------------------
+        const uint64_t sg = p.step0 + n;
+        PointTerm<R> pt[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int j = t + m * T;
+            R v = Vs[m];
+            if (vtime) v = p.lt.V[(int64_t)sg * N + j];
+            pt[m] = point_term(p.lt, v, (uint32_t)j, gp, (uint32_t)sg);
+            x[1][m] = apply_N(x[0][m], pt[m], gdt);     // N(a)
+        }
+        // a_I = D a, k1 = D N(a)
+        fft<N, E, -1, 2>(x, t, sm2, L, sync, tw);
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            x[0][m] = cmul(x[0][m], Ek[m]);
+            x[1][m] = cmul(x[1][m], Ek[m]);
+        }
+        fft<N, E, +1, 2>(x, t, sm2, L, sync, tw);
+        // k2, k3 in real space; x[0] <- a_I + k3, x[1] <- a_I + k1/6 + k2/3 + k3/3
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const V aI = x[0][m], k1 = x[1][m];
+            const V k2 = apply_N(caxpy(aI, half, k1), pt[m], gdt);
+            const V k3 = apply_N(caxpy(aI, half, k2), pt[m], gdt);
+            x[0][m] = cadd(aI, k3);
+            x[1][m] = caxpy(caxpy(caxpy(aI, sixth, k1), third, k2), third, k3);
+        }
+        fft<N, E, -1, 2>(x, t, sm2, L, sync, tw);
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            x[0][m] = cmul(x[0][m], Ek[m]);
+            x[1][m] = cmul(x[1][m], Ek[m]);
+        }
+        fft<N, E, +1, 2>(x, t, sm2, L, sync, tw);
+        // k4 = N(D(a_I + k3)); a <- D(acc) + k4/6
+#pragma unroll
+        for (int m = 0; m < E; ++m) x[0][m] = caxpy(x[1][m], sixth, apply_N(x[0][m], pt[m], gdt));
+    }
+
+    if (active) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) psi[t + m * T] = x[0][m];
+    }
+}
+
+template <typename R, int N> cudaError_t launch_n(const Params1D<R> &p, cudaStream_t s) {
+    constexpr int E = 8, T = N / E, PPC = T >= 128 ? 1 : 128 / T;
+    const size_t smem = (size_t)(N + PPC * 2 * padded_len<N>()) * sizeof(cx<R>);
+    auto kern = rk4ip_1d_kernel<R, N, E, PPC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (p.npaths + PPC - 1) / PPC;
+    kern<<<(unsigned)blocks, PPC * T, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename R> cudaError_t launch_rk4ip_1d(int n, const Params1D<R> &p, cudaStream_t s) {
+    switch (n) {
+        case 16: return launch_n<R, 16>(p, s);
+        case 32: return launch_n<R, 32>(p, s);
+        case 64: return launch_n<R, 64>(p, s);
+        case 128: return launch_n<R, 128>(p, s);
+        case 256: return launch_n<R, 256>(p, s);
+        case 512: return launch_n<R, 512>(p, s);
+        case 1024: return launch_n<R, 1024>(p, s);
+        case 2048: return launch_n<R, 2048>(p, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// XSDE_REAL_BITS selects one precision per translation unit (parallel builds)
+#if !defined(XSDE_REAL_BITS) || XSDE_REAL_BITS == 32
+template cudaError_t launch_rk4ip_1d<float>(int, const Params1D<float> &, cudaStream_t);
+#endif
+#if !defined(XSDE_REAL_BITS) || XSDE_REAL_BITS == 64
+template cudaError_t launch_rk4ip_1d<double>(int, const Params1D<double> &, cudaStream_t);
+#endif
+
+}  // namespace xsde

@@ -1,0 +1,358 @@
+// rk4ip_2d.cu -- RK4IP on 2D lattices as four fused passes per step.
+//
+// XMDS2 (arXiv:1204.4255) Sec. 2.6: exp(L dt/2) is applied by transforming to
+// Fourier space, multiplying, and transforming back; Sec. 2.2: the transform of
+// a tensor-product lattice factorises per dimension.  Between passes the fields
+// are kept transformed along the contiguous dimension 1 only, so
+//   row pass    (dimension 1): F1^-1 -> real-space RK4 stage work -> F1
+//   column pass (dimension 0): F0 -> * exp(L(k) dt/2)/(n0 n1) -> F0^-1
+// and a step is row(S4 of step n-1 + S1 of step n) -> col -> row(S2) -> col.
+// Every pass reads two fields and writes two (in place, whole lines per CTA),
+// i.e. 16 field accesses per point per step.
+#include "fft.cuh"
+#include "kernels.h"
+
+namespace xsde {
+namespace {
+
+template <int T>
+__device__ __forceinline__ void group_sum2(double (&v)[2], int t, double *scratch) {
+    // sum over the T threads of a line; T <= 32: xor shuffles inside the group,
+    // T > 32: warp sums combined through shared memory (all threads call this)
+    if constexpr (T <= 32) {
+#pragma unroll
+        for (int o = T / 2; o > 0; o >>= 1)
+#pragma unroll
+            for (int i = 0; i < 2; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    } else {
+        constexpr int W = T / 32;
+        const int line = threadIdx.x / T;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) v[i] = warp_sum(v[i]);
+        __syncthreads();
+        if ((t & 31) == 0)
+#pragma unroll
+            for (int i = 0; i < 2; ++i) scratch[(line * W + (t >> 5)) * 2 + i] = v[i];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) s += scratch[(line * W + w) * 2 + i];
+            v[i] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Row pass: T = N1/8 threads per line, LINES lines per CTA.
+// ---------------------------------------------------------------------------
+template <int N1> struct RowCfg {
+    static constexpr int E = 8;
+    static constexpr int T = N1 / E;
+    static constexpr int LINES = T >= 256 ? 1 : 256 / T;
+    static constexpr int THREADS = LINES * T;
+};
+
+template <typename R, int N1, int MODE>
+__global__ void __launch_bounds__(RowCfg<N1>::THREADS) row_pass_kernel(const Params2D<R> p) {
+    using V = cx<R>;
+    using Cfg = RowCfg<N1>;
+    constexpr int E = Cfg::E, T = Cfg::T, LINES = Cfg::LINES;
+    constexpr int BUF = padded_len<N1>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *smem = reinterpret_cast<V *>(smem_raw);
+    const int line = threadIdx.x / T;
+    const int t = threadIdx.x - line * T;
+    V *const sm2[2] = {smem + line * 2 * BUF, smem + line * 2 * BUF + BUF};
+    V *const sm1[1] = {smem + line * 2 * BUF};
+    double *scratch = reinterpret_cast<double *>(smem + LINES * 2 * BUF);
+    const SyncBlock sync{};
+    const TwiddleLdg<V> tw{p.tw1};
+    const PaddedLine L{};
+
+    const int64_t nrows = p.npaths * (int64_t)p.n0;
+    const int64_t row = (int64_t)blockIdx.x * LINES + line;
+    const bool active = row < nrows;
+    const int64_t rrow = active ? row : 0;
+    const int64_t path = rrow / p.n0;
+    const int i0 = (int)(rrow - path * p.n0);
+    const uint32_t gp = (uint32_t)(p.lt.path_offset + path);
+    V *Arow = p.A + rrow * N1;
+    V *Brow = p.B + rrow * N1;
+    const R gdt = p.lt.gdt;
+    const R sixth = R(1) / R(6), third = R(1) / R(3), half = R(0.5);
+    const bool sample = p.sample_slot >= 0;
+
+    // raw potential of point (i0, t + m T) at global step gs
+    auto pot = [&](int m, uint64_t gs) -> R {
+        const int i1 = t + m * T;
+        const int idx[3] = {i0, i1, 0};
+        return potential(p.lt, 2, idx, (int64_t)i0 * N1 + i1, gs);
+    };
+    auto pterm = [&](int m, uint64_t gs) -> PointTerm<R> {
+        const int i1 = t + m * T;
+        return point_term(p.lt, pot(m, gs), (uint32_t)(i0 * N1 + i1), gp, (uint32_t)gs);
+    };
+    // local part of the sampling group for the real-space field f at global step gs
+    auto sample_local = [&](const V (&f)[E], uint64_t gs) {
+        double acc[2] = {0.0, 0.0};
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const double m2 = (double)cabs2(f[m]);
+            acc[0] += m2;
+            acc[1] += (double)pot(m, gs) * m2 + 0.5 * p.sm.g * m2 * m2;
+            if (active && (p.sm.which & (MOM_MOD2 | MOM_MOD4)) && p.sm.per_point) {
+                double *pp = p.sm.per_point + 2 * ((int64_t)p.sample_slot * p.lt.npts + (int64_t)i0 * N1 + t + m * T);
+                atomicAdd(pp, m2 * p.sm.inv_paths);
+                atomicAdd(pp + 1, m2 * m2 * p.sm.inv_paths);
+            }
+        }
+        group_sum2<T>(acc, t, scratch);
+        if (t == 0 && active) {
+            if ((p.sm.which & (MOM_NORM | MOM_ENERGY)) && p.sm.per_path) {
+                double *pq = p.sm.per_path + 2 * ((int64_t)p.sample_slot * p.npaths + path);
+                atomicAdd(pq, acc[0] * p.sm.dV);
+                atomicAdd(pq + 1, acc[1] * p.sm.dV);
+            }
+            if (!isfinite(acc[0])) atomicOr(p.status, ST_NONFINITE);
+        }
+    };
+
+    V x[2][E];
+    if constexpr (MODE == ROW_PROLOGUE || MODE == ROW_FFT_ONLY) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) x[0][m] = Arow[t + m * T];
+        if (sample) sample_local(x[0], p.sg);
+        if constexpr (MODE == ROW_FFT_ONLY) {
+            V y[1][E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) y[0][m] = x[0][m];
+            fft<N1, E, -1, 1>(y, t, sm1, L, sync, tw);
+            if (active)
+#pragma unroll
+                for (int m = 0; m < E; ++m) Brow[t + m * T] = y[0][m];
+            return;
+        } else {
+#pragma unroll
+            for (int m = 0; m < E; ++m) x[1][m] = apply_N(x[0][m], pterm(m, p.sg), gdt);
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            x[0][m] = Arow[t + m * T];
+            x[1][m] = Brow[t + m * T];
+        }
+        fft<N1, E, +1, 2>(x, t, sm2, L, sync, tw);
+        if constexpr (MODE == ROW_STAGE2) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const PointTerm<R> pt = pterm(m, p.sg);
+                const V aI = x[0][m], k1 = x[1][m];
+                const V k2 = apply_N(caxpy(aI, half, k1), pt, gdt);
+                const V k3 = apply_N(caxpy(aI, half, k2), pt, gdt);
+                x[0][m] = cadd(aI, k3);
+                x[1][m] = caxpy(caxpy(caxpy(aI, sixth, k1), third, k2), third, k3);
+            }
+        } else {
+            // k4 = N(D(a_I + k3)) at step sg; a' = D(acc) + k4/6
+#pragma unroll
+            for (int m = 0; m < E; ++m) x[0][m] = caxpy(x[1][m], sixth, apply_N(x[0][m], pterm(m, p.sg), gdt));
+            if constexpr (MODE == ROW_EPILOGUE) {
+                if (active)
+#pragma unroll
+                    for (int m = 0; m < E; ++m) Arow[t + m * T] = x[0][m];
+                return;
+            } else {
+                if (sample) sample_local(x[0], p.sg + 1);
+#pragma unroll
+                for (int m = 0; m < E; ++m) x[1][m] = apply_N(x[0][m], pterm(m, p.sg + 1), gdt);
+            }
+        }
+    }
+    fft<N1, E, -1, 2>(x, t, sm2, L, sync, tw);
+    if (active) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            Arow[t + m * T] = x[0][m];
+            Brow[t + m * T] = x[1][m];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Column pass: a tile of C adjacent columns of one path; T = N0/E threads per
+// column; lanes run over columns first so every load is a 128-byte segment.
+// ---------------------------------------------------------------------------
+template <typename R, int N0> struct ColCfg {
+    // 128-byte row segments (16 c64 / 8 c128 columns) up to 1024 (c64) or 512
+    // (c128) threads per CTA; longer columns use narrower tiles.
+    static constexpr int CMAX = sizeof(R) == 4 ? 16 : 8;
+    static constexpr int TMAX = sizeof(R) == 4 ? 1024 : 512;
+    static constexpr int E = 8;
+    static constexpr int T = N0 / E;
+    static constexpr int C = (CMAX * T <= TMAX) ? CMAX : TMAX / T;
+    static constexpr int THREADS = C * T;
+};
+
+template <typename R, int N0, int MODE>
+__global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const Params2D<R> p) {
+    using V = cx<R>;
+    using Cfg = ColCfg<R, N0>;
+    constexpr int C = Cfg::C, E = Cfg::E, T = Cfg::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *smem = reinterpret_cast<V *>(smem_raw);
+    V *const sm2[2] = {smem, smem + N0 * C};
+    V *const sm1[1] = {smem};
+    double *scratch = reinterpret_cast<double *>(smem + 2 * N0 * C);
+    const int c = threadIdx.x % C;
+    const int t = threadIdx.x / C;
+    const SyncBlock sync{};
+    const TwiddleLdg<V> tw{p.tw0};
+    const ColumnTile<C> L{c};
+
+    const int col = blockIdx.x * C + c;
+    const int64_t path = blockIdx.y;
+    const int n1 = p.n1;
+    const int64_t base = path * (int64_t)N0 * n1 + col;
+    const bool sample = p.sample_slot >= 0;
+
+    auto kinetic = [&](const V (&f)[E]) {
+        // sum_k Re(i L(k)) |F psi|^2 dV / (n0 n1), accumulated into the energy of this path
+        const int k1i = col < n1 / 2 ? col : col - n1;
+        const double k1 = p.sm.kscale[1] * k1i;
+        double s = 0.0;
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int kj = t + m * T;
+            const double k0 = p.sm.kscale[0] * (kj < N0 / 2 ? kj : kj - N0);
+            s += (p.sm.h0 + p.sm.h2 * (k0 * k0 + k1 * k1)) * (double)cabs2(f[m]);
+        }
+        s = warp_sum(s);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) scratch[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += scratch[w];
+            if ((p.sm.which & (MOM_NORM | MOM_ENERGY)) && p.sm.per_path)
+                atomicAdd(p.sm.per_path + 2 * ((int64_t)p.sample_slot * p.npaths + path) + 1,
+                          tot * p.sm.dV / ((double)N0 * n1));
+        }
+    };
+
+    if constexpr (MODE == COL_SPECTRAL) {
+        V y[1][E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) y[0][m] = p.B[base + (int64_t)(t + m * T) * n1];
+        fft<N0, E, -1, 1>(y, t, sm1, L, sync, tw);
+        kinetic(y[0]);
+        return;
+    } else {
+        V x[2][E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            x[0][m] = p.A[base + (int64_t)(t + m * T) * n1];
+            x[1][m] = p.B[base + (int64_t)(t + m * T) * n1];
+        }
+        fft<N0, E, -1, 2>(x, t, sm2, L, sync, tw);
+        if (sample) kinetic(x[0]);
+        const V e1 = p.E1[col];
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const V e = cmul(__ldg(p.E0 + t + m * T), e1);
+            x[0][m] = cmul(x[0][m], e);
+            x[1][m] = cmul(x[1][m], e);
+        }
+        fft<N0, E, +1, 2>(x, t, sm2, L, sync, tw);
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            p.A[base + (int64_t)(t + m * T) * n1] = x[0][m];
+            p.B[base + (int64_t)(t + m * T) * n1] = x[1][m];
+        }
+    }
+}
+
+template <typename R, int N1, int MODE> cudaError_t row_launch(const Params2D<R> &p, cudaStream_t s) {
+    using Cfg = RowCfg<N1>;
+    const size_t smem = (size_t)Cfg::LINES * 2 * padded_len<N1>() * sizeof(cx<R>) +
+                        (size_t)Cfg::LINES * (Cfg::T / 32 + 1) * 2 * sizeof(double);
+    auto kern = row_pass_kernel<R, N1, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t rows = p.npaths * (int64_t)p.n0;
+    const int64_t blocks = (rows + Cfg::LINES - 1) / Cfg::LINES;
+    kern<<<(unsigned)blocks, Cfg::THREADS, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename R, int N1> cudaError_t row_mode(int mode, const Params2D<R> &p, cudaStream_t s) {
+    switch (mode) {
+        case ROW_PROLOGUE: return row_launch<R, N1, ROW_PROLOGUE>(p, s);
+        case ROW_STAGE2: return row_launch<R, N1, ROW_STAGE2>(p, s);
+        case ROW_STEADY: return row_launch<R, N1, ROW_STEADY>(p, s);
+        case ROW_EPILOGUE: return row_launch<R, N1, ROW_EPILOGUE>(p, s);
+        case ROW_FFT_ONLY: return row_launch<R, N1, ROW_FFT_ONLY>(p, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename R, int N0, int MODE> cudaError_t col_launch(const Params2D<R> &p, cudaStream_t s) {
+    using Cfg = ColCfg<R, N0>;
+    const size_t smem = (size_t)2 * N0 * Cfg::C * sizeof(cx<R>) + (Cfg::THREADS / 32 + 1) * sizeof(double);
+    auto kern = col_pass_kernel<R, N0, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)(p.n1 / Cfg::C), (unsigned)p.npaths);
+    kern<<<grid, Cfg::THREADS, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename R, int N0> cudaError_t col_mode(int mode, const Params2D<R> &p, cudaStream_t s) {
+    if (p.n1 % ColCfg<R, N0>::C) return cudaErrorInvalidValue;
+    return mode == COL_SPECTRAL ? col_launch<R, N0, COL_SPECTRAL>(p, s) : col_launch<R, N0, COL_PROPAGATE>(p, s);
+}
+
+}  // namespace
+
+
+template <typename R> cudaError_t launch_row_pass(int mode, const Params2D<R> &p, cudaStream_t s) {
+    switch (p.n1) {
+        case 16: return row_mode<R, 16>(mode, p, s);
+        case 32: return row_mode<R, 32>(mode, p, s);
+        case 64: return row_mode<R, 64>(mode, p, s);
+        case 128: return row_mode<R, 128>(mode, p, s);
+        case 256: return row_mode<R, 256>(mode, p, s);
+        case 512: return row_mode<R, 512>(mode, p, s);
+        case 1024: return row_mode<R, 1024>(mode, p, s);
+        case 2048: return row_mode<R, 2048>(mode, p, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename R> cudaError_t launch_col_pass(int mode, const Params2D<R> &p, cudaStream_t s) {
+    switch (p.n0) {
+        case 16: return col_mode<R, 16>(mode, p, s);
+        case 32: return col_mode<R, 32>(mode, p, s);
+        case 64: return col_mode<R, 64>(mode, p, s);
+        case 128: return col_mode<R, 128>(mode, p, s);
+        case 256: return col_mode<R, 256>(mode, p, s);
+        case 512: return col_mode<R, 512>(mode, p, s);
+        case 1024: return col_mode<R, 1024>(mode, p, s);
+        case 2048: return col_mode<R, 2048>(mode, p, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// XSDE_REAL_BITS selects one precision per translation unit (parallel builds)
+#if !defined(XSDE_REAL_BITS) || XSDE_REAL_BITS == 32
+template cudaError_t launch_row_pass<float>(int, const Params2D<float> &, cudaStream_t);
+template cudaError_t launch_col_pass<float>(int, const Params2D<float> &, cudaStream_t);
+#endif
+#if !defined(XSDE_REAL_BITS) || XSDE_REAL_BITS == 64
+template cudaError_t launch_row_pass<double>(int, const Params2D<double> &, cudaStream_t);
+template cudaError_t launch_col_pass<double>(int, const Params2D<double> &, cudaStream_t);
+#endif
+
+}  // namespace xsde

@@ -1,0 +1,307 @@
+"""Thin Python binding of the C-ABI in ``include/xsde.h`` (ctypes).
+
+Functions carry the C names and only marshal arguments: torch tensors are
+passed as device pointers, torch streams as ``cudaStream_t``.  Every step of
+the time integration runs in the CUDA kernels of ``libxsde.so``; there is no
+CPU path.  If the library has not been built, loading raises ``RuntimeError``.
+
+The ``Problem`` class bundles the handle calls for convenience; it adds no
+arithmetic of its own.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libxsde.so")
+
+XSDE_OK, XSDE_EINVAL, XSDE_ENOMEM, XSDE_ECUDA, XSDE_ETIMEOUT, XSDE_ENONFINITE, XSDE_EUNSUPPORTED = range(7)
+XSDE_C64, XSDE_C128 = 1, 2
+XSDE_POT_NONE, XSDE_POT_HARMONIC, XSDE_POT_TABLE = 0, 1, 2
+XSDE_NOISE_NONE, XSDE_NOISE_WIENER_REAL, XSDE_NOISE_WIENER_COMPLEX = 0, 1, 2
+XSDE_COUPLE_ADDITIVE, XSDE_COUPLE_MULTIPLICATIVE = 0, 1
+XSDE_MOM_NORM, XSDE_MOM_ENERGY, XSDE_MOM_MOD2, XSDE_MOM_MOD4 = 1, 2, 4, 8
+
+EXPORTED = (
+    "xsde_grid_create", "xsde_grid_destroy", "xsde_grid_points",
+    "xsde_vector_alloc", "xsde_vector_wrap", "xsde_vector_data", "xsde_vector_free",
+    "xsde_noise_alloc", "xsde_noise_free", "xsde_noise_philox", "xsde_noise_normals",
+    "xsde_problem_create", "xsde_problem_destroy", "xsde_set_operators", "xsde_moments",
+    "xsde_integrate", "xsde_synchronize", "xsde_last_error", "xsde_version",
+    "xsde_profile", "xsde_profile_report", "xsde_kernel_name",
+)
+XSDE_KERNEL_KINDS = 9
+
+
+class XsdeError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"xsde status {status}: {message}")
+        self.status = status
+
+
+class xsde_linear_op(ctypes.Structure):
+    _fields_ = [("c0_re", ctypes.c_double), ("c0_im", ctypes.c_double),
+                ("c2_re", ctypes.c_double), ("c2_im", ctypes.c_double)]
+
+
+class xsde_nonlinear_op(ctypes.Structure):
+    _fields_ = [("pot_kind", ctypes.c_int32), ("omega", ctypes.c_double * 3), ("V", ctypes.c_void_p),
+                ("V_nt", ctypes.c_int64), ("g", ctypes.c_double), ("noise", ctypes.c_void_p),
+                ("coupling", ctypes.c_int32), ("amplitude", ctypes.c_double)]
+
+
+class xsde_sampling(ctypes.Structure):
+    _fields_ = [("every", ctypes.c_int32), ("which", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libxsde.so (raises RuntimeError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not found: build it with paper_1204_4255_gb300.build.build() "
+                           "(or __graft_entry__.build()); there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, u64, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    pvp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "xsde_grid_create": (ctypes.c_int, [ctypes.c_int, vp, vp, vp, pvp]),
+        "xsde_grid_destroy": (None, [vp]),
+        "xsde_grid_points": (i64, [vp]),
+        "xsde_vector_alloc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, i64, pvp]),
+        "xsde_vector_wrap": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, i64, vp, pvp]),
+        "xsde_vector_data": (vp, [vp]),
+        "xsde_vector_free": (None, [vp]),
+        "xsde_noise_alloc": (ctypes.c_int, [vp, ctypes.c_int, u64, pvp]),
+        "xsde_noise_free": (None, [vp]),
+        "xsde_noise_philox": (ctypes.c_int, [vp, u64, i64, vp, vp]),
+        "xsde_noise_normals": (ctypes.c_int, [vp, ctypes.c_int, i64, i64, i64, u64, vp, vp]),
+        "xsde_problem_create": (ctypes.c_int, [vp, ctypes.c_int, pvp]),
+        "xsde_problem_destroy": (None, [vp]),
+        "xsde_set_operators": (ctypes.c_int, [vp, ctypes.POINTER(xsde_linear_op), ctypes.POINTER(xsde_nonlinear_op)]),
+        "xsde_moments": (ctypes.c_int, [vp, ctypes.POINTER(xsde_sampling), vp, vp]),
+        "xsde_integrate": (ctypes.c_int, [vp, vp, dp, i64, i64, i64, u64, vp]),
+        "xsde_synchronize": (ctypes.c_int, [vp, vp]),
+        "xsde_last_error": (ctypes.c_char_p, []),
+        "xsde_version": (ctypes.c_char_p, []),
+        "xsde_profile": (ctypes.c_int, [vp, ctypes.c_int]),
+        "xsde_profile_report": (ctypes.c_int, [vp, vp, vp]),
+        "xsde_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int) -> None:
+    if status != XSDE_OK:
+        raise XsdeError(status, load().xsde_last_error().decode())
+
+
+def _arr(ctype, vals):
+    vals = list(vals)
+    return (ctype * max(1, len(vals)))(*vals) if vals else None
+
+
+# --------------------------------------------------------------------------- #
+# C calls, same names                                                         #
+# --------------------------------------------------------------------------- #
+
+def xsde_grid_create(npts, xmin, xmax) -> ctypes.c_void_p:
+    out = ctypes.c_void_p()
+    nd = len(npts)
+    _check(load().xsde_grid_create(nd, _arr(ctypes.c_int32, npts), _arr(ctypes.c_double, xmin),
+                                   _arr(ctypes.c_double, xmax), ctypes.byref(out)))
+    return out
+
+
+def xsde_grid_destroy(grid) -> None:
+    load().xsde_grid_destroy(grid)
+
+
+def xsde_grid_points(grid) -> int:
+    return int(load().xsde_grid_points(grid))
+
+
+def xsde_vector_wrap(grid, dtype: int, ncomp: int, npaths: int, dev_ptr: int) -> ctypes.c_void_p:
+    out = ctypes.c_void_p()
+    _check(load().xsde_vector_wrap(grid, dtype, ncomp, npaths, ctypes.c_void_p(dev_ptr), ctypes.byref(out)))
+    return out
+
+
+def xsde_vector_alloc(grid, dtype: int, ncomp: int, npaths: int) -> ctypes.c_void_p:
+    out = ctypes.c_void_p()
+    _check(load().xsde_vector_alloc(grid, dtype, ncomp, npaths, ctypes.byref(out)))
+    return out
+
+
+def xsde_vector_data(vec) -> int:
+    return int(load().xsde_vector_data(vec) or 0)
+
+
+def xsde_vector_free(vec) -> None:
+    load().xsde_vector_free(vec)
+
+
+def xsde_noise_alloc(grid, kind: int, seed: int) -> ctypes.c_void_p:
+    out = ctypes.c_void_p()
+    _check(load().xsde_noise_alloc(grid, kind, ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), ctypes.byref(out)))
+    return out
+
+
+def xsde_noise_free(noise) -> None:
+    load().xsde_noise_free(noise)
+
+
+def xsde_noise_philox(counters_ptr: int, seed: int, n: int, out_ptr: int, stream: int = 0) -> None:
+    _check(load().xsde_noise_philox(ctypes.c_void_p(counters_ptr), ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), n,
+                                    ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream or None)))
+
+
+def xsde_noise_normals(noise, dtype: int, npts: int, npaths: int, path_offset: int, step: int, out_ptr: int,
+                       stream: int = 0) -> None:
+    _check(load().xsde_noise_normals(noise, dtype, npts, npaths, path_offset, step, ctypes.c_void_p(out_ptr),
+                                     ctypes.c_void_p(stream or None)))
+
+
+def xsde_problem_create(grid, dtype: int) -> ctypes.c_void_p:
+    out = ctypes.c_void_p()
+    _check(load().xsde_problem_create(grid, dtype, ctypes.byref(out)))
+    return out
+
+
+def xsde_problem_destroy(prob) -> None:
+    load().xsde_problem_destroy(prob)
+
+
+def xsde_set_operators(prob, L: xsde_linear_op, N: xsde_nonlinear_op) -> None:
+    _check(load().xsde_set_operators(prob, ctypes.byref(L), ctypes.byref(N)))
+
+
+def xsde_moments(prob, spec: xsde_sampling | None, per_path_ptr: int = 0, per_point_ptr: int = 0) -> None:
+    _check(load().xsde_moments(prob, ctypes.byref(spec) if spec is not None else None,
+                               ctypes.c_void_p(per_path_ptr or None), ctypes.c_void_p(per_point_ptr or None)))
+
+
+def xsde_integrate(prob, vec, dt: float, nsteps: int, npaths: int, path_offset: int = 0, step_offset: int = 0,
+                   stream: int = 0) -> None:
+    _check(load().xsde_integrate(prob, vec, dt, nsteps, npaths, path_offset, step_offset,
+                                 ctypes.c_void_p(stream or None)))
+
+
+def xsde_synchronize(prob, stream: int = 0) -> None:
+    _check(load().xsde_synchronize(prob, ctypes.c_void_p(stream or None)))
+
+
+def xsde_profile(prob, enable: bool) -> None:
+    _check(load().xsde_profile(prob, 1 if enable else 0))
+
+
+def xsde_profile_report(prob) -> dict:
+    """{kernel name: (total ms, launches)} since xsde_profile(prob, True)."""
+    ms = (ctypes.c_double * XSDE_KERNEL_KINDS)()
+    n = (ctypes.c_int64 * XSDE_KERNEL_KINDS)()
+    _check(load().xsde_profile_report(prob, ms, n))
+    return {xsde_kernel_name(k): (ms[k], n[k]) for k in range(XSDE_KERNEL_KINDS)}
+
+
+def xsde_kernel_name(kind: int) -> str:
+    return load().xsde_kernel_name(kind).decode()
+
+
+def xsde_last_error() -> str:
+    return load().xsde_last_error().decode()
+
+
+def xsde_version() -> str:
+    return load().xsde_version().decode()
+
+
+# --------------------------------------------------------------------------- #
+# Convenience wrapper over the handles (torch tensors in, no arithmetic)      #
+# --------------------------------------------------------------------------- #
+
+def _stream_handle(stream) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Problem:
+    """A lattice + precision + operators (one xsde_problem handle)."""
+
+    def __init__(self, npts, xmin, xmax, dtype: str = "c64"):
+        self.shape = tuple(int(n) for n in npts)
+        self.dtype_code = XSDE_C64 if dtype == "c64" else XSDE_C128
+        self.grid = xsde_grid_create(self.shape, xmin, xmax)
+        self.prob = xsde_problem_create(self.grid, self.dtype_code)
+        self.noise = None
+        self._keep = []
+
+    def set_operators(self, c0=0j, c2=-0.5j, g=0.0, pot_kind=XSDE_POT_NONE, omega=(0.0, 0.0, 0.0), V=None,
+                      noise_kind=XSDE_NOISE_NONE, seed=0, coupling=XSDE_COUPLE_ADDITIVE, amplitude=0.0):
+        L = xsde_linear_op(complex(c0).real, complex(c0).imag, complex(c2).real, complex(c2).imag)
+        om = list(omega) + [0.0] * (3 - len(omega))
+        N = xsde_nonlinear_op()
+        N.pot_kind = pot_kind
+        for d in range(3):
+            N.omega[d] = om[d]
+        if V is not None:
+            N.V = V.data_ptr()
+            N.V_nt = V.shape[0] if V.dim() == 2 else 1
+            self._keep = [V]
+        if self.noise is not None:
+            xsde_noise_free(self.noise)
+            self.noise = None
+        if noise_kind != XSDE_NOISE_NONE:
+            self.noise = xsde_noise_alloc(self.grid, noise_kind, seed)
+            N.noise = self.noise
+        N.g = g
+        N.coupling = coupling
+        N.amplitude = amplitude
+        xsde_set_operators(self.prob, L, N)
+
+    def moments(self, every: int, which: int, per_path=None, per_point=None):
+        spec = xsde_sampling(every, which)
+        self._keep_moments = (per_path, per_point)
+        xsde_moments(self.prob, spec, per_path.data_ptr() if per_path is not None else 0,
+                     per_point.data_ptr() if per_point is not None else 0)
+
+    def integrate(self, psi, dt: float, nsteps: int, path_offset: int = 0, step_offset: int = 0, stream=None):
+        """psi: CUDA complex tensor [npaths, *shape], advanced in place."""
+        if not psi.is_cuda or not psi.is_contiguous():
+            raise ValueError("psi must be a contiguous CUDA tensor")
+        npaths = psi.shape[0]
+        vec = xsde_vector_wrap(self.grid, self.dtype_code, 1, npaths, psi.data_ptr())
+        try:
+            xsde_integrate(self.prob, vec, dt, nsteps, npaths, path_offset, step_offset, _stream_handle(stream))
+        finally:
+            xsde_vector_free(vec)
+
+    def synchronize(self, stream=None):
+        xsde_synchronize(self.prob, _stream_handle(stream))
+
+    def close(self):
+        if self.prob:
+            xsde_problem_destroy(self.prob)
+            self.prob = None
+        if self.noise is not None:
+            xsde_noise_free(self.noise)
+            self.noise = None
+        if self.grid:
+            xsde_grid_destroy(self.grid)
+            self.grid = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

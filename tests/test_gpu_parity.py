@@ -1,0 +1,237 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle on the
+same seeded inputs, plus closed forms the paper's problems fix.
+
+Tolerances (spec bar): raw Philox words bit-exact; C128 runs within
+1e-10 relative L2 of the oracle after the full run; C64 runs within 1e-4
+relative L2 of the FP64 oracle; ensemble moments within 3 standard errors.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import oracle as O
+from gpu_util import gpu_run, make_problem, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c128": 1e-10, "c64": 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1204_4255_gb300 import build, xsde
+    build.build()
+    xsde.load()
+
+
+# --------------------------------------------------------------------------- #
+# Noise generator (Sec. 2.5)                                                  #
+# --------------------------------------------------------------------------- #
+
+def test_philox_words_bit_exact():
+    import torch
+    from paper_1204_4255_gb300 import xsde
+    rng = np.random.default_rng(5)
+    ctr = rng.integers(0, 2 ** 32, size=(100003, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:4] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [1, 2, 3, 4], [7, 0, 0, 0]]
+    seed = 0xDEADBEEF12345678
+    d_ctr = torch.from_numpy(ctr.view(np.int32)).cuda()
+    d_out = torch.empty_like(d_ctr)
+    xsde.xsde_noise_philox(d_ctr.data_ptr(), seed, ctr.shape[0], d_out.data_ptr())
+    torch.cuda.synchronize()
+    got = d_out.cpu().numpy().view(np.uint32)
+    ref = O.philox4x32_10(ctr, [seed & 0xFFFFFFFF, seed >> 32])
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_wiener_normals_match_oracle(dtype):
+    import torch
+    from paper_1204_4255_gb300 import xsde
+    npts, npaths, p0, step, seed = 1000, 37, 11, 123, 77
+    g = xsde.xsde_grid_create((1024,), (0.0,), (1.0,))
+    noise = xsde.xsde_noise_alloc(g, xsde.XSDE_NOISE_WIENER_COMPLEX, seed)
+    out = torch.empty((npaths, npts), dtype=torch.complex128 if dtype == "c128" else torch.complex64, device="cuda")
+    code = xsde.XSDE_C128 if dtype == "c128" else xsde.XSDE_C64
+    xsde.xsde_noise_normals(noise, code, npts, npaths, p0, step, out.data_ptr())
+    torch.cuda.synchronize()
+    z = out.cpu().numpy().astype(np.complex128)
+    ref = O.wiener_normals(seed, npts, npaths, p0, step)
+    ref = ref[..., 0] + 1j * ref[..., 1]
+    err = np.abs(z - ref)
+    if dtype == "c128":
+        assert err.max() < 1e-13
+    else:
+        assert np.max(err / np.maximum(1.0, np.abs(ref))) < 2e-5
+    xsde.xsde_noise_free(noise)
+    xsde.xsde_grid_destroy(g)
+
+
+# --------------------------------------------------------------------------- #
+# 1D whole-run kernel                                                         #
+# --------------------------------------------------------------------------- #
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_nls_soliton_full_run(dtype):
+    """1D NLS, 256 points, 1000 steps: oracle parity and the exact soliton."""
+    w = W.nls_soliton()
+    got, pp, _ = gpu_run(w, dtype, sample_every=500, which=3)
+    ref, opp, _ = O.run_workload(w, sample_every=500)
+    assert rel_l2(got, ref) < TOL[dtype]
+    exact = np.exp(0.5j * w.dt * w.nsteps) / np.cosh(w.coords(0))
+    assert rel_l2(got[0], exact) < (1e-8 if dtype == "c128" else 1e-4)
+    assert np.allclose(pp, opp, rtol=0, atol=1e-10 if dtype == "c128" else 1e-5)
+
+
+@pytest.mark.parametrize("n", [16, 32, 64, 128, 256, 512, 1024, 2048])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_1d_sizes_trap_and_nonlinearity(n, dtype):
+    """Every supported length, harmonic trap + repulsive g, a ragged path count."""
+    L = 12.0
+    x = -L + np.arange(n) * (2 * L / n)
+    rng = np.random.default_rng(n)
+    npaths = 5
+    psi0 = np.exp(-(x[None] - rng.uniform(-1, 1, (npaths, 1))) ** 2 / 2) * (1 + 0.1j * rng.standard_normal((npaths, n)))
+    w = W.Workload("trap", (n,), (-L,), (L,), 0j, -0.5j, 2.0, W.POT_HARMONIC, (1.3,), None, W.NOISE_NONE, 0.0, 0,
+                   1e-3, 25, psi0.astype(np.complex128))
+    got, _, _ = gpu_run(w, dtype)
+    ref, _, _ = O.run_workload(w)
+    assert np.max(rel_l2(got, ref, axis=1)) < (1e-11 if dtype == "c128" else 1e-4)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_1d_additive_noise_paths_and_moments(dtype):
+    """Truncated-Wigner-type ensemble: per-path parity with global path indices,
+    and the FP64 sampling group (norm, energy, per-point moments)."""
+    w = W.truncated_wigner(npaths=40, n=256, nsteps=30, sample_every=10, box=20.0, sigma=0.3)
+    p0, P = 3, 29
+    got, pp, pq = gpu_run(w, dtype, npaths=P, path0=p0, sample_every=10)
+    ref, opp, opq = O.run_workload(w, npaths=P, path0=p0, sample_every=10)
+    tol = 1e-10 if dtype == "c128" else 1e-4
+    assert np.max(rel_l2(got, ref, axis=1)) < tol
+    assert np.max(np.abs(pp - opp) / np.abs(opp)) < tol
+    assert np.max(np.abs(pq - opq) / np.abs(opq)) < tol
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_1d_time_dependent_potential_table(dtype):
+    w = W.adjoint_control(n=1024, nsteps=60)
+    got, _, _ = gpu_run(w, dtype)
+    ref, _, _ = O.run_workload(w)
+    assert rel_l2(got, ref) < (1e-10 if dtype == "c128" else 1e-4)
+
+
+def test_1d_resume_with_step_offset_is_exact():
+    """Two calls of 10 steps with step_offset reproduce one call of 20 (noise too)."""
+    w = W.truncated_wigner(npaths=6, n=128, nsteps=20, sample_every=0, box=10.0, sigma=0.5)
+    one, _, _ = gpu_run(w, "c128", nsteps=20)
+    half, _, _ = gpu_run(w, "c128", nsteps=10)
+    two, _, _ = gpu_run(w, "c128", nsteps=10, step_offset=10, psi0=half)
+    assert np.array_equal(one, two)
+
+
+# --------------------------------------------------------------------------- #
+# 2D row/column passes                                                        #
+# --------------------------------------------------------------------------- #
+
+@pytest.mark.parametrize("shape", [(64, 64), (32, 128), (128, 32), (16, 256), (256, 16)])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_2d_gpe_shapes(shape, dtype):
+    n0, n1 = shape
+    rng = np.random.default_rng(n0 * 7 + n1)
+    x0 = -8 + np.arange(n0) * 16 / n0
+    x1 = -8 + np.arange(n1) * 16 / n1
+    base = np.exp(-(x0[:, None] ** 2 + x1[None, :] ** 2) / 4)
+    psi0 = np.stack([base * np.exp(0.3j * rng.standard_normal(shape)) for _ in range(3)])
+    w = W.Workload("gpe2", shape, (-8.0, -8.0), (8.0, 8.0), 0j, -0.5j, 5.0, W.POT_HARMONIC, (1.0, 0.7), None,
+                   W.NOISE_NONE, 0.0, 0, 1e-3, 12, psi0.astype(np.complex128))
+    got, _, _ = gpu_run(w, dtype)
+    ref, _, _ = O.run_workload(w)
+    assert np.max(rel_l2(got.reshape(3, -1), ref.reshape(3, -1), axis=1)) < (1e-11 if dtype == "c128" else 1e-4)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_2d_moments_and_noise(dtype):
+    rng = np.random.default_rng(9)
+    shape = (32, 64)
+    psi0 = (1 + 0.2 * rng.standard_normal((4,) + shape) + 0.2j * rng.standard_normal((4,) + shape))
+    w = W.Workload("tw2", shape, (-4.0, -8.0), (4.0, 8.0), 0j, -0.5j, 0.3, W.POT_HARMONIC, (0.5, 0.5), None,
+                   W.NOISE_ADD_COMPLEX, 0.2, 1234, 2e-3, 15, psi0.astype(np.complex128), 5)
+    got, pp, pq = gpu_run(w, dtype, sample_every=5, path0=0)
+    ref, opp, opq = O.run_workload(w, sample_every=5)
+    tol = 1e-10 if dtype == "c128" else 1e-4
+    assert np.max(rel_l2(got.reshape(4, -1), ref.reshape(4, -1), axis=1)) < tol
+    assert np.max(np.abs(pp - opp) / np.abs(opp)) < tol
+    assert np.max(np.abs(pq - opq) / np.abs(opq)) < tol
+
+
+def test_2d_gpe_512_c128_first_steps():
+    """The 512^2 Thomas-Fermi GPE at full lattice size, 6 steps, against the oracle."""
+    w = W.gpe_2d(n=512, nsteps=6)
+    got, pp, _ = gpu_run(w, "c128", sample_every=3, which=3)
+    ref, opp, _ = O.run_workload(w, sample_every=3)
+    assert rel_l2(got, ref) < 1e-10
+    assert np.allclose(pp, opp, rtol=1e-11, atol=0)
+
+
+# --------------------------------------------------------------------------- #
+# 0D SDEs (Sec. 2.5) and their closed forms                                   #
+# --------------------------------------------------------------------------- #
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("which", ["ou", "kubo"])
+def test_0d_paths_match_oracle(which, dtype):
+    w = (W.ornstein_uhlenbeck if which == "ou" else W.kubo_oscillator)(npaths=1000, nsteps=200, sample_every=50)
+    got, pp, pq = gpu_run(w, dtype, sample_every=50)
+    ref, opp, opq = O.run_workload(w)
+    tol = 1e-12 if dtype == "c128" else 2e-5
+    assert np.max(np.abs(got - ref)) < tol
+    assert np.max(np.abs(pp - opp)) < 10 * tol
+    assert np.max(np.abs(pq - opq)) < 10 * tol
+
+
+def test_ou_65536_paths_closed_form():
+    w = W.ornstein_uhlenbeck()
+    got, _, pq = gpu_run(w, "c128", sample_every=100, which=4)
+    x = got.real
+    th, s, dt, n, P = 1.0, 0.5, w.dt, w.nsteps, w.npaths
+    c = (math.exp(-th * dt) + 4 * math.exp(-th * dt / 2) + 1) / 6
+    var = s * s * dt * c * c * (1 - math.exp(-2 * th * dt * n)) / (1 - math.exp(-2 * th * dt))
+    assert abs(x.mean() - math.exp(-th * dt * n)) < 3 * math.sqrt(var / P)
+    assert abs(x.var() - var) < 3 * var * math.sqrt(2 / P)
+    assert abs(var - 0.125 * (1 - math.exp(-10))) < 1e-4          # continuous limit
+    assert abs(pq[-1, 0, 0] - np.mean(x ** 2)) < 1e-12
+
+
+def test_kubo_65536_paths_stratonovich_mean():
+    w = W.kubo_oscillator()
+    got, _, _ = gpu_run(w, "c128")
+    om, be, dt, n, P = 1.0, 0.5, w.dt, w.nsteps, w.npaths
+    m = (np.exp(1j * om * dt) * (1 - be ** 2 * dt / 2 + be ** 4 * dt ** 2 / 8)) ** n
+    se = math.sqrt(np.var(got.real) / P) + math.sqrt(np.var(got.imag) / P)
+    assert abs(got.mean() - m) < 3 * se
+    assert abs(got.mean() - np.exp(1j * om * dt * n)) > 10 * se        # the Ito mean is excluded
+
+
+# --------------------------------------------------------------------------- #
+# Host-side rejection on a GPU machine                                            #
+# --------------------------------------------------------------------------- #
+
+def test_integrate_rejects_bad_arguments():
+    import torch
+    from paper_1204_4255_gb300 import xsde
+    w = W.nls_soliton(n=64, nsteps=2)
+    P = make_problem(w, "c64")
+    psi = torch.zeros((1, 64), dtype=torch.complex128, device="cuda")
+    with pytest.raises(xsde.XsdeError):
+        P.integrate(psi, w.dt, 2)                    # dtype differs from the problem's
+    psi = torch.zeros((1, 64), dtype=torch.complex64, device="cuda")
+    with pytest.raises(xsde.XsdeError):
+        P.integrate(psi, -1.0, 2)
+    with pytest.raises(xsde.XsdeError):
+        P.integrate(psi, w.dt, -3)
+    P.integrate(psi, w.dt, 0)
+    P.synchronize()
+    P.close()
