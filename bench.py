@@ -34,7 +34,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_GRID = 512
-STEPS_PER_CALL = 100
 METRIC = "RK4IP grid-point-steps/s"
 UNIT = "pt-steps/s"
 BYTES_PER_PT_PASS = {"c64": 32, "c128": 64}   # 2 fields in + 2 out per pass
@@ -184,7 +183,8 @@ def run_gpu(args) -> None:
 
     prob = xsde.Problem(w.n, w.xmin, w.xmax, dtype)
     prob.set_operators(c0=w.c0, c2=w.c2, g=w.gnl, pot_kind=w.pot_kind, omega=(1.0, 1.0, 0.0))
-    nsamp = STEPS_PER_CALL // STEPS_PER_CALL + 1
+    STEPS_PER_CALL = args.steps_per_call
+    nsamp = 2
     per_path = torch.zeros((nsamp, P, 2), dtype=torch.float64, device="cuda")
     prob.moments(STEPS_PER_CALL, xsde.XSDE_MOM_NORM | xsde.XSDE_MOM_ENERGY, per_path, None)
     host_psi = torch.from_numpy(w.psi0).to(tdt).pin_memory()
@@ -249,7 +249,7 @@ def run_gpu(args) -> None:
 
     # ---- end to end through the public API with host buffers ----------------
     e2e = None
-    if rank == 0 or world > 1:
+    if not args.no_e2e:
         host_out = torch.empty_like(host_psi).pin_memory()
         host_mom = torch.empty_like(per_path, device="cpu").pin_memory()
         k_e2e = max(2, min(args.steps, 5))
@@ -295,7 +295,10 @@ def main():
     ap.add_argument("--impl", default="xsde", choices=["xsde", "reference"])
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--paths", type=int, default=64)
+    ap.add_argument("--steps-per-call", type=int, default=100,
+                    help="RK4IP steps per xsde_integrate call (one bench step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -226,8 +226,8 @@ void fill_terms(const xsde_problem *p, double dt, int64_t npaths, int64_t path_o
     lt.pot = p->N.pot_kind;
     for (int d = 0; d < 3; ++d) {
         lt.hw2[d] = (R)(d < g.ndim ? 0.5 * p->N.omega[d] * p->N.omega[d] : 0.0);
-        lt.xmin[d] = d < g.ndim ? g.xmin[d] : 0.0;
-        lt.dx[d] = d < g.ndim ? grid_dx(g, d) : 0.0;
+        lt.xmin[d] = (R)(d < g.ndim ? g.xmin[d] : 0.0);
+        lt.dx[d] = (R)(d < g.ndim ? grid_dx(g, d) : 0.0);
     }
     lt.V = static_cast<const R *>(p->N.V);
     lt.V_nt = p->N.V_nt;

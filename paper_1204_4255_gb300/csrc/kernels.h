@@ -24,7 +24,7 @@ template <typename R> struct LocalTerm {
     R gdt;                // g_nl * dt
     int pot;              // PotMode
     R hw2[3];             // omega_d^2 / 2
-    double xmin[3], dx[3];
+    R xmin[3], dx[3];     // lattice origin and spacing (working precision)
     const R *V;           // [V_nt][npts] raw potential (PM_TABLE)
     int64_t V_nt;
     int64_t npts;
@@ -156,7 +156,7 @@ __device__ __forceinline__ R potential(const LocalTerm<R> &lt, int ndim, const i
     if (lt.pot == PM_HARMONIC) {
         R v = R(0);
         for (int d = 0; d < ndim; ++d) {
-            R x = R(lt.xmin[d] + idx[d] * lt.dx[d]);
+            const R x = lt.xmin[d] + R(idx[d]) * lt.dx[d];
             v += lt.hw2[d] * x * x;
         }
         return v;

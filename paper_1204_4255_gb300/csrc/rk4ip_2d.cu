@@ -91,9 +91,16 @@ __global__ void __launch_bounds__(RowCfg<N1>::THREADS) row_pass_kernel(const Par
         const int idx[3] = {i0, i1, 0};
         return potential(p.lt, 2, idx, (int64_t)i0 * N1 + i1, gs);
     };
+    // static potentials are evaluated once per element; tables with one row per
+    // step are read for the step at hand
+    const bool vtime = p.lt.pot == PM_TABLE && p.lt.V_nt > 1;
+    R Vst[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) Vst[m] = vtime ? R(0) : pot(m, 0);
+    auto potv = [&](int m, uint64_t gs) -> R { return vtime ? pot(m, gs) : Vst[m]; };
     auto pterm = [&](int m, uint64_t gs) -> PointTerm<R> {
         const int i1 = t + m * T;
-        return point_term(p.lt, pot(m, gs), (uint32_t)(i0 * N1 + i1), gp, (uint32_t)gs);
+        return point_term(p.lt, potv(m, gs), (uint32_t)(i0 * N1 + i1), gp, (uint32_t)gs);
     };
     // local part of the sampling group for the real-space field f at global step gs
     auto sample_local = [&](const V (&f)[E], uint64_t gs) {
@@ -102,7 +109,7 @@ __global__ void __launch_bounds__(RowCfg<N1>::THREADS) row_pass_kernel(const Par
         for (int m = 0; m < E; ++m) {
             const double m2 = (double)cabs2(f[m]);
             acc[0] += m2;
-            acc[1] += (double)pot(m, gs) * m2 + 0.5 * p.sm.g * m2 * m2;
+            acc[1] += (double)potv(m, gs) * m2 + 0.5 * p.sm.g * m2 * m2;
             if (active && (p.sm.which & (MOM_MOD2 | MOM_MOD4)) && p.sm.per_point) {
                 double *pp = p.sm.per_point + 2 * ((int64_t)p.sample_slot * p.lt.npts + (int64_t)i0 * N1 + t + m * T);
                 atomicAdd(pp, m2 * p.sm.inv_paths);

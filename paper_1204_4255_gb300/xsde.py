@@ -277,10 +277,16 @@ class Problem:
 
     def integrate(self, psi, dt: float, nsteps: int, path_offset: int = 0, step_offset: int = 0, stream=None):
         """psi: CUDA complex tensor [npaths, *shape], advanced in place."""
+        import torch
         if not psi.is_cuda or not psi.is_contiguous():
             raise ValueError("psi must be a contiguous CUDA tensor")
+        if tuple(psi.shape[1:]) != self.shape:
+            raise ValueError(f"psi has shape {tuple(psi.shape)}, expected [npaths, *{self.shape}]")
+        codes = {torch.complex64: XSDE_C64, torch.complex128: XSDE_C128}
+        if psi.dtype not in codes:
+            raise ValueError(f"psi must be complex64 or complex128, not {psi.dtype}")
         npaths = psi.shape[0]
-        vec = xsde_vector_wrap(self.grid, self.dtype_code, 1, npaths, psi.data_ptr())
+        vec = xsde_vector_wrap(self.grid, codes[psi.dtype], 1, npaths, psi.data_ptr())
         try:
             xsde_integrate(self.prob, vec, dt, nsteps, npaths, path_offset, step_offset, _stream_handle(stream))
         finally:
