@@ -2,10 +2,15 @@
 // Fourier-space tables, and the pass schedule of one xsde_integrate call.
 //
 // Tables (XMDS2 Sec. 2.6: only exp(+-L dt) factors are needed for fixed steps)
-// are evaluated in FP64 on the host and rounded once to the working precision;
-// for FP32 each complex entry takes, among the neighbouring floats of its real
-// and imaginary parts, the pair whose modulus is closest to the exact one, so
-// that repeated application does not drift the norm.
+// are evaluated in FP64 on the host and rounded once to the working precision.
+// FP32 rounding is chosen for what a long run accumulates:
+//  - FFT twiddles: a butterfly with a unit-modulus twiddle is exactly unitary
+//    and the inverse uses the conjugate, so phase errors cancel but modulus
+//    errors bias the norm every stage; each twiddle takes, within +-4 ulp of
+//    its components, the pair whose modulus is closest to 1.
+//  - exp(L dt/2): applied to the same mode every step, so both phase and
+//    modulus errors grow linearly with the step count; it is stored as FP32
+//    hi + lo (lo = rounded remainder) and applied with compensated FMAs.
 #include <cfloat>
 #include <cmath>
 #include <complex>
@@ -149,17 +154,22 @@ double kval(const xsde_grid &g, int d, int i) {
     return 2.0 * M_PI / (g.xmax[d] - g.xmin[d]) * (i < n / 2 ? i : i - n);
 }
 
-// complex double -> working precision, rounded once (see file comment)
-void round_to(const std::complex<double> &z, float2 *out) {
-    const double r = std::abs(z);
+float step_float(float v, int k) {
+    for (; k > 0; --k) v = std::nextafterf(v, FLT_MAX);
+    for (; k < 0; ++k) v = std::nextafterf(v, -FLT_MAX);
+    return v;
+}
+
+// unit-modulus value (a twiddle) -> FP32 pair with the modulus closest to 1
+// within +-4 ulp per component (see file comment)
+void round_unit(const std::complex<double> &z, float2 *out) {
     const float re = (float)z.real(), im = (float)z.imag();
     float best_re = re, best_im = im;
-    double best = std::fabs(std::hypot((double)re, (double)im) - r);
-    for (int a = -1; a <= 1; ++a) {
-        for (int b = -1; b <= 1; ++b) {
-            float cr = a == 0 ? re : std::nextafterf(re, a < 0 ? -FLT_MAX : FLT_MAX);
-            float ci = b == 0 ? im : std::nextafterf(im, b < 0 ? -FLT_MAX : FLT_MAX);
-            double err = std::fabs(std::hypot((double)cr, (double)ci) - r);
+    double best = std::fabs(std::hypot((double)re, (double)im) - 1.0);
+    for (int a = -4; a <= 4; ++a) {
+        for (int b = -4; b <= 4; ++b) {
+            const float cr = step_float(re, a), ci = step_float(im, b);
+            const double err = std::fabs(std::hypot((double)cr, (double)ci) - 1.0);
             if (err < best) {
                 best = err;
                 best_re = cr;
@@ -169,11 +179,20 @@ void round_to(const std::complex<double> &z, float2 *out) {
     }
     *out = make_float2(best_re, best_im);
 }
-void round_to(const std::complex<double> &z, double2 *out) { *out = make_double2(z.real(), z.imag()); }
+void round_unit(const std::complex<double> &z, double2 *out) { *out = make_double2(z.real(), z.imag()); }
 
-template <typename V> int upload(const std::vector<std::complex<double>> &h, void **dptr, cudaStream_t s) {
-    std::vector<V> tmp(h.size());
-    for (size_t i = 0; i < h.size(); ++i) round_to(h[i], &tmp[i]);
+// value -> hi (nearest) and lo (nearest to the remainder); FP64 keeps lo = 0
+void split_hi_lo(const std::complex<double> &z, float2 *hi, float2 *lo) {
+    const float hr = (float)z.real(), hm = (float)z.imag();
+    *hi = make_float2(hr, hm);
+    *lo = make_float2((float)(z.real() - (double)hr), (float)(z.imag() - (double)hm));
+}
+void split_hi_lo(const std::complex<double> &z, double2 *hi, double2 *lo) {
+    *hi = make_double2(z.real(), z.imag());
+    *lo = make_double2(0.0, 0.0);
+}
+
+template <typename V> int upload_raw(const std::vector<V> &tmp, void **dptr, cudaStream_t s) {
     if (!*dptr) XSDE_CUDA(cudaMalloc(dptr, tmp.size() * sizeof(V)), "cudaMalloc(table)");
     XSDE_CUDA(cudaMemcpyAsync(*dptr, tmp.data(), tmp.size() * sizeof(V), cudaMemcpyHostToDevice, s),
               "cudaMemcpyAsync(table)");
@@ -181,17 +200,29 @@ template <typename V> int upload(const std::vector<std::complex<double>> &h, voi
     return XSDE_OK;
 }
 
-// twiddles exp(-2 pi i m/n) and the exp(L dt/2) factors for this dt
+// twiddle table exp(-2 pi i m/n), m < n
+template <typename V> int upload_twiddles(int n, void **dptr, cudaStream_t s) {
+    std::vector<V> tmp(n);
+    for (int m = 0; m < n; ++m) round_unit(std::polar(1.0, -2.0 * M_PI * m / n), &tmp[m]);
+    return upload_raw(tmp, dptr, s);
+}
+
+// factor table as [hi[0..n), lo[0..n)]
+template <typename V> int upload(const std::vector<std::complex<double>> &h, void **dptr, cudaStream_t s) {
+    const size_t n = h.size();
+    std::vector<V> tmp(2 * n);
+    for (size_t i = 0; i < n; ++i) split_hi_lo(h[i], &tmp[i], &tmp[n + i]);
+    return upload_raw(tmp, dptr, s);
+}
+
+// twiddles and the exp(L dt/2) factors for this dt
 template <typename V> int ensure_tables(xsde_problem *p, double dt, cudaStream_t s) {
     if (p->table_dt == dt) return XSDE_OK;
     const xsde_grid &g = p->grid;
     const std::complex<double> c0(p->L.c0_re, p->L.c0_im), c2(p->L.c2_re, p->L.c2_im);
     int rc;
-    for (int d = 0; d < g.ndim; ++d) {
-        std::vector<std::complex<double>> tw(g.n[d]);
-        for (int m = 0; m < g.n[d]; ++m) tw[m] = std::polar(1.0, -2.0 * M_PI * m / g.n[d]);
-        if ((rc = upload<V>(tw, &p->d_tw[d], s)) != XSDE_OK) return rc;
-    }
+    for (int d = 0; d < g.ndim; ++d)
+        if ((rc = upload_twiddles<V>(g.n[d], &p->d_tw[d], s)) != XSDE_OK) return rc;
     if (g.ndim == 1) {
         std::vector<std::complex<double>> e(g.n[0]);
         for (int i = 0; i < g.n[0]; ++i) {

@@ -23,6 +23,17 @@ template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
 template <typename V> __device__ __forceinline__ V cmulconj(V a, V b) {
     return mk<V>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
+// x * (hi + lo): a factor stored as an FP32 pair whose sum carries ~46 bits; the
+// lo product is folded in with FMAs (FP64 tables have lo = 0 and skip it)
+template <typename V> __device__ __forceinline__ V cmul_hilo(V x, V hi, V lo) {
+    V r = cmul(x, hi);
+    if constexpr (sizeof(x.x) == 4) {
+        r.x = fmaf(x.x, lo.x, fmaf(-x.y, lo.y, r.x));
+        r.y = fmaf(x.x, lo.y, fmaf(x.y, lo.x, r.y));
+    }
+    return r;
+}
+
 // a + s*b
 template <typename V> __device__ __forceinline__ V caxpy(V a, decltype(V::x) s, V b) {
     return mk<V>(a.x + s * b.x, a.y + s * b.y);

@@ -57,7 +57,7 @@ template <typename R> struct Params1D {
     int64_t npaths;
     int64_t nsteps;
     uint64_t step0;        // global index of local step 0
-    const cx<R> *Etab;     // exp(L(k) dt/2)/N in FFT order [N]
+    const cx<R> *Etab;     // exp(L(k) dt/2)/N in FFT order, hi [N] then lo [N]
     const cx<R> *tw;       // exp(-2 pi i m/N) [N]
     LocalTerm<R> lt;
     Sampling sm;
@@ -77,7 +77,7 @@ enum RowMode {
     ROW_FFT_ONLY = 4    // A (real) -> B = F1 A (for the spectral part of the energy)
 };
 enum ColMode {
-    COL_PROPAGATE = 0,  // A, B -> F0^-1 exp(L dt/2)/N F0 (A, B)
+    COL_PROPAGATE = 0,  // A, B -> F0^-1 E0 F0 (A, B)
     COL_SPECTRAL = 1    // B: accumulate the kinetic energy only (no write)
 };
 
@@ -87,7 +87,10 @@ template <typename R> struct Params2D {
     int64_t npaths;
     int n0, n1;
     const cx<R> *tw0, *tw1;   // twiddles per dimension
-    const cx<R> *E0, *E1;     // separable exp(L dt/2) factors; E0 carries exp(c0 dt/2)/(n0 n1)
+    // separable exp(L dt/2) = E0(k0) E1(k1), each hi [n] then lo [n]; E0 carries
+    // exp(c0 dt/2)/(n0 n1) and is applied by the column pass, E1 by the row
+    // passes whose output feeds a column pass
+    const cx<R> *E0, *E1;
     LocalTerm<R> lt;
     Sampling sm;
     int sample_slot;       // sample written by this pass (-1: none)

@@ -81,13 +81,14 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
     const bool vtime = p.lt.pot == PM_TABLE && p.lt.V_nt > 1;
 
     V x[2][E];
-    V Ek[E];
+    V Ek[E], El[E];
     R Vs[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int j = t + m * T;
         x[0][m] = active ? psi[j] : mk<V>(R(0), R(0));
         Ek[m] = p.Etab[j];
+        El[m] = p.Etab[N + j];
         const int idx[3] = {j, 0, 0};
         Vs[m] = vtime ? R(0) : potential(p.lt, 1, idx, j, 0);
     }
@@ -152,8 +153,8 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
         fft<N, E, -1, 2>(x, t, sm2, L, sync, tw);
 #pragma unroll
         for (int m = 0; m < E; ++m) {
-            x[0][m] = cmul(x[0][m], Ek[m]);
-            x[1][m] = cmul(x[1][m], Ek[m]);
+            x[0][m] = cmul_hilo(x[0][m], Ek[m], El[m]);
+            x[1][m] = cmul_hilo(x[1][m], Ek[m], El[m]);
         }
         fft<N, E, +1, 2>(x, t, sm2, L, sync, tw);
         // k2, k3 in real space; x[0] <- a_I + k3, x[1] <- a_I + k1/6 + k2/3 + k3/3
@@ -168,8 +169,8 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
         fft<N, E, -1, 2>(x, t, sm2, L, sync, tw);
 #pragma unroll
         for (int m = 0; m < E; ++m) {
-            x[0][m] = cmul(x[0][m], Ek[m]);
-            x[1][m] = cmul(x[1][m], Ek[m]);
+            x[0][m] = cmul_hilo(x[0][m], Ek[m], El[m]);
+            x[1][m] = cmul_hilo(x[1][m], Ek[m], El[m]);
         }
         fft<N, E, +1, 2>(x, t, sm2, L, sync, tw);
         // k4 = N(D(a_I + k3)); a <- D(acc) + k4/6

@@ -179,11 +179,13 @@ __global__ void __launch_bounds__(RowCfg<N1>::THREADS) row_pass_kernel(const Par
         }
     }
     fft<N1, E, -1, 2>(x, t, sm2, L, sync, tw);
+    // the dimension-1 factor of exp(L dt/2); the column pass applies the rest
     if (active) {
 #pragma unroll
         for (int m = 0; m < E; ++m) {
-            Arow[t + m * T] = x[0][m];
-            Brow[t + m * T] = x[1][m];
+            const V eh = __ldg(p.E1 + t + m * T), el = __ldg(p.E1 + N1 + t + m * T);
+            Arow[t + m * T] = cmul_hilo(x[0][m], eh, el);
+            Brow[t + m * T] = cmul_hilo(x[1][m], eh, el);
         }
     }
 }
@@ -229,6 +231,9 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
         // sum_k Re(i L(k)) |F psi|^2 dV / (n0 n1), accumulated into the energy of this path
         const int k1i = col < n1 / 2 ? col : col - n1;
         const double k1 = p.sm.kscale[1] * k1i;
+        // fields written by propagating row passes already carry the
+        // dimension-1 factor of exp(L dt/2); divide its modulus back out
+        const double w = (MODE == COL_SPECTRAL) ? 1.0 : 1.0 / (double)cabs2(p.E1[col]);
         double s = 0.0;
 #pragma unroll
         for (int m = 0; m < E; ++m) {
@@ -236,6 +241,7 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
             const double k0 = p.sm.kscale[0] * (kj < N0 / 2 ? kj : kj - N0);
             s += (p.sm.h0 + p.sm.h2 * (k0 * k0 + k1 * k1)) * (double)cabs2(f[m]);
         }
+        s *= w;
         s = warp_sum(s);
         __syncthreads();
         if ((threadIdx.x & 31) == 0) scratch[threadIdx.x >> 5] = s;
@@ -265,12 +271,11 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
         }
         fft<N0, E, -1, 2>(x, t, sm2, L, sync, tw);
         if (sample) kinetic(x[0]);
-        const V e1 = p.E1[col];
 #pragma unroll
         for (int m = 0; m < E; ++m) {
-            const V e = cmul(__ldg(p.E0 + t + m * T), e1);
-            x[0][m] = cmul(x[0][m], e);
-            x[1][m] = cmul(x[1][m], e);
+            const V eh = __ldg(p.E0 + t + m * T), el = __ldg(p.E0 + N0 + t + m * T);
+            x[0][m] = cmul_hilo(x[0][m], eh, el);
+            x[1][m] = cmul_hilo(x[1][m], eh, el);
         }
         fft<N0, E, +1, 2>(x, t, sm2, L, sync, tw);
 #pragma unroll
