@@ -4,13 +4,12 @@
 // Tables (XMDS2 Sec. 2.6: only exp(+-L dt) factors are needed for fixed steps)
 // are evaluated in FP64 on the host and rounded once to the working precision.
 // FP32 rounding is chosen for what a long run accumulates:
-//  - FFT twiddles: a butterfly with a unit-modulus twiddle is exactly unitary
-//    and the inverse uses the conjugate, so phase errors cancel but modulus
-//    errors bias the norm every stage; each twiddle takes, within +-4 ulp of
-//    its components, the pair whose modulus is closest to 1.
+//  - FFT twiddles: FP32 twiddles sit on average ~1e-8 below unit modulus at
+//    the angles the early stages use, which drains the norm every transform;
 //  - exp(L dt/2): applied to the same mode every step, so both phase and
-//    modulus errors grow linearly with the step count; it is stored as FP32
-//    hi + lo (lo = rounded remainder) and applied with compensated FMAs.
+//    modulus errors grow linearly with the step count.
+// Both are therefore stored as FP32 hi + lo (lo = rounded remainder of the
+// FP64 value) and applied with compensated FMAs (device_common.cuh).
 #include <cfloat>
 #include <cmath>
 #include <complex>
@@ -154,33 +153,6 @@ double kval(const xsde_grid &g, int d, int i) {
     return 2.0 * M_PI / (g.xmax[d] - g.xmin[d]) * (i < n / 2 ? i : i - n);
 }
 
-float step_float(float v, int k) {
-    for (; k > 0; --k) v = std::nextafterf(v, FLT_MAX);
-    for (; k < 0; ++k) v = std::nextafterf(v, -FLT_MAX);
-    return v;
-}
-
-// unit-modulus value (a twiddle) -> FP32 pair with the modulus closest to 1
-// within +-4 ulp per component (see file comment)
-void round_unit(const std::complex<double> &z, float2 *out) {
-    const float re = (float)z.real(), im = (float)z.imag();
-    float best_re = re, best_im = im;
-    double best = std::fabs(std::hypot((double)re, (double)im) - 1.0);
-    for (int a = -4; a <= 4; ++a) {
-        for (int b = -4; b <= 4; ++b) {
-            const float cr = step_float(re, a), ci = step_float(im, b);
-            const double err = std::fabs(std::hypot((double)cr, (double)ci) - 1.0);
-            if (err < best) {
-                best = err;
-                best_re = cr;
-                best_im = ci;
-            }
-        }
-    }
-    *out = make_float2(best_re, best_im);
-}
-void round_unit(const std::complex<double> &z, double2 *out) { *out = make_double2(z.real(), z.imag()); }
-
 // value -> hi (nearest) and lo (nearest to the remainder); FP64 keeps lo = 0
 void split_hi_lo(const std::complex<double> &z, float2 *hi, float2 *lo) {
     const float hr = (float)z.real(), hm = (float)z.imag();
@@ -200,10 +172,17 @@ template <typename V> int upload_raw(const std::vector<V> &tmp, void **dptr, cud
     return XSDE_OK;
 }
 
-// twiddle table exp(-2 pi i m/n), m < n
-template <typename V> int upload_twiddles(int n, void **dptr, cudaStream_t s) {
-    std::vector<V> tmp(n);
-    for (int m = 0; m < n; ++m) round_unit(std::polar(1.0, -2.0 * M_PI * m / n), &tmp[m]);
+// twiddle table exp(-2 pi i m/n), m < n: FP64 (cos, sin); FP32 (hi, lo) split
+void make_twiddle(const std::complex<double> &z, double2 *out) { *out = make_double2(z.real(), z.imag()); }
+void make_twiddle(const std::complex<double> &z, float4 *out) {
+    float2 hi, lo;
+    split_hi_lo(z, &hi, &lo);
+    *out = make_float4(hi.x, hi.y, lo.x, lo.y);
+}
+
+template <typename R> int upload_twiddles(int n, void **dptr, cudaStream_t s) {
+    std::vector<tw_t<R>> tmp(n);
+    for (int m = 0; m < n; ++m) make_twiddle(std::polar(1.0, -2.0 * M_PI * m / n), &tmp[m]);
     return upload_raw(tmp, dptr, s);
 }
 
@@ -222,7 +201,7 @@ template <typename V> int ensure_tables(xsde_problem *p, double dt, cudaStream_t
     const std::complex<double> c0(p->L.c0_re, p->L.c0_im), c2(p->L.c2_re, p->L.c2_im);
     int rc;
     for (int d = 0; d < g.ndim; ++d)
-        if ((rc = upload_twiddles<V>(g.n[d], &p->d_tw[d], s)) != XSDE_OK) return rc;
+        if ((rc = upload_twiddles<decltype(V::x)>(g.n[d], &p->d_tw[d], s)) != XSDE_OK) return rc;
     if (g.ndim == 1) {
         std::vector<std::complex<double>> e(g.n[0]);
         for (int i = 0; i < g.n[0]; ++i) {
@@ -334,7 +313,7 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
         q.nsteps = nsteps;
         q.step0 = step0;
         q.Etab = static_cast<const V *>(p->d_E[0]);
-        q.tw = static_cast<const V *>(p->d_tw[0]);
+        q.tw = static_cast<const tw_t<R> *>(p->d_tw[0]);
         q.lt = lt;
         q.sm = sm;
         q.status = p->d_status;
@@ -359,8 +338,8 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
     q.npaths = npaths;
     q.n0 = g.n[0];
     q.n1 = g.n[1];
-    q.tw0 = static_cast<const V *>(p->d_tw[0]);
-    q.tw1 = static_cast<const V *>(p->d_tw[1]);
+    q.tw0 = static_cast<const tw_t<R> *>(p->d_tw[0]);
+    q.tw1 = static_cast<const tw_t<R> *>(p->d_tw[1]);
     q.E0 = static_cast<const V *>(p->d_E[0]);
     q.E1 = static_cast<const V *>(p->d_E[1]);
     q.lt = lt;

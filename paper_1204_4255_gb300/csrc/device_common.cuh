@@ -23,16 +23,23 @@ template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
 template <typename V> __device__ __forceinline__ V cmulconj(V a, V b) {
     return mk<V>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
-// x * (hi + lo): a factor stored as an FP32 pair whose sum carries ~46 bits; the
-// lo product is folded in with FMAs (FP64 tables have lo = 0 and skip it)
-template <typename V> __device__ __forceinline__ V cmul_hilo(V x, V hi, V lo) {
-    V r = cmul(x, hi);
-    if constexpr (sizeof(x.x) == 4) {
-        r.x = fmaf(x.x, lo.x, fmaf(-x.y, lo.y, r.x));
-        r.y = fmaf(x.x, lo.y, fmaf(x.y, lo.x, r.y));
-    }
-    return r;
+// x * (hi + lo) for a factor stored as an FP32 pair whose sum carries ~46 bits.
+// The small lo products are formed first and the hi products are added to them
+// by FMA, so each component is rounded once with the full factor; adding the lo
+// part to an already rounded product would be lost (it is below half an ulp).
+// FP64 tables have lo = 0 and use the plain product.
+__device__ __forceinline__ float2 cmul_hilo(float2 x, float2 hi, float2 lo) {
+    const float tx = fmaf(x.x, lo.x, -x.y * lo.y);
+    const float ty = fmaf(x.x, lo.y, x.y * lo.x);
+    return make_float2(fmaf(x.x, hi.x, fmaf(-x.y, hi.y, tx)), fmaf(x.x, hi.y, fmaf(x.y, hi.x, ty)));
 }
+// x * conj(hi + lo), same ordering
+__device__ __forceinline__ float2 cmulconj_hilo(float2 x, float2 hi, float2 lo) {
+    const float tx = fmaf(x.x, lo.x, x.y * lo.y);
+    const float ty = fmaf(x.y, lo.x, -x.x * lo.y);
+    return make_float2(fmaf(x.x, hi.x, fmaf(x.y, hi.y, tx)), fmaf(x.y, hi.x, fmaf(-x.x, hi.y, ty)));
+}
+__device__ __forceinline__ double2 cmul_hilo(double2 x, double2 hi, double2) { return cmul(x, hi); }
 
 // a + s*b
 template <typename V> __device__ __forceinline__ V caxpy(V a, decltype(V::x) s, V b) {

@@ -86,14 +86,37 @@ template <int R, int S, typename V> __device__ __forceinline__ void dft(V *u) {
 }
 
 // ---------------------------------------------------------------------------
+// Twiddles.  FP64: (cos, sin).  FP32: (cos_hi, sin_hi, cos_lo, sin_lo), the
+// FP64 value split into a rounded pair and its rounded remainder, applied by
+// cmul_hilo so every twiddle acts with ~46-bit accuracy.  (FP32 twiddles alone
+// sit ~1e-8 below unit modulus on average at the angles the early stages use;
+// a butterfly with a unit-modulus twiddle is unitary, one without it drains
+// ~1e-8 of the norm per transform, i.e. ~1e-4 over a 2000-step 2D run.)
+// ---------------------------------------------------------------------------
+template <typename R> struct tw_of;
+template <> struct tw_of<float> { using type = float4; };
+template <> struct tw_of<double> { using type = double2; };
+template <typename R> using tw_t = typename tw_of<R>::type;
+
+// u * w (S < 0) or u * conj(w) (S > 0)
+template <int S> __device__ __forceinline__ float2 twiddle_mul(float2 u, float4 w) {
+    const float2 hi = make_float2(w.x, w.y), lo = make_float2(w.z, w.w);
+    return (S < 0) ? cmul_hilo(u, hi, lo) : cmulconj_hilo(u, hi, lo);
+}
+template <int S> __device__ __forceinline__ double2 twiddle_mul(double2 u, double2 w) {
+    return (S < 0) ? cmul(u, w) : cmulconj(u, w);
+}
+
+// ---------------------------------------------------------------------------
 // one stage on NV vectors held by this thread
 // ---------------------------------------------------------------------------
 template <int N, int E, int R, int Ns, int S, int NV, typename V, typename Tw>
 __device__ __forceinline__ void fft_stage(V (&v)[NV][E], int t, const Tw &tw) {
     constexpr int B = E / R, T = N / E;
+    using TW = decltype(tw(0));
 #pragma unroll
     for (int q = 0; q < B; ++q) {
-        V w[R];
+        TW w[R];
         if constexpr (Ns > 1) {
             const int k = (t + q * T) & (Ns - 1);
 #pragma unroll
@@ -106,7 +129,7 @@ __device__ __forceinline__ void fft_stage(V (&v)[NV][E], int t, const Tw &tw) {
             for (int r = 0; r < R; ++r) u[r] = v[iv][q + r * B];
             if constexpr (Ns > 1) {
 #pragma unroll
-                for (int r = 1; r < R; ++r) u[r] = (S < 0) ? cmul(u[r], w[r]) : cmulconj(u[r], w[r]);
+                for (int r = 1; r < R; ++r) u[r] = twiddle_mul<S>(u[r], w[r]);
             }
             dft<R, S>(u);
 #pragma unroll

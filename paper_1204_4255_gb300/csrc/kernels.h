@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
+#include "fft.cuh"
 
 namespace xsde {
 
@@ -58,7 +59,7 @@ template <typename R> struct Params1D {
     int64_t nsteps;
     uint64_t step0;        // global index of local step 0
     const cx<R> *Etab;     // exp(L(k) dt/2)/N in FFT order, hi [N] then lo [N]
-    const cx<R> *tw;       // exp(-2 pi i m/N) [N]
+    const tw_t<R> *tw;     // exp(-2 pi i m/N) [N] (FP32: with radial correction)
     LocalTerm<R> lt;
     Sampling sm;
     int *status;
@@ -86,7 +87,7 @@ template <typename R> struct Params2D {
     cx<R> *B;              // scratch, same shape
     int64_t npaths;
     int n0, n1;
-    const cx<R> *tw0, *tw1;   // twiddles per dimension
+    const tw_t<R> *tw0, *tw1; // twiddles per dimension
     // separable exp(L dt/2) = E0(k0) E1(k1), each hi [n] then lo [n]; E0 carries
     // exp(c0 dt/2)/(n0 n1) and is applied by the column pass, E1 by the row
     // passes whose output feeds a column pass

@@ -60,15 +60,15 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
     constexpr int T = N / E;
     constexpr int BUF = padded_len<N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V *tws = reinterpret_cast<V *>(smem_raw);
+    tw_t<R> *tws = reinterpret_cast<tw_t<R> *>(smem_raw);
     const int slot = threadIdx.x / T;
     const int t = threadIdx.x - slot * T;
-    V *bufA = tws + N + slot * 2 * BUF;
+    V *bufA = reinterpret_cast<V *>(tws + N) + slot * 2 * BUF;
     V *bufB = bufA + BUF;
     V *const sm2[2] = {bufA, bufB};
     V *const sm1[1] = {bufA};
     const SlotSync<T, PPC> sync{slot};
-    const TwiddleTable<V> tw{tws};
+    const TwiddleTable<tw_t<R>> tw{tws};
     const PaddedLine L{};
 
     for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = p.tw[i];
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
 
 template <typename R, int N> cudaError_t launch_n(const Params1D<R> &p, cudaStream_t s) {
     constexpr int E = 8, T = N / E, PPC = T >= 128 ? 1 : 128 / T;
-    const size_t smem = (size_t)(N + PPC * 2 * padded_len<N>()) * sizeof(cx<R>);
+    const size_t smem = (size_t)N * sizeof(tw_t<R>) + (size_t)PPC * 2 * padded_len<N>() * sizeof(cx<R>);
     auto kern = rk4ip_1d_kernel<R, N, E, PPC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(RowCfg<N1>::THREADS) row_pass_kernel(const Par
     V *const sm1[1] = {smem + line * 2 * BUF};
     double *scratch = reinterpret_cast<double *>(smem + LINES * 2 * BUF);
     const SyncBlock sync{};
-    const TwiddleLdg<V> tw{p.tw1};
+    const TwiddleLdg<tw_t<R>> tw{p.tw1};
     const PaddedLine L{};
 
     const int64_t nrows = p.npaths * (int64_t)p.n0;
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
     const int c = threadIdx.x % C;
     const int t = threadIdx.x / C;
     const SyncBlock sync{};
-    const TwiddleLdg<V> tw{p.tw0};
+    const TwiddleLdg<tw_t<R>> tw{p.tw0};
     const ColumnTile<C> L{c};
 
     const int col = blockIdx.x * C + c;
