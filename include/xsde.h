@@ -202,6 +202,12 @@ int xsde_integrate(xsde_problem *prob, xsde_vector *psi, double dt, int64_t nste
  * wait gave up.  Clears the device error word. */
 int xsde_synchronize(xsde_problem *prob, void *stream);
 
+/* Kernel implementation for this problem: 0 (default) uses the fastest kernels
+ * available for the lattice and precision (e.g. the persistent TMA-pipelined
+ * complex64 2D passes); 1 forces the generic kernels.  Both compute the same
+ * scheme; the switch exists to cross-check and to compare them. */
+int xsde_set_kernel_variant(xsde_problem *prob, int variant);
+
 /* ---- launch profiling ------------------------------------------------------ */
 
 /* Kernel kinds reported by xsde_profile_report, in this order:

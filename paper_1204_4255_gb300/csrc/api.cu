@@ -18,7 +18,10 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
+
+#include <cudaTypedefs.h>
 
 #include "../../include/xsde.h"
 #include "kernels.h"
@@ -62,6 +65,8 @@ struct xsde_problem {
     void *d_scratch = nullptr;
     size_t scratch_bytes = 0;
     int *d_status = nullptr;
+    int num_sms = 1;
+    int kernel_variant = 0;   // 0: fastest available kernels, 1: generic kernels only
     // launch profiling: CUDA events around every kernel launch of this problem
     bool profiling = false;
     struct Mark {
@@ -272,6 +277,33 @@ void fill_terms(const xsde_problem *p, double dt, int64_t npaths, int64_t path_o
     sm.g = p->N.g;
 }
 
+// cuTensorMapEncodeTiled from the driver, fetched once through the runtime
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    }();
+    return fn;
+}
+
+// A 2D complex64 field [npaths*n0][n1] as 8-byte elements, box 16 x col_tma_box_rows(n0)
+bool encode_field_map(CUtensorMap *m, void *base, const xsde_grid &g, int64_t npaths) {
+    auto fn = tensor_map_encoder();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)g.n[1], (cuuint64_t)(npaths * g.n[0])};
+    cuuint64_t strides[1] = {(cuuint64_t)g.n[1] * 8};
+    cuuint32_t box[2] = {16u, (cuuint32_t)col_tma_box_rows(g.n[0])};
+    cuuint32_t estr[2] = {1u, 1u};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <typename R>
 int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t npaths, int64_t path_offset,
                   uint64_t step0, cudaStream_t s) {
@@ -346,14 +378,32 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
     q.sm = sm;
     q.status = p->d_status;
     const int S = sm.every;
+    // complex64 lattices the persistent TMA passes cover take the hot modes there
+    bool use_tma = false;
+    CUtensorMap mapA, mapB;
+    if constexpr (std::is_same<R, float>::value) {
+        if (p->kernel_variant == 0 && tma_passes_supported(g.n[0], g.n[1]) &&
+            (uintptr_t)psi % 16 == 0 && (uintptr_t)p->d_scratch % 16 == 0) {
+            use_tma = encode_field_map(&mapA, psi, g, npaths) && encode_field_map(&mapB, p->d_scratch, g, npaths);
+        }
+    }
     auto row = [&](int mode, uint64_t sg, int slot) -> cudaError_t {
         q.sg = sg;
         q.sample_slot = slot;
-        return timed(p, 2 + mode, s, [&] { return launch_row_pass<R>(mode, q, s); });
+        return timed(p, 2 + mode, s, [&] {
+            if constexpr (std::is_same<R, float>::value)
+                if (use_tma && (mode == ROW_STAGE2 || mode == ROW_STEADY))
+                    return launch_row_pass_tma(mode, q, p->num_sms, s);
+            return launch_row_pass<R>(mode, q, s);
+        });
     };
     auto col = [&](int mode, int slot) -> cudaError_t {
         q.sample_slot = slot;
-        return timed(p, 7 + mode, s, [&] { return launch_col_pass<R>(mode, q, s); });
+        return timed(p, 7 + mode, s, [&] {
+            if constexpr (std::is_same<R, float>::value)
+                if (use_tma && mode == COL_PROPAGATE) return launch_col_pass_tma(q, mapA, mapB, p->num_sms, s);
+            return launch_col_pass<R>(mode, q, s);
+        });
     };
     if (nsteps > 0) {
         XSDE_CUDA(row(ROW_PROLOGUE, step0, sampling ? 0 : -1), "row pass");
@@ -486,6 +536,8 @@ int xsde_problem_create(const xsde_grid *grid, xsde_dtype dtype, xsde_problem **
     p->grid = *grid;
     p->dtype = dtype;
     cudaGetDevice(&p->device);
+    cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (p->num_sms < 1) p->num_sms = 1;
     cudaError_t e = cudaMalloc(&p->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
     if (e != cudaSuccess) {
@@ -586,6 +638,13 @@ int xsde_integrate(xsde_problem *p, xsde_vector *psi, double dt, int64_t nsteps,
     return p->dtype == XSDE_C64
                ? run_integrate<float>(p, psi->data, dt, nsteps, npaths, path_offset, step_offset, s)
                : run_integrate<double>(p, psi->data, dt, nsteps, npaths, path_offset, step_offset, s);
+}
+
+int xsde_set_kernel_variant(xsde_problem *p, int variant) {
+    if (!p) return fail(XSDE_EINVAL, "xsde_set_kernel_variant: problem is NULL");
+    if (variant != 0 && variant != 1) return fail(XSDE_EINVAL, "xsde_set_kernel_variant: variant %d", variant);
+    p->kernel_variant = variant;
+    return XSDE_OK;
 }
 
 int xsde_profile(xsde_problem *p, int enable) {

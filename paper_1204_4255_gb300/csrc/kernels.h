@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
@@ -100,6 +101,17 @@ template <typename R> struct Params2D {
 };
 template <typename R> cudaError_t launch_row_pass(int mode, const Params2D<R> &p, cudaStream_t s);
 template <typename R> cudaError_t launch_col_pass(int mode, const Params2D<R> &p, cudaStream_t s);
+
+// complex64 persistent TMA-pipelined variants (rk4ip_2d_tma.cu): the row pass
+// for ROW_STAGE2/ROW_STEADY and the column pass for COL_PROPAGATE; `grid` is
+// the number of persistent CTAs (one per SM).  Field bases must be 16-byte
+// aligned; mapA/mapB describe A and B as [npaths*n0][n1] 8-byte elements with
+// a 16 x col_tma_box_rows(n0) box.
+bool tma_passes_supported(int n0, int n1);
+size_t col_tma_box_rows(int n0);
+cudaError_t launch_row_pass_tma(int mode, const Params2D<float> &p, int grid, cudaStream_t s);
+cudaError_t launch_col_pass_tma(const Params2D<float> &p, const CUtensorMap &mapA, const CUtensorMap &mapB, int grid,
+                                cudaStream_t s);
 
 // --------------------------------------------------------------------------
 // 0D: one thread per path (an ordinary SDE; D is a scalar factor).

@@ -29,7 +29,7 @@ EXPORTED = (
     "xsde_noise_alloc", "xsde_noise_free", "xsde_noise_philox", "xsde_noise_normals",
     "xsde_problem_create", "xsde_problem_destroy", "xsde_set_operators", "xsde_moments",
     "xsde_integrate", "xsde_synchronize", "xsde_last_error", "xsde_version",
-    "xsde_profile", "xsde_profile_report", "xsde_kernel_name",
+    "xsde_profile", "xsde_profile_report", "xsde_kernel_name", "xsde_set_kernel_variant",
 )
 XSDE_KERNEL_KINDS = 9
 
@@ -92,6 +92,7 @@ def load(path: str = LIB_PATH):
         "xsde_profile": (ctypes.c_int, [vp, ctypes.c_int]),
         "xsde_profile_report": (ctypes.c_int, [vp, vp, vp]),
         "xsde_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
+        "xsde_set_kernel_variant": (ctypes.c_int, [vp, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -199,6 +200,10 @@ def xsde_integrate(prob, vec, dt: float, nsteps: int, npaths: int, path_offset: 
 
 def xsde_synchronize(prob, stream: int = 0) -> None:
     _check(load().xsde_synchronize(prob, ctypes.c_void_p(stream or None)))
+
+
+def xsde_set_kernel_variant(prob, variant: int) -> None:
+    _check(load().xsde_set_kernel_variant(prob, variant))
 
 
 def xsde_profile(prob, enable: bool) -> None:

@@ -167,6 +167,28 @@ def test_2d_moments_and_noise(dtype):
     assert np.max(np.abs(pq - opq) / np.abs(opq)) < tol
 
 
+@pytest.mark.parametrize("shape", [(256, 512), (512, 256), (256, 1024), (512, 512)])
+def test_2d_c64_pipelined_passes_match_generic_and_oracle(shape):
+    """The persistent TMA-pipelined complex64 passes (lattices 256/512 x
+    256/512/1024) against the generic passes and the FP64 oracle, with noise,
+    a ragged path count and the sampling group on."""
+    rng = np.random.default_rng(sum(shape))
+    n0, n1 = shape
+    x0 = -6 + np.arange(n0) * 12 / n0
+    x1 = -6 + np.arange(n1) * 12 / n1
+    base = np.exp(-(x0[:, None] ** 2 + x1[None, :] ** 2) / 3)
+    psi0 = np.stack([base * np.exp(0.2j * rng.standard_normal(shape)) for _ in range(3)])
+    w = W.Workload("gpe2n", shape, (-6.0, -6.0), (6.0, 6.0), 0j, -0.5j, 20.0, W.POT_HARMONIC, (1.0, 1.0), None,
+                   W.NOISE_ADD_COMPLEX, 0.05, 77, 5e-4, 9, psi0.astype(np.complex128), 3)
+    fast, pp_f, pq_f = gpu_run(w, "c64", sample_every=3, path0=4, variant=0)
+    gen, pp_g, pq_g = gpu_run(w, "c64", sample_every=3, path0=4, variant=1)
+    ref, opp, opq = O.run_workload(w, sample_every=3, path0=4)
+    assert np.max(rel_l2(fast.reshape(3, -1), ref.reshape(3, -1), axis=1)) < 1e-4
+    assert np.max(rel_l2(fast.reshape(3, -1), gen.reshape(3, -1), axis=1)) < 1e-5
+    assert np.max(np.abs(pp_f - opp) / np.abs(opp)) < 1e-4
+    assert np.max(np.abs(pq_f - opq) / np.abs(opq)) < 1e-4
+
+
 def test_2d_gpe_512_c128_first_steps():
     """The 512^2 Thomas-Fermi GPE at full lattice size, 6 steps, against the oracle."""
     w = W.gpe_2d(n=512, nsteps=6)
