@@ -185,9 +185,24 @@ void make_twiddle(const std::complex<double> &z, float4 *out) {
     *out = make_float4(hi.x, hi.y, lo.x, lo.y);
 }
 
+// per-stage layout of fft.cuh: stage (Ns, R) holds w_n^(r k n/(Ns R)) at
+// [stage_table_offset(n, Ns) + (r-1) Ns + k]; n entries are allocated (the
+// table needs at most n - 1)
 template <typename R> int upload_twiddles(int n, void **dptr, cudaStream_t s) {
     std::vector<tw_t<R>> tmp(n);
-    for (int m = 0; m < n; ++m) make_twiddle(std::polar(1.0, -2.0 * M_PI * m / n), &tmp[m]);
+    make_twiddle(std::complex<double>(0.0, 0.0), &tmp[n - 1]);
+    for (int ns = 1; ns < n;) {
+        const int rad = stage_radix<8>(n / ns);
+        if (ns > 1) {
+            const int off = stage_table_offset(n, ns);
+            for (int r = 1; r < rad; ++r)
+                for (int k = 0; k < ns; ++k) {
+                    const long m = (long)r * k * (n / (ns * rad));
+                    make_twiddle(std::polar(1.0, -2.0 * M_PI * (double)m / n), &tmp[off + (r - 1) * ns + k]);
+                }
+        }
+        ns *= rad;
+    }
     return upload_raw(tmp, dptr, s);
 }
 

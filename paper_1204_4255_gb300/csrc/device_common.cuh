@@ -46,6 +46,13 @@ template <typename V> __device__ __forceinline__ V caxpy(V a, decltype(V::x) s, 
     return mk<V>(a.x + s * b.x, a.y + s * b.y);
 }
 template <typename V> __device__ __forceinline__ decltype(V::x) cabs2(V a) { return a.x * a.x + a.y * a.y; }
+
+// complex64: one packed (2 x FP32) instruction per complex add, subtract and
+// axpy (sm_100-family FADD2/FFMA2); a - b is b * (-1) + a, rounded once, i.e.
+// exactly the FP32 difference
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 caxpy(float2 a, float s, float2 b) { return __ffma2_rn(make_float2(s, s), b, a); }
 // i*a and -i*a
 template <typename V> __device__ __forceinline__ V cmul_i(V a) { return mk<V>(-a.y, a.x); }
 template <typename V> __device__ __forceinline__ V cmul_mi(V a) { return mk<V>(a.y, -a.x); }

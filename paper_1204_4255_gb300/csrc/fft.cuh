@@ -32,6 +32,21 @@ template <int E> __host__ __device__ constexpr int stage_radix(int rem) {
     return (ilog2c(rem) % lr) ? (1 << (ilog2c(rem) % lr)) : rmax;
 }
 
+// Twiddles are stored per stage: the stage starting at Ns with radix R holds
+// w_N^(r k N/(Ns R)) at [offset(Ns) + (r-1) Ns + k], r in [1,R), k in [0,Ns),
+// so the lanes of a warp (consecutive k) read consecutive entries.  The radix
+// plan is the same for every E >= 8 used here.
+__host__ __device__ constexpr int stage_table_offset(int N, int Ns) {
+    int off = 0, ns = 1;
+    while (ns < Ns) {
+        const int R = stage_radix<8>(N / ns);
+        if (ns > 1) off += (R - 1) * ns;
+        ns *= R;
+    }
+    return off;
+}
+__host__ __device__ constexpr int stage_table_size(int N) { return stage_table_offset(N, N); }
+
 // ---------------------------------------------------------------------------
 // small DFTs in registers, natural-order output
 // ---------------------------------------------------------------------------
@@ -118,9 +133,11 @@ __device__ __forceinline__ void fft_stage(V (&v)[NV][E], int t, const Tw &tw) {
     for (int q = 0; q < B; ++q) {
         TW w[R];
         if constexpr (Ns > 1) {
+            static_assert(E >= 8 || N <= E, "per-stage twiddle tables follow the E >= 8 radix plan");
             const int k = (t + q * T) & (Ns - 1);
+            constexpr int off = stage_table_offset(N, Ns);
 #pragma unroll
-            for (int r = 1; r < R; ++r) w[r] = tw(r * k * (N / (Ns * R)));
+            for (int r = 1; r < R; ++r) w[r] = tw(off + (r - 1) * Ns + k);
         }
 #pragma unroll
         for (int iv = 0; iv < NV; ++iv) {
