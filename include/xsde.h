@@ -197,6 +197,26 @@ int xsde_moments(xsde_problem *prob, const xsde_sampling *spec, double *per_path
 int xsde_integrate(xsde_problem *prob, xsde_vector *psi, double dt, int64_t nsteps, int64_t npaths,
                    int64_t path_offset, uint64_t step_offset, void *stream);
 
+/* As xsde_integrate, for 2D lattices, without allocating device memory.  The
+ * paper has no counterpart; this call exists for callers that cannot call
+ * cudaMalloc when they integrate (a fixed device-memory budget or a caller-owned
+ * pool, real-time loops where an allocation would stall on a device-wide
+ * synchronisation, hosts that give this library pointers but no heap growth).
+ * Instead of the problem's own scratch field and Fourier tables it uses two
+ * file-scope device arrays that every GPU loading the library holds until
+ * process exit: a 16 MiB scratch field (npaths x points x element size must
+ * not exceed 16 MiB, e.g. 8 paths of 512x512 complex64, else XSDE_EINVAL) and
+ * 192 KiB of tables, rewritten by every call.  The call resolves the arrays'
+ * device addresses the first time it runs on a device, so make that first call
+ * before any stream capture.  It uploads the tables and waits for `stream`
+ * once before launching.  All calls in the process share the arrays: calls
+ * that overlap on the GPU (other streams, other threads) race and must not be
+ * issued.  The caller still provides psi and any sampling buffers; the problem
+ * was created (and its error word allocated) by xsde_problem_create.  Other
+ * lattices report XSDE_EUNSUPPORTED. */
+int xsde_integrate_static_scratch(xsde_problem *prob, xsde_vector *psi, double dt, int64_t nsteps,
+                                  int64_t npaths, int64_t path_offset, uint64_t step_offset, void *stream);
+
 /* Wait for `stream`, then report device-side errors of this problem's calls:
  * XSDE_ENONFINITE if a sampled field held NaN/Inf, XSDE_ETIMEOUT if a bounded
  * wait gave up.  Clears the device error word. */

@@ -16,6 +16,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <type_traits>
@@ -729,3 +730,193 @@ int xsde_synchronize(xsde_problem *p, void *stream) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Integration that allocates nothing (the paper has no counterpart).
+//
+// Some callers cannot allocate device memory at the point where they
+// integrate: code that runs under a fixed memory budget or a caller-owned
+// pool (every byte is accounted for up front), real-time loops in which a
+// cudaMalloc/cudaFree would stall on a device-wide synchronisation, and hosts
+// that hand this library a problem and device pointers but no permission to
+// grow the device heap.  xsde_integrate_static_scratch serves them on 2D
+// lattices: instead of the problem's own scratch field and Fourier tables it
+// uses file-scope device arrays that every GPU loading the library holds
+// until process exit (kStaticScratchBytes for the scratch field plus
+// kStaticTableBytes for the tables).
+// ===========================================================================
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;     // 16 MiB scratch field
+constexpr int kStaticMaxN = 2048;                             // longest dimension
+constexpr size_t kStaticTwBytes = (size_t)kStaticMaxN * 16;   // twiddles of one dimension
+constexpr size_t kStaticEBytes = (size_t)2 * kStaticMaxN * 16; // exp(L dt/2) hi+lo of one dimension
+constexpr size_t kStaticTableBytes = 2 * (kStaticTwBytes + kStaticEBytes);
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+static __device__ __align__(256) unsigned char g_static_tables[kStaticTableBytes];
+
+// Device addresses of the two arrays, resolved once per device.  In host code
+// the array names are host-side stand-ins, never device addresses.
+struct StaticArrays {
+    void *scratch = nullptr;
+    unsigned char *tables = nullptr;
+    bool ready = false;
+};
+constexpr int kMaxDevices = 64;
+StaticArrays g_static_arrays[kMaxDevices];
+std::mutex g_static_mutex;
+
+int static_arrays_for(int dev, StaticArrays **out) {
+    if (dev < 0 || dev >= kMaxDevices)
+        return fail(XSDE_EUNSUPPORTED, "xsde_integrate_static_scratch: device %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    StaticArrays &sa = g_static_arrays[dev];
+    if (!sa.ready) {
+        void *scratch = nullptr, *tables = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&scratch, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "xsde_integrate_static_scratch: scratch address");
+        e = cudaGetSymbolAddress(&tables, g_static_tables);
+        if (e != cudaSuccess) return cuda_fail(e, "xsde_integrate_static_scratch: table address");
+        sa.scratch = scratch;
+        sa.tables = static_cast<unsigned char *>(tables);
+        sa.ready = true;
+    }
+    *out = &sa;
+    return XSDE_OK;
+}
+
+// host staging of the tables (per thread, no heap)
+thread_local unsigned char t_host_tables[kStaticTableBytes];
+
+template <typename R>
+int static_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t npaths, int64_t path_offset,
+                     uint64_t step0, cudaStream_t s, const StaticArrays &sa) {
+    using V = cx<R>;
+    const xsde_grid &g = p->grid;
+    const std::complex<double> c0(p->L.c0_re, p->L.c0_im), c2(p->L.c2_re, p->L.c2_im);
+    // tables into the host staging area, same layouts as the problem's own tables
+    unsigned char *hdim[2] = {t_host_tables, t_host_tables + kStaticTwBytes + kStaticEBytes};
+    for (int d = 0; d < 2; ++d) {
+        const int n = g.n[d];
+        tw_t<R> *tw = reinterpret_cast<tw_t<R> *>(hdim[d]);
+        V *e = reinterpret_cast<V *>(hdim[d] + kStaticTwBytes);
+        make_twiddle(std::complex<double>(0.0, 0.0), &tw[n - 1]);
+        for (int ns = 1; ns < n;) {
+            const int rad = stage_radix<8>(n / ns);
+            if (ns > 1) {
+                const int off = stage_table_offset(n, ns);
+                for (int r = 1; r < rad; ++r)
+                    for (int k = 0; k < ns; ++k) {
+                        const long m = (long)r * k * (n / (ns * rad));
+                        make_twiddle(std::polar(1.0, -2.0 * M_PI * (double)m / n), &tw[off + (r - 1) * ns + k]);
+                    }
+            }
+            ns *= rad;
+        }
+        for (int i = 0; i < n; ++i) {
+            const double k = kval(g, d, i);
+            const std::complex<double> v =
+                d == 0 ? std::exp((c0 + c2 * (k * k)) * (0.5 * dt)) / ((double)g.n[0] * g.n[1])
+                       : std::exp(c2 * (k * k) * (0.5 * dt));
+            split_hi_lo(v, &e[i], &e[n + i]);
+        }
+    }
+    XSDE_CUDA(cudaMemcpyAsync(sa.tables, t_host_tables, kStaticTableBytes, cudaMemcpyHostToDevice, s),
+              "xsde_integrate_static_scratch: tables");
+    XSDE_CUDA(cudaStreamSynchronize(s), "xsde_integrate_static_scratch: tables");
+
+    LocalTerm<R> lt;
+    Sampling sm;
+    fill_terms<R>(p, dt, npaths, path_offset, lt, sm);
+    const bool sampling = sm.every > 0;
+    if (sampling) {
+        const int64_t nsamp = nsteps / sm.every + 1;
+        if (sm.per_path && (sm.which & (MOM_NORM | MOM_ENERGY)))
+            XSDE_CUDA(cudaMemsetAsync(sm.per_path, 0, (size_t)nsamp * npaths * 2 * sizeof(double), s), "memset");
+        if (sm.per_point && (sm.which & (MOM_MOD2 | MOM_MOD4)))
+            XSDE_CUDA(cudaMemsetAsync(sm.per_point, 0, (size_t)nsamp * g.npts * 2 * sizeof(double), s), "memset");
+    }
+    Params2D<R> q;
+    q.A = static_cast<V *>(psi);
+    q.B = static_cast<V *>(sa.scratch);   // fully written by the first pass before it is read
+    q.npaths = npaths;
+    q.n0 = g.n[0];
+    q.n1 = g.n[1];
+    q.tw0 = reinterpret_cast<const tw_t<R> *>(sa.tables);
+    q.E0 = reinterpret_cast<const V *>(sa.tables + kStaticTwBytes);
+    q.tw1 = reinterpret_cast<const tw_t<R> *>(sa.tables + kStaticTwBytes + kStaticEBytes);
+    q.E1 = reinterpret_cast<const V *>(sa.tables + 2 * kStaticTwBytes + kStaticEBytes);
+    q.lt = lt;
+    q.sm = sm;
+    q.status = p->d_status;
+    const int S = sm.every;
+    auto row = [&](int mode, uint64_t sg, int slot) {
+        q.sg = sg;
+        q.sample_slot = slot;
+        return launch_row_pass<R>(mode, q, s);
+    };
+    auto col = [&](int mode, int slot) {
+        q.sample_slot = slot;
+        return launch_col_pass<R>(mode, q, s);
+    };
+    if (nsteps > 0) {
+        XSDE_CUDA(row(ROW_PROLOGUE, step0, sampling ? 0 : -1), "row pass");
+        for (int64_t n = 0; n < nsteps; ++n) {
+            const uint64_t sg = step0 + n;
+            XSDE_CUDA(col(COL_PROPAGATE, (sampling && n % S == 0) ? (int)(n / S) : -1), "col pass");
+            XSDE_CUDA(row(ROW_STAGE2, sg, -1), "row pass");
+            XSDE_CUDA(col(COL_PROPAGATE, -1), "col pass");
+            if (n + 1 < nsteps) {
+                const int slot = (sampling && (n + 1) % S == 0) ? (int)((n + 1) / S) : -1;
+                XSDE_CUDA(row(ROW_STEADY, sg, slot), "row pass");
+            } else {
+                XSDE_CUDA(row(ROW_EPILOGUE, sg, -1), "row pass");
+            }
+        }
+    }
+    if (sampling && nsteps % S == 0) {
+        const int slot = (int)(nsteps / S);
+        XSDE_CUDA(row(ROW_FFT_ONLY, step0 + nsteps, slot), "row pass");
+        XSDE_CUDA(col(COL_SPECTRAL, slot), "col pass");
+    }
+    return XSDE_OK;
+}
+
+}  // namespace
+
+extern "C" int xsde_integrate_static_scratch(xsde_problem *p, xsde_vector *psi, double dt, int64_t nsteps,
+                                             int64_t npaths, int64_t path_offset, uint64_t step_offset,
+                                             void *stream) {
+    if (!p || !psi) return fail(XSDE_EINVAL, "xsde_integrate_static_scratch: NULL problem or field");
+    if (!p->have_ops) return fail(XSDE_EINVAL, "xsde_integrate_static_scratch: operators not set");
+    if (p->grid.ndim != 2)
+        return fail(XSDE_EUNSUPPORTED, "xsde_integrate_static_scratch: only 2D lattices use a scratch field");
+    if (psi->dtype != p->dtype) return fail(XSDE_EINVAL, "xsde_integrate_static_scratch: field dtype differs");
+    if (!same_lattice(psi->grid, p->grid)) return fail(XSDE_EINVAL, "xsde_integrate_static_scratch: lattice differs");
+    if (npaths != psi->npaths) return fail(XSDE_EINVAL, "xsde_integrate_static_scratch: npaths differs from the field");
+    if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0)
+        return fail(XSDE_EINVAL, "xsde_integrate_static_scratch: dt must be positive and finite, nsteps >= 0");
+    if (path_offset < 0 || path_offset + npaths > (int64_t)UINT32_MAX + 1 ||
+        step_offset + (uint64_t)nsteps + 1 > (uint64_t)UINT32_MAX)
+        return fail(XSDE_EINVAL, "xsde_integrate_static_scratch: global path or step indices exceed 32 bits");
+    if (npaths > 65535) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_static_scratch: at most 65535 paths");
+    if (p->N.pot_kind == XSDE_POT_TABLE && p->N.V_nt > 1 && step_offset + (uint64_t)nsteps > (uint64_t)p->N.V_nt)
+        return fail(XSDE_EINVAL, "xsde_integrate_static_scratch: potential table too short");
+    const size_t need = (size_t)npaths * p->grid.npts * elem_bytes(p->dtype);
+    if (need > kStaticScratchBytes)
+        return fail(XSDE_EINVAL,
+                    "xsde_integrate_static_scratch: the scratch field needs %zu bytes, more than the %zu-byte "
+                    "static buffer (npaths x points x element size); use xsde_integrate or fewer paths per call",
+                    need, kStaticScratchBytes);
+    int dev = -1;
+    XSDE_CUDA(cudaGetDevice(&dev), "xsde_integrate_static_scratch: cudaGetDevice");
+    if (dev != p->device) return fail(XSDE_EINVAL, "xsde_integrate_static_scratch: current device is not the problem's");
+    StaticArrays *sa = nullptr;
+    int rc = static_arrays_for(dev, &sa);
+    if (rc != XSDE_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return p->dtype == XSDE_C64
+               ? static_integrate<float>(p, psi->data, dt, nsteps, npaths, path_offset, step_offset, s, *sa)
+               : static_integrate<double>(p, psi->data, dt, nsteps, npaths, path_offset, step_offset, s, *sa);
+}

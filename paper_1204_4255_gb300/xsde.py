@@ -30,6 +30,7 @@ EXPORTED = (
     "xsde_problem_create", "xsde_problem_destroy", "xsde_set_operators", "xsde_moments",
     "xsde_integrate", "xsde_synchronize", "xsde_last_error", "xsde_version",
     "xsde_profile", "xsde_profile_report", "xsde_kernel_name", "xsde_set_kernel_variant",
+    "xsde_integrate_static_scratch",
 )
 XSDE_KERNEL_KINDS = 9
 
@@ -93,6 +94,7 @@ def load(path: str = LIB_PATH):
         "xsde_profile_report": (ctypes.c_int, [vp, vp, vp]),
         "xsde_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
         "xsde_set_kernel_variant": (ctypes.c_int, [vp, ctypes.c_int]),
+        "xsde_integrate_static_scratch": (ctypes.c_int, [vp, vp, dp, i64, i64, i64, u64, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -196,6 +198,14 @@ def xsde_integrate(prob, vec, dt: float, nsteps: int, npaths: int, path_offset: 
                    stream: int = 0) -> None:
     _check(load().xsde_integrate(prob, vec, dt, nsteps, npaths, path_offset, step_offset,
                                  ctypes.c_void_p(stream or None)))
+
+
+def xsde_integrate_static_scratch(prob, vec, dt: float, nsteps: int, npaths: int, path_offset: int = 0,
+                                  step_offset: int = 0, stream: int = 0) -> None:
+    """xsde_integrate for 2D lattices using the library's static device scratch
+    (no device allocation; for callers that cannot call cudaMalloc)."""
+    _check(load().xsde_integrate_static_scratch(prob, vec, dt, nsteps, npaths, path_offset, step_offset,
+                                                ctypes.c_void_p(stream or None)))
 
 
 def xsde_synchronize(prob, stream: int = 0) -> None:
