@@ -249,3 +249,65 @@ def run_workload(w, nsteps: int | None = None, npaths: int | None = None, path0:
     return rk4ip(psi, grid, ops, w.dt, w.nsteps if nsteps is None else nsteps, path0=path0,
                  sample_every=w.sample_every if sample_every is None else sample_every,
                  threads=threads)
+
+
+def _load_adjoint(lib):
+    if not hasattr(lib, "_adjoint_ready"):
+        dp, i64 = ctypes.c_void_p, ctypes.c_int64
+        lib.oracle_adjoint.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Ops), dp, i64, dp, ctypes.c_double,
+                                       i64, dp, dp, dp]
+        lib.oracle_adjoint.restype = ctypes.c_int
+        lib.oracle_step_tangent.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Ops), dp, dp, dp, i64,
+                                            ctypes.c_double, dp]
+        lib.oracle_step_adjoint.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Ops), dp, dp, i64,
+                                            ctypes.c_double, dp, dp]
+        lib._adjoint_ready = True
+    return lib
+
+
+def adjoint(psi0: np.ndarray, grid: Grid, ops: Ops, target: np.ndarray, dt: float, nsteps: int):
+    """Loss sum_p (1 - |<target|psi_N>|^2), dL/dV [nsteps, npts] and the cotangent
+    dL/dpsi0 [npaths, *shape] (dL = Re sum conj(lam) dpsi0) of nsteps RK4IP steps."""
+    lib = _load_adjoint(_load())
+    a = np.ascontiguousarray(psi0, dtype=np.complex128)
+    npaths = a.size // grid.npts
+    tgt = np.ascontiguousarray(target, dtype=np.complex128)
+    loss = np.zeros(1)
+    dV = np.zeros((nsteps, grid.npts))
+    dpsi = np.zeros(a.shape, dtype=np.complex128)
+    rc = lib.oracle_adjoint(ctypes.byref(grid._c()), ctypes.byref(ops._c()), _ptr(a), npaths, _ptr(tgt), dt,
+                            nsteps, _ptr(loss), _ptr(dV), _ptr(dpsi))
+    if rc != 0:
+        raise ValueError("oracle_adjoint rejected its arguments")
+    return float(loss[0]), dV, dpsi
+
+
+def loss(psi0: np.ndarray, grid: Grid, ops: Ops, target: np.ndarray, dt: float, nsteps: int) -> float:
+    """sum_p 1 - |<target|psi_N>|^2 by a plain forward run."""
+    out, _, _ = rk4ip(psi0, grid, ops, dt, nsteps)
+    dV = float(np.prod([(grid.xmax[d] - grid.xmin[d]) / grid.n[d] for d in range(grid.ndim)]))
+    c = np.sum(np.conj(target)[None] * out.reshape(out.shape[0], -1).reshape((out.shape[0],) + tuple(grid.n)),
+               axis=tuple(range(1, 1 + grid.ndim))) * dV
+    return float(np.sum(1.0 - np.abs(c) ** 2))
+
+
+def step_tangent(a, da, dVrow, grid: Grid, ops: Ops, step: int, dt: float) -> np.ndarray:
+    lib = _load_adjoint(_load())
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    da = np.ascontiguousarray(da, dtype=np.complex128)
+    dVrow = np.ascontiguousarray(dVrow, dtype=np.float64)
+    out = np.empty_like(a)
+    lib.oracle_step_tangent(ctypes.byref(grid._c()), ctypes.byref(ops._c()), _ptr(a), _ptr(da), _ptr(dVrow), step,
+                            dt, _ptr(out))
+    return out
+
+
+def step_adjoint(a, lam, grid: Grid, ops: Ops, step: int, dt: float):
+    lib = _load_adjoint(_load())
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    lam = np.ascontiguousarray(lam, dtype=np.complex128)
+    out = np.empty_like(a)
+    gV = np.empty(grid.npts)
+    lib.oracle_step_adjoint(ctypes.byref(grid._c()), ctypes.byref(ops._c()), _ptr(a), _ptr(lam), step, dt,
+                            _ptr(out), _ptr(gV))
+    return out, gV

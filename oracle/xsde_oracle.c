@@ -499,3 +499,229 @@ int32_t oracle_get_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------- */
+/* Adjoint of the discrete RK4IP step (discretise-then-differentiate)        */
+/* ------------------------------------------------------------------------- */
+/*
+ * Fields are real vectors (Re, Im) with the inner product <u, v> = Re sum conj(u) v.
+ * For N(u) = dt (-i (V + g|u|^2) u) (no noise), the tangent is
+ *   dN = A du + B conj(du),   A = -i dt (V + 2 g |u|^2),  B = -i dt g u^2,
+ * and its adjoint maps a cotangent mu to conj(A) mu + B conj(mu).  D = F^-1 E F
+ * has adjoint F^-1 conj(E) F.  dN/dV_j = -i dt u_j, so a stage with cotangent
+ * mu adds Re(conj(mu_j) (-i dt u_j)) to dL/dV_j.
+ */
+
+static void apply_Dadj(cplx *u, const cplx *E, const oracle_grid *g, int64_t npaths)
+{
+    int64_t npts = grid_points(g);
+    fft_nd(u, g, npaths, -1);
+    for (int64_t i = 0; i < npaths * npts; i++) u[i] *= conj(E[i % npts]);
+    fft_nd(u, g, npaths, +1);
+}
+
+/* one path: the forward step's intermediates from its input a */
+typedef struct {
+    cplx *a, *aI, *k1, *w2, *k2, *w3, *k3, *Du1, *acc;
+} step_state;
+
+static void step_forward_store(step_state *s, const cplx *E, const oracle_grid *g, const oracle_ops *ops,
+                               const step_inputs *in, double dt, cplx *out)
+{
+    int64_t m = grid_points(g);
+    memcpy(s->aI, s->a, sizeof(cplx) * m);
+    apply_D(s->aI, E, g, 1);
+    nonlinear(s->k1, s->a, ops, in, m, 1, dt);
+    apply_D(s->k1, E, g, 1);
+    for (int64_t i = 0; i < m; i++) s->w2[i] = s->aI[i] + 0.5 * s->k1[i];
+    nonlinear(s->k2, s->w2, ops, in, m, 1, dt);
+    for (int64_t i = 0; i < m; i++) s->w3[i] = s->aI[i] + 0.5 * s->k2[i];
+    nonlinear(s->k3, s->w3, ops, in, m, 1, dt);
+    for (int64_t i = 0; i < m; i++) s->Du1[i] = s->aI[i] + s->k3[i];
+    apply_D(s->Du1, E, g, 1);
+    for (int64_t i = 0; i < m; i++) s->acc[i] = s->aI[i] + s->k1[i] / 6.0 + s->k2[i] / 3.0 + s->k3[i] / 3.0;
+    apply_D(s->acc, E, g, 1);
+    if (out) {
+        cplx *k4 = malloc(sizeof(cplx) * m);
+        nonlinear(k4, s->Du1, ops, in, m, 1, dt);
+        for (int64_t i = 0; i < m; i++) out[i] = s->acc[i] + k4[i] / 6.0;
+        free(k4);
+    }
+}
+
+/* cotangent of N's input for cotangent mu of its output, at input u */
+static cplx adj_N(cplx u, cplx mu, double Vj, double g, double dt)
+{
+    double m2 = creal(u) * creal(u) + cimag(u) * cimag(u);
+    cplx A = -I * dt * (Vj + 2.0 * g * m2);
+    cplx B = -I * dt * g * u * u;
+    return conj(A) * mu + B * conj(mu);
+}
+
+static double dV_term(cplx mu, cplx u, double dt)
+{
+    return creal(conj(mu) * (-I * dt * u));
+}
+
+/* Reverse of one step: lam (cotangent of a_{n+1}) -> cotangent of a_n; adds dL/dV_n to gV. */
+static void step_adjoint(const step_state *s, const cplx *E, const oracle_grid *g, const oracle_ops *ops,
+                         const step_inputs *in, double dt, const cplx *lam_next, cplx *lam, double *gV)
+{
+    int64_t m = grid_points(g);
+    cplx *l_acc = malloc(sizeof(cplx) * m), *l_u1 = malloc(sizeof(cplx) * m);
+    cplx *l_k1 = malloc(sizeof(cplx) * m), *l_aI = malloc(sizeof(cplx) * m);
+    /* a' = D acc + k4/6, k4 = N(Du1) */
+    for (int64_t i = 0; i < m; i++) {
+        cplx l_k4 = lam_next[i] / 6.0;
+        l_acc[i] = lam_next[i];
+        l_u1[i] = adj_N(s->Du1[i], l_k4, in->Vrow[i], ops->gnl, dt);
+        gV[i] += dV_term(l_k4, s->Du1[i], dt);
+    }
+    apply_Dadj(l_acc, E, g, 1);     /* acc = a_I + k1/6 + k2/3 + k3/3 */
+    apply_Dadj(l_u1, E, g, 1);      /* Du1 = D(a_I + k3) */
+    for (int64_t i = 0; i < m; i++) {
+        cplx la = l_acc[i], lu = l_u1[i];
+        cplx l_aIi = la + lu;
+        cplx l_k3 = la / 3.0 + lu;
+        cplx l_w3 = adj_N(s->w3[i], l_k3, in->Vrow[i], ops->gnl, dt);     /* k3 = N(w3), w3 = a_I + k2/2 */
+        gV[i] += dV_term(l_k3, s->w3[i], dt);
+        l_aIi += l_w3;
+        cplx l_k2 = la / 3.0 + 0.5 * l_w3;
+        cplx l_w2 = adj_N(s->w2[i], l_k2, in->Vrow[i], ops->gnl, dt);     /* k2 = N(w2), w2 = a_I + k1/2 */
+        gV[i] += dV_term(l_k2, s->w2[i], dt);
+        l_aIi += l_w2;
+        l_k1[i] = la / 6.0 + 0.5 * l_w2;
+        l_aI[i] = l_aIi;
+    }
+    apply_Dadj(l_k1, E, g, 1);      /* k1 = D N(a) */
+    apply_Dadj(l_aI, E, g, 1);      /* a_I = D a */
+    for (int64_t i = 0; i < m; i++) {
+        lam[i] = adj_N(s->a[i], l_k1[i], in->Vrow[i], ops->gnl, dt) + l_aI[i];
+        gV[i] += dV_term(l_k1[i], s->a[i], dt);
+    }
+    free(l_acc); free(l_u1); free(l_k1); free(l_aI);
+}
+
+static void state_alloc(step_state *s, int64_t m)
+{
+    cplx **f[] = {&s->a, &s->aI, &s->k1, &s->w2, &s->k2, &s->w3, &s->k3, &s->Du1, &s->acc};
+    for (int i = 0; i < 9; i++) *f[i] = malloc(sizeof(cplx) * m);
+}
+
+static void state_free(step_state *s)
+{
+    cplx *f[] = {s->a, s->aI, s->k1, s->w2, s->k2, s->w3, s->k3, s->Du1, s->acc};
+    for (int i = 0; i < 9; i++) free(f[i]);
+}
+
+/*
+ * Loss L = sum over paths of 1 - |<target|psi_N>|^2, <a|b> = sum conj(a) b dV,
+ * after nsteps RK4IP steps (deterministic; potential from ops, a table with one
+ * row per step or static).  Writes the loss, dL/dV[n][j] (w.r.t. the table
+ * entries of step n; zero rows are written when the potential is not a table)
+ * and dL/dpsi0 as the cotangent lam with dL = Re sum conj(lam) dpsi0.
+ * All states are stored (no checkpointing: this is the plain reference).
+ */
+int oracle_adjoint(const oracle_grid *g, const oracle_ops *ops, const double *psi0_in, int64_t npaths,
+                   const double *target_in, double dt, int64_t nsteps, double *loss, double *dLdV,
+                   double *dLdpsi0)
+{
+    if (ops->noise_kind != NOISE_NONE || nsteps < 1) return -1;
+    if (ops->pot_kind == POT_TABLE && ops->V_nt > 1 && nsteps > ops->V_nt) return -1;
+    int64_t m = grid_points(g);
+    double dV = grid_dV(g);
+    const cplx *target = (const cplx *)target_in;
+    cplx *E = malloc(sizeof(cplx) * m);
+    half_step_factors(g, ops, dt, E);
+    cplx *states = malloc(sizeof(cplx) * m * (nsteps + 1));
+    step_state s;
+    state_alloc(&s, m);
+    step_inputs in = {malloc(sizeof(double) * m), NULL, NULL};
+    cplx *lam = malloc(sizeof(cplx) * m), *lam_prev = malloc(sizeof(cplx) * m);
+    memset(dLdV, 0, sizeof(double) * nsteps * m);
+    *loss = 0.0;
+    for (int64_t p = 0; p < npaths; p++) {
+        memcpy(states, psi0_in + 2 * p * m, sizeof(cplx) * m);
+        for (int64_t n = 0; n < nsteps; n++) {
+            fill_step_inputs(&in, g, ops, 1, p, n, dt);
+            memcpy(s.a, states + n * m, sizeof(cplx) * m);
+            step_forward_store(&s, E, g, ops, &in, dt, states + (n + 1) * m);
+        }
+        cplx c = 0.0;
+        for (int64_t j = 0; j < m; j++) c += conj(target[j]) * states[nsteps * m + j] * dV;
+        *loss += 1.0 - (creal(c) * creal(c) + cimag(c) * cimag(c));
+        for (int64_t j = 0; j < m; j++) lam[j] = -2.0 * c * target[j] * dV;
+        for (int64_t n = nsteps - 1; n >= 0; n--) {
+            fill_step_inputs(&in, g, ops, 1, p, n, dt);
+            memcpy(s.a, states + n * m, sizeof(cplx) * m);
+            step_forward_store(&s, E, g, ops, &in, dt, NULL);
+            step_adjoint(&s, E, g, ops, &in, dt, lam, lam_prev, dLdV + n * m);
+            memcpy(lam, lam_prev, sizeof(cplx) * m);
+        }
+        if (dLdpsi0) memcpy(dLdpsi0 + 2 * p * m, lam, sizeof(cplx) * m);
+    }
+    state_free(&s);
+    free(E); free(states); free(in.Vrow); free(lam); free(lam_prev);
+    return 0;
+}
+
+/*
+ * One step's tangent (forward mode) and adjoint, for the transpose test:
+ *   tangent: da_out = J_a da + J_V dV   (dV a perturbation of this step's potential)
+ *   adjoint: lam_out = J_a^T lam, gV = J_V^T lam
+ */
+int oracle_step_tangent(const oracle_grid *g, const oracle_ops *ops, const double *a_in, const double *da_in,
+                        const double *dVrow, int64_t step, double dt, double *da_out)
+{
+    int64_t m = grid_points(g);
+    const cplx *a = (const cplx *)a_in, *da = (const cplx *)da_in;
+    cplx *E = malloc(sizeof(cplx) * m);
+    half_step_factors(g, ops, dt, E);
+    step_inputs in = {malloc(sizeof(double) * m), NULL, NULL};
+    fill_step_inputs(&in, g, ops, 1, 0, step, dt);
+    step_state s;
+    state_alloc(&s, m);
+    memcpy(s.a, a, sizeof(cplx) * m);
+    step_forward_store(&s, E, g, ops, &in, dt, NULL);
+    /* tangent of N at u: A du + B conj(du) + (-i dt u) dV */
+    #define TAN_N(u, du, j) (-I * dt * (in.Vrow[j] + 2.0 * ops->gnl * (creal(u) * creal(u) + cimag(u) * cimag(u))) * (du) \
+                             - I * dt * ops->gnl * (u) * (u) * conj(du) - I * dt * (u) * dVrow[j])
+    cplx *t_aI = malloc(sizeof(cplx) * m), *t_k1 = malloc(sizeof(cplx) * m), *t_k2 = malloc(sizeof(cplx) * m);
+    cplx *t_k3 = malloc(sizeof(cplx) * m), *t_u1 = malloc(sizeof(cplx) * m), *t_acc = malloc(sizeof(cplx) * m);
+    memcpy(t_aI, da, sizeof(cplx) * m);
+    apply_D(t_aI, E, g, 1);
+    for (int64_t j = 0; j < m; j++) t_k1[j] = TAN_N(a[j], da[j], j);
+    apply_D(t_k1, E, g, 1);
+    for (int64_t j = 0; j < m; j++) t_k2[j] = TAN_N(s.w2[j], t_aI[j] + 0.5 * t_k1[j], j);
+    for (int64_t j = 0; j < m; j++) t_k3[j] = TAN_N(s.w3[j], t_aI[j] + 0.5 * t_k2[j], j);
+    for (int64_t j = 0; j < m; j++) t_u1[j] = t_aI[j] + t_k3[j];
+    apply_D(t_u1, E, g, 1);
+    for (int64_t j = 0; j < m; j++) t_acc[j] = t_aI[j] + t_k1[j] / 6.0 + t_k2[j] / 3.0 + t_k3[j] / 3.0;
+    apply_D(t_acc, E, g, 1);
+    cplx *out = (cplx *)da_out;
+    for (int64_t j = 0; j < m; j++) out[j] = t_acc[j] + TAN_N(s.Du1[j], t_u1[j], j) / 6.0;
+    #undef TAN_N
+    free(t_aI); free(t_k1); free(t_k2); free(t_k3); free(t_u1); free(t_acc);
+    state_free(&s);
+    free(E); free(in.Vrow);
+    return 0;
+}
+
+int oracle_step_adjoint(const oracle_grid *g, const oracle_ops *ops, const double *a_in, const double *lam_in,
+                        int64_t step, double dt, double *lam_out, double *gV)
+{
+    int64_t m = grid_points(g);
+    cplx *E = malloc(sizeof(cplx) * m);
+    half_step_factors(g, ops, dt, E);
+    step_inputs in = {malloc(sizeof(double) * m), NULL, NULL};
+    fill_step_inputs(&in, g, ops, 1, 0, step, dt);
+    step_state s;
+    state_alloc(&s, m);
+    memcpy(s.a, a_in, sizeof(cplx) * m);
+    step_forward_store(&s, E, g, ops, &in, dt, NULL);
+    memset(gV, 0, sizeof(double) * m);
+    step_adjoint(&s, E, g, ops, &in, dt, (const cplx *)lam_in, (cplx *)lam_out, gV);
+    state_free(&s);
+    free(E); free(in.Vrow);
+    return 0;
+}
