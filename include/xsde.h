@@ -197,6 +197,22 @@ int xsde_moments(xsde_problem *prob, const xsde_sampling *spec, double *per_path
 int xsde_integrate(xsde_problem *prob, xsde_vector *psi, double dt, int64_t nsteps, int64_t npaths,
                    int64_t path_offset, uint64_t step_offset, void *stream);
 
+/* Gradient of a final-state fidelity through the discrete RK4IP scheme
+ * (reverse mode through the step of Secs. 2.5-2.6; the workload of
+ * Eq. InitialCondition driven by a space-time potential).  For the problem's
+ * operators (deterministic; 1D lattice of 256..2048 points; the potential table,
+ * if any, with one row per step and at least nsteps rows), the fields psi0
+ * [npaths][N] and target [1][N] (device, borrowed, not modified):
+ *   loss  (device, 1 double)          = sum_p 1 - |<target|psi_N>|^2, <a|b> = sum conj(a) b dx
+ *   dLdV  (device, nsteps x N doubles) = dL/dV[n][j] with respect to the table
+ *                                       entries (the potential of step n at point j)
+ *   dLdpsi0 (device like psi0, or NULL) = lambda with dL = Re sum conj(lambda) dpsi0
+ * psi_N is reached by nsteps steps of size dt.  States are checkpointed every
+ * ckpt_every steps and each segment is recomputed once during the reverse sweep
+ * (the library owns that workspace).  Asynchronous on `stream`. */
+int xsde_adjoint(xsde_problem *prob, const xsde_vector *psi0, const xsde_vector *target, double dt, int64_t nsteps,
+                 int32_t ckpt_every, double *loss, double *dLdV, void *dLdpsi0, void *stream);
+
 /* As xsde_integrate, for 2D lattices, without allocating device memory.  The
  * paper has no counterpart; this call exists for callers that cannot call
  * cudaMalloc when they integrate (a fixed device-memory budget or a caller-owned

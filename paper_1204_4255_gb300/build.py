@@ -31,6 +31,7 @@ UNITS = [
     ("rk4ip_2d.cu", 32),
     ("rk4ip_2d.cu", 64),
     ("rk4ip_2d_tma.cu", None),
+    ("rk4ip_adjoint.cu", None),
 ]
 
 

@@ -68,6 +68,8 @@ struct xsde_problem {
     int *d_status = nullptr;
     int num_sms = 1;
     int kernel_variant = 0;   // 0: fastest available kernels, 1: generic kernels only
+    void *d_adj = nullptr;    // adjoint checkpoints and stage inputs
+    size_t adj_bytes = 0;
     // launch profiling: CUDA events around every kernel launch of this problem
     bool profiling = false;
     struct Mark {
@@ -577,6 +579,7 @@ void xsde_problem_destroy(xsde_problem *p) {
         cudaFree(p->d_E[d]);
     }
     cudaFree(p->d_scratch);
+    cudaFree(p->d_adj);
     cudaFree(p->d_status);
     delete p;
 }
@@ -716,6 +719,67 @@ int xsde_noise_normals(const xsde_noise *noise, xsde_dtype dtype, int64_t npts, 
                         : launch_normals<double>(noise->seed, npts, npaths, path_offset, (uint32_t)step, out, s);
     XSDE_CUDA(e, "xsde_noise_normals");
     return XSDE_OK;
+}
+
+int xsde_adjoint(xsde_problem *p, const xsde_vector *psi0, const xsde_vector *target, double dt, int64_t nsteps,
+                 int32_t ckpt_every, double *loss, double *dLdV, void *dLdpsi0, void *stream) {
+    if (!p || !psi0 || !target || !loss || !dLdV) return fail(XSDE_EINVAL, "xsde_adjoint: NULL argument");
+    if (!p->have_ops) return fail(XSDE_EINVAL, "xsde_adjoint: operators not set");
+    const xsde_grid &g = p->grid;
+    if (g.ndim != 1 || g.n[0] < 256) return fail(XSDE_EUNSUPPORTED, "xsde_adjoint: 1D lattices of 256..2048 points");
+    if (psi0->dtype != p->dtype || target->dtype != p->dtype)
+        return fail(XSDE_EINVAL, "xsde_adjoint: field dtypes differ from the problem's");
+    if (!same_lattice(psi0->grid, g) || !same_lattice(target->grid, g))
+        return fail(XSDE_EINVAL, "xsde_adjoint: lattice differs");
+    if (target->npaths != 1) return fail(XSDE_EINVAL, "xsde_adjoint: the target is a single field");
+    if (p->noise.kind != XSDE_NOISE_NONE) return fail(XSDE_EUNSUPPORTED, "xsde_adjoint: deterministic problems only");
+    if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 1 || ckpt_every < 1)
+        return fail(XSDE_EINVAL, "xsde_adjoint: need dt > 0, nsteps >= 1, ckpt_every >= 1");
+    if (p->N.pot_kind == XSDE_POT_TABLE && p->N.V_nt > 1 && nsteps > p->N.V_nt)
+        return fail(XSDE_EINVAL, "xsde_adjoint: potential table has fewer rows than steps");
+    const int64_t npaths = psi0->npaths;
+    const int64_t K = ckpt_every < nsteps ? ckpt_every : nsteps;
+    const int64_t nck = (nsteps + K - 1) / K;
+    const size_t eb = elem_bytes(p->dtype);
+    const size_t need = (size_t)(nck + 4 * K) * npaths * g.npts * eb;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (p->adj_bytes < need) {
+        if (p->d_adj) {
+            XSDE_CUDA(cudaStreamSynchronize(s), "xsde_adjoint: workspace");
+            cudaFree(p->d_adj);
+            p->d_adj = nullptr;
+            p->adj_bytes = 0;
+        }
+        XSDE_CUDA(cudaMalloc(&p->d_adj, need), "xsde_adjoint: workspace");
+        p->adj_bytes = need;
+    }
+    XSDE_CUDA(cudaMemsetAsync(loss, 0, sizeof(double), s), "xsde_adjoint: memset");
+    XSDE_CUDA(cudaMemsetAsync(dLdV, 0, (size_t)nsteps * g.npts * sizeof(double), s), "xsde_adjoint: memset");
+    auto run = [&](auto tag) -> int {
+        using R = decltype(tag);
+        using V = cx<R>;
+        int rc = ensure_tables<V>(p, dt, s);
+        if (rc != XSDE_OK) return rc;
+        AdjParams<R> q;
+        Sampling sm;
+        fill_terms<R>(p, dt, npaths, 0, q.lt, sm);
+        q.psi0 = static_cast<const V *>(psi0->data);
+        q.target = static_cast<const V *>(target->data);
+        q.npaths = npaths;
+        q.nsteps = nsteps;
+        q.K = K;
+        q.Etab = static_cast<const V *>(p->d_E[0]);
+        q.tw = static_cast<const tw_t<R> *>(p->d_tw[0]);
+        q.dx = grid_dx(g, 0);
+        q.ckpt = static_cast<V *>(p->d_adj);
+        q.interm = q.ckpt + (size_t)nck * npaths * g.npts;
+        q.loss = loss;
+        q.dLdV = dLdV;
+        q.dLdpsi0 = static_cast<V *>(dLdpsi0);
+        XSDE_CUDA(timed(p, 1, s, [&] { return launch_adjoint_1d<R>(g.n[0], q, s); }), "xsde_adjoint launch");
+        return XSDE_OK;
+    };
+    return p->dtype == XSDE_C64 ? run(0.0f) : run(0.0);
 }
 
 int xsde_synchronize(xsde_problem *p, void *stream) {

@@ -40,6 +40,7 @@ __device__ __forceinline__ float2 cmulconj_hilo(float2 x, float2 hi, float2 lo) 
     return make_float2(fmaf(x.x, hi.x, fmaf(x.y, hi.y, tx)), fmaf(x.y, hi.x, fmaf(-x.x, hi.y, ty)));
 }
 __device__ __forceinline__ double2 cmul_hilo(double2 x, double2 hi, double2) { return cmul(x, hi); }
+__device__ __forceinline__ double2 cmulconj_hilo(double2 x, double2 hi, double2) { return cmulconj(x, hi); }
 
 // a + s*b
 template <typename V> __device__ __forceinline__ V caxpy(V a, decltype(V::x) s, V b) {

@@ -114,6 +114,27 @@ cudaError_t launch_col_pass_tma(const Params2D<float> &p, const CUtensorMap &map
                                 cudaStream_t s);
 
 // --------------------------------------------------------------------------
+// 1D adjoint: loss sum_p 1 - |<target|psi_N>|^2 and dL/dV (rk4ip_adjoint.cu)
+// --------------------------------------------------------------------------
+template <typename R> struct AdjParams {
+    const cx<R> *psi0;     // [npaths][N]
+    const cx<R> *target;   // [N]
+    int64_t npaths;
+    int64_t nsteps;
+    int64_t K;             // checkpoint interval
+    const cx<R> *Etab;     // hi [N] then lo [N]
+    const tw_t<R> *tw;
+    LocalTerm<R> lt;       // deterministic: noise off
+    double dx;
+    cx<R> *ckpt;           // [ceil(nsteps/K)][npaths][N]
+    cx<R> *interm;         // [npaths][K][4][N]
+    double *loss;          // accumulated (zeroed by the caller)
+    double *dLdV;          // [nsteps][N], accumulated (zeroed by the caller)
+    cx<R> *dLdpsi0;        // [npaths][N] or nullptr
+};
+template <typename R> cudaError_t launch_adjoint_1d(int n, const AdjParams<R> &p, cudaStream_t s);
+
+// --------------------------------------------------------------------------
 // 0D: one thread per path (an ordinary SDE; D is a scalar factor).
 // --------------------------------------------------------------------------
 template <typename R> struct Params0D {

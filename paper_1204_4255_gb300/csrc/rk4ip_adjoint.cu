@@ -1,0 +1,252 @@
+// rk4ip_adjoint.cu -- gradient of a final-state fidelity with respect to a
+// space-time potential, through the discrete RK4IP scheme (1D lattices).
+//
+// Loss L = sum_p 1 - |<target|psi_N>|^2, <a|b> = sum conj(a) b dx, for the
+// deterministic equation d psi/dt = L psi - i (V(x, t_n) + g|psi|^2) psi
+// (XMDS2 Sec. 2.6, Eq. NonlinearSchrodingerEquationDimensionless with a
+// time-dependent trap; the step of Sec. 2.5/2.6 as in rk4ip_1d.cu).
+// Reverse mode on real vectors (Re, Im) with <u, v> = Re sum conj(u) v:
+//   N(u) = dt(-i(V + g|u|^2)u) has tangent A du + B conj(du), A = -i dt (V + 2g|u|^2),
+//   B = -i dt g u^2, adjoint mu -> conj(A) mu + B conj(mu); D^T = F^-1 conj(E) F;
+//   dN/dV_j = -i dt u_j, so a stage with cotangent mu adds dt (mu.x u.y - mu.y u.x)
+//   to dL/dV_j.
+// One CTA per path: a forward sweep keeps a checkpoint every K steps; then, per
+// segment from the last, the forward steps are recomputed from the checkpoint
+// with their four stage inputs (a, a_I + k1/2, a_I + k2/2, D(a_I + k3)) stored,
+// and the reverse steps consume them.  Every transform pair runs on two vectors
+// in lockstep, so a reverse step costs about one forward step.
+#include "fft.cuh"
+#include "kernels.h"
+
+namespace xsde {
+namespace {
+
+template <typename R> struct AdjMath {
+    using V = cx<R>;
+    // conj(A) mu + B conj(mu) at input u; dtV = dt (V + alpha xi), gdt = dt g
+    __device__ __forceinline__ static V adjN(V u, V mu, R dtV, R gdt) {
+        const R s = dtV + R(2) * gdt * cabs2(u);            // conj(A) = i s
+        const R bx = gdt * R(2) * u.x * u.y;                  // B = gdt (2 ux uy, -(ux^2 - uy^2))
+        const R by = -gdt * (u.x * u.x - u.y * u.y);
+        return mk<V>(-s * mu.y + bx * mu.x + by * mu.y, s * mu.x + by * mu.x - bx * mu.y);
+    }
+    // Re(conj(mu) (-i dt u)) / dt
+    __device__ __forceinline__ static R dv(V mu, V u) { return mu.x * u.y - mu.y * u.x; }
+};
+
+template <typename R, int N, int E>
+__global__ void __launch_bounds__(N / E) rk4ip_adjoint_kernel(const AdjParams<R> p) {
+    using V = cx<R>;
+    using M = AdjMath<R>;
+    constexpr int T = N / E;
+    constexpr int BUF = padded_len<N>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    tw_t<R> *tws = reinterpret_cast<tw_t<R> *>(smem_raw);
+    V *bufA = reinterpret_cast<V *>(tws + N);
+    V *bufB = bufA + BUF;
+    double *red = reinterpret_cast<double *>(bufB + BUF);
+    V *const sm2[2] = {bufA, bufB};
+    const SyncBlock sync{};
+    const TwiddleTable<tw_t<R>> tw{tws};
+    const PaddedLine L{};
+    const int t = threadIdx.x;
+    const int64_t path = blockIdx.x;
+
+    for (int i = t; i < N; i += blockDim.x) tws[i] = p.tw[i];
+    __syncthreads();
+
+    V Ek[E], El[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        Ek[m] = p.Etab[t + m * T];
+        El[m] = p.Etab[N + t + m * T];
+    }
+    const R gdt = p.lt.gdt, dt = p.lt.dt;
+    const R sixth = R(1) / R(6), third = R(1) / R(3), half = R(0.5);
+    const bool vtime = p.lt.pot == PM_TABLE && p.lt.V_nt > 1;
+    auto dtV_at = [&](int m, int64_t n) -> R {
+        const int j = t + m * T;
+        const int idx[3] = {j, 0, 0};
+        return dt * (vtime ? p.lt.V[n * N + j] : potential(p.lt, 1, idx, j, 0));
+    };
+    auto nl = [&](V u, R dtv) -> V {   // N(u) = dt(-i(V + g|u|^2)u)
+        const R s = dtv + gdt * cabs2(u);
+        return mk<V>(s * u.y, -s * u.x);
+    };
+    // D (S = -1 then +1 with E) or its adjoint (conj(E)) on both vectors
+    auto Dpair = [&](V (&x)[2][E], bool adjoint) {
+        fft<N, E, -1, 2>(x, t, sm2, L, sync, tw);
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            if (adjoint) {
+                x[0][m] = cmulconj_hilo(x[0][m], Ek[m], El[m]);
+                x[1][m] = cmulconj_hilo(x[1][m], Ek[m], El[m]);
+            } else {
+                x[0][m] = cmul_hilo(x[0][m], Ek[m], El[m]);
+                x[1][m] = cmul_hilo(x[1][m], Ek[m], El[m]);
+            }
+        }
+        fft<N, E, +1, 2>(x, t, sm2, L, sync, tw);
+    };
+    const size_t stride = (size_t)p.npaths * N;              // one field of all paths
+    V *interm = p.interm + (size_t)path * p.K * 4 * N;       // [K][4][N] for this path
+    // one forward step from x[0]; with `store`, keeps the stage inputs of step n
+    auto forward = [&](V (&x)[2][E], int64_t n, bool store, int64_t slot) {
+        R dtv[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            dtv[m] = dtV_at(m, n);
+            if (store) interm[(slot * 4 + 0) * N + t + m * T] = x[0][m];
+            x[1][m] = nl(x[0][m], dtv[m]);
+        }
+        Dpair(x, false);
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const V aI = x[0][m], k1 = x[1][m];
+            const V w2 = caxpy(aI, half, k1);
+            const V k2 = nl(w2, dtv[m]);
+            const V w3 = caxpy(aI, half, k2);
+            const V k3 = nl(w3, dtv[m]);
+            if (store) {
+                interm[(slot * 4 + 1) * N + t + m * T] = w2;
+                interm[(slot * 4 + 2) * N + t + m * T] = w3;
+            }
+            x[0][m] = cadd(aI, k3);
+            x[1][m] = caxpy(caxpy(caxpy(aI, sixth, k1), third, k2), third, k3);
+        }
+        Dpair(x, false);
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            if (store) interm[(slot * 4 + 3) * N + t + m * T] = x[0][m];
+            x[0][m] = caxpy(x[1][m], sixth, nl(x[0][m], dtv[m]));
+        }
+    };
+
+    // ---- forward sweep with checkpoints ------------------------------------
+    V x[2][E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) x[0][m] = p.psi0[path * N + t + m * T];
+    for (int64_t n = 0; n < p.nsteps; ++n) {
+        if (n % p.K == 0) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) p.ckpt[(n / p.K) * stride + path * N + t + m * T] = x[0][m];
+        }
+        forward(x, n, false, 0);
+    }
+
+    // ---- loss and the final cotangent ----------------------------------------
+    double cr = 0.0, ci = 0.0;
+    V tg[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        tg[m] = p.target[t + m * T];
+        const V a = x[0][m];     // conj(tg) a
+        cr += (double)tg[m].x * a.x + (double)tg[m].y * a.y;
+        ci += (double)tg[m].x * a.y - (double)tg[m].y * a.x;
+    }
+    cr = warp_sum(cr);
+    ci = warp_sum(ci);
+    if ((t & 31) == 0) {
+        red[2 * (t >> 5)] = cr;
+        red[2 * (t >> 5) + 1] = ci;
+    }
+    __syncthreads();
+    cr = 0.0;
+    ci = 0.0;
+    for (int w = 0; w < T / 32; ++w) {   // T = N/8 >= 32 for the supported lengths
+        cr += red[2 * w];
+        ci += red[2 * w + 1];
+    }
+    cr *= p.dx;
+    ci *= p.dx;
+    if (t == 0) atomicAdd(p.loss, 1.0 - (cr * cr + ci * ci));
+    // lambda_N = -2 c target dx
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        const double lr = -2.0 * p.dx * (cr * tg[m].x - ci * tg[m].y);
+        const double li = -2.0 * p.dx * (cr * tg[m].y + ci * tg[m].x);
+        x[0][m] = mk<V>((R)lr, (R)li);
+    }
+
+    // ---- reverse sweep, segment by segment -----------------------------------
+    const int64_t nseg = (p.nsteps + p.K - 1) / p.K;
+    V lam[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) lam[m] = x[0][m];
+    for (int64_t sgi = nseg - 1; sgi >= 0; --sgi) {
+        const int64_t n0 = sgi * p.K;
+        const int64_t n1 = (n0 + p.K < p.nsteps) ? n0 + p.K : p.nsteps;
+#pragma unroll
+        for (int m = 0; m < E; ++m) x[0][m] = p.ckpt[sgi * stride + path * N + t + m * T];
+        for (int64_t n = n0; n < n1; ++n) forward(x, n, true, n - n0);
+        for (int64_t n = n1 - 1; n >= n0; --n) {
+            const int64_t slot = n - n0;
+            R dtv[E], gv[E];
+            V y[2][E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                dtv[m] = dtV_at(m, n);
+                const V Du1 = interm[(slot * 4 + 3) * N + t + m * T];
+                const V l4 = cscale(lam[m], sixth);
+                y[0][m] = lam[m];
+                y[1][m] = M::adjN(Du1, l4, dtv[m], gdt);
+                gv[m] = M::dv(l4, Du1);
+            }
+            Dpair(y, true);
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const V w2 = interm[(slot * 4 + 1) * N + t + m * T];
+                const V w3 = interm[(slot * 4 + 2) * N + t + m * T];
+                const V la = y[0][m], lu = y[1][m];
+                const V lk3 = caxpy(lu, third, la);
+                const V lw3 = M::adjN(w3, lk3, dtv[m], gdt);
+                gv[m] += M::dv(lk3, w3);
+                const V lk2 = caxpy(cscale(la, third), half, lw3);
+                const V lw2 = M::adjN(w2, lk2, dtv[m], gdt);
+                gv[m] += M::dv(lk2, w2);
+                y[0][m] = caxpy(cscale(la, sixth), half, lw2);        // lambda_k1
+                y[1][m] = cadd(cadd(cadd(la, lu), lw3), lw2);          // lambda_aI
+            }
+            Dpair(y, true);
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const V a = interm[(slot * 4 + 0) * N + t + m * T];
+                lam[m] = cadd(M::adjN(a, y[0][m], dtv[m], gdt), y[1][m]);
+                gv[m] += M::dv(y[0][m], a);
+                atomicAdd(p.dLdV + n * N + t + m * T, (double)(gv[m] * dt));
+            }
+        }
+    }
+    if (p.dLdpsi0) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) p.dLdpsi0[path * N + t + m * T] = lam[m];
+    }
+}
+
+template <typename R, int N> cudaError_t adj_launch(const AdjParams<R> &p, cudaStream_t s) {
+    constexpr int E = 8, T = N / E;
+    const size_t smem = (size_t)N * sizeof(tw_t<R>) + (size_t)2 * padded_len<N>() * sizeof(cx<R>) +
+                        (size_t)2 * ((T + 31) / 32) * sizeof(double);
+    auto kern = rk4ip_adjoint_kernel<R, N, E>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)p.npaths, T, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename R> cudaError_t launch_adjoint_1d(int n, const AdjParams<R> &p, cudaStream_t s) {
+    switch (n) {
+        case 256: return adj_launch<R, 256>(p, s);
+        case 512: return adj_launch<R, 512>(p, s);
+        case 1024: return adj_launch<R, 1024>(p, s);
+        case 2048: return adj_launch<R, 2048>(p, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template cudaError_t launch_adjoint_1d<float>(int, const AdjParams<float> &, cudaStream_t);
+template cudaError_t launch_adjoint_1d<double>(int, const AdjParams<double> &, cudaStream_t);
+
+}  // namespace xsde

@@ -30,7 +30,7 @@ EXPORTED = (
     "xsde_problem_create", "xsde_problem_destroy", "xsde_set_operators", "xsde_moments",
     "xsde_integrate", "xsde_synchronize", "xsde_last_error", "xsde_version",
     "xsde_profile", "xsde_profile_report", "xsde_kernel_name", "xsde_set_kernel_variant",
-    "xsde_integrate_static_scratch",
+    "xsde_integrate_static_scratch", "xsde_adjoint",
 )
 XSDE_KERNEL_KINDS = 9
 
@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH):
         "xsde_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
         "xsde_set_kernel_variant": (ctypes.c_int, [vp, ctypes.c_int]),
         "xsde_integrate_static_scratch": (ctypes.c_int, [vp, vp, dp, i64, i64, i64, u64, vp]),
+        "xsde_adjoint": (ctypes.c_int, [vp, vp, vp, dp, i64, i32, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -206,6 +207,13 @@ def xsde_integrate_static_scratch(prob, vec, dt: float, nsteps: int, npaths: int
     (no device allocation; for callers that cannot call cudaMalloc)."""
     _check(load().xsde_integrate_static_scratch(prob, vec, dt, nsteps, npaths, path_offset, step_offset,
                                                 ctypes.c_void_p(stream or None)))
+
+
+def xsde_adjoint(prob, psi0_vec, target_vec, dt: float, nsteps: int, ckpt_every: int, loss_ptr: int,
+                 dLdV_ptr: int, dLdpsi0_ptr: int = 0, stream: int = 0) -> None:
+    _check(load().xsde_adjoint(prob, psi0_vec, target_vec, dt, nsteps, ckpt_every, ctypes.c_void_p(loss_ptr),
+                               ctypes.c_void_p(dLdV_ptr), ctypes.c_void_p(dLdpsi0_ptr or None),
+                               ctypes.c_void_p(stream or None)))
 
 
 def xsde_synchronize(prob, stream: int = 0) -> None:
@@ -326,3 +334,63 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+
+def adjoint(problem: Problem, psi0, target, dt: float, nsteps: int, ckpt_every: int = 50, stream=None):
+    """Loss sum_p 1 - |<target|psi_N>|^2 and dL/dV [nsteps, N] (FP64 CUDA tensors)
+    through xsde_adjoint; psi0 [npaths, N], target [N] CUDA complex tensors."""
+    import torch
+    codes = {torch.complex64: XSDE_C64, torch.complex128: XSDE_C128}
+    code = codes[psi0.dtype]
+    tgt = target.reshape(1, -1).contiguous()
+    loss = torch.zeros(1, dtype=torch.float64, device=psi0.device)
+    dLdV = torch.empty((nsteps, tgt.shape[1]), dtype=torch.float64, device=psi0.device)
+    v0 = xsde_vector_wrap(problem.grid, code, 1, psi0.shape[0], psi0.data_ptr())
+    vt = xsde_vector_wrap(problem.grid, code, 1, 1, tgt.data_ptr())
+    try:
+        xsde_adjoint(problem.prob, v0, vt, dt, nsteps, ckpt_every, loss.data_ptr(), dLdV.data_ptr(), 0,
+                     _stream_handle(stream))
+    finally:
+        xsde_vector_free(v0)
+        xsde_vector_free(vt)
+    return loss, dLdV
+
+
+def _make_rk4ip_adjoint():
+    import torch
+
+    class RK4IPAdjoint(torch.autograd.Function):
+        """loss = RK4IPAdjoint.apply(V, psi0, target, spec): the fidelity loss of
+        the RK4IP run driven by the space-time potential V [nsteps, N] (CUDA, the
+        problem's real type); backward returns dL/dV from the hand-written
+        adjoint kernel (xsde_adjoint).  spec = dict(npts, xmin, xmax, dtype, c2,
+        g, dt, ckpt_every)."""
+
+        @staticmethod
+        def forward(ctx, V, psi0, target, spec):
+            P = Problem((spec["npts"],), (spec["xmin"],), (spec["xmax"],), spec.get("dtype", "c64"))
+            try:
+                P.set_operators(c2=spec.get("c2", -0.5j), g=spec["g"], pot_kind=XSDE_POT_TABLE,
+                                V=V.detach().contiguous())
+                loss, dLdV = adjoint(P, psi0, target, spec["dt"], V.shape[0], spec.get("ckpt_every", 50))
+                torch.cuda.current_stream().synchronize()
+                P.synchronize()
+            finally:
+                P.close()
+            ctx.save_for_backward(dLdV)
+            return loss[0].to(V.dtype)
+
+        @staticmethod
+        def backward(ctx, grad):
+            (dLdV,) = ctx.saved_tensors
+            return (grad.to(torch.float64) * dLdV).to(grad.dtype), None, None, None
+
+    return RK4IPAdjoint
+
+
+def __getattr__(name):
+    if name == "RK4IPAdjoint":
+        cls = _make_rk4ip_adjoint()
+        globals()["RK4IPAdjoint"] = cls
+        return cls
+    raise AttributeError(name)
