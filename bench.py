@@ -130,6 +130,43 @@ def cpu_baseline(budget_s: float = 12.0) -> dict:
             "sample": f"1 instance of 512x512, {steps} RK4IP steps, FP64, {el:.1f} s"}
 
 
+def adjoint_cost(dtype: str = "c64", reps: int = 5) -> dict:
+    """Control workload (1D GPE, 1024 points, V on a 1024 x 500 space-time grid,
+    500 steps, checkpoints every 50): device time of loss + dL/dV through
+    xsde_adjoint over a plain 500-step forward run through xsde_integrate."""
+    import torch
+    import workloads as W
+    from paper_1204_4255_gb300 import xsde
+    w = W.adjoint_control()
+    tdt = torch.complex64 if dtype == "c64" else torch.complex128
+    rdt = torch.float32 if dtype == "c64" else torch.float64
+    P = xsde.Problem(w.n, w.xmin, w.xmax, dtype)
+    V = torch.from_numpy(w.V).to(rdt).cuda()
+    P.set_operators(c2=w.c2, g=w.gnl, pot_kind=xsde.XSDE_POT_TABLE, V=V)
+    p0 = torch.from_numpy(w.psi0).to(tdt).cuda()
+    tg = torch.from_numpy(w.extra["target"]).to(tdt).cuda()
+    psi = p0.clone()
+    for _ in range(2):
+        P.integrate(psi, w.dt, w.nsteps)
+        xsde.adjoint(P, p0, tg, w.dt, w.nsteps, w.extra["ckpt_every"])
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    e[0].record()
+    for _ in range(reps):
+        P.integrate(psi, w.dt, w.nsteps)
+    e[1].record()
+    e[2].record()
+    for _ in range(reps):
+        xsde.adjoint(P, p0, tg, w.dt, w.nsteps, w.extra["ckpt_every"])
+    e[3].record()
+    torch.cuda.synchronize()
+    P.synchronize()
+    P.close()
+    tf, ta = e[0].elapsed_time(e[1]) / reps, e[2].elapsed_time(e[3]) / reps
+    return {"workload": "1D GPE 1024 pts, V(x,t) 1024x500, 500 steps, ckpt 50", "dtype": dtype,
+            "forward_ms": tf, "loss_and_gradient_ms": ta, "cost_ratio": ta / tf}
+
+
 def run_reference(args) -> None:
     rank, world, _ = _dist()
     if rank != 0:
@@ -269,6 +306,7 @@ def run_gpu(args) -> None:
 
     if rank == 0:
         cpu = cpu_baseline() if world == 1 and not args.no_cpu_baseline else None
+        adj = adjoint_cost("c64") if not args.no_e2e else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -279,7 +317,7 @@ def run_gpu(args) -> None:
                        "parallelism": f"paths sharded over {world} GPU(s), no collective"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]},
-            "norm_check": ok,
+            "norm_check": ok, "adjoint": adj,
         }
         print(json.dumps(line), flush=True)
     prob.close()

@@ -126,12 +126,16 @@ __global__ void __launch_bounds__(N / E) rk4ip_adjoint_kernel(const AdjParams<R>
     V x[2][E];
 #pragma unroll
     for (int m = 0; m < E; ++m) x[0][m] = p.psi0[path * N + t + m * T];
+    // the last segment keeps its stage inputs right away: the reverse sweep
+    // starts there and needs no recomputation of it
+    const int64_t nseg = (p.nsteps + p.K - 1) / p.K;
+    const int64_t last0 = (nseg - 1) * p.K;
     for (int64_t n = 0; n < p.nsteps; ++n) {
         if (n % p.K == 0) {
 #pragma unroll
             for (int m = 0; m < E; ++m) p.ckpt[(n / p.K) * stride + path * N + t + m * T] = x[0][m];
         }
-        forward(x, n, false, 0);
+        forward(x, n, n >= last0, n - last0);
     }
 
     // ---- loss and the final cotangent ----------------------------------------
@@ -169,22 +173,27 @@ __global__ void __launch_bounds__(N / E) rk4ip_adjoint_kernel(const AdjParams<R>
     }
 
     // ---- reverse sweep, segment by segment -----------------------------------
-    const int64_t nseg = (p.nsteps + p.K - 1) / p.K;
     V lam[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) lam[m] = x[0][m];
     for (int64_t sgi = nseg - 1; sgi >= 0; --sgi) {
         const int64_t n0 = sgi * p.K;
         const int64_t n1 = (n0 + p.K < p.nsteps) ? n0 + p.K : p.nsteps;
+        if (sgi != nseg - 1) {
 #pragma unroll
-        for (int m = 0; m < E; ++m) x[0][m] = p.ckpt[sgi * stride + path * N + t + m * T];
-        for (int64_t n = n0; n < n1; ++n) forward(x, n, true, n - n0);
+            for (int m = 0; m < E; ++m) x[0][m] = p.ckpt[sgi * stride + path * N + t + m * T];
+            for (int64_t n = n0; n < n1; ++n) forward(x, n, true, n - n0);
+        }
         for (int64_t n = n1 - 1; n >= n0; --n) {
             const int64_t slot = n - n0;
             R dtv[E], gv[E];
-            V y[2][E];
+            V y[2][E], w2s[E], w3s[E];
 #pragma unroll
             for (int m = 0; m < E; ++m) {
+                // the later stage inputs are fetched now; their latency hides
+                // behind the first transform pair
+                w2s[m] = interm[(slot * 4 + 1) * N + t + m * T];
+                w3s[m] = interm[(slot * 4 + 2) * N + t + m * T];
                 dtv[m] = dtV_at(m, n);
                 const V Du1 = interm[(slot * 4 + 3) * N + t + m * T];
                 const V l4 = cscale(lam[m], sixth);
@@ -195,8 +204,8 @@ __global__ void __launch_bounds__(N / E) rk4ip_adjoint_kernel(const AdjParams<R>
             Dpair(y, true);
 #pragma unroll
             for (int m = 0; m < E; ++m) {
-                const V w2 = interm[(slot * 4 + 1) * N + t + m * T];
-                const V w3 = interm[(slot * 4 + 2) * N + t + m * T];
+                const V w2 = w2s[m];
+                const V w3 = w3s[m];
                 const V la = y[0][m], lu = y[1][m];
                 const V lk3 = caxpy(lu, third, la);
                 const V lw3 = M::adjN(w3, lk3, dtv[m], gdt);
