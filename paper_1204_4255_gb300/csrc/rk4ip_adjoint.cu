@@ -190,10 +190,13 @@ __global__ void __launch_bounds__(N / E) rk4ip_adjoint_kernel(const AdjParams<R>
             V y[2][E], w2s[E], w3s[E];
 #pragma unroll
             for (int m = 0; m < E; ++m) {
-                // the later stage inputs are fetched now; their latency hides
-                // behind the first transform pair
-                w2s[m] = interm[(slot * 4 + 1) * N + t + m * T];
-                w3s[m] = interm[(slot * 4 + 2) * N + t + m * T];
+                // FP64: the later stage inputs are fetched now so their latency
+                // hides behind the first transform pair (FP32 fetches them late:
+                // the extra live registers cost more than the latency there)
+                if constexpr (sizeof(R) == 8) {
+                    w2s[m] = interm[(slot * 4 + 1) * N + t + m * T];
+                    w3s[m] = interm[(slot * 4 + 2) * N + t + m * T];
+                }
                 dtv[m] = dtV_at(m, n);
                 const V Du1 = interm[(slot * 4 + 3) * N + t + m * T];
                 const V l4 = cscale(lam[m], sixth);
@@ -204,8 +207,8 @@ __global__ void __launch_bounds__(N / E) rk4ip_adjoint_kernel(const AdjParams<R>
             Dpair(y, true);
 #pragma unroll
             for (int m = 0; m < E; ++m) {
-                const V w2 = w2s[m];
-                const V w3 = w3s[m];
+                const V w2 = (sizeof(R) == 8) ? w2s[m] : interm[(slot * 4 + 1) * N + t + m * T];
+                const V w3 = (sizeof(R) == 8) ? w3s[m] : interm[(slot * 4 + 2) * N + t + m * T];
                 const V la = y[0][m], lu = y[1][m];
                 const V lk3 = caxpy(lu, third, la);
                 const V lw3 = M::adjN(w3, lk3, dtv[m], gdt);
