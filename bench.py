@@ -37,6 +37,11 @@ N_GRID = 512
 METRIC = "RK4IP grid-point-steps/s"
 UNIT = "pt-steps/s"
 BYTES_PER_PT_PASS = {"c64": 32, "c128": 64}   # 2 fields in + 2 out per pass
+# DRAM read + write per launch measured by ncu for the default configuration
+# (profiles/gpe2d_512x512x64_c64_launch_list.md); reported only for that
+# configuration and only while the kernels are unchanged since the capture.
+MEASURED_TRAFFIC = {("c64", 64, "col_propagate"): 472.4e6, ("c64", 64, "row_steady"): 472.2e6,
+                    ("c64", 64, "row_stage2"): 472.1e6}
 
 
 def _dist():
@@ -279,8 +284,9 @@ def run_gpu(args) -> None:
     if dom in ("row_prologue", "row_epilogue", "row_fft_only", "col_spectral"):
         alg_bytes //= 2
     achieved = alg_bytes / (dom_ms / dom_n / 1e3) / 1e9
+    traffic = MEASURED_TRAFFIC.get((dtype, P, dom)) if STEPS_PER_CALL == 100 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": dom, "peak_source": f"hbm_gbs of {peak_kind}",
+                "traffic": traffic, "kernel": dom, "peak_source": f"hbm_gbs of {peak_kind}",
                 "launch_ms": dom_ms / dom_n, "algorithmic_bytes_per_launch": alg_bytes,
                 "kernel_share": dom_ms / sum(v[0] for v in prof.values())}
 
