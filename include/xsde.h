@@ -124,8 +124,7 @@ typedef struct {
 
 /* ndim in 0..3 (0 = a single point: an ordinary SDE, dV = 1).  npts[d] is a
  * power of two in [16, 2048]; xmin[d] < xmax[d].  Arrays are read, not kept.
- * 3D lattices are accepted here but xsde_integrate reports XSDE_EUNSUPPORTED
- * for them.  *out is owned by the caller (xsde_grid_destroy). */
+ * *out is owned by the caller (xsde_grid_destroy). */
 int xsde_grid_create(int ndim, const int32_t *npts, const double *xmin, const double *xmax,
                      xsde_grid **out);
 void xsde_grid_destroy(xsde_grid *grid);

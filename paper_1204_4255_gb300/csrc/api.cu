@@ -244,6 +244,17 @@ template <typename V> int ensure_tables(xsde_problem *p, double dt, cudaStream_t
         }
         if ((rc = upload<V>(e0, &p->d_E[0], s)) != XSDE_OK) return rc;
         if ((rc = upload<V>(e1, &p->d_E[1], s)) != XSDE_OK) return rc;
+    } else if (g.ndim == 3) {
+        // exp(L dt/2) = E0(k0) E1(k1) E2(k2); E0 carries exp(c0 dt/2)/(n0 n1 n2)
+        for (int d = 0; d < 3; ++d) {
+            std::vector<std::complex<double>> e(g.n[d]);
+            for (int i = 0; i < g.n[d]; ++i) {
+                const double k = kval(g, d, i);
+                e[i] = d == 0 ? std::exp((c0 + c2 * (k * k)) * (0.5 * dt)) / ((double)g.n[0] * g.n[1] * g.n[2])
+                              : std::exp(c2 * (k * k) * (0.5 * dt));
+            }
+            if ((rc = upload<V>(e, &p->d_E[d], s)) != XSDE_OK) return rc;
+        }
     }
     p->table_dt = dt;
     return XSDE_OK;
@@ -322,6 +333,92 @@ bool encode_field_map(CUtensorMap *m, void *base, const xsde_grid &g, int64_t np
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 3D: per exp(L dt/2) application a row pass along dimension 2 (with E2) and
+// column passes along dimensions 1 and 0 (E1, E0): the three one-dimensional
+// propagators commute.  Sampling splits the run into chunks that end in real
+// space; a sample is the row pass's local terms plus a forward transform
+// (dimension 2 rows, dimension 1 columns) and the kinetic reduction along
+// dimension 0.
+template <typename R>
+int run_3d(xsde_problem *p, void *psi, int64_t nsteps, int64_t npaths, uint64_t step0, const LocalTerm<R> &lt,
+           const Sampling &sm, cudaStream_t s) {
+    using V = cx<R>;
+    const xsde_grid &g = p->grid;
+    const size_t need = (size_t)npaths * g.npts * sizeof(V);
+    if (p->scratch_bytes < need) {
+        if (p->d_scratch) {
+            XSDE_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize(scratch)");
+            cudaFree(p->d_scratch);
+            p->d_scratch = nullptr;
+            p->scratch_bytes = 0;
+        }
+        XSDE_CUDA(cudaMalloc(&p->d_scratch, need), "cudaMalloc(scratch)");
+        p->scratch_bytes = need;
+    }
+    Params2D<R> base;
+    base.A = static_cast<V *>(psi);
+    base.B = static_cast<V *>(p->d_scratch);
+    base.lt = lt;
+    base.sm = sm;
+    base.status = p->d_status;
+    base.sample_slot = -1;
+    base.sg = 0;
+    base.ndim = 3;
+    Params2D<R> qr = base, q1 = base, q0 = base;
+    qr.npaths = npaths;                       // rows: lines along dimension 2
+    qr.n0 = g.n[0] * g.n[1];
+    qr.n1 = g.n[2];
+    qr.nmid = g.n[1];
+    qr.tw1 = static_cast<const tw_t<R> *>(p->d_tw[2]);
+    qr.E1 = static_cast<const V *>(p->d_E[2]);
+    q1.npaths = npaths * g.n[0];              // columns along dimension 1, one slab per (path, i0)
+    q1.n0 = g.n[1];
+    q1.n1 = g.n[2];
+    q1.tw0 = static_cast<const tw_t<R> *>(p->d_tw[1]);
+    q1.E0 = static_cast<const V *>(p->d_E[1]);
+    q0.npaths = npaths;                       // columns along dimension 0
+    q0.n0 = g.n[0];
+    q0.n1 = g.n[1] * g.n[2];
+    q0.tw0 = static_cast<const tw_t<R> *>(p->d_tw[0]);
+    q0.E0 = static_cast<const V *>(p->d_E[0]);
+    q0.kinner = g.n[2];
+    auto row = [&](int mode, uint64_t sg, int slot) -> cudaError_t {
+        qr.sg = sg;
+        qr.sample_slot = slot;
+        return timed(p, 2 + mode, s, [&] { return launch_row_pass<R>(mode, qr, s); });
+    };
+    auto col = [&](Params2D<R> &q, int mode, int slot) -> cudaError_t {
+        q.sample_slot = slot;
+        return timed(p, 7 + (mode == COL_SPECTRAL ? 1 : 0), s, [&] { return launch_col_pass<R>(mode, q, s); });
+    };
+    auto sample = [&](int slot, uint64_t gs) -> int {
+        XSDE_CUDA(row(ROW_FFT_ONLY, gs, slot), "row pass");
+        XSDE_CUDA(col(q1, COL_FFT_FWD, -1), "col pass");
+        XSDE_CUDA(col(q0, COL_SPECTRAL, slot), "col pass");
+        return XSDE_OK;
+    };
+    const int S = sm.every;
+    const int64_t chunk = S > 0 ? S : (nsteps > 0 ? nsteps : 1);
+    int rc;
+    for (int64_t c0 = 0; c0 < nsteps || (S > 0 && c0 == nsteps); c0 += chunk) {
+        if (S > 0 && (rc = sample((int)(c0 / S), step0 + c0)) != XSDE_OK) return rc;
+        if (c0 == nsteps) break;
+        const int64_t len = (c0 + chunk <= nsteps) ? chunk : nsteps - c0;
+        XSDE_CUDA(row(ROW_PROLOGUE, step0 + c0, -1), "row pass");
+        for (int64_t n = 0; n < len; ++n) {
+            const uint64_t sg = step0 + c0 + n;
+            XSDE_CUDA(col(q1, COL_PROPAGATE, -1), "col pass");
+            XSDE_CUDA(col(q0, COL_PROPAGATE, -1), "col pass");
+            XSDE_CUDA(row(ROW_STAGE2, sg, -1), "row pass");
+            XSDE_CUDA(col(q1, COL_PROPAGATE, -1), "col pass");
+            XSDE_CUDA(col(q0, COL_PROPAGATE, -1), "col pass");
+            XSDE_CUDA(row(n + 1 < len ? ROW_STEADY : ROW_EPILOGUE, sg, -1), "row pass");
+        }
+        if (S > 0 && c0 + len == nsteps && nsteps % S != 0) break;
+    }
+    return XSDE_OK;
+}
+
 template <typename R>
 int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t npaths, int64_t path_offset,
                   uint64_t step0, cudaStream_t s) {
@@ -370,6 +467,7 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
         XSDE_CUDA(timed(p, 1, s, [&] { return launch_rk4ip_1d<R>(g.n[0], q, s); }), "rk4ip_1d launch");
         return XSDE_OK;
     }
+    if (g.ndim == 3) return run_3d<R>(p, psi, nsteps, npaths, step0, lt, sm, s);
     // 2D: scratch field B (same shape as psi)
     const size_t need = (size_t)npaths * g.npts * sizeof(V);
     if (p->scratch_bytes < need) {
@@ -645,7 +743,8 @@ int xsde_integrate(xsde_problem *p, xsde_vector *psi, double dt, int64_t nsteps,
     if (p->N.pot_kind == XSDE_POT_TABLE && p->N.V_nt > 1 && step_offset + (uint64_t)nsteps > (uint64_t)p->N.V_nt)
         return fail(XSDE_EINVAL, "xsde_integrate: potential table has %lld rows, steps up to %llu needed",
                     (long long)p->N.V_nt, (unsigned long long)(step_offset + nsteps));
-    if (p->grid.ndim == 3) return fail(XSDE_EUNSUPPORTED, "xsde_integrate: 3D lattices are not implemented");
+    if (p->grid.ndim == 3 && npaths * p->grid.n[0] > 65535)
+        return fail(XSDE_EUNSUPPORTED, "xsde_integrate: at most 65535 paths x n0 slabs per call on a 3D lattice");
     if (p->grid.ndim == 2 && npaths > 65535)
         return fail(XSDE_EUNSUPPORTED, "xsde_integrate: at most 65535 paths per call on a 2D lattice");
     if (p->samp.every > 0 && nsteps / p->samp.every + 1 > (int64_t)INT32_MAX)

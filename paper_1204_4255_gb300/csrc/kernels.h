@@ -80,7 +80,8 @@ enum RowMode {
 };
 enum ColMode {
     COL_PROPAGATE = 0,  // A, B -> F0^-1 E0 F0 (A, B)
-    COL_SPECTRAL = 1    // B: accumulate the kinetic energy only (no write)
+    COL_SPECTRAL = 1,   // B: accumulate the kinetic energy only (no write)
+    COL_FFT_FWD = 2     // B <- F0 B (the middle transform of a 3D spectral sample)
 };
 
 template <typename R> struct Params2D {
@@ -98,6 +99,15 @@ template <typename R> struct Params2D {
     int sample_slot;       // sample written by this pass (-1: none)
     uint64_t sg;           // global step index of the step this pass belongs to
     int *status;
+    // 3D lattices reuse these passes: a row pass transforms the contiguous
+    // dimension 2 (n0 := lines per path = N0*N1, n1 := N2, its line r is the
+    // point pair (r / nmid, r % nmid) with nmid = N1); a column pass transforms
+    // one strided dimension (n0 := its length, n1 := columns per slab, npaths :=
+    // slabs).  kinner = N2 in the spectral pass along dimension 0 splits its
+    // column index into (k1, k2); 0 for 2D.
+    int ndim = 2;
+    int nmid = 1;
+    int kinner = 0;
 };
 template <typename R> cudaError_t launch_row_pass(int mode, const Params2D<R> &p, cudaStream_t s);
 template <typename R> cudaError_t launch_col_pass(int mode, const Params2D<R> &p, cudaStream_t s);

@@ -77,7 +77,10 @@ __global__ void __launch_bounds__(RowCfg<N1>::THREADS) row_pass_kernel(const Par
     const bool active = row < nrows;
     const int64_t rrow = active ? row : 0;
     const int64_t path = rrow / p.n0;
+    // line within the path; its lattice indices are (i0) in 2D, (i0, i1) in 3D
     const int i0 = (int)(rrow - path * p.n0);
+    const int la = p.ndim == 3 ? i0 / p.nmid : i0;
+    const int lb = p.ndim == 3 ? i0 - la * p.nmid : 0;
     const uint32_t gp = (uint32_t)(p.lt.path_offset + path);
     V *Arow = p.A + rrow * N1;
     V *Brow = p.B + rrow * N1;
@@ -85,11 +88,12 @@ __global__ void __launch_bounds__(RowCfg<N1>::THREADS) row_pass_kernel(const Par
     const R sixth = R(1) / R(6), third = R(1) / R(3), half = R(0.5);
     const bool sample = p.sample_slot >= 0;
 
-    // raw potential of point (i0, t + m T) at global step gs
+    // raw potential of point (line, t + m T) at global step gs
     auto pot = [&](int m, uint64_t gs) -> R {
-        const int i1 = t + m * T;
-        const int idx[3] = {i0, i1, 0};
-        return potential(p.lt, 2, idx, (int64_t)i0 * N1 + i1, gs);
+        const int ic = t + m * T;
+        const int idx2[3] = {la, ic, 0};
+        const int idx3[3] = {la, lb, ic};
+        return potential(p.lt, p.ndim, p.ndim == 3 ? idx3 : idx2, (int64_t)i0 * N1 + ic, gs);
     };
     // static potentials are evaluated once per element; tables with one row per
     // step are read for the step at hand
@@ -228,9 +232,18 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
     const bool sample = p.sample_slot >= 0;
 
     auto kinetic = [&](const V (&f)[E]) {
-        // sum_k Re(i L(k)) |F psi|^2 dV / (n0 n1), accumulated into the energy of this path
-        const int k1i = col < n1 / 2 ? col : col - n1;
-        const double k1 = p.sm.kscale[1] * k1i;
+        // sum_k Re(i L(k)) |F psi|^2 dV / N, accumulated into the energy of this path.
+        // The column index is k1 (2D) or the pair (k1, k2) = (col / kinner, col % kinner) (3D).
+        double kc2;
+        if (p.kinner > 0) {
+            const int ia = col / p.kinner, ib = col - ia * p.kinner, nm = n1 / p.kinner;
+            const double ka = p.sm.kscale[1] * (ia < nm / 2 ? ia : ia - nm);
+            const double kb = p.sm.kscale[2] * (ib < p.kinner / 2 ? ib : ib - p.kinner);
+            kc2 = ka * ka + kb * kb;
+        } else {
+            const double k1 = p.sm.kscale[1] * (col < n1 / 2 ? col : col - n1);
+            kc2 = k1 * k1;
+        }
         // fields written by propagating row passes already carry the
         // dimension-1 factor of exp(L dt/2); divide its modulus back out
         const double w = (MODE == COL_SPECTRAL) ? 1.0 : 1.0 / (double)cabs2(p.E1[col]);
@@ -239,7 +252,7 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
         for (int m = 0; m < E; ++m) {
             const int kj = t + m * T;
             const double k0 = p.sm.kscale[0] * (kj < N0 / 2 ? kj : kj - N0);
-            s += (p.sm.h0 + p.sm.h2 * (k0 * k0 + k1 * k1)) * (double)cabs2(f[m]);
+            s += (p.sm.h0 + p.sm.h2 * (k0 * k0 + kc2)) * (double)cabs2(f[m]);
         }
         s *= w;
         s = warp_sum(s);
@@ -255,12 +268,17 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
         }
     };
 
-    if constexpr (MODE == COL_SPECTRAL) {
+    if constexpr (MODE == COL_SPECTRAL || MODE == COL_FFT_FWD) {
         V y[1][E];
 #pragma unroll
         for (int m = 0; m < E; ++m) y[0][m] = p.B[base + (int64_t)(t + m * T) * n1];
         fft<N0, E, -1, 1>(y, t, sm1, L, sync, tw);
-        kinetic(y[0]);
+        if constexpr (MODE == COL_SPECTRAL) {
+            kinetic(y[0]);
+        } else {
+#pragma unroll
+            for (int m = 0; m < E; ++m) p.B[base + (int64_t)(t + m * T) * n1] = y[0][m];
+        }
         return;
     } else {
         V x[2][E];
@@ -323,7 +341,12 @@ template <typename R, int N0, int MODE> cudaError_t col_launch(const Params2D<R>
 
 template <typename R, int N0> cudaError_t col_mode(int mode, const Params2D<R> &p, cudaStream_t s) {
     if (p.n1 % ColCfg<R, N0>::C) return cudaErrorInvalidValue;
-    return mode == COL_SPECTRAL ? col_launch<R, N0, COL_SPECTRAL>(p, s) : col_launch<R, N0, COL_PROPAGATE>(p, s);
+    switch (mode) {
+        case COL_PROPAGATE: return col_launch<R, N0, COL_PROPAGATE>(p, s);
+        case COL_SPECTRAL: return col_launch<R, N0, COL_SPECTRAL>(p, s);
+        case COL_FFT_FWD: return col_launch<R, N0, COL_FFT_FWD>(p, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace

@@ -257,3 +257,36 @@ def test_integrate_rejects_bad_arguments():
     P.integrate(psi, w.dt, 0)
     P.synchronize()
     P.close()
+
+
+# --------------------------------------------------------------------------- #
+# 3D: row pass along dimension 2, column passes along dimensions 1 and 0      #
+# --------------------------------------------------------------------------- #
+
+@pytest.mark.parametrize("shape", [(16, 32, 64), (32, 32, 32), (64, 16, 32)])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_3d_gpe_noise_and_moments(shape, dtype):
+    rng = np.random.default_rng(sum(shape))
+    axes = [-5 + np.arange(n) * 10 / n for n in shape]
+    X, Y, Z = np.meshgrid(*axes, indexing="ij")
+    base = np.exp(-(X ** 2 + 0.8 * Y ** 2 + 1.2 * Z ** 2) / 4)
+    psi0 = np.stack([base * np.exp(0.2j * rng.standard_normal(shape)) for _ in range(2)])
+    w = W.Workload("gpe3", shape, (-5.0,) * 3, (5.0,) * 3, 0j, -0.5j, 3.0, W.POT_HARMONIC, (1.0, 0.8, 1.2), None,
+                   W.NOISE_ADD_COMPLEX, 0.1, 55, 1e-3, 7, psi0.astype(np.complex128), 3)
+    got, pp, pq = gpu_run(w, dtype, sample_every=3, path0=2)
+    ref, opp, opq = O.run_workload(w, sample_every=3, path0=2)
+    tol = 1e-11 if dtype == "c128" else 1e-4
+    assert np.max(rel_l2(got.reshape(2, -1), ref.reshape(2, -1), axis=1)) < tol
+    assert np.max(np.abs(pp - opp) / np.abs(opp)) < tol
+    assert np.max(np.abs(pq - opq) / np.abs(opq)) < tol
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_3d_gpe_128_cubed(dtype):
+    """The 128^3 Thomas-Fermi GPE (V = r^2/2, g = 200, box [-10,10)^3) at full size."""
+    w = W.gpe_3d(nsteps=8)
+    got, pp, _ = gpu_run(w, dtype, sample_every=4, which=3)
+    ref, opp, _ = O.run_workload(w, sample_every=4)
+    tol = 1e-10 if dtype == "c128" else 1e-4
+    assert rel_l2(got, ref) < tol
+    assert np.allclose(pp, opp, rtol=tol, atol=0)
