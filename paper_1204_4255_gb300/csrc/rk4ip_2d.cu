@@ -205,8 +205,11 @@ template <typename R, int N0> struct ColCfg {
     static constexpr int TMAX = sizeof(R) == 4 ? 1024 : 512;
     static constexpr int E = 8;
     static constexpr int T = N0 / E;
-    static constexpr int C = (CMAX * T <= TMAX) ? CMAX : TMAX / T;
+    static constexpr int C0 = (CMAX * T <= TMAX) ? CMAX : TMAX / T;
+    // at least one full warp per CTA (the sample reductions use whole-warp shuffles)
+    static constexpr int C = (C0 * T < 32) ? 32 / T : C0;
     static constexpr int THREADS = C * T;
+    static_assert(THREADS % 32 == 0, "column tiles are whole warps");
 };
 
 template <typename R, int N0, int MODE>

@@ -152,10 +152,10 @@ def test_2d_gpe_shapes(shape, dtype):
     assert np.max(rel_l2(got.reshape(3, -1), ref.reshape(3, -1), axis=1)) < (1e-11 if dtype == "c128" else 1e-4)
 
 
+@pytest.mark.parametrize("shape", [(32, 64), (16, 64)])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-def test_2d_moments_and_noise(dtype):
+def test_2d_moments_and_noise(dtype, shape):
     rng = np.random.default_rng(9)
-    shape = (32, 64)
     psi0 = (1 + 0.2 * rng.standard_normal((4,) + shape) + 0.2j * rng.standard_normal((4,) + shape))
     w = W.Workload("tw2", shape, (-4.0, -8.0), (4.0, 8.0), 0j, -0.5j, 0.3, W.POT_HARMONIC, (0.5, 0.5), None,
                    W.NOISE_ADD_COMPLEX, 0.2, 1234, 2e-3, 15, psi0.astype(np.complex128), 5)
