@@ -172,6 +172,91 @@ def adjoint_cost(dtype: str = "c64", reps: int = 5) -> dict:
             "forward_ms": tf, "loss_and_gradient_ms": ta, "cost_ratio": ta / tf}
 
 
+def plain_vs_fused(P: int = 64, nsteps: int = 20) -> dict:
+    """The bench lattice (P instances of the 2D GPE at 512x512) through the fused
+    passes (xsde_integrate) and through the unfused comparison step
+    (xsde_integrate_plain: cuFFT + elementwise kernels), complex64 and
+    complex128, nsteps steps each after a warm-up call."""
+    import torch
+    from paper_1204_4255_gb300 import xsde
+    w = workload(P)
+    out = {"workload": f"2D GPE 512x512 x {P} instances, {nsteps} RK4IP steps"}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for kind, dtype in (("fused", "c64"), ("fused", "c128"), ("plain", "c64"), ("plain", "c128")):
+        prob = xsde.Problem(w.n, w.xmin, w.xmax, dtype)
+        prob.set_operators(c0=w.c0, c2=w.c2, g=w.gnl, pot_kind=w.pot_kind, omega=(1.0, 1.0, 0.0))
+        psi = torch.from_numpy(w.psi0).to(torch.complex64 if dtype == "c64" else torch.complex128).cuda()
+        call = prob.integrate if kind == "fused" else prob.integrate_plain
+        call(psi, w.dt, 2)
+        torch.cuda.synchronize()
+        e0.record()
+        call(psi, w.dt, nsteps, step_offset=2)
+        e1.record()
+        torch.cuda.synchronize()
+        prob.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[f"{kind}_{dtype}"] = {"value": P * w.npts * nsteps / (ms / 1e3), "unit": UNIT,
+                                  "ms_per_rk4ip_step": ms / nsteps}
+        prob.close()
+        del psi
+    torch.cuda.empty_cache()
+    return out
+
+
+def batched_cost(reps: int = 3) -> dict:
+    """Uneven instances advanced together (xsde_batch, autotuned, one CUDA graph
+    replay per call): one 3D GPE 128^3, 32 2D GPEs at 256^2 and 32 at 512^2, and
+    256 1D NLS instances at each of 256, 512, 1024 and 2048 points; complex64,
+    dt = 1e-4, 500 steps.  Aggregate pt-steps/s of the graph replay, and per
+    lattice class the same metric of the member integrated alone."""
+    import torch
+    import workloads as W
+    from paper_1204_4255_gb300 import xsde
+    ws = W.batched_instances()
+    probs, psis = [], []
+    for w in ws:
+        P = xsde.Problem(w.n, w.xmin, w.xmax, "c64")
+        P.set_operators(c0=w.c0, c2=w.c2, g=w.gnl, pot_kind=w.pot_kind,
+                        omega=tuple(w.omega) + (0.0,) * (3 - len(w.omega)))
+        probs.append(P)
+        psis.append(torch.from_numpy(w.psi0).to(torch.complex64).cuda())
+    dt, nsteps = ws[0].dt, ws[0].nsteps
+    B = xsde.Batch([(P, psi, 0) for P, psi in zip(probs, psis)], autotune=True)
+    B.integrate(dt, nsteps)                     # tunes, records and replays once
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for r in range(reps):
+        e0.record()
+        B.integrate(dt, nsteps, step_offset=0)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    B.synchronize()
+    ms = statistics.median(times)
+    pts = sum(w.npaths * w.npts for w in ws)
+    classes = {}
+    for w, P, psi in zip(ws, probs, psis):
+        P.integrate(psi, dt, nsteps)            # warm
+        e0.record()
+        P.integrate(psi, dt, nsteps)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        classes[w.name] = {"pts": w.npaths * w.npts, "ms_alone": t,
+                           "value_alone": w.npaths * w.npts * nsteps / (t / 1e3),
+                           "variant": P.autotune(psi, dt)}
+    for P in probs:
+        P.synchronize()
+    B.close()
+    for P in probs:
+        P.close()
+    return {"workload": "1x3D 128^3 + 32x2D 256^2 + 32x2D 512^2 + 4x256 1D NLS (256..2048), c64, dt=1e-4, "
+                        "500 steps, one graph replay", "points": pts, "steps": nsteps, "ms": ms,
+            "value": pts * nsteps / (ms / 1e3), "unit": UNIT,
+            "sum_of_alone_ms": sum(c["ms_alone"] for c in classes.values()), "classes": classes}
+
+
 def run_reference(args) -> None:
     rank, world, _ = _dist()
     if rank != 0:
@@ -313,6 +398,8 @@ def run_gpu(args) -> None:
     if rank == 0:
         cpu = cpu_baseline() if world == 1 and not args.no_cpu_baseline else None
         adj = adjoint_cost("c64") if not args.no_e2e else None
+        bat = batched_cost() if not args.no_batch else None
+        plain = plain_vs_fused() if not args.no_batch else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -323,7 +410,7 @@ def run_gpu(args) -> None:
                        "parallelism": f"paths sharded over {world} GPU(s), no collective"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]},
-            "norm_check": ok, "adjoint": adj,
+            "norm_check": ok, "adjoint": adj, "batched": bat, "plain_vs_fused": plain,
         }
         print(json.dumps(line), flush=True)
     prob.close()
@@ -343,6 +430,7 @@ def main():
                     help="RK4IP steps per xsde_integrate call (one bench step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched and plain-vs-fused figures")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -212,6 +212,19 @@ int xsde_integrate(xsde_problem *prob, xsde_vector *psi, double dt, int64_t nste
 int xsde_adjoint(xsde_problem *prob, const xsde_vector *psi0, const xsde_vector *target, double dt, int64_t nsteps,
                  int32_t ckpt_every, double *loss, double *dLdV, void *dLdpsi0, void *stream);
 
+/* As xsde_integrate (1D-3D lattices, no sampling group), computed the plain
+ * unfused way, for comparison with the fused passes: every transform is a
+ * cuFFT call over all paths and every other operation of the step (exp(L dt/2)
+ * from a table over all k, each N(u) = dt g(u), each Runge-Kutta combination)
+ * is its own elementwise kernel with its operands in device memory.  The same
+ * scheme (Secs. 2.5-2.6), noise counters and potential as xsde_integrate; the
+ * results agree to rounding.  Allocates a cuFFT plan, four work fields and the
+ * table on first use (or when the shape or dt changes) and waits for `stream`
+ * then.  A registered sampling group, or a 0D lattice, reports
+ * XSDE_EUNSUPPORTED. */
+int xsde_integrate_plain(xsde_problem *prob, xsde_vector *psi, double dt, int64_t nsteps, int64_t npaths,
+                         int64_t path_offset, uint64_t step_offset, void *stream);
+
 /* As xsde_integrate, for 2D lattices, without allocating device memory.  The
  * paper has no counterpart; this call exists for callers that cannot call
  * cudaMalloc when they integrate (a fixed device-memory budget or a caller-owned
@@ -237,11 +250,70 @@ int xsde_integrate_static_scratch(xsde_problem *prob, xsde_vector *psi, double d
  * wait gave up.  Clears the device error word. */
 int xsde_synchronize(xsde_problem *prob, void *stream);
 
-/* Kernel implementation for this problem: 0 (default) uses the fastest kernels
- * available for the lattice and precision (e.g. the persistent TMA-pipelined
- * complex64 2D passes); 1 forces the generic kernels.  Both compute the same
- * scheme; the switch exists to cross-check and to compare them. */
+/* Kernel implementation for this problem, in [0, xsde_kernel_variants(prob)).
+ * All variants compute the same scheme; they differ in launch shape:
+ *   1D lattices (4 variants): one CTA carries the default number of paths
+ *     (filling 128 threads; one path for N >= 1024), or a half (variant 1),
+ *     a quarter (variant 2, at least one path) or twice (variant 3, at most
+ *     256 threads) as many; where a bound applies a variant repeats another;
+ *   2D lattices (2 variants): 0 uses the fastest kernels available (the
+ *     persistent TMA-pipelined complex64 passes where they apply), 1 forces
+ *     the generic passes;
+ *   0D and 3D lattices (1 variant).
+ * Out-of-range variants report XSDE_EINVAL.  xsde_autotune picks one by
+ * timing. */
 int xsde_set_kernel_variant(xsde_problem *prob, int variant);
+/* Number of kernel variants of the problem's lattice (0 if prob is NULL). */
+int xsde_kernel_variants(const xsde_problem *prob);
+
+/* ---- autotuning and batches ---------------------------------------------- */
+
+/* Time every kernel variant of the problem (xsde_set_kernel_variant) over
+ * nsteps >= 1 steps of size dt, on a device copy of psi (psi is read, not
+ * modified; sampling and profiling are suspended meanwhile), and select the
+ * fastest.  best (host, or NULL) receives its index; ms (host array of
+ * xsde_kernel_variants(prob) doubles, or NULL) the best of three timed runs of
+ * each variant.  With ms == NULL an earlier result for the same device,
+ * lattice, precision and path count is reused: from this process, or from the
+ * file named by the environment variable XSDE_AUTOTUNE_CACHE (text lines
+ * "key variant", appended as results are found).  Allocates one field-sized
+ * temporary and waits for `stream`. */
+int xsde_autotune(xsde_problem *prob, const xsde_vector *psi, double dt, int64_t nsteps, int *best, double *ms,
+                  void *stream);
+
+/* A batch advances several independent problems together (the paper's paths
+ * and separate simulations, Secs. 2.5 and 3): uneven lattices (0D..3D, any
+ * sizes, either precision) in one replay of a CUDA graph whose branches are the
+ * members' pass schedules, so their kernels overlap on the GPU.  Each member
+ * names its own problem (its operators, sampling group, kernel variant and
+ * scratch) and its field; the results equal those of one xsde_integrate per
+ * member.  The paper has no batching call: its simulations run one at a time. */
+typedef struct xsde_batch xsde_batch;
+typedef struct {
+    xsde_problem *prob;    /* borrowed; distinct across members */
+    xsde_vector *psi;      /* borrowed; advanced in place; distinct across members */
+    int64_t path_offset;   /* global path index of the field's path 0 */
+} xsde_batch_member;
+
+#define XSDE_BATCH_AUTOTUNE 1  /* xsde_autotune every member before the first replay */
+
+/* Bind n >= 1 members (the array is copied; problems and fields must outlive
+ * the batch and live on the current device).  Members that share a problem or
+ * a field report XSDE_EINVAL. */
+int xsde_batch_create(const xsde_batch_member *members, int n, int flags, xsde_batch **out);
+
+/* Advance every member by nsteps steps of size dt from global step step_offset
+ * (as xsde_integrate with npaths = the field's npaths), asynchronously on
+ * `stream`.  The first call, and any call after a member's operators,
+ * sampling group, kernel variant, field or workspace changed or with other
+ * (dt, nsteps, step_offset), records the graph again (and, with
+ * XSDE_BATCH_AUTOTUNE, the first call tunes the members); otherwise the call
+ * is one graph launch.  Recording waits for `stream`.  Device-side errors are
+ * reported per member by xsde_synchronize(member problem, stream). */
+int xsde_batch_integrate(xsde_batch *batch, double dt, int64_t nsteps, uint64_t step_offset, void *stream);
+
+/* Wait for the device, then free the batch (not its members). */
+void xsde_batch_destroy(xsde_batch *batch);
 
 /* ---- launch profiling ------------------------------------------------------ */
 

@@ -32,6 +32,7 @@ UNITS = [
     ("rk4ip_2d.cu", 64),
     ("rk4ip_2d_tma.cu", None),
     ("rk4ip_adjoint.cu", None),
+    ("plain.cu", None),
 ]
 
 
@@ -82,7 +83,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(workers) as ex:
         objs = list(ex.map(lambda u: _compile(u, verbose), UNITS))
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs]
+    cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-lcufft"]
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)

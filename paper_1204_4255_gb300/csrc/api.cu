@@ -10,12 +10,15 @@
 //    modulus errors grow linearly with the step count.
 // Both are therefore stored as FP32 hi + lo (lo = rounded remainder of the
 // FP64 value) and applied with compensated FMAs (device_common.cuh).
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 #include <complex>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -67,9 +70,17 @@ struct xsde_problem {
     size_t scratch_bytes = 0;
     int *d_status = nullptr;
     int num_sms = 1;
-    int kernel_variant = 0;   // 0: fastest available kernels, 1: generic kernels only
+    int kernel_variant = 0;   // see xsde_set_kernel_variant
+    uint64_t generation = 0;  // bumped by every call that changes what integrate launches
     void *d_adj = nullptr;    // adjoint checkpoints and stage inputs
     size_t adj_bytes = 0;
+    // unfused comparison path (xsde_integrate_plain)
+    PlainPlan *plain = nullptr;
+    void *d_plain = nullptr;  // four work fields
+    size_t plain_bytes = 0;
+    void *d_plain_E = nullptr;  // exp(L dt/2)/npts at every k
+    double plain_dt = -1.0;
+    uint64_t plain_gen = ~0ull;
     // launch profiling: CUDA events around every kernel launch of this problem
     bool profiling = false;
     struct Mark {
@@ -339,22 +350,27 @@ bool encode_field_map(CUtensorMap *m, void *base, const xsde_grid &g, int64_t np
 // space; a sample is the row pass's local terms plus a forward transform
 // (dimension 2 rows, dimension 1 columns) and the kinetic reduction along
 // dimension 0.
+// the scratch field B of the 2D/3D pass schedule (grown, never shrunk)
+int ensure_scratch(xsde_problem *p, size_t need, cudaStream_t s) {
+    if (p->scratch_bytes >= need) return XSDE_OK;
+    if (p->d_scratch) {
+        XSDE_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize(scratch)");
+        cudaFree(p->d_scratch);
+        p->d_scratch = nullptr;
+        p->scratch_bytes = 0;
+    }
+    XSDE_CUDA(cudaMalloc(&p->d_scratch, need), "cudaMalloc(scratch)");
+    p->scratch_bytes = need;
+    return XSDE_OK;
+}
+
 template <typename R>
 int run_3d(xsde_problem *p, void *psi, int64_t nsteps, int64_t npaths, uint64_t step0, const LocalTerm<R> &lt,
            const Sampling &sm, cudaStream_t s) {
     using V = cx<R>;
     const xsde_grid &g = p->grid;
-    const size_t need = (size_t)npaths * g.npts * sizeof(V);
-    if (p->scratch_bytes < need) {
-        if (p->d_scratch) {
-            XSDE_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize(scratch)");
-            cudaFree(p->d_scratch);
-            p->d_scratch = nullptr;
-            p->scratch_bytes = 0;
-        }
-        XSDE_CUDA(cudaMalloc(&p->d_scratch, need), "cudaMalloc(scratch)");
-        p->scratch_bytes = need;
-    }
+    int rc_s = ensure_scratch(p, (size_t)npaths * g.npts * sizeof(V), s);
+    if (rc_s != XSDE_OK) return rc_s;
     Params2D<R> base;
     base.A = static_cast<V *>(psi);
     base.B = static_cast<V *>(p->d_scratch);
@@ -464,22 +480,13 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
         q.lt = lt;
         q.sm = sm;
         q.status = p->d_status;
-        XSDE_CUDA(timed(p, 1, s, [&] { return launch_rk4ip_1d<R>(g.n[0], q, s); }), "rk4ip_1d launch");
+        XSDE_CUDA(timed(p, 1, s, [&] { return launch_rk4ip_1d<R>(g.n[0], p->kernel_variant, q, s); }), "rk4ip_1d launch");
         return XSDE_OK;
     }
     if (g.ndim == 3) return run_3d<R>(p, psi, nsteps, npaths, step0, lt, sm, s);
     // 2D: scratch field B (same shape as psi)
-    const size_t need = (size_t)npaths * g.npts * sizeof(V);
-    if (p->scratch_bytes < need) {
-        if (p->d_scratch) {
-            XSDE_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize(scratch)");
-            cudaFree(p->d_scratch);
-            p->d_scratch = nullptr;
-            p->scratch_bytes = 0;
-        }
-        XSDE_CUDA(cudaMalloc(&p->d_scratch, need), "cudaMalloc(scratch)");
-        p->scratch_bytes = need;
-    }
+    int rc_s = ensure_scratch(p, (size_t)npaths * g.npts * sizeof(V), s);
+    if (rc_s != XSDE_OK) return rc_s;
     Params2D<R> q;
     q.A = static_cast<V *>(psi);
     q.B = static_cast<V *>(p->d_scratch);
@@ -549,6 +556,52 @@ bool same_lattice(const xsde_grid &a, const xsde_grid &b) {
     for (int d = 0; d < a.ndim; ++d)
         if (a.n[d] != b.n[d] || a.xmin[d] != b.xmin[d] || a.xmax[d] != b.xmax[d]) return false;
     return true;
+}
+
+// Argument checks shared by the integrating entry points.
+int check_integrate(const char *who, xsde_problem *p, const xsde_vector *psi, double dt, int64_t nsteps,
+                    int64_t npaths, int64_t path_offset, uint64_t step_offset) {
+    if (!p || !psi) return fail(XSDE_EINVAL, "%s: NULL problem or field", who);
+    if (!p->have_ops) return fail(XSDE_EINVAL, "%s: operators not set", who);
+    if (psi->dtype != p->dtype) return fail(XSDE_EINVAL, "%s: field dtype differs from the problem's", who);
+    if (!same_lattice(psi->grid, p->grid)) return fail(XSDE_EINVAL, "%s: field lattice differs", who);
+    if (npaths != psi->npaths)
+        return fail(XSDE_EINVAL, "%s: npaths %lld != field npaths %lld", who, (long long)npaths,
+                    (long long)psi->npaths);
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(XSDE_EINVAL, "%s: dt must be positive and finite", who);
+    if (nsteps < 0) return fail(XSDE_EINVAL, "%s: nsteps < 0", who);
+    if (path_offset < 0 || path_offset + npaths > (int64_t)UINT32_MAX + 1)
+        return fail(XSDE_EINVAL, "%s: global path indices exceed 32 bits", who);
+    if (step_offset + (uint64_t)nsteps + 1 > (uint64_t)UINT32_MAX)
+        return fail(XSDE_EINVAL, "%s: global step indices exceed 32 bits", who);
+    if (p->N.pot_kind == XSDE_POT_TABLE && p->N.V_nt > 1 && step_offset + (uint64_t)nsteps > (uint64_t)p->N.V_nt)
+        return fail(XSDE_EINVAL, "%s: potential table has %lld rows, steps up to %llu needed", who,
+                    (long long)p->N.V_nt, (unsigned long long)(step_offset + nsteps));
+    if (p->grid.ndim == 3 && npaths * p->grid.n[0] > 65535)
+        return fail(XSDE_EUNSUPPORTED, "%s: at most 65535 paths x n0 slabs per call on a 3D lattice", who);
+    if (p->grid.ndim == 2 && npaths > 65535)
+        return fail(XSDE_EUNSUPPORTED, "%s: at most 65535 paths per call on a 2D lattice", who);
+    if (p->samp.every > 0 && nsteps / p->samp.every + 1 > (int64_t)INT32_MAX)
+        return fail(XSDE_EINVAL, "%s: too many samples", who);
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != p->device) return fail(XSDE_EINVAL, "%s: current device %d is not the problem's %d", who, dev, p->device);
+    return XSDE_OK;
+}
+
+int integrate_on(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t npaths, int64_t path_offset,
+                 uint64_t step_offset, cudaStream_t s) {
+    return p->dtype == XSDE_C64 ? run_integrate<float>(p, psi, dt, nsteps, npaths, path_offset, step_offset, s)
+                                : run_integrate<double>(p, psi, dt, nsteps, npaths, path_offset, step_offset, s);
+}
+
+// Number of kernel variants the lattice offers (xsde_set_kernel_variant).
+int variants_for(const xsde_problem *p) {
+    switch (p->grid.ndim) {
+        case 1: return rk4ip_1d_variants();
+        case 2: return 2;
+        default: return 1;
+    }
 }
 
 }  // namespace
@@ -679,6 +732,9 @@ void xsde_problem_destroy(xsde_problem *p) {
     cudaFree(p->d_scratch);
     cudaFree(p->d_adj);
     cudaFree(p->d_status);
+    cudaFree(p->d_plain);
+    cudaFree(p->d_plain_E);
+    plain_plan_destroy(p->plain);
     delete p;
 }
 
@@ -702,6 +758,7 @@ int xsde_set_operators(xsde_problem *p, const xsde_linear_op *L, const xsde_nonl
     p->N.noise = nullptr;
     p->have_ops = true;
     p->table_dt = -1.0;
+    ++p->generation;
     return XSDE_OK;
 }
 
@@ -710,6 +767,7 @@ int xsde_moments(xsde_problem *p, const xsde_sampling *spec, double *per_path, d
     if (!spec || spec->every == 0) {
         p->samp = xsde_sampling{0, 0};
         p->per_path = p->per_point = nullptr;
+        ++p->generation;
         return XSDE_OK;
     }
     if (spec->every < 0) return fail(XSDE_EINVAL, "xsde_moments: every = %d", spec->every);
@@ -722,48 +780,28 @@ int xsde_moments(xsde_problem *p, const xsde_sampling *spec, double *per_path, d
     p->samp = *spec;
     p->per_path = per_path;
     p->per_point = per_point;
+    ++p->generation;
     return XSDE_OK;
 }
 
 int xsde_integrate(xsde_problem *p, xsde_vector *psi, double dt, int64_t nsteps, int64_t npaths,
                    int64_t path_offset, uint64_t step_offset, void *stream) {
-    if (!p || !psi) return fail(XSDE_EINVAL, "xsde_integrate: NULL problem or field");
-    if (!p->have_ops) return fail(XSDE_EINVAL, "xsde_integrate: operators not set");
-    if (psi->dtype != p->dtype) return fail(XSDE_EINVAL, "xsde_integrate: field dtype differs from the problem's");
-    if (!same_lattice(psi->grid, p->grid)) return fail(XSDE_EINVAL, "xsde_integrate: field lattice differs");
-    if (npaths != psi->npaths)
-        return fail(XSDE_EINVAL, "xsde_integrate: npaths %lld != field npaths %lld", (long long)npaths,
-                    (long long)psi->npaths);
-    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(XSDE_EINVAL, "xsde_integrate: dt must be positive and finite");
-    if (nsteps < 0) return fail(XSDE_EINVAL, "xsde_integrate: nsteps < 0");
-    if (path_offset < 0 || path_offset + npaths > (int64_t)UINT32_MAX + 1)
-        return fail(XSDE_EINVAL, "xsde_integrate: global path indices exceed 32 bits");
-    if (step_offset + (uint64_t)nsteps + 1 > (uint64_t)UINT32_MAX)
-        return fail(XSDE_EINVAL, "xsde_integrate: global step indices exceed 32 bits");
-    if (p->N.pot_kind == XSDE_POT_TABLE && p->N.V_nt > 1 && step_offset + (uint64_t)nsteps > (uint64_t)p->N.V_nt)
-        return fail(XSDE_EINVAL, "xsde_integrate: potential table has %lld rows, steps up to %llu needed",
-                    (long long)p->N.V_nt, (unsigned long long)(step_offset + nsteps));
-    if (p->grid.ndim == 3 && npaths * p->grid.n[0] > 65535)
-        return fail(XSDE_EUNSUPPORTED, "xsde_integrate: at most 65535 paths x n0 slabs per call on a 3D lattice");
-    if (p->grid.ndim == 2 && npaths > 65535)
-        return fail(XSDE_EUNSUPPORTED, "xsde_integrate: at most 65535 paths per call on a 2D lattice");
-    if (p->samp.every > 0 && nsteps / p->samp.every + 1 > (int64_t)INT32_MAX)
-        return fail(XSDE_EINVAL, "xsde_integrate: too many samples");
-    int dev = -1;
-    cudaGetDevice(&dev);
-    if (dev != p->device) return fail(XSDE_EINVAL, "xsde_integrate: current device %d is not the problem's %d", dev, p->device);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    return p->dtype == XSDE_C64
-               ? run_integrate<float>(p, psi->data, dt, nsteps, npaths, path_offset, step_offset, s)
-               : run_integrate<double>(p, psi->data, dt, nsteps, npaths, path_offset, step_offset, s);
+    const int rc = check_integrate("xsde_integrate", p, psi, dt, nsteps, npaths, path_offset, step_offset);
+    if (rc != XSDE_OK) return rc;
+    return integrate_on(p, psi->data, dt, nsteps, npaths, path_offset, step_offset, static_cast<cudaStream_t>(stream));
 }
 
 int xsde_set_kernel_variant(xsde_problem *p, int variant) {
     if (!p) return fail(XSDE_EINVAL, "xsde_set_kernel_variant: problem is NULL");
-    if (variant != 0 && variant != 1) return fail(XSDE_EINVAL, "xsde_set_kernel_variant: variant %d", variant);
+    if (variant < 0 || variant >= variants_for(p))
+        return fail(XSDE_EINVAL, "xsde_set_kernel_variant: variant %d (the lattice has %d)", variant, variants_for(p));
+    if (p->kernel_variant != variant) ++p->generation;
     p->kernel_variant = variant;
     return XSDE_OK;
 }
+
+int xsde_kernel_variants(const xsde_problem *p) { return p ? variants_for(p) : 0; }
+
 
 int xsde_profile(xsde_problem *p, int enable) {
     if (!p) return fail(XSDE_EINVAL, "xsde_profile: problem is NULL");
@@ -881,6 +919,93 @@ int xsde_adjoint(xsde_problem *p, const xsde_vector *psi0, const xsde_vector *ta
     return p->dtype == XSDE_C64 ? run(0.0f) : run(0.0);
 }
 
+int xsde_integrate_plain(xsde_problem *p, xsde_vector *psi, double dt, int64_t nsteps, int64_t npaths,
+                         int64_t path_offset, uint64_t step_offset, void *stream) {
+    int rc = check_integrate("xsde_integrate_plain", p, psi, dt, nsteps, npaths, path_offset, step_offset);
+    if (rc != XSDE_OK) return rc;
+    const xsde_grid &g = p->grid;
+    if (g.ndim == 0) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_plain: 0D problems have no transform");
+    if (p->samp.every > 0) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_plain: sampling groups are not supported");
+    if (npaths * g.npts > (int64_t)INT32_MAX)
+        return fail(XSDE_EUNSUPPORTED, "xsde_integrate_plain: more than 2^31 points per call");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool fp64 = p->dtype == XSDE_C128;
+    const size_t eb = elem_bytes(p->dtype);
+    const size_t field = (size_t)npaths * g.npts * eb;
+    if (!plain_plan_matches(p->plain, g.ndim, g.n, npaths, fp64)) {
+        XSDE_CUDA(cudaStreamSynchronize(s), "xsde_integrate_plain");
+        plain_plan_destroy(p->plain);
+        p->plain = nullptr;
+        XSDE_CUDA(plain_plan_create(g.ndim, g.n, npaths, fp64, &p->plain), "xsde_integrate_plain: cuFFT plan");
+    }
+    if (p->plain_bytes < 4 * field) {
+        XSDE_CUDA(cudaStreamSynchronize(s), "xsde_integrate_plain");
+        cudaFree(p->d_plain);
+        p->d_plain = nullptr;
+        p->plain_bytes = 0;
+        XSDE_CUDA(cudaMalloc(&p->d_plain, 4 * field), "xsde_integrate_plain: work fields");
+        p->plain_bytes = 4 * field;
+    }
+    if (p->plain_dt != dt || p->plain_gen != p->generation || !p->d_plain_E) {
+        // exp((c0 + c2 |k|^2) dt/2) / npts in FP64, rounded once
+        const std::complex<double> c0(p->L.c0_re, p->L.c0_im), c2(p->L.c2_re, p->L.c2_im);
+        std::vector<std::complex<double>> e((size_t)g.npts);
+        for (int64_t j = 0; j < g.npts; ++j) {
+            int64_t r = j;
+            double k2 = 0.0;
+            for (int d = g.ndim - 1; d >= 0; --d) {
+                const double k = kval(g, d, (int)(r % g.n[d]));
+                k2 += k * k;
+                r /= g.n[d];
+            }
+            e[(size_t)j] = std::exp((c0 + c2 * k2) * (0.5 * dt)) / (double)g.npts;
+        }
+        XSDE_CUDA(cudaStreamSynchronize(s), "xsde_integrate_plain");
+        cudaFree(p->d_plain_E);
+        p->d_plain_E = nullptr;
+        XSDE_CUDA(cudaMalloc(&p->d_plain_E, (size_t)g.npts * eb), "xsde_integrate_plain: table");
+        if (fp64) {
+            std::vector<double2> h((size_t)g.npts);
+            for (size_t j = 0; j < h.size(); ++j) h[j] = make_double2(e[j].real(), e[j].imag());
+            XSDE_CUDA(cudaMemcpy(p->d_plain_E, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice),
+                      "xsde_integrate_plain: table");
+        } else {
+            std::vector<float2> h((size_t)g.npts);
+            for (size_t j = 0; j < h.size(); ++j) h[j] = make_float2((float)e[j].real(), (float)e[j].imag());
+            XSDE_CUDA(cudaMemcpy(p->d_plain_E, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice),
+                      "xsde_integrate_plain: table");
+        }
+        p->plain_dt = dt;
+        p->plain_gen = p->generation;
+    }
+    auto run = [&](auto zero) -> int {
+        using R = decltype(zero);
+        using V = cx<R>;
+        PlainParams<R> q;
+        LocalTerm<R> lt;
+        Sampling sm;
+        fill_terms<R>(p, dt, npaths, path_offset, lt, sm);
+        V *w = static_cast<V *>(p->d_plain);
+        const int64_t n = npaths * g.npts;
+        q.a = static_cast<V *>(psi->data);
+        q.aI = w;
+        q.k = w + n;
+        q.acc = w + 2 * n;
+        q.tmp = w + 3 * n;
+        q.E = static_cast<const V *>(p->d_plain_E);
+        q.npaths = npaths;
+        q.npts = g.npts;
+        q.ndim = g.ndim;
+        for (int d = 0; d < 3; ++d) q.n[d] = d < g.ndim ? g.n[d] : 1;
+        q.nsteps = nsteps;
+        q.step0 = step_offset;
+        q.lt = lt;
+        XSDE_CUDA(run_plain<R>(p->plain, q, p->num_sms, s), "xsde_integrate_plain");
+        return XSDE_OK;
+    };
+    return fp64 ? run(0.0) : run(0.0f);
+}
+
 int xsde_synchronize(xsde_problem *p, void *stream) {
     if (!p) return fail(XSDE_EINVAL, "xsde_synchronize: problem is NULL");
     XSDE_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)), "xsde_synchronize");
@@ -890,6 +1015,346 @@ int xsde_synchronize(xsde_problem *p, void *stream) {
     if (st & ST_TIMEOUT) return fail(XSDE_ETIMEOUT, "a bounded device-side wait gave up");
     if (st & ST_NONFINITE) return fail(XSDE_ENONFINITE, "the field became non-finite");
     return XSDE_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Autotuning and batches of uneven instances (the paper's many paths and
+// independent simulations, Secs. 2.5 and 3, gathered into one launch).
+//
+// A lattice offers a few kernel variants that compute the same scheme with
+// different launch shapes: 1D, the number of paths one CTA carries; 2D
+// complex64, the persistent TMA-pipelined passes or the generic tiles.
+// xsde_autotune times each on a copy of the caller's field and keeps the
+// fastest.  A batch binds several problems to their fields and records all
+// their pass schedules as parallel branches of one CUDA graph: one host launch
+// replays the whole batch, and the many small 1D and 2D kernels of the
+// members run concurrently instead of one after the other.
+// ===========================================================================
+struct xsde_batch {
+    int device = -1;
+    int flags = 0;
+    bool tuned = false;
+    std::vector<xsde_batch_member> m;
+    cudaStream_t cap = nullptr;               // capture origin
+    std::vector<cudaStream_t> streams;        // one branch per member
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    cudaGraphExec_t exec = nullptr;
+    // what the instantiated graph was recorded for
+    double dt = -1.0;
+    int64_t nsteps = -1;
+    uint64_t step0 = 0;
+    std::vector<std::vector<uintptr_t>> sig;
+};
+
+namespace {
+
+std::mutex g_tune_mutex;
+std::map<std::string, int> g_tune_cache;
+bool g_tune_file_loaded = false;
+
+const char *tune_cache_path() {
+    const char *path = std::getenv("XSDE_AUTOTUNE_CACHE");
+    return (path && *path) ? path : nullptr;
+}
+
+std::string tune_key(const xsde_problem *p, int64_t npaths) {
+    char name[256] = "unknown";
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, p->device) == cudaSuccess) snprintf(name, sizeof name, "%s", prop.name);
+    for (char *c = name; *c; ++c)
+        if (*c == ' ' || *c == '\t') *c = '_';
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s/sm%d/%s/d%d/%dx%dx%d/p%lld", name, p->num_sms, p->dtype == XSDE_C64 ? "c64" : "c128",
+             p->grid.ndim, p->grid.n[0], p->grid.ndim > 1 ? p->grid.n[1] : 1, p->grid.ndim > 2 ? p->grid.n[2] : 1,
+             (long long)npaths);
+    return buf;
+}
+
+// lines "key variant"; later lines win
+void tune_file_load_locked() {
+    if (g_tune_file_loaded) return;
+    g_tune_file_loaded = true;
+    const char *path = tune_cache_path();
+    if (!path) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    char key[512];
+    int v = 0;
+    while (std::fscanf(f, "%511s %d", key, &v) == 2) g_tune_cache[key] = v;
+    std::fclose(f);
+}
+
+void tune_file_append_locked(const std::string &key, int v) {
+    const char *path = tune_cache_path();
+    if (!path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d\n", key.c_str(), v);
+    std::fclose(f);
+}
+
+int tune_problem(xsde_problem *p, const xsde_vector *psi, double dt, int64_t nsteps, bool reuse, int *best_out,
+                 double *ms_out, cudaStream_t s) {
+    const int nv = variants_for(p);
+    const std::string key = tune_key(p, psi->npaths);
+    if (reuse) {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        tune_file_load_locked();
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end() && it->second >= 0 && it->second < nv) {
+            if (p->kernel_variant != it->second) ++p->generation;
+            p->kernel_variant = it->second;
+            if (best_out) *best_out = it->second;
+            return XSDE_OK;
+        }
+    }
+    // a time-dependent potential table bounds the steps that can be taken
+    if (p->N.pot_kind == XSDE_POT_TABLE && p->N.V_nt > 1) nsteps = std::min<int64_t>(nsteps, p->N.V_nt);
+    const size_t bytes = (size_t)psi->npaths * psi->grid.npts * elem_bytes(p->dtype);
+    void *tmp = nullptr;
+    XSDE_CUDA(cudaMalloc(&tmp, bytes ? bytes : 16), "xsde_autotune: field copy");
+    // sampling and profiling are suspended while tuning
+    const xsde_sampling samp = p->samp;
+    double *const per_path = p->per_path, *const per_point = p->per_point;
+    const bool profiling = p->profiling;
+    const int old_variant = p->kernel_variant;
+    p->samp = xsde_sampling{0, 0};
+    p->per_path = p->per_point = nullptr;
+    p->profiling = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int rc = XSDE_OK;
+    cudaError_t e = cudaEventCreate(&ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev1);
+    if (e != cudaSuccess) rc = cuda_fail(e, "xsde_autotune: events");
+    int best = 0;
+    double best_ms = 0.0;
+    for (int v = 0; v < nv && rc == XSDE_OK; ++v) {
+        p->kernel_variant = v;
+        double vmin = INFINITY;
+        for (int rep = 0; rep < 4 && rc == XSDE_OK; ++rep) {   // rep 0 warms up
+            e = cudaMemcpyAsync(tmp, psi->data, bytes, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) e = cudaEventRecord(ev0, s);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "xsde_autotune");
+                break;
+            }
+            rc = integrate_on(p, tmp, dt, nsteps, psi->npaths, 0, 0, s);
+            if (rc != XSDE_OK) break;
+            e = cudaEventRecord(ev1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev0, ev1);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "xsde_autotune: timing");
+                break;
+            }
+            if (rep > 0) vmin = std::min(vmin, (double)ms);
+        }
+        if (rc != XSDE_OK) break;
+        if (ms_out) ms_out[v] = vmin;
+        if (v == 0 || vmin < best_ms) {
+            best_ms = vmin;
+            best = v;
+        }
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(tmp);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    p->samp = samp;
+    p->per_path = per_path;
+    p->per_point = per_point;
+    p->profiling = profiling;
+    if (rc != XSDE_OK) {
+        p->kernel_variant = old_variant;
+        return rc;
+    }
+    if (best != old_variant) ++p->generation;
+    p->kernel_variant = best;
+    if (best_out) *best_out = best;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    tune_file_load_locked();
+    auto it = g_tune_cache.find(key);
+    if (it == g_tune_cache.end() || it->second != best) {
+        g_tune_cache[key] = best;
+        tune_file_append_locked(key, best);
+    }
+    return XSDE_OK;
+}
+
+// Tables for dt and the scratch field, made ready outside any capture.
+int prepare_member(xsde_problem *p, double dt, int64_t npaths, cudaStream_t s) {
+    int rc = p->dtype == XSDE_C64 ? ensure_tables<cx<float>>(p, dt, s) : ensure_tables<cx<double>>(p, dt, s);
+    if (rc == XSDE_OK && p->grid.ndim >= 2)
+        rc = ensure_scratch(p, (size_t)npaths * p->grid.npts * elem_bytes(p->dtype), s);
+    return rc;
+}
+
+// Everything a recorded launch sequence depends on besides (dt, nsteps, step0).
+std::vector<uintptr_t> member_signature(const xsde_batch_member &m) {
+    const xsde_problem *p = m.prob;
+    std::vector<uintptr_t> v = {(uintptr_t)p->generation, (uintptr_t)m.psi->data, (uintptr_t)p->d_scratch,
+                                (uintptr_t)m.psi->npaths, (uintptr_t)m.path_offset};
+    for (int d = 0; d < 3; ++d) {
+        v.push_back((uintptr_t)p->d_tw[d]);
+        v.push_back((uintptr_t)p->d_E[d]);
+    }
+    return v;
+}
+
+void batch_release(xsde_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (cudaEvent_t e : b->join)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (cudaStream_t st : b->streams)
+        if (st) cudaStreamDestroy(st);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+}
+
+// Record every member's schedule as one branch of a graph and instantiate it
+// (or update the existing executable graph in place).
+int batch_capture(xsde_batch *b, double dt, int64_t nsteps, uint64_t step0) {
+    const size_t n = b->m.size();
+    std::vector<bool> profiling(n);
+    for (size_t i = 0; i < n; ++i) {
+        profiling[i] = b->m[i].prob->profiling;
+        b->m[i].prob->profiling = false;   // no event pairs inside the graph
+    }
+    cudaGraph_t graph = nullptr;
+    int rc = XSDE_OK;
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        e = cudaEventRecord(b->fork, b->cap);
+        for (size_t i = 0; i < n && e == cudaSuccess && rc == XSDE_OK; ++i) {
+            const xsde_batch_member &m = b->m[i];
+            e = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+            if (e != cudaSuccess) break;
+            rc = integrate_on(m.prob, m.psi->data, dt, nsteps, m.psi->npaths, m.path_offset, step0, b->streams[i]);
+            if (rc != XSDE_OK) break;
+            e = cudaEventRecord(b->join[i], b->streams[i]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->join[i], 0);
+        }
+        const cudaError_t e_end = cudaStreamEndCapture(b->cap, &graph);
+        if (e == cudaSuccess) e = e_end;
+    }
+    for (size_t i = 0; i < n; ++i) b->m[i].prob->profiling = profiling[i];
+    if (rc != XSDE_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rc != XSDE_OK ? rc : cuda_fail(e, "xsde_batch_integrate: graph capture");
+    }
+    if (b->exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(b->exec, graph, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+    }
+    if (!b->exec) e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        b->exec = nullptr;
+        return cuda_fail(e, "xsde_batch_integrate: graph instantiate");
+    }
+    b->dt = dt;
+    b->nsteps = nsteps;
+    b->step0 = step0;
+    b->sig.resize(n);
+    for (size_t i = 0; i < n; ++i) b->sig[i] = member_signature(b->m[i]);
+    return XSDE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int xsde_autotune(xsde_problem *p, const xsde_vector *psi, double dt, int64_t nsteps, int *best, double *ms,
+                  void *stream) {
+    if (!psi) return fail(XSDE_EINVAL, "xsde_autotune: field is NULL");
+    if (nsteps < 1) return fail(XSDE_EINVAL, "xsde_autotune: nsteps must be >= 1");
+    const int rc = check_integrate("xsde_autotune", p, psi, dt, nsteps, psi->npaths, 0, 0);
+    if (rc != XSDE_OK) return rc;
+    return tune_problem(p, psi, dt, nsteps, ms == nullptr, best, ms, static_cast<cudaStream_t>(stream));
+}
+
+int xsde_batch_create(const xsde_batch_member *members, int n, int flags, xsde_batch **out) {
+    if (!out) return fail(XSDE_EINVAL, "xsde_batch_create: out is NULL");
+    *out = nullptr;
+    if (!members || n < 1) return fail(XSDE_EINVAL, "xsde_batch_create: no members");
+    if (flags & ~XSDE_BATCH_AUTOTUNE) return fail(XSDE_EINVAL, "xsde_batch_create: unknown flags 0x%x", flags);
+    int dev = -1;
+    cudaGetDevice(&dev);
+    for (int i = 0; i < n; ++i) {
+        const xsde_batch_member &m = members[i];
+        if (!m.prob || !m.psi) return fail(XSDE_EINVAL, "xsde_batch_create: member %d has a NULL problem or field", i);
+        if (m.prob->device != dev)
+            return fail(XSDE_EINVAL, "xsde_batch_create: member %d lives on device %d, not the current %d", i,
+                        m.prob->device, dev);
+        for (int j = 0; j < i; ++j) {
+            if (members[j].prob == m.prob)
+                return fail(XSDE_EINVAL, "xsde_batch_create: members %d and %d share a problem (its scratch)", j, i);
+            if (members[j].psi->data == m.psi->data)
+                return fail(XSDE_EINVAL, "xsde_batch_create: members %d and %d share a field", j, i);
+        }
+    }
+    xsde_batch *b = new (std::nothrow) xsde_batch();
+    if (!b) return fail(XSDE_ENOMEM, "xsde_batch_create: out of host memory");
+    b->device = dev;
+    b->flags = flags;
+    b->m.assign(members, members + n);
+    b->streams.assign(n, nullptr);
+    b->join.assign(n, nullptr);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        batch_release(b);
+        return cuda_fail(e, "xsde_batch_create");
+    }
+    *out = b;
+    return XSDE_OK;
+}
+
+int xsde_batch_integrate(xsde_batch *b, double dt, int64_t nsteps, uint64_t step_offset, void *stream) {
+    if (!b) return fail(XSDE_EINVAL, "xsde_batch_integrate: batch is NULL");
+    int rc;
+    for (const xsde_batch_member &m : b->m)
+        if ((rc = check_integrate("xsde_batch_integrate", m.prob, m.psi, dt, nsteps, m.psi->npaths, m.path_offset,
+                                  step_offset)) != XSDE_OK)
+            return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((b->flags & XSDE_BATCH_AUTOTUNE) && !b->tuned) {
+        const int64_t probe = std::max<int64_t>(1, std::min<int64_t>(nsteps, 10));
+        for (const xsde_batch_member &m : b->m)
+            if ((rc = tune_problem(m.prob, m.psi, dt, probe, true, nullptr, nullptr, s)) != XSDE_OK) return rc;
+        b->tuned = true;
+    }
+    for (const xsde_batch_member &m : b->m)
+        if ((rc = prepare_member(m.prob, dt, m.psi->npaths, s)) != XSDE_OK) return rc;
+    bool stale = !b->exec || b->dt != dt || b->nsteps != nsteps || b->step0 != step_offset;
+    for (size_t i = 0; i < b->m.size() && !stale; ++i) stale = b->sig[i] != member_signature(b->m[i]);
+    if (stale) {
+        // an update must not race a replay of the previous graph
+        if (b->exec) XSDE_CUDA(cudaStreamSynchronize(s), "xsde_batch_integrate");
+        if ((rc = batch_capture(b, dt, nsteps, step_offset)) != XSDE_OK) return rc;
+    }
+    XSDE_CUDA(cudaGraphLaunch(b->exec, s), "xsde_batch_integrate: graph launch");
+    return XSDE_OK;
+}
+
+void xsde_batch_destroy(xsde_batch *b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    batch_release(b);
 }
 
 }  // extern "C"

@@ -65,7 +65,11 @@ template <typename R> struct Params1D {
     Sampling sm;
     int *status;
 };
-template <typename R> cudaError_t launch_rk4ip_1d(int n, const Params1D<R> &p, cudaStream_t s);
+// variant v in [0, rk4ip_1d_variants()) sets the paths per CTA: the default
+// (filling 128 threads), a half, a quarter (at least one), or twice (at most
+// 256 threads) as many
+int rk4ip_1d_variants();
+template <typename R> cudaError_t launch_rk4ip_1d(int n, int variant, const Params1D<R> &p, cudaStream_t s);
 
 // --------------------------------------------------------------------------
 // 2D: row passes (contiguous dimension 1, real-space work) and column passes
@@ -158,6 +162,27 @@ template <typename R> struct Params0D {
     int *status;
 };
 template <typename R> cudaError_t launch_rk4ip_0d(const Params0D<R> &p, cudaStream_t s);
+
+// --------------------------------------------------------------------------
+// Unfused comparison step (plain.cu): cuFFT transforms plus one elementwise
+// kernel per operation, all fields in HBM between operations.
+// --------------------------------------------------------------------------
+template <typename R> struct PlainParams {
+    cx<R> *a;              // [npaths][npts] real space, in/out
+    cx<R> *aI, *k, *acc, *tmp; // work fields, same shape
+    const cx<R> *E;        // exp(L(k) dt/2)/npts at every k (FFT order)
+    int64_t npaths, npts;
+    int ndim;
+    int n[3];
+    int64_t nsteps;
+    uint64_t step0;
+    LocalTerm<R> lt;
+};
+struct PlainPlan;
+cudaError_t plain_plan_create(int ndim, const int *n, int64_t npaths, bool fp64, PlainPlan **out);
+void plain_plan_destroy(PlainPlan *pl);
+bool plain_plan_matches(const PlainPlan *pl, int ndim, const int *n, int64_t npaths, bool fp64);
+template <typename R> cudaError_t run_plain(PlainPlan *pl, const PlainParams<R> &p, int num_sms, cudaStream_t s);
 
 // Generator entry points (noise.cu).
 cudaError_t launch_philox(const uint32_t *ctr, uint64_t seed, int64_t n, uint32_t *out, cudaStream_t s);

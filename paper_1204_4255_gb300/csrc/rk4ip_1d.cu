@@ -184,8 +184,8 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
     }
 }
 
-template <typename R, int N> cudaError_t launch_n(const Params1D<R> &p, cudaStream_t s) {
-    constexpr int E = 8, T = N / E, PPC = T >= 128 ? 1 : 128 / T;
+template <typename R, int N, int PPC> cudaError_t launch_ppc(const Params1D<R> &p, cudaStream_t s) {
+    constexpr int E = 8, T = N / E;
     const size_t smem = (size_t)N * sizeof(tw_t<R>) + (size_t)PPC * 2 * padded_len<N>() * sizeof(cx<R>);
     auto kern = rk4ip_1d_kernel<R, N, E, PPC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -195,28 +195,45 @@ template <typename R, int N> cudaError_t launch_n(const Params1D<R> &p, cudaStre
     return cudaGetLastError();
 }
 
+// paths per CTA: the default fills 128 threads; variants 1 and 2 carry a half
+// and a quarter of that (at least one path: more CTAs for small ensembles),
+// variant 3 twice as many (at most 256 threads, so no variant is squeezed
+// below 255 registers a thread)
+template <typename R, int N> cudaError_t launch_n(int variant, const Params1D<R> &p, cudaStream_t s) {
+    constexpr int T = N / 8, P0 = T >= 128 ? 1 : 128 / T;
+    constexpr int P1 = P0 >= 2 ? P0 / 2 : 1, P2 = P0 >= 4 ? P0 / 4 : 1;
+    constexpr int P3 = 2 * P0 * T <= 256 ? 2 * P0 : P0;
+    switch (variant) {
+        case 1: return launch_ppc<R, N, P1>(p, s);
+        case 2: return launch_ppc<R, N, P2>(p, s);
+        case 3: return launch_ppc<R, N, P3>(p, s);
+        default: return launch_ppc<R, N, P0>(p, s);
+    }
+}
+
 }  // namespace
 
-template <typename R> cudaError_t launch_rk4ip_1d(int n, const Params1D<R> &p, cudaStream_t s) {
+template <typename R> cudaError_t launch_rk4ip_1d(int n, int variant, const Params1D<R> &p, cudaStream_t s) {
     switch (n) {
-        case 16: return launch_n<R, 16>(p, s);
-        case 32: return launch_n<R, 32>(p, s);
-        case 64: return launch_n<R, 64>(p, s);
-        case 128: return launch_n<R, 128>(p, s);
-        case 256: return launch_n<R, 256>(p, s);
-        case 512: return launch_n<R, 512>(p, s);
-        case 1024: return launch_n<R, 1024>(p, s);
-        case 2048: return launch_n<R, 2048>(p, s);
+        case 16: return launch_n<R, 16>(variant, p, s);
+        case 32: return launch_n<R, 32>(variant, p, s);
+        case 64: return launch_n<R, 64>(variant, p, s);
+        case 128: return launch_n<R, 128>(variant, p, s);
+        case 256: return launch_n<R, 256>(variant, p, s);
+        case 512: return launch_n<R, 512>(variant, p, s);
+        case 1024: return launch_n<R, 1024>(variant, p, s);
+        case 2048: return launch_n<R, 2048>(variant, p, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 // XSDE_REAL_BITS selects one precision per translation unit (parallel builds)
 #if !defined(XSDE_REAL_BITS) || XSDE_REAL_BITS == 32
-template cudaError_t launch_rk4ip_1d<float>(int, const Params1D<float> &, cudaStream_t);
+int rk4ip_1d_variants() { return 4; }
+template cudaError_t launch_rk4ip_1d<float>(int, int, const Params1D<float> &, cudaStream_t);
 #endif
 #if !defined(XSDE_REAL_BITS) || XSDE_REAL_BITS == 64
-template cudaError_t launch_rk4ip_1d<double>(int, const Params1D<double> &, cudaStream_t);
+template cudaError_t launch_rk4ip_1d<double>(int, int, const Params1D<double> &, cudaStream_t);
 #endif
 
 }  // namespace xsde

@@ -30,8 +30,10 @@ EXPORTED = (
     "xsde_problem_create", "xsde_problem_destroy", "xsde_set_operators", "xsde_moments",
     "xsde_integrate", "xsde_synchronize", "xsde_last_error", "xsde_version",
     "xsde_profile", "xsde_profile_report", "xsde_kernel_name", "xsde_set_kernel_variant",
-    "xsde_integrate_static_scratch", "xsde_adjoint",
+    "xsde_integrate_static_scratch", "xsde_adjoint", "xsde_kernel_variants", "xsde_autotune",
+    "xsde_batch_create", "xsde_batch_integrate", "xsde_batch_destroy", "xsde_integrate_plain",
 )
+XSDE_BATCH_AUTOTUNE = 1
 XSDE_KERNEL_KINDS = 9
 
 
@@ -54,6 +56,10 @@ class xsde_nonlinear_op(ctypes.Structure):
 
 class xsde_sampling(ctypes.Structure):
     _fields_ = [("every", ctypes.c_int32), ("which", ctypes.c_int32)]
+
+
+class xsde_batch_member(ctypes.Structure):
+    _fields_ = [("prob", ctypes.c_void_p), ("psi", ctypes.c_void_p), ("path_offset", ctypes.c_int64)]
 
 
 _lib = None
@@ -96,6 +102,12 @@ def load(path: str = LIB_PATH):
         "xsde_set_kernel_variant": (ctypes.c_int, [vp, ctypes.c_int]),
         "xsde_integrate_static_scratch": (ctypes.c_int, [vp, vp, dp, i64, i64, i64, u64, vp]),
         "xsde_adjoint": (ctypes.c_int, [vp, vp, vp, dp, i64, i32, vp, vp, vp, vp]),
+        "xsde_kernel_variants": (ctypes.c_int, [vp]),
+        "xsde_autotune": (ctypes.c_int, [vp, vp, dp, i64, vp, vp, vp]),
+        "xsde_batch_create": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, pvp]),
+        "xsde_batch_integrate": (ctypes.c_int, [vp, dp, i64, u64, vp]),
+        "xsde_batch_destroy": (None, [vp]),
+        "xsde_integrate_plain": (ctypes.c_int, [vp, vp, dp, i64, i64, i64, u64, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -201,6 +213,13 @@ def xsde_integrate(prob, vec, dt: float, nsteps: int, npaths: int, path_offset: 
                                  ctypes.c_void_p(stream or None)))
 
 
+def xsde_integrate_plain(prob, vec, dt: float, nsteps: int, npaths: int, path_offset: int = 0,
+                         step_offset: int = 0, stream: int = 0) -> None:
+    """The unfused comparison step (cuFFT + elementwise kernels)."""
+    _check(load().xsde_integrate_plain(prob, vec, dt, nsteps, npaths, path_offset, step_offset,
+                                       ctypes.c_void_p(stream or None)))
+
+
 def xsde_integrate_static_scratch(prob, vec, dt: float, nsteps: int, npaths: int, path_offset: int = 0,
                                   step_offset: int = 0, stream: int = 0) -> None:
     """xsde_integrate for 2D lattices using the library's static device scratch
@@ -222,6 +241,36 @@ def xsde_synchronize(prob, stream: int = 0) -> None:
 
 def xsde_set_kernel_variant(prob, variant: int) -> None:
     _check(load().xsde_set_kernel_variant(prob, variant))
+
+
+def xsde_kernel_variants(prob) -> int:
+    return int(load().xsde_kernel_variants(prob))
+
+
+def xsde_autotune(prob, vec, dt: float, nsteps: int, timings: bool = False, stream: int = 0):
+    """Select the fastest kernel variant; returns its index, or (index, [ms per
+    variant]) with timings=True (which always re-times)."""
+    best = ctypes.c_int(-1)
+    nv = xsde_kernel_variants(prob)
+    ms = (ctypes.c_double * max(1, nv))() if timings else None
+    _check(load().xsde_autotune(prob, vec, dt, nsteps, ctypes.byref(best), ms, ctypes.c_void_p(stream or None)))
+    return (best.value, [ms[i] for i in range(nv)]) if timings else best.value
+
+
+def xsde_batch_create(members, flags: int = 0) -> ctypes.c_void_p:
+    """members: sequence of (problem handle, vector handle, path_offset)."""
+    arr = (xsde_batch_member * len(members))(*[xsde_batch_member(p, v, o) for p, v, o in members])
+    out = ctypes.c_void_p()
+    _check(load().xsde_batch_create(arr, len(members), flags, ctypes.byref(out)))
+    return out
+
+
+def xsde_batch_integrate(batch, dt: float, nsteps: int, step_offset: int = 0, stream: int = 0) -> None:
+    _check(load().xsde_batch_integrate(batch, dt, nsteps, step_offset, ctypes.c_void_p(stream or None)))
+
+
+def xsde_batch_destroy(batch) -> None:
+    load().xsde_batch_destroy(batch)
 
 
 def xsde_profile(prob, enable: bool) -> None:
@@ -298,8 +347,9 @@ class Problem:
         xsde_moments(self.prob, spec, per_path.data_ptr() if per_path is not None else 0,
                      per_point.data_ptr() if per_point is not None else 0)
 
-    def integrate(self, psi, dt: float, nsteps: int, path_offset: int = 0, step_offset: int = 0, stream=None):
-        """psi: CUDA complex tensor [npaths, *shape], advanced in place."""
+    def wrap(self, psi):
+        """An xsde_vector handle borrowing the CUDA tensor psi [npaths, *shape]
+        (free it with xsde_vector_free)."""
         import torch
         if not psi.is_cuda or not psi.is_contiguous():
             raise ValueError("psi must be a contiguous CUDA tensor")
@@ -308,10 +358,31 @@ class Problem:
         codes = {torch.complex64: XSDE_C64, torch.complex128: XSDE_C128}
         if psi.dtype not in codes:
             raise ValueError(f"psi must be complex64 or complex128, not {psi.dtype}")
+        return xsde_vector_wrap(self.grid, codes[psi.dtype], 1, psi.shape[0], psi.data_ptr())
+
+    def autotune(self, psi, dt: float, nsteps: int = 10, timings: bool = False, stream=None):
+        vec = self.wrap(psi)
+        try:
+            return xsde_autotune(self.prob, vec, dt, nsteps, timings, _stream_handle(stream))
+        finally:
+            xsde_vector_free(vec)
+
+    def integrate(self, psi, dt: float, nsteps: int, path_offset: int = 0, step_offset: int = 0, stream=None):
+        """psi: CUDA complex tensor [npaths, *shape], advanced in place."""
         npaths = psi.shape[0]
-        vec = xsde_vector_wrap(self.grid, codes[psi.dtype], 1, npaths, psi.data_ptr())
+        vec = self.wrap(psi)
         try:
             xsde_integrate(self.prob, vec, dt, nsteps, npaths, path_offset, step_offset, _stream_handle(stream))
+        finally:
+            xsde_vector_free(vec)
+
+    def integrate_plain(self, psi, dt: float, nsteps: int, path_offset: int = 0, step_offset: int = 0,
+                        stream=None):
+        """As integrate, through the unfused comparison step."""
+        vec = self.wrap(psi)
+        try:
+            xsde_integrate_plain(self.prob, vec, dt, nsteps, psi.shape[0], path_offset, step_offset,
+                                 _stream_handle(stream))
         finally:
             xsde_vector_free(vec)
 
@@ -328,6 +399,47 @@ class Problem:
         if self.grid:
             xsde_grid_destroy(self.grid)
             self.grid = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several (Problem, field tensor, path_offset) members advanced together by
+    one graph replay (xsde_batch_*).  The tensors stay borrowed: keep them
+    alive and in place while the batch exists."""
+
+    def __init__(self, members, autotune: bool = False):
+        self.batch = None
+        self._members = [(P, psi) for P, psi, _ in members]
+        self._vecs = [P.wrap(psi) for P, psi, _ in members]
+        try:
+            self.batch = xsde_batch_create([(P.prob, v, int(off)) for (P, _, off), v in zip(members, self._vecs)],
+                                           XSDE_BATCH_AUTOTUNE if autotune else 0)
+        except Exception:
+            for v in self._vecs:
+                xsde_vector_free(v)
+            self._vecs = []
+            self.batch = None
+            raise
+
+    def integrate(self, dt: float, nsteps: int, step_offset: int = 0, stream=None):
+        xsde_batch_integrate(self.batch, dt, nsteps, step_offset, _stream_handle(stream))
+
+    def synchronize(self, stream=None):
+        for P, _ in self._members:
+            P.synchronize(stream)
+
+    def close(self):
+        if getattr(self, "batch", None):
+            xsde_batch_destroy(self.batch)
+            self.batch = None
+        for v in getattr(self, "_vecs", []):
+            xsde_vector_free(v)
+        self._vecs = []
 
     def __del__(self):
         try:

@@ -1,0 +1,235 @@
+"""Batches of uneven instances and the kernel-variant autotuner, through the
+C-ABI (xsde_batch_*, xsde_autotune, xsde_set_kernel_variant).
+
+A batch replays every member's pass schedule as a branch of one CUDA graph, so
+each member must come out exactly as one xsde_integrate call with the same
+kernel variant would leave it (bit for bit: the same kernels run on the same
+data), and within the oracle's tolerances (1e-10 relative L2 for complex128,
+1e-4 for complex64) whatever variants the autotuner picked.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import oracle as O
+from gpu_util import make_problem, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1204_4255_gb300 import build, xsde
+    build.build()
+    xsde.load()
+    O.set_threads(os.cpu_count() or 1)
+
+
+def _tensor(w, dtype):
+    import torch
+    tdt = torch.complex64 if dtype == "c64" else torch.complex128
+    return torch.from_numpy(np.ascontiguousarray(w.psi0)).to(tdt).cuda().contiguous()
+
+
+def _small_members(nsteps=12, dt=1e-4):
+    """1D NLS at 256 and 512 points, a 2D GPE at 64^2 and at 256^2, a 3D GPE at
+    16 x 32 x 32 (ragged path counts per member)."""
+    out = W.batched_instances(n3=0, sizes2=(64, 256), count2=2, sizes1=(256, 512), count1=5,
+                              dt=dt, nsteps=nsteps)
+    w3 = W.gpe_3d(n=16, dt=dt, nsteps=nsteps)
+    shape = (16, 32, 32)
+    tf = W.thomas_fermi(shape, (-10.0,) * 3, (10.0,) * 3, (1.0, 1.0, 1.0), 200.0)
+    w3.n = shape
+    w3.psi0 = (tf * np.exp(1j * 0.01 * np.random.default_rng(7).standard_normal(shape)))[None]
+    out.append(w3)
+    # one stochastic member: additive complex noise on the first 1D lattice
+    wn = out[2]
+    wn.noise_kind, wn.noise_amp, wn.seed = W.NOISE_ADD_COMPLEX, 0.01, 11
+    return out
+
+
+def _run_batch(ws, dtype, nsteps, autotune=False, calls=1):
+    """Advance all workloads as one batch (calls x nsteps steps); returns the
+    fields as complex128 numpy arrays."""
+    import torch
+    from paper_1204_4255_gb300 import xsde
+    probs = [make_problem(w, dtype) for w in ws]
+    psis = [_tensor(w, dtype) for w in ws]
+    B = xsde.Batch([(P, psi, 0) for P, psi in zip(probs, psis)], autotune=autotune)
+    try:
+        for c in range(calls):
+            B.integrate(ws[0].dt, nsteps, step_offset=c * nsteps)
+        torch.cuda.synchronize()
+        B.synchronize()
+        got = [p.cpu().numpy().astype(np.complex128) for p in psis]
+    finally:
+        B.close()
+        for P in probs:
+            P.close()
+    return got
+
+
+def _run_each(ws, dtype, nsteps, variants=None, calls=1):
+    from paper_1204_4255_gb300 import xsde
+    import torch
+    out = []
+    for i, w in enumerate(ws):
+        P = make_problem(w, dtype)
+        if variants is not None:
+            xsde.xsde_set_kernel_variant(P.prob, variants[i])
+        psi = _tensor(w, dtype)
+        for c in range(calls):
+            P.integrate(psi, w.dt, nsteps, step_offset=c * nsteps)
+        torch.cuda.synchronize()
+        P.synchronize()
+        out.append(psi.cpu().numpy().astype(np.complex128))
+        P.close()
+    return out
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_batch_equals_individual_integrate_calls_bitwise(dtype):
+    ws = _small_members()
+    got = _run_batch(ws, dtype, 12, calls=2)
+    ref = _run_each(ws, dtype, 12, calls=2)
+    for w, a, b in zip(ws, got, ref):
+        assert np.array_equal(a, b), f"{w.name}: batch differs from xsde_integrate"
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-10), ("c64", 1e-4)])
+def test_autotuned_batch_matches_oracle(dtype, tol):
+    ws = _small_members()
+    got = _run_batch(ws, dtype, 12, autotune=True, calls=2)
+    for w, a in zip(ws, got):
+        ref, _, _ = O.run_workload(w, nsteps=24)
+        err = rel_l2(a, ref)
+        print(f"{w.name} {dtype}: rel L2 {err:.2e}")
+        assert err < tol, f"{w.name}: {err:.2e}"
+
+
+def test_batch_records_again_after_operator_change():
+    """A member whose operators changed between replays is recorded again."""
+    import torch
+    from paper_1204_4255_gb300 import xsde
+    ws = _small_members()[:3]
+    probs = [make_problem(w, "c128") for w in ws]
+    psis = [_tensor(w, "c128") for w in ws]
+    B = xsde.Batch([(P, psi, 0) for P, psi in zip(probs, psis)])
+    try:
+        B.integrate(ws[0].dt, 6)
+        torch.cuda.synchronize()
+        w = ws[1]
+        probs[1].set_operators(c0=w.c0, c2=w.c2, g=2.0 * w.gnl, pot_kind=w.pot_kind, omega=(1.0, 1.0, 0.0))
+        B.integrate(ws[0].dt, 6, step_offset=6)
+        torch.cuda.synchronize()
+        got = psis[1].cpu().numpy()
+    finally:
+        B.close()
+        for P in probs:
+            P.close()
+    grid, ops = O.from_workload(w)
+    mid, _, _ = O.rk4ip(w.psi0, grid, ops, w.dt, 6)
+    ops.gnl = 2.0 * w.gnl
+    ref, _, _ = O.rk4ip(mid, grid, ops, w.dt, 6, step0=6)
+    assert rel_l2(got, ref) < 1e-10
+
+
+def test_batch_samples_equal_individual_samples():
+    import torch
+    from paper_1204_4255_gb300 import xsde
+    ws = _small_members()
+    nsteps, every = 12, 4
+    ns = nsteps // every + 1
+
+    def run(batch):
+        probs = [make_problem(w, "c128") for w in ws]
+        psis = [_tensor(w, "c128") for w in ws]
+        bufs = []
+        for P, w in zip(probs, ws):
+            pp = torch.zeros((ns, w.npaths, 2), dtype=torch.float64, device="cuda")
+            pq = torch.zeros((ns, w.npts, 2), dtype=torch.float64, device="cuda")
+            P.moments(every, 15, pp, pq)
+            bufs.append((pp, pq))
+        if batch:
+            B = xsde.Batch([(P, psi, 0) for P, psi in zip(probs, psis)])
+            B.integrate(ws[0].dt, nsteps)
+            torch.cuda.synchronize()
+            B.close()
+        else:
+            for P, psi, w in zip(probs, psis, ws):
+                P.integrate(psi, w.dt, nsteps)
+            torch.cuda.synchronize()
+        out = [(pp.cpu().numpy(), pq.cpu().numpy()) for pp, pq in bufs]
+        for P in probs:
+            P.close()
+        return out
+
+    for w, (a_pp, a_pq), (b_pp, b_pq) in zip(ws, run(True), run(False)):
+        np.testing.assert_allclose(a_pp, b_pp, rtol=1e-13, atol=0, err_msg=w.name)
+        np.testing.assert_allclose(a_pq, b_pq, rtol=1e-12, atol=1e-300, err_msg=w.name)
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("n", [16, 128, 256, 1024, 2048])
+def test_1d_variants_agree(dtype, n):
+    """Paths per CTA changes the launch shape, not a path's operations.  Each
+    variant is its own compiled kernel, and the compiler may fuse a multiply and
+    an add into one FMA in one instantiation and not in another, so variants
+    agree to rounding rather than bit for bit; each is held to the oracle."""
+    from paper_1204_4255_gb300 import xsde
+    ws = W.batched_instances(n3=0, sizes2=(), count2=0, sizes1=(n,), count1=9, nsteps=20)
+    w = ws[0]
+    w.noise_kind, w.noise_amp, w.seed = W.NOISE_ADD_COMPLEX, 0.01, 5
+    P = make_problem(w, dtype)
+    nv = xsde.xsde_kernel_variants(P.prob)
+    P.close()
+    assert nv == 4
+    outs = _run_each([w] * nv, dtype, 20, variants=list(range(nv)))
+    ref, _, _ = O.run_workload(w, nsteps=20)
+    close, tol = (1e-13, 1e-10) if dtype == "c128" else (2e-6, 1e-4)
+    for v in range(nv):
+        assert rel_l2(outs[v], outs[0]) < close, f"variant {v} vs 0"
+        assert rel_l2(outs[v], ref) < tol, f"variant {v} vs oracle"
+
+
+def test_autotune_times_every_variant_and_leaves_the_field(tmp_path, monkeypatch):
+    import torch
+    from paper_1204_4255_gb300 import xsde
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("XSDE_AUTOTUNE_CACHE", str(cache))
+    for w in (W.batched_instances(n3=0, sizes2=(), count2=0, sizes1=(512,), count1=37, nsteps=10)[0],
+              W.gpe_2d(n=256, npaths=3, nsteps=4)):
+        P = make_problem(w, "c64")
+        psi = _tensor(w, "c64")
+        before = psi.clone()
+        best, ms = P.autotune(psi, w.dt, 4, timings=True)
+        torch.cuda.synchronize()
+        assert torch.equal(psi, before)
+        assert len(ms) == xsde.xsde_kernel_variants(P.prob)
+        assert all(np.isfinite(m) and m > 0 for m in ms)
+        assert best == int(np.argmin(ms))
+        # without timings the recorded choice is reused (from the cache)
+        assert P.autotune(psi, w.dt, 4) == best
+        P.close()
+    lines = cache.read_text().split("\n")
+    assert any("/d1/512x1x1/p37 " in ln for ln in lines)
+    assert any("/d2/256x256x1/p3 " in ln for ln in lines)
+
+
+def test_batch_rejects_shared_problem_or_field():
+    from paper_1204_4255_gb300 import xsde
+    w = W.nls_soliton(n=256, nsteps=2)
+    P = make_problem(w, "c128")
+    Q = make_problem(w, "c128")
+    psi = _tensor(w, "c128")
+    psi2 = _tensor(w, "c128")
+    with pytest.raises(xsde.XsdeError):
+        xsde.Batch([(P, psi, 0), (P, psi2, 0)])
+    with pytest.raises(xsde.XsdeError):
+        xsde.Batch([(P, psi, 0), (Q, psi, 0)])
+    with pytest.raises(xsde.XsdeError):
+        xsde.xsde_set_kernel_variant(P.prob, 4)
+    P.close()
+    Q.close()

@@ -221,3 +221,27 @@ def batched_1d_instances(count_per_size: int = 256, sizes=(256, 512, 1024, 2048)
             out.append(Workload(f"nls_1d_{n}_{i}", (n,), (-L,), (L,), 0j, -0.5j, -1.0, POT_NONE, (0.0,),
                                 None, NOISE_NONE, 0.0, 0, dt, nsteps, psi.astype(np.complex128)[None, :]))
     return out
+
+
+def batched_instances(n3: int = 128, sizes2=(256, 512), count2: int = 32, sizes1=(256, 512, 1024, 2048),
+                      count1: int = 256, dt: float = 1e-4, nsteps: int = 500) -> list:
+    """Uneven instances advanced together: one 3D GPE at n3^3 (V = r^2/2, g = 200,
+    box [-10,10)^3), count2 2D GPEs at each size of sizes2 (the 2D GPE physics:
+    g = 500, box [-12,12)^2, each its own phase noise) and count1 1D NLS
+    instances at each size of sizes1 (random sech / Gaussian states).  Instances
+    of one lattice share their operators, so each lattice is one Workload whose
+    paths are the instances: 1 + len(sizes2) + len(sizes1) Workloads."""
+    out = [gpe_3d(n=n3, dt=dt, nsteps=nsteps)] if n3 else []
+    for i, n in enumerate(sizes2):
+        w = gpe_2d(n=n, dt=dt, nsteps=nsteps, seed=20 + i, npaths=count2)
+        w.name = f"gpe_2d_{n}x{count2}"
+        out.append(w)
+    if count1:
+        one = batched_1d_instances(count_per_size=count1, sizes=sizes1, dt=dt, nsteps=nsteps)
+        for k, n in enumerate(sizes1):
+            group = one[k * count1:(k + 1) * count1]
+            w = group[0]
+            out.append(Workload(f"nls_1d_{n}x{count1}", w.n, w.xmin, w.xmax, w.c0, w.c2, w.gnl, w.pot_kind,
+                                w.omega, None, w.noise_kind, w.noise_amp, w.seed, dt, nsteps,
+                                np.concatenate([g.psi0 for g in group], axis=0)))
+    return out
