@@ -207,8 +207,11 @@ int xsde_integrate(xsde_problem *prob, xsde_vector *psi, double dt, int64_t nste
  *                                       entries (the potential of step n at point j)
  *   dLdpsi0 (device like psi0, or NULL) = lambda with dL = Re sum conj(lambda) dpsi0
  * psi_N is reached by nsteps steps of size dt.  States are checkpointed every
- * ckpt_every steps and each segment is recomputed once during the reverse sweep
- * (the library owns that workspace).  Asynchronous on `stream`. */
+ * ckpt_every steps and each segment is recomputed once from its checkpoint (the
+ * library owns that workspace).  When the stage inputs of all steps fit in
+ * XSDE_ADJOINT_MAX_BYTES bytes of workspace (environment variable, default
+ * 2 GiB) all segments are recomputed at once before the reverse sweep; else one
+ * at a time during it, in a buffer of one segment.  Asynchronous on `stream`. */
 int xsde_adjoint(xsde_problem *prob, const xsde_vector *psi0, const xsde_vector *target, double dt, int64_t nsteps,
                  int32_t ckpt_every, double *loss, double *dLdV, void *dLdpsi0, void *stream);
 

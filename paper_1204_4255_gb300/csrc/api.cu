@@ -878,7 +878,13 @@ int xsde_adjoint(xsde_problem *p, const xsde_vector *psi0, const xsde_vector *ta
     const int64_t K = ckpt_every < nsteps ? ckpt_every : nsteps;
     const int64_t nck = (nsteps + K - 1) / K;
     const size_t eb = elem_bytes(p->dtype);
-    const size_t need = (size_t)(nck + 4 * K) * npaths * g.npts * eb;
+    // all stage inputs kept (segments recomputed in parallel) when that takes at
+    // most kAdjFullBytes; else one segment's at a time
+    size_t full_limit = (size_t)2 << 30;
+    if (const char *env = std::getenv("XSDE_ADJOINT_MAX_BYTES")) full_limit = (size_t)std::strtoull(env, nullptr, 10);
+    const size_t full_need = (size_t)(nck + 4 * nsteps + 1) * npaths * g.npts * eb;
+    const bool full = full_need <= full_limit && nck - 1 <= 65535;
+    const size_t need = full ? full_need : (size_t)(nck + 4 * K) * npaths * g.npts * eb;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (p->adj_bytes < need) {
         if (p->d_adj) {
@@ -910,10 +916,15 @@ int xsde_adjoint(xsde_problem *p, const xsde_vector *psi0, const xsde_vector *ta
         q.dx = grid_dx(g, 0);
         q.ckpt = static_cast<V *>(p->d_adj);
         q.interm = q.ckpt + (size_t)nck * npaths * g.npts;
+        q.final_state = q.interm + (size_t)(full ? nsteps : K) * 4 * npaths * g.npts;
         q.loss = loss;
         q.dLdV = dLdV;
         q.dLdpsi0 = static_cast<V *>(dLdpsi0);
-        XSDE_CUDA(timed(p, 1, s, [&] { return launch_adjoint_1d<R>(g.n[0], q, s); }), "xsde_adjoint launch");
+        const int phases[3] = {ADJ_FORWARD, ADJ_RECOMPUTE, ADJ_REVERSE};
+        for (int i = 0; i < (full ? 3 : 1); ++i) {
+            q.phase = full ? phases[i] : ADJ_SEQUENTIAL;
+            XSDE_CUDA(timed(p, 1, s, [&] { return launch_adjoint_1d<R>(g.n[0], q, s); }), "xsde_adjoint launch");
+        }
         return XSDE_OK;
     };
     return p->dtype == XSDE_C64 ? run(0.0f) : run(0.0);

@@ -130,7 +130,9 @@ cudaError_t launch_col_pass_tma(const Params2D<float> &p, const CUtensorMap &map
 // --------------------------------------------------------------------------
 // 1D adjoint: loss sum_p 1 - |<target|psi_N>|^2 and dL/dV (rk4ip_adjoint.cu)
 // --------------------------------------------------------------------------
+enum AdjPhase { ADJ_SEQUENTIAL = 0, ADJ_FORWARD = 1, ADJ_RECOMPUTE = 2, ADJ_REVERSE = 3 };
 template <typename R> struct AdjParams {
+    int phase;             // AdjPhase (see rk4ip_adjoint.cu)
     const cx<R> *psi0;     // [npaths][N]
     const cx<R> *target;   // [N]
     int64_t npaths;
@@ -141,7 +143,8 @@ template <typename R> struct AdjParams {
     LocalTerm<R> lt;       // deterministic: noise off
     double dx;
     cx<R> *ckpt;           // [ceil(nsteps/K)][npaths][N]
-    cx<R> *interm;         // [npaths][K][4][N]
+    cx<R> *interm;         // [npaths][nsteps][4][N], or [npaths][K][4][N] (ADJ_SEQUENTIAL)
+    cx<R> *final_state;    // [npaths][N] (the three-launch schedule)
     double *loss;          // accumulated (zeroed by the caller)
     double *dLdV;          // [nsteps][N], accumulated (zeroed by the caller)
     cx<R> *dLdpsi0;        // [npaths][N] or nullptr

@@ -10,11 +10,18 @@
 //   B = -i dt g u^2, adjoint mu -> conj(A) mu + B conj(mu); D^T = F^-1 conj(E) F;
 //   dN/dV_j = -i dt u_j, so a stage with cotangent mu adds dt (mu.x u.y - mu.y u.x)
 //   to dL/dV_j.
-// One CTA per path: a forward sweep keeps a checkpoint every K steps; then, per
-// segment from the last, the forward steps are recomputed from the checkpoint
-// with their four stage inputs (a, a_I + k1/2, a_I + k2/2, D(a_I + k3)) stored,
-// and the reverse steps consume them.  Every transform pair runs on two vectors
-// in lockstep, so a reverse step costs about one forward step.
+// A forward sweep keeps a checkpoint every K steps; every segment but the last
+// is then recomputed from its checkpoint with the four stage inputs of each
+// step (a, a_I + k1/2, a_I + k2/2, D(a_I + k3)) stored, and the reverse steps
+// consume them.  Every transform pair runs on two vectors in lockstep, so a
+// reverse step costs about one forward step.  Two schedules (AdjParams::phase):
+//  - ADJ_FORWARD, ADJ_RECOMPUTE, ADJ_REVERSE: three launches.  The forward
+//    sweep (one CTA per path) also stores the last segment's stage inputs and
+//    the final state; all other segments are recomputed at once, one CTA per
+//    (segment, path); the reverse sweep (one CTA per path) starts from the final
+//    state.  Stage inputs of all steps are kept ([paths][nsteps][4][N]).
+//  - ADJ_SEQUENTIAL: one launch, one CTA per path, recomputing one segment at a
+//    time into a [paths][K][4][N] buffer (when the full buffer does not fit).
 #include "fft.cuh"
 #include "kernels.h"
 
@@ -89,7 +96,9 @@ __global__ void __launch_bounds__(N / E) rk4ip_adjoint_kernel(const AdjParams<R>
         fft<N, E, +1, 2>(x, t, sm2, L, sync, tw);
     };
     const size_t stride = (size_t)p.npaths * N;              // one field of all paths
-    V *interm = p.interm + (size_t)path * p.K * 4 * N;       // [K][4][N] for this path
+    const bool full = p.phase != ADJ_SEQUENTIAL;
+    // stage inputs of this path: [nsteps][4][N] (full) or [K][4][N]
+    V *interm = p.interm + (size_t)path * (full ? p.nsteps : p.K) * 4 * N;
     // one forward step from x[0]; with `store`, keeps the stage inputs of step n
     auto forward = [&](V (&x)[2][E], int64_t n, bool store, int64_t slot) {
         R dtv[E];
@@ -122,20 +131,40 @@ __global__ void __launch_bounds__(N / E) rk4ip_adjoint_kernel(const AdjParams<R>
         }
     };
 
-    // ---- forward sweep with checkpoints ------------------------------------
-    V x[2][E];
-#pragma unroll
-    for (int m = 0; m < E; ++m) x[0][m] = p.psi0[path * N + t + m * T];
-    // the last segment keeps its stage inputs right away: the reverse sweep
-    // starts there and needs no recomputation of it
     const int64_t nseg = (p.nsteps + p.K - 1) / p.K;
     const int64_t last0 = (nseg - 1) * p.K;
-    for (int64_t n = 0; n < p.nsteps; ++n) {
-        if (n % p.K == 0) {
+    V x[2][E];
+
+    // ---- recomputation of segment blockIdx.y from its checkpoint ------------
+    if (p.phase == ADJ_RECOMPUTE) {
+        const int64_t n0 = (int64_t)blockIdx.y * p.K, n1 = n0 + p.K;   // never the last segment
 #pragma unroll
-            for (int m = 0; m < E; ++m) p.ckpt[(n / p.K) * stride + path * N + t + m * T] = x[0][m];
+        for (int m = 0; m < E; ++m) x[0][m] = p.ckpt[blockIdx.y * stride + path * N + t + m * T];
+        for (int64_t n = n0; n < n1; ++n) forward(x, n, true, n);
+        return;
+    }
+
+    // ---- forward sweep with checkpoints ------------------------------------
+    if (p.phase == ADJ_REVERSE) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) x[0][m] = p.final_state[path * N + t + m * T];
+    } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m) x[0][m] = p.psi0[path * N + t + m * T];
+        // the last segment keeps its stage inputs right away: the reverse
+        // sweep starts there and needs no recomputation of it
+        for (int64_t n = 0; n < p.nsteps; ++n) {
+            if (n % p.K == 0) {
+#pragma unroll
+                for (int m = 0; m < E; ++m) p.ckpt[(n / p.K) * stride + path * N + t + m * T] = x[0][m];
+            }
+            forward(x, n, n >= last0, full ? n : n - last0);
         }
-        forward(x, n, n >= last0, n - last0);
+        if (p.phase == ADJ_FORWARD) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) p.final_state[path * N + t + m * T] = x[0][m];
+            return;
+        }
     }
 
     // ---- loss and the final cotangent ----------------------------------------
@@ -179,13 +208,13 @@ __global__ void __launch_bounds__(N / E) rk4ip_adjoint_kernel(const AdjParams<R>
     for (int64_t sgi = nseg - 1; sgi >= 0; --sgi) {
         const int64_t n0 = sgi * p.K;
         const int64_t n1 = (n0 + p.K < p.nsteps) ? n0 + p.K : p.nsteps;
-        if (sgi != nseg - 1) {
+        if (!full && sgi != nseg - 1) {
 #pragma unroll
             for (int m = 0; m < E; ++m) x[0][m] = p.ckpt[sgi * stride + path * N + t + m * T];
             for (int64_t n = n0; n < n1; ++n) forward(x, n, true, n - n0);
         }
         for (int64_t n = n1 - 1; n >= n0; --n) {
-            const int64_t slot = n - n0;
+            const int64_t slot = full ? n : n - n0;
             R dtv[E], gv[E];
             V y[2][E], w2s[E], w3s[E];
 #pragma unroll
@@ -242,7 +271,10 @@ template <typename R, int N> cudaError_t adj_launch(const AdjParams<R> &p, cudaS
     auto kern = rk4ip_adjoint_kernel<R, N, E>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)p.npaths, T, smem, s>>>(p);
+    const unsigned segs = (unsigned)((p.nsteps + p.K - 1) / p.K);
+    const dim3 grid((unsigned)p.npaths, p.phase == ADJ_RECOMPUTE ? segs - 1 : 1u);
+    if (grid.y == 0) return cudaSuccess;     // a single segment: nothing to recompute
+    kern<<<grid, T, smem, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -94,6 +94,21 @@ def test_checkpoint_interval_does_not_change_the_gradient():
         assert np.max(np.abs(d - base)) <= 1e-14 * np.max(np.abs(base))
 
 
+@pytest.mark.parametrize("npaths,k", [(1, 50), (3, 7)])
+def test_sequential_and_parallel_recompute_agree(monkeypatch, npaths, k):
+    """One segment at a time (workspace of one segment) and all segments at once
+    (stage inputs of every step kept) run the same arithmetic."""
+    w = W.adjoint_control(n=512, nsteps=120, L=16.0)
+    rng = np.random.default_rng(9)
+    psi0 = np.stack([w.psi0[0] * np.exp(0.1j * rng.standard_normal(512)) for _ in range(npaths)])
+    l_par, d_par = gpu_adjoint(w, "c128", ckpt=k, psi0=psi0)
+    monkeypatch.setenv("XSDE_ADJOINT_MAX_BYTES", "1")
+    l_seq, d_seq = gpu_adjoint(w, "c128", ckpt=k, psi0=psi0)
+    tol = 0.0 if npaths == 1 else 1e-14
+    assert abs(l_seq - l_par) <= tol
+    assert np.max(np.abs(d_seq - d_par)) <= tol * np.max(np.abs(d_par))
+
+
 def test_adjoint_sums_over_paths():
     w = W.adjoint_control(n=512, nsteps=80, L=16.0)
     rng = np.random.default_rng(4)
