@@ -331,13 +331,13 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// A 2D complex64 field [npaths*n0][n1] as 8-byte elements, box 16 x col_tma_box_rows(n0)
+// A 2D complex64 field [npaths*n0][n1] as 8-byte elements, box COL_TMA_C x col_tma_box_rows(n0)
 bool encode_field_map(CUtensorMap *m, void *base, const xsde_grid &g, int64_t npaths) {
     auto fn = tensor_map_encoder();
     if (!fn) return false;
     cuuint64_t dims[2] = {(cuuint64_t)g.n[1], (cuuint64_t)(npaths * g.n[0])};
     cuuint64_t strides[1] = {(cuuint64_t)g.n[1] * 8};
-    cuuint32_t box[2] = {16u, (cuuint32_t)col_tma_box_rows(g.n[0])};
+    cuuint32_t box[2] = {(cuuint32_t)COL_TMA_C, (cuuint32_t)col_tma_box_rows(g.n[0])};
     cuuint32_t estr[2] = {1u, 1u};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,

@@ -157,10 +157,19 @@ __device__ __forceinline__ void fft_stage(V (&v)[NV][E], int t, const Tw &tw) {
 
 // Move stage outputs to their Stockham positions and fetch the next inputs.
 // sm[iv] is the exchange buffer of vector iv; L maps logical index -> slot.
+template <typename Layout> struct odd_swap_first {
+    static constexpr bool value = false;
+};
+
 template <int N, int E, int R, int Ns, int NV, typename V, typename Layout, typename Sync>
 __device__ __forceinline__ void fft_exchange(V (&v)[NV][E], int t, V *const (&sm)[NV], const Layout &L,
                                              const Sync &sync) {
     constexpr int B = E / R, T = N / E;
+    // In the first exchange, threads t and t+1 write lines R apart.  Layouts
+    // where that lands both in the same banks have odd t write its R outputs in
+    // pairwise-swapped order, so simultaneous writes are R +- 1 lines apart.
+    constexpr bool swap = Ns == 1 && odd_swap_first<Layout>::value;
+    const bool odd = swap && (t & 1);
 #pragma unroll
     for (int q = 0; q < B; ++q) {
         const int j = t + q * T;
@@ -168,9 +177,15 @@ __device__ __forceinline__ void fft_exchange(V (&v)[NV][E], int t, V *const (&sm
         const int base = (j - k) * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int slot = L(base + r * Ns);
+            if constexpr (swap) {
+                const int slot = L(base + (odd ? (r ^ 1) : r));
 #pragma unroll
-            for (int iv = 0; iv < NV; ++iv) sm[iv][slot] = v[iv][q + r * B];
+                for (int iv = 0; iv < NV; ++iv) sm[iv][slot] = odd ? v[iv][q + (r ^ 1) * B] : v[iv][q + r * B];
+            } else {
+                const int slot = L(base + r * Ns);
+#pragma unroll
+                for (int iv = 0; iv < NV; ++iv) sm[iv][slot] = v[iv][q + r * B];
+            }
         }
     }
     sync();
@@ -216,6 +231,11 @@ template <int N> __host__ __device__ constexpr int padded_len() { return N + N /
 template <int C> struct ColumnTile {
     int c;
     __device__ __forceinline__ int operator()(int i) const { return i * C + c; }
+};
+// 8 complex64 columns: a row is 64 B, so two rows an even distance apart share
+// banks, and a half-warp (two threads per column) writing lines R apart conflicts
+template <> struct odd_swap_first<ColumnTile<8>> {
+    static constexpr bool value = true;
 };
 
 struct SyncBlock {

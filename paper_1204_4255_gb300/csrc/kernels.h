@@ -118,9 +118,10 @@ template <typename R> cudaError_t launch_col_pass(int mode, const Params2D<R> &p
 
 // complex64 persistent TMA-pipelined variants (rk4ip_2d_tma.cu): the row pass
 // for ROW_STAGE2/ROW_STEADY and the column pass for COL_PROPAGATE; `grid` is
-// the number of persistent CTAs (one per SM).  Field bases must be 16-byte
-// aligned; mapA/mapB describe A and B as [npaths*n0][n1] 8-byte elements with
-// a 16 x col_tma_box_rows(n0) box.
+// the number of SMs (the launchers place their persistent CTAs per SM).  Field
+// bases must be 16-byte aligned; mapA/mapB describe A and B as [npaths*n0][n1]
+// 8-byte elements with a COL_TMA_C x col_tma_box_rows(n0) box.
+constexpr int COL_TMA_C = 8;   // columns per column-pass tile
 bool tma_passes_supported(int n0, int n1);
 size_t col_tma_box_rows(int n0);
 cudaError_t launch_row_pass_tma(int mode, const Params2D<float> &p, int grid, cudaStream_t s);

@@ -9,9 +9,12 @@
 // and the result leaves through a bulk store, so the SM never waits on a global
 // load while it computes and no register holds data in flight.
 //   row item    : ROWS consecutive lines of A and of B (2 x 32 KB, 1D bulk copies)
-//   column item : a 16-column x n0-row tile of A or of B (64 KB, 2D tensor copies)
+//   column item : an 8-column x n0-row tile of A or of B (32 KB, 2D tensor copies);
+//                 two CTAs per SM, so one CTA's exchanges overlap the other's arithmetic
 // Row exchanges use an XOR swizzle within each line (conflict-free for n1 = 512);
-// column tiles are naturally conflict-free (a warp touches whole 128-byte rows).
+// column tiles are naturally conflict-free (a half-warp touches two whole 64-byte rows).
+#include <type_traits>
+
 #include "fft.cuh"
 #include "kernels.h"
 #include "tma.cuh"
@@ -125,7 +128,12 @@ __global__ void __launch_bounds__(RowTma<N1>::THREADS, 1) row_pass_tma_kernel(co
     const bool vtime = p.lt.pot == PM_TABLE && p.lt.V_nt > 1;
     const TwiddleTable<TW> tw{tw_s};
     const SwizzledLine L{};
-    const SyncBlock sync{};
+    // a line's exchanges involve only its own T threads: one warp, or a named
+    // barrier per line (ids 1..ROWS), so the lines of an item drift apart and
+    // one line's arithmetic overlaps another's exchanges
+    using LineSync = std::conditional_t<(T <= 32), SyncWarp, SyncNamed>;
+    LineSync sync{};
+    if constexpr (T > 32) sync = SyncNamed{1 + line, T};
 
     for (int64_t k = 0; k < mine; ++k) {
         const int s = (int)(k % NST);
@@ -165,7 +173,7 @@ __global__ void __launch_bounds__(RowTma<N1>::THREADS, 1) row_pass_tma_kernel(co
             x[0][m] = lineA[t + m * T];
             x[1][m] = lineB[t + m * T];
         }
-        __syncthreads();   // natural-order reads complete before swizzled exchanges
+        sync();   // the line's natural-order reads complete before swizzled exchanges
         fft<N1, E, +1, 2>(x, t, sm2, L, sync, tw);
         if constexpr (MODE == ROW_STAGE2) {
 #pragma unroll
@@ -235,7 +243,8 @@ __global__ void __launch_bounds__(RowTma<N1>::THREADS, 1) row_pass_tma_kernel(co
 // Column pass
 // ---------------------------------------------------------------------------
 template <int N0> struct ColTma {
-    static constexpr int C = 16;                          // 128-byte row segments
+    static constexpr int C = COL_TMA_C;                   // 64-byte row segments
+    static constexpr int CTAS_PER_SM = 2;                 // independent CTAs overlap their phases
     static constexpr int E = 16;
     static constexpr int T = N0 / E;
     static constexpr int THREADS = C * T;
@@ -246,7 +255,7 @@ template <int N0> struct ColTma {
 };
 
 template <int N0>
-__global__ void __launch_bounds__(ColTma<N0>::THREADS, 1)
+__global__ void __launch_bounds__(ColTma<N0>::THREADS, ColTma<N0>::CTAS_PER_SM)
     col_pass_tma_kernel(const Params2D<float> p, const __grid_constant__ CUtensorMap mapA,
                         const __grid_constant__ CUtensorMap mapB) {
     using Cfg = ColTma<N0>;
@@ -394,7 +403,8 @@ cudaError_t col_tma_launch(const Params2D<float> &p, const CUtensorMap &a, const
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
     if (e != cudaSuccess) return e;
     const int64_t items = p.npaths * (int64_t)(p.n1 / Cfg::C) * 2;
-    const int g = (int)(items < grid ? items : grid);
+    const int64_t want = (int64_t)grid * Cfg::CTAS_PER_SM;
+    const int g = (int)(items < want ? items : want);
     kern<<<g, Cfg::THREADS, Cfg::SMEM, s>>>(p, a, b);
     return cudaGetLastError();
 }
