@@ -259,10 +259,10 @@ int xsde_synchronize(xsde_problem *prob, void *stream);
  *     (filling 128 threads; one path for N >= 1024), or a half (variant 1),
  *     a quarter (variant 2, at least one path) or twice (variant 3, at most
  *     256 threads) as many; where a bound applies a variant repeats another;
- *   2D lattices (2 variants): 0 uses the fastest kernels available (the
- *     persistent TMA-pipelined complex64 passes where they apply), 1 forces
- *     the generic passes;
- *   0D and 3D lattices (1 variant).
+ *   2D and 3D lattices (2 variants): 0 uses the fastest kernels available
+ *     (the persistent TMA-pipelined complex64 passes where they apply: lines
+ *     of 128..1024 points, columns of 128..512), 1 forces the generic passes;
+ *   0D lattices (1 variant).
  * Out-of-range variants report XSDE_EINVAL.  xsde_autotune picks one by
  * timing. */
 int xsde_set_kernel_variant(xsde_problem *prob, int variant);

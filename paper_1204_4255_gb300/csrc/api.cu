@@ -331,18 +331,23 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// A 2D complex64 field [npaths*n0][n1] as 8-byte elements, box COL_TMA_C x col_tma_box_rows(n0)
-bool encode_field_map(CUtensorMap *m, void *base, const xsde_grid &g, int64_t npaths) {
+// A complex64 field viewed as [rows][cols] 8-byte elements for the column
+// pass: box COL_TMA_C x col_tma_box_rows(n0) (n0 = the column length).
+bool encode_field_map(CUtensorMap *m, void *base, int64_t rows, int64_t cols, int n0) {
     auto fn = tensor_map_encoder();
     if (!fn) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)g.n[1], (cuuint64_t)(npaths * g.n[0])};
-    cuuint64_t strides[1] = {(cuuint64_t)g.n[1] * 8};
-    cuuint32_t box[2] = {(cuuint32_t)COL_TMA_C, (cuuint32_t)col_tma_box_rows(g.n[0])};
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 8};
+    cuuint32_t box[2] = {(cuuint32_t)COL_TMA_C, (cuuint32_t)col_tma_box_rows(n0)};
     cuuint32_t estr[2] = {1u, 1u};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
+// The persistent TMA row pass applies to lines of n1 points when the line
+// count fills whole work items.
+bool tma_rows_ok(int n1, int64_t lines) { return tma_row_supported(n1) && lines % (4096 / n1) == 0; }
 
 // 3D: per exp(L dt/2) application a row pass along dimension 2 (with E2) and
 // column passes along dimensions 1 and 0 (E1, E0): the three one-dimensional
@@ -398,14 +403,42 @@ int run_3d(xsde_problem *p, void *psi, int64_t nsteps, int64_t npaths, uint64_t 
     q0.tw0 = static_cast<const tw_t<R> *>(p->d_tw[0]);
     q0.E0 = static_cast<const V *>(p->d_E[0]);
     q0.kinner = g.n[2];
+    // complex64: the persistent TMA passes for the hot modes where they apply
+    bool tma_row = false, tma_col1 = false, tma_col0 = false;
+    CUtensorMap map1A, map1B, map0A, map0B;
+    if constexpr (std::is_same<R, float>::value) {
+        if (p->kernel_variant == 0 && (uintptr_t)psi % 16 == 0 && (uintptr_t)p->d_scratch % 16 == 0) {
+            tma_row = tma_rows_ok(g.n[2], npaths * g.n[0] * g.n[1]);
+            // dimension 1: [npaths n0 n1][n2]; dimension 0: [npaths n0][n1 n2]
+            tma_col1 = tma_col_supported(g.n[1]) && g.n[2] % COL_TMA_C == 0 &&
+                       encode_field_map(&map1A, psi, npaths * g.n[0] * g.n[1], g.n[2], g.n[1]) &&
+                       encode_field_map(&map1B, p->d_scratch, npaths * g.n[0] * g.n[1], g.n[2], g.n[1]);
+            tma_col0 = tma_col_supported(g.n[0]) && encode_field_map(&map0A, psi, npaths * g.n[0],
+                                                                       (int64_t)g.n[1] * g.n[2], g.n[0]) &&
+                       encode_field_map(&map0B, p->d_scratch, npaths * g.n[0], (int64_t)g.n[1] * g.n[2], g.n[0]);
+        }
+    }
     auto row = [&](int mode, uint64_t sg, int slot) -> cudaError_t {
         qr.sg = sg;
         qr.sample_slot = slot;
-        return timed(p, 2 + mode, s, [&] { return launch_row_pass<R>(mode, qr, s); });
+        return timed(p, 2 + mode, s, [&] {
+            if constexpr (std::is_same<R, float>::value)
+                if (tma_row && (mode == ROW_STAGE2 || mode == ROW_STEADY))
+                    return launch_row_pass_tma(mode, qr, p->num_sms, s);
+            return launch_row_pass<R>(mode, qr, s);
+        });
     };
     auto col = [&](Params2D<R> &q, int mode, int slot) -> cudaError_t {
         q.sample_slot = slot;
-        return timed(p, 7 + (mode == COL_SPECTRAL ? 1 : 0), s, [&] { return launch_col_pass<R>(mode, q, s); });
+        return timed(p, 7 + (mode == COL_SPECTRAL ? 1 : 0), s, [&] {
+            if constexpr (std::is_same<R, float>::value) {
+                if (mode == COL_PROPAGATE && &q == &q1 && tma_col1)
+                    return launch_col_pass_tma(q, map1A, map1B, p->num_sms, s);
+                if (mode == COL_PROPAGATE && &q == &q0 && tma_col0)
+                    return launch_col_pass_tma(q, map0A, map0B, p->num_sms, s);
+            }
+            return launch_col_pass<R>(mode, q, s);
+        });
     };
     auto sample = [&](int slot, uint64_t gs) -> int {
         XSDE_CUDA(row(ROW_FFT_ONLY, gs, slot), "row pass");
@@ -502,12 +535,14 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
     q.status = p->d_status;
     const int S = sm.every;
     // complex64 lattices the persistent TMA passes cover take the hot modes there
-    bool use_tma = false;
+    bool tma_row = false, tma_col = false;
     CUtensorMap mapA, mapB;
     if constexpr (std::is_same<R, float>::value) {
-        if (p->kernel_variant == 0 && tma_passes_supported(g.n[0], g.n[1]) &&
-            (uintptr_t)psi % 16 == 0 && (uintptr_t)p->d_scratch % 16 == 0) {
-            use_tma = encode_field_map(&mapA, psi, g, npaths) && encode_field_map(&mapB, p->d_scratch, g, npaths);
+        if (p->kernel_variant == 0 && (uintptr_t)psi % 16 == 0 && (uintptr_t)p->d_scratch % 16 == 0) {
+            tma_row = tma_rows_ok(g.n[1], npaths * g.n[0]);
+            tma_col = tma_col_supported(g.n[0]) && g.n[1] % COL_TMA_C == 0 &&
+                      encode_field_map(&mapA, psi, npaths * g.n[0], g.n[1], g.n[0]) &&
+                      encode_field_map(&mapB, p->d_scratch, npaths * g.n[0], g.n[1], g.n[0]);
         }
     }
     auto row = [&](int mode, uint64_t sg, int slot) -> cudaError_t {
@@ -515,7 +550,7 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
         q.sample_slot = slot;
         return timed(p, 2 + mode, s, [&] {
             if constexpr (std::is_same<R, float>::value)
-                if (use_tma && (mode == ROW_STAGE2 || mode == ROW_STEADY))
+                if (tma_row && (mode == ROW_STAGE2 || mode == ROW_STEADY))
                     return launch_row_pass_tma(mode, q, p->num_sms, s);
             return launch_row_pass<R>(mode, q, s);
         });
@@ -524,7 +559,7 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
         q.sample_slot = slot;
         return timed(p, 7 + mode, s, [&] {
             if constexpr (std::is_same<R, float>::value)
-                if (use_tma && mode == COL_PROPAGATE) return launch_col_pass_tma(q, mapA, mapB, p->num_sms, s);
+                if (tma_col && mode == COL_PROPAGATE) return launch_col_pass_tma(q, mapA, mapB, p->num_sms, s);
             return launch_col_pass<R>(mode, q, s);
         });
     };
@@ -599,7 +634,8 @@ int integrate_on(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t 
 int variants_for(const xsde_problem *p) {
     switch (p->grid.ndim) {
         case 1: return rk4ip_1d_variants();
-        case 2: return 2;
+        case 2:
+        case 3: return 2;
         default: return 1;
     }
 }

@@ -122,7 +122,8 @@ template <typename R> cudaError_t launch_col_pass(int mode, const Params2D<R> &p
 // bases must be 16-byte aligned; mapA/mapB describe A and B as [npaths*n0][n1]
 // 8-byte elements with a COL_TMA_C x col_tma_box_rows(n0) box.
 constexpr int COL_TMA_C = 8;   // columns per column-pass tile
-bool tma_passes_supported(int n0, int n1);
+bool tma_row_supported(int n1);   // row-pass line length
+bool tma_col_supported(int n0);   // column length
 size_t col_tma_box_rows(int n0);
 cudaError_t launch_row_pass_tma(int mode, const Params2D<float> &p, int grid, cudaStream_t s);
 cudaError_t launch_col_pass_tma(const Params2D<float> &p, const CUtensorMap &mapA, const CUtensorMap &mapB, int grid,

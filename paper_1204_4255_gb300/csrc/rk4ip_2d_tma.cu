@@ -110,6 +110,9 @@ __global__ void __launch_bounds__(RowTma<N1>::THREADS, 1) row_pass_tma_kernel(co
         fence_barrier_init();
     }
     __syncthreads();
+    // the tables above are constants; the fields are the previous pass's output
+    grid_launch_dependents();
+    grid_dependency_wait();
 
     auto issue_load = [&](int64_t k) {   // item k of this CTA into stage k % NST
         const int s = (int)(k % NST);
@@ -154,10 +157,32 @@ __global__ void __launch_bounds__(RowTma<N1>::THREADS, 1) row_pass_tma_kernel(co
         V *lineB = lineA + ROWS * N1;
         V *const sm2[2] = {lineA, lineB};
 
+        // 3D lattices: line i0 of a path is the point pair (i0 / nmid, i0 % nmid)
+        const int la = p.ndim == 3 ? i0 / p.nmid : i0;
+        const int lb = p.ndim == 3 ? i0 - la * p.nmid : 0;
+        // the potential of potential() written out per dimension (no indexed
+        // coordinate array, which a run-time dimension count would put in
+        // local memory)
         auto pot = [&](int m, uint64_t gs) -> float {
             const int i1 = t + m * T;
-            const int idx[3] = {i0, i1, 0};
-            return potential(p.lt, 2, idx, (int64_t)i0 * N1 + i1, gs);
+            if (p.lt.pot == PM_HARMONIC) {
+                const float xa = p.lt.xmin[0] + (float)la * p.lt.dx[0];
+                const float xb = p.lt.xmin[1] + (float)(p.ndim == 3 ? lb : i1) * p.lt.dx[1];
+                float v = 0.0f;
+                v += p.lt.hw2[0] * xa * xa;
+                v += p.lt.hw2[1] * xb * xb;
+                if (p.ndim == 3) {
+                    const float xc = p.lt.xmin[2] + (float)i1 * p.lt.dx[2];
+                    v += p.lt.hw2[2] * xc * xc;
+                }
+                return v;
+            }
+            if (p.lt.pot == PM_TABLE) {
+                int64_t r = p.lt.V_nt > 1 ? (int64_t)gs : 0;
+                if (r >= p.lt.V_nt) r = p.lt.V_nt - 1;
+                return p.lt.V[r * p.lt.npts + (int64_t)i0 * N1 + i1];
+            }
+            return 0.0f;
         };
         float Vst[E];
 #pragma unroll
@@ -244,9 +269,10 @@ __global__ void __launch_bounds__(RowTma<N1>::THREADS, 1) row_pass_tma_kernel(co
 // ---------------------------------------------------------------------------
 template <int N0> struct ColTma {
     static constexpr int C = COL_TMA_C;                   // 64-byte row segments
-    static constexpr int CTAS_PER_SM = 2;                 // independent CTAs overlap their phases
-    static constexpr int E = 16;
-    static constexpr int T = N0 / E;
+    static constexpr int E = N0 >= 512 ? 16 : 8;
+    static constexpr int T = N0 / E;                      // threads per column
+    // independent CTAs per SM overlap their phases: 16 warps per SM
+    static constexpr int CTAS_PER_SM = 512 / (C * T);
     static constexpr int THREADS = C * T;
     static constexpr int BOXR = N0 < 256 ? N0 : 256;      // tensor-copy box rows
     static constexpr size_t ITEM = (size_t)N0 * C * sizeof(V);
@@ -283,6 +309,9 @@ __global__ void __launch_bounds__(ColTma<N0>::THREADS, ColTma<N0>::CTAS_PER_SM)
         fence_barrier_init();
     }
     __syncthreads();
+    // the tables above are constants; the fields are the previous pass's output
+    grid_launch_dependents();
+    grid_dependency_wait();
 
     // item -> (vector, path, column tile)
     auto decode = [&](int64_t k, int &vec, int64_t &path, int &tile) {
@@ -384,6 +413,24 @@ __global__ void __launch_bounds__(ColTma<N0>::THREADS, ColTma<N0>::CTAS_PER_SM)
     if (tid == 0) bulk_wait<0>();
 }
 
+// Launch with programmatic stream serialization: the kernel may start while
+// the previous kernel of the stream drains; it waits for that kernel's results
+// in grid_dependency_wait() after loading its tables.
+template <typename K, typename... Args>
+cudaError_t launch_dependent(K kern, int grid, int threads, size_t smem, cudaStream_t s, const Args &...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <int N1, int MODE> cudaError_t row_tma_launch(const Params2D<float> &p, int grid, cudaStream_t s) {
     using Cfg = RowTma<N1>;
     auto kern = row_pass_tma_kernel<N1, MODE>;
@@ -391,8 +438,7 @@ template <int N1, int MODE> cudaError_t row_tma_launch(const Params2D<float> &p,
     if (e != cudaSuccess) return e;
     const int64_t items = p.npaths * (int64_t)p.n0 / Cfg::ROWS;
     const int g = (int)(items < grid ? items : grid);
-    kern<<<g, Cfg::THREADS, Cfg::SMEM, s>>>(p);
-    return cudaGetLastError();
+    return launch_dependent(kern, g, Cfg::THREADS, Cfg::SMEM, s, p);
 }
 
 template <int N0>
@@ -405,22 +451,19 @@ cudaError_t col_tma_launch(const Params2D<float> &p, const CUtensorMap &a, const
     const int64_t items = p.npaths * (int64_t)(p.n1 / Cfg::C) * 2;
     const int64_t want = (int64_t)grid * Cfg::CTAS_PER_SM;
     const int g = (int)(items < want ? items : want);
-    kern<<<g, Cfg::THREADS, Cfg::SMEM, s>>>(p, a, b);
-    return cudaGetLastError();
+    return launch_dependent(kern, g, Cfg::THREADS, Cfg::SMEM, s, p, a, b);
 }
 
 }  // namespace
 
-bool tma_passes_supported(int n0, int n1) {
-    const bool r = n1 == 256 || n1 == 512 || n1 == 1024;
-    const bool c = n0 == 256 || n0 == 512;
-    return r && c;
-}
+bool tma_row_supported(int n1) { return n1 == 128 || n1 == 256 || n1 == 512 || n1 == 1024; }
+bool tma_col_supported(int n0) { return n0 == 128 || n0 == 256 || n0 == 512; }
 
 cudaError_t launch_row_pass_tma(int mode, const Params2D<float> &p, int grid, cudaStream_t s) {
     if (mode != ROW_STAGE2 && mode != ROW_STEADY) return cudaErrorInvalidValue;
     const bool st = mode == ROW_STEADY;
     switch (p.n1) {
+        case 128: return st ? row_tma_launch<128, ROW_STEADY>(p, grid, s) : row_tma_launch<128, ROW_STAGE2>(p, grid, s);
         case 256: return st ? row_tma_launch<256, ROW_STEADY>(p, grid, s) : row_tma_launch<256, ROW_STAGE2>(p, grid, s);
         case 512: return st ? row_tma_launch<512, ROW_STEADY>(p, grid, s) : row_tma_launch<512, ROW_STAGE2>(p, grid, s);
         case 1024: return st ? row_tma_launch<1024, ROW_STEADY>(p, grid, s) : row_tma_launch<1024, ROW_STAGE2>(p, grid, s);
@@ -431,6 +474,7 @@ cudaError_t launch_row_pass_tma(int mode, const Params2D<float> &p, int grid, cu
 cudaError_t launch_col_pass_tma(const Params2D<float> &p, const CUtensorMap &a, const CUtensorMap &b, int grid,
                                 cudaStream_t s) {
     switch (p.n0) {
+        case 128: return col_tma_launch<128>(p, a, b, grid, s);
         case 256: return col_tma_launch<256>(p, a, b, grid, s);
         case 512: return col_tma_launch<512>(p, a, b, grid, s);
         default: return cudaErrorInvalidValue;

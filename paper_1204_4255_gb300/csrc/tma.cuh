@@ -100,4 +100,12 @@ template <int N> __device__ __forceinline__ void bulk_wait() {
 // make generic-proxy shared-memory writes visible to the async proxy (TMA)
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Programmatic dependent launch: let the next kernel of the stream (launched
+// with programmatic stream serialization) be scheduled once every CTA of this
+// grid has called this or exited ...
+__device__ __forceinline__ void grid_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// ... and wait until the grids this one depends on have completed and their
+// memory operations are visible (a no-op without a programmatic dependency).
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 }  // namespace xsde

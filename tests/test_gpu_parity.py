@@ -281,6 +281,32 @@ def test_3d_gpe_noise_and_moments(shape, dtype):
     assert np.max(np.abs(pq - opq) / np.abs(opq)) < tol
 
 
+@pytest.mark.parametrize("shape", [(16, 128, 128), (128, 16, 128), (128, 128, 16), (128, 128), (16, 128),
+                                   (128, 16)])
+def test_c64_pipelined_passes_3d_and_short_lines(shape):
+    """The TMA-pipelined complex64 passes on 128-point lines and columns and on
+    3D lattices (row pass along dimension 2, column passes along 1 and 0, each
+    where its length applies) against the generic passes and the FP64 oracle,
+    with noise, a ragged path count and the sampling group on."""
+    rng = np.random.default_rng(sum(shape) + len(shape))
+    nd = len(shape)
+    axes = [-5 + np.arange(n) * 10 / n for n in shape]
+    grids = np.meshgrid(*axes, indexing="ij")
+    base = np.exp(-sum((0.8 + 0.2 * d) * g ** 2 for d, g in enumerate(grids)) / 4)
+    npaths = 3
+    psi0 = np.stack([base * np.exp(0.2j * rng.standard_normal(shape)) for _ in range(npaths)])
+    w = W.Workload("gpe_tma", shape, (-5.0,) * nd, (5.0,) * nd, 0j, -0.5j, 3.0, W.POT_HARMONIC,
+                   tuple(0.8 + 0.2 * d for d in range(nd)), None, W.NOISE_ADD_COMPLEX, 0.1, 56, 1e-3, 7,
+                   psi0.astype(np.complex128), 3)
+    fast, pp_f, pq_f = gpu_run(w, "c64", sample_every=3, path0=1, variant=0)
+    gen, _, _ = gpu_run(w, "c64", sample_every=3, path0=1, variant=1)
+    ref, opp, opq = O.run_workload(w, sample_every=3, path0=1)
+    assert np.max(rel_l2(fast.reshape(npaths, -1), ref.reshape(npaths, -1), axis=1)) < 1e-4
+    assert np.max(rel_l2(fast.reshape(npaths, -1), gen.reshape(npaths, -1), axis=1)) < 1e-5
+    assert np.max(np.abs(pp_f - opp) / np.abs(opp)) < 1e-4
+    assert np.max(np.abs(pq_f - opq) / np.abs(opq)) < 1e-4
+
+
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_3d_gpe_128_cubed(dtype):
     """The 128^3 Thomas-Fermi GPE (V = r^2/2, g = 200, box [-10,10)^3) at full size."""
