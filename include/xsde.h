@@ -255,10 +255,13 @@ int xsde_synchronize(xsde_problem *prob, void *stream);
 
 /* Kernel implementation for this problem, in [0, xsde_kernel_variants(prob)).
  * All variants compute the same scheme; they differ in launch shape:
- *   1D lattices (4 variants): one CTA carries the default number of paths
- *     (filling 128 threads; one path for N >= 1024), or a half (variant 1),
- *     a quarter (variant 2, at least one path) or twice (variant 3, at most
- *     256 threads) as many; where a bound applies a variant repeats another;
+ *   1D lattices (6 variants): variants 0-3 give each thread 8 points of a
+ *     path (radix-8 stages) and one CTA the default number of paths (filling
+ *     128 threads; one path for N >= 1024), a half (1), a quarter (2, at least
+ *     one path) or twice (3, at most 256 threads) as many; variants 4 and 5
+ *     give each thread 4 or 2 points (radix-4 or radix-2 stages, so a path
+ *     spreads over more warps) with the default paths per CTA for that shape;
+ *     where a bound applies a variant repeats another;
  *   2D and 3D lattices (2 variants): 0 uses the fastest kernels available
  *     (the persistent TMA-pipelined complex64 passes where they apply: lines
  *     of 128..1024 points, columns of 128..512), 1 forces the generic passes;

@@ -65,6 +65,7 @@ struct xsde_problem {
     double *per_path = nullptr, *per_point = nullptr;
     double table_dt = -1.0;
     void *d_tw[3] = {nullptr, nullptr, nullptr};
+    void *d_tw1d[2] = {nullptr, nullptr};   // 1D: twiddles of the radix-4 and radix-2 plans
     void *d_E[3] = {nullptr, nullptr, nullptr};
     void *d_scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -202,13 +203,13 @@ void make_twiddle(const std::complex<double> &z, float4 *out) {
 // per-stage layout of fft.cuh: stage (Ns, R) holds w_n^(r k n/(Ns R)) at
 // [stage_table_offset(n, Ns) + (r-1) Ns + k]; n entries are allocated (the
 // table needs at most n - 1)
-template <typename R> int upload_twiddles(int n, void **dptr, cudaStream_t s) {
+template <typename R, int E = 8> int upload_twiddles(int n, void **dptr, cudaStream_t s) {
     std::vector<tw_t<R>> tmp(n);
     make_twiddle(std::complex<double>(0.0, 0.0), &tmp[n - 1]);
     for (int ns = 1; ns < n;) {
-        const int rad = stage_radix<8>(n / ns);
+        const int rad = stage_radix<E>(n / ns);
         if (ns > 1) {
-            const int off = stage_table_offset(n, ns);
+            const int off = stage_table_offset<E>(n, ns);
             for (int r = 1; r < rad; ++r)
                 for (int k = 0; k < ns; ++k) {
                     const long m = (long)r * k * (n / (ns * rad));
@@ -237,6 +238,9 @@ template <typename V> int ensure_tables(xsde_problem *p, double dt, cudaStream_t
     for (int d = 0; d < g.ndim; ++d)
         if ((rc = upload_twiddles<decltype(V::x)>(g.n[d], &p->d_tw[d], s)) != XSDE_OK) return rc;
     if (g.ndim == 1) {
+        // the radix-4 and radix-2 plans of the 4- and 2-element launch shapes
+        if ((rc = upload_twiddles<decltype(V::x), 4>(g.n[0], &p->d_tw1d[0], s)) != XSDE_OK) return rc;
+        if ((rc = upload_twiddles<decltype(V::x), 2>(g.n[0], &p->d_tw1d[1], s)) != XSDE_OK) return rc;
         std::vector<std::complex<double>> e(g.n[0]);
         for (int i = 0; i < g.n[0]; ++i) {
             const double k = kval(g, 0, i);
@@ -509,7 +513,8 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
         q.nsteps = nsteps;
         q.step0 = step0;
         q.Etab = static_cast<const V *>(p->d_E[0]);
-        q.tw = static_cast<const tw_t<R> *>(p->d_tw[0]);
+        const int elems = rk4ip_1d_elems(p->kernel_variant);
+        q.tw = static_cast<const tw_t<R> *>(elems == 8 ? p->d_tw[0] : p->d_tw1d[elems == 4 ? 0 : 1]);
         q.lt = lt;
         q.sm = sm;
         q.status = p->d_status;
@@ -765,6 +770,8 @@ void xsde_problem_destroy(xsde_problem *p) {
         cudaFree(p->d_tw[d]);
         cudaFree(p->d_E[d]);
     }
+    cudaFree(p->d_tw1d[0]);
+    cudaFree(p->d_tw1d[1]);
     cudaFree(p->d_scratch);
     cudaFree(p->d_adj);
     cudaFree(p->d_status);
@@ -1249,6 +1256,8 @@ std::vector<uintptr_t> member_signature(const xsde_batch_member &m) {
         v.push_back((uintptr_t)p->d_tw[d]);
         v.push_back((uintptr_t)p->d_E[d]);
     }
+    v.push_back((uintptr_t)p->d_tw1d[0]);
+    v.push_back((uintptr_t)p->d_tw1d[1]);
     return v;
 }
 

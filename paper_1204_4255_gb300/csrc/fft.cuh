@@ -35,16 +35,18 @@ template <int E> __host__ __device__ constexpr int stage_radix(int rem) {
 // Twiddles are stored per stage: the stage starting at Ns with radix R holds
 // w_N^(r k N/(Ns R)) at [offset(Ns) + (r-1) Ns + k], r in [1,R), k in [0,Ns),
 // so the lanes of a warp (consecutive k) read consecutive entries.  The radix
-// plan is the same for every E >= 8 used here.
-__host__ __device__ constexpr int stage_table_offset(int N, int Ns) {
+// plan depends on E only through the largest radix min(E, 8): one table serves
+// every E >= 8, others need the table of their own plan.
+template <int E> __host__ __device__ constexpr int stage_table_offset(int N, int Ns) {
     int off = 0, ns = 1;
     while (ns < Ns) {
-        const int R = stage_radix<8>(N / ns);
+        const int R = stage_radix<E>(N / ns);
         if (ns > 1) off += (R - 1) * ns;
         ns *= R;
     }
     return off;
 }
+__host__ __device__ constexpr int stage_table_offset(int N, int Ns) { return stage_table_offset<8>(N, Ns); }
 __host__ __device__ constexpr int stage_table_size(int N) { return stage_table_offset(N, N); }
 
 // ---------------------------------------------------------------------------
@@ -133,9 +135,8 @@ __device__ __forceinline__ void fft_stage(V (&v)[NV][E], int t, const Tw &tw) {
     for (int q = 0; q < B; ++q) {
         TW w[R];
         if constexpr (Ns > 1) {
-            static_assert(E >= 8 || N <= E, "per-stage twiddle tables follow the E >= 8 radix plan");
             const int k = (t + q * T) & (Ns - 1);
-            constexpr int off = stage_table_offset(N, Ns);
+            constexpr int off = stage_table_offset<E>(N, Ns);
 #pragma unroll
             for (int r = 1; r < R; ++r) w[r] = tw(off + (r - 1) * Ns + k);
         }

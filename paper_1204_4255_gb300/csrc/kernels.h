@@ -60,15 +60,17 @@ template <typename R> struct Params1D {
     int64_t nsteps;
     uint64_t step0;        // global index of local step 0
     const cx<R> *Etab;     // exp(L(k) dt/2)/N in FFT order, hi [N] then lo [N]
-    const tw_t<R> *tw;     // exp(-2 pi i m/N) [N] (FP32: with radial correction)
+    const tw_t<R> *tw;     // per-stage twiddles of the variant's radix plan [N] (FP32: hi, lo)
     LocalTerm<R> lt;
     Sampling sm;
     int *status;
 };
-// variant v in [0, rk4ip_1d_variants()) sets the paths per CTA: the default
-// (filling 128 threads), a half, a quarter (at least one), or twice (at most
-// 256 threads) as many
+// variant v in [0, rk4ip_1d_variants()) sets the launch shape: elements per
+// thread rk4ip_1d_elems(v) (8, or 4 / 2 for variants 4 / 5, whose twiddle
+// table follows the radix-4 / radix-2 plan) and paths per CTA (variants 0-3:
+// the default filling 128 threads, a half, a quarter, twice)
 int rk4ip_1d_variants();
+int rk4ip_1d_elems(int variant);
 template <typename R> cudaError_t launch_rk4ip_1d(int n, int variant, const Params1D<R> &p, cudaStream_t s);
 
 // --------------------------------------------------------------------------

@@ -184,8 +184,8 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
     }
 }
 
-template <typename R, int N, int PPC> cudaError_t launch_ppc(const Params1D<R> &p, cudaStream_t s) {
-    constexpr int E = 8, T = N / E;
+template <typename R, int N, int E, int PPC> cudaError_t launch_ppc(const Params1D<R> &p, cudaStream_t s) {
+    constexpr int T = N / E;
     const size_t smem = (size_t)N * sizeof(tw_t<R>) + (size_t)PPC * 2 * padded_len<N>() * sizeof(cx<R>);
     auto kern = rk4ip_1d_kernel<R, N, E, PPC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -195,19 +195,26 @@ template <typename R, int N, int PPC> cudaError_t launch_ppc(const Params1D<R> &
     return cudaGetLastError();
 }
 
-// paths per CTA: the default fills 128 threads; variants 1 and 2 carry a half
-// and a quarter of that (at least one path: more CTAs for small ensembles),
-// variant 3 twice as many (at most 256 threads, so no variant is squeezed
-// below 255 registers a thread)
+// default paths per CTA for E elements per thread: fill 128 threads
+template <int N, int E> constexpr int default_ppc() { return N / E >= 128 ? 1 : 128 / (N / E); }
+
+// Launch shapes.  Variants 0-3 keep 8 elements per thread (radix-8 stages):
+// the default paths per CTA, a half, a quarter (at least one; more CTAs for
+// small ensembles) and twice as many (at most 256 threads, so no variant is
+// squeezed below 255 registers a thread).  Variants 4 and 5 spread a path over
+// more threads, 4 or 2 elements each (radix-4 or radix-2 stages): more warps
+// per path for few, long, latency-bound paths.
 template <typename R, int N> cudaError_t launch_n(int variant, const Params1D<R> &p, cudaStream_t s) {
-    constexpr int T = N / 8, P0 = T >= 128 ? 1 : 128 / T;
+    constexpr int P0 = default_ppc<N, 8>(), T = N / 8;
     constexpr int P1 = P0 >= 2 ? P0 / 2 : 1, P2 = P0 >= 4 ? P0 / 4 : 1;
     constexpr int P3 = 2 * P0 * T <= 256 ? 2 * P0 : P0;
     switch (variant) {
-        case 1: return launch_ppc<R, N, P1>(p, s);
-        case 2: return launch_ppc<R, N, P2>(p, s);
-        case 3: return launch_ppc<R, N, P3>(p, s);
-        default: return launch_ppc<R, N, P0>(p, s);
+        case 1: return launch_ppc<R, N, 8, P1>(p, s);
+        case 2: return launch_ppc<R, N, 8, P2>(p, s);
+        case 3: return launch_ppc<R, N, 8, P3>(p, s);
+        case 4: return launch_ppc<R, N, 4, default_ppc<N, 4>()>(p, s);
+        case 5: return launch_ppc<R, N, 2, default_ppc<N, 2>()>(p, s);
+        default: return launch_ppc<R, N, 8, P0>(p, s);
     }
 }
 
@@ -229,7 +236,8 @@ template <typename R> cudaError_t launch_rk4ip_1d(int n, int variant, const Para
 
 // XSDE_REAL_BITS selects one precision per translation unit (parallel builds)
 #if !defined(XSDE_REAL_BITS) || XSDE_REAL_BITS == 32
-int rk4ip_1d_variants() { return 4; }
+int rk4ip_1d_variants() { return 6; }
+int rk4ip_1d_elems(int variant) { return variant == 4 ? 4 : variant == 5 ? 2 : 8; }
 template cudaError_t launch_rk4ip_1d<float>(int, int, const Params1D<float> &, cudaStream_t);
 #endif
 #if !defined(XSDE_REAL_BITS) || XSDE_REAL_BITS == 64

@@ -174,10 +174,10 @@ def test_batch_samples_equal_individual_samples():
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
 @pytest.mark.parametrize("n", [16, 128, 256, 1024, 2048])
 def test_1d_variants_agree(dtype, n):
-    """Paths per CTA changes the launch shape, not a path's operations.  Each
-    variant is its own compiled kernel, and the compiler may fuse a multiply and
-    an add into one FMA in one instantiation and not in another, so variants
-    agree to rounding rather than bit for bit; each is held to the oracle."""
+    """Paths per CTA and points per thread (radix-8, -4 or -2 stages) change the
+    launch shape and the order of the transform's operations.  Each variant is
+    its own compiled kernel, so variants agree to rounding rather than bit for
+    bit; each is held to the oracle."""
     from paper_1204_4255_gb300 import xsde
     ws = W.batched_instances(n3=0, sizes2=(), count2=0, sizes1=(n,), count1=9, nsteps=20)
     w = ws[0]
@@ -185,10 +185,10 @@ def test_1d_variants_agree(dtype, n):
     P = make_problem(w, dtype)
     nv = xsde.xsde_kernel_variants(P.prob)
     P.close()
-    assert nv == 4
+    assert nv == 6
     outs = _run_each([w] * nv, dtype, 20, variants=list(range(nv)))
     ref, _, _ = O.run_workload(w, nsteps=20)
-    close, tol = (1e-13, 1e-10) if dtype == "c128" else (2e-6, 1e-4)
+    close, tol = (1e-12, 1e-10) if dtype == "c128" else (1e-5, 1e-4)
     for v in range(nv):
         assert rel_l2(outs[v], outs[0]) < close, f"variant {v} vs 0"
         assert rel_l2(outs[v], ref) < tol, f"variant {v} vs oracle"
@@ -230,6 +230,6 @@ def test_batch_rejects_shared_problem_or_field():
     with pytest.raises(xsde.XsdeError):
         xsde.Batch([(P, psi, 0), (Q, psi, 0)])
     with pytest.raises(xsde.XsdeError):
-        xsde.xsde_set_kernel_variant(P.prob, 4)
+        xsde.xsde_set_kernel_variant(P.prob, xsde.xsde_kernel_variants(P.prob))
     P.close()
     Q.close()
