@@ -83,7 +83,10 @@ template <int N1> struct RowTma {
                                    NST * sizeof(uint64_t);
 };
 
-template <int N1, int MODE>
+// SAMPLE: this pass writes a sample (ROW_STEADY only); NOISE: the problem has
+// Wiener noise.  Both are template flags so the common pass carries neither the
+// sampling code nor the generator.
+template <int N1, int MODE, bool SAMPLE, bool NOISE>
 __global__ void __launch_bounds__(RowTma<N1>::THREADS, 1) row_pass_tma_kernel(const Params2D<float> p) {
     using Cfg = RowTma<N1>;
     constexpr int E = Cfg::E, T = Cfg::T, ROWS = Cfg::ROWS;
@@ -127,7 +130,6 @@ __global__ void __launch_bounds__(RowTma<N1>::THREADS, 1) row_pass_tma_kernel(co
 
     const float gdt = p.lt.gdt;
     const float sixth = 1.0f / 6.0f, third = 1.0f / 3.0f, half = 0.5f;
-    const bool sample = p.sample_slot >= 0;
     const bool vtime = p.lt.pot == PM_TABLE && p.lt.V_nt > 1;
     const TwiddleTable<TW> tw{tw_s};
     const SwizzledLine L{};
@@ -189,7 +191,14 @@ __global__ void __launch_bounds__(RowTma<N1>::THREADS, 1) row_pass_tma_kernel(co
         for (int m = 0; m < E; ++m) Vst[m] = vtime ? 0.0f : pot(m, 0);
         auto potv = [&](int m, uint64_t gs) -> float { return vtime ? pot(m, gs) : Vst[m]; };
         auto pterm = [&](int m, uint64_t gs) -> PointTerm<float> {
-            return point_term(p.lt, potv(m, gs), (uint32_t)(i0 * N1 + t + m * T), gp, (uint32_t)gs);
+            if constexpr (NOISE) {
+                return point_term(p.lt, potv(m, gs), (uint32_t)(i0 * N1 + t + m * T), gp, (uint32_t)gs);
+            } else {
+                PointTerm<float> pt;
+                pt.dtV = p.lt.dt * potv(m, gs);
+                pt.na = make_float2(0.0f, 0.0f);
+                return pt;
+            }
         };
 
         V x[2][E];
@@ -213,7 +222,7 @@ __global__ void __launch_bounds__(RowTma<N1>::THREADS, 1) row_pass_tma_kernel(co
         } else {
 #pragma unroll
             for (int m = 0; m < E; ++m) x[0][m] = caxpy(x[1][m], sixth, apply_N(x[0][m], pterm(m, p.sg), gdt));
-            if (sample) {
+            if constexpr (SAMPLE) {
                 double acc[2] = {0.0, 0.0};
 #pragma unroll
                 for (int m = 0; m < E; ++m) {
@@ -431,9 +440,10 @@ cudaError_t launch_dependent(K kern, int grid, int threads, size_t smem, cudaStr
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-template <int N1, int MODE> cudaError_t row_tma_launch(const Params2D<float> &p, int grid, cudaStream_t s) {
+template <int N1, int MODE, bool SAMPLE, bool NOISE>
+cudaError_t row_tma_launch(const Params2D<float> &p, int grid, cudaStream_t s) {
     using Cfg = RowTma<N1>;
-    auto kern = row_pass_tma_kernel<N1, MODE>;
+    auto kern = row_pass_tma_kernel<N1, MODE, SAMPLE, NOISE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
     if (e != cudaSuccess) return e;
     const int64_t items = p.npaths * (int64_t)p.n0 / Cfg::ROWS;
@@ -459,14 +469,25 @@ cudaError_t col_tma_launch(const Params2D<float> &p, const CUtensorMap &a, const
 bool tma_row_supported(int n1) { return n1 == 128 || n1 == 256 || n1 == 512 || n1 == 1024; }
 bool tma_col_supported(int n0) { return n0 == 128 || n0 == 256 || n0 == 512; }
 
+template <int N1> cudaError_t row_tma_dispatch(int mode, const Params2D<float> &p, int grid, cudaStream_t s) {
+    const bool noise = p.lt.noise != NM_NONE, sample = p.sample_slot >= 0;
+    if (mode == ROW_STAGE2)
+        return noise ? row_tma_launch<N1, ROW_STAGE2, false, true>(p, grid, s)
+                     : row_tma_launch<N1, ROW_STAGE2, false, false>(p, grid, s);
+    if (sample)
+        return noise ? row_tma_launch<N1, ROW_STEADY, true, true>(p, grid, s)
+                     : row_tma_launch<N1, ROW_STEADY, true, false>(p, grid, s);
+    return noise ? row_tma_launch<N1, ROW_STEADY, false, true>(p, grid, s)
+                 : row_tma_launch<N1, ROW_STEADY, false, false>(p, grid, s);
+}
+
 cudaError_t launch_row_pass_tma(int mode, const Params2D<float> &p, int grid, cudaStream_t s) {
     if (mode != ROW_STAGE2 && mode != ROW_STEADY) return cudaErrorInvalidValue;
-    const bool st = mode == ROW_STEADY;
     switch (p.n1) {
-        case 128: return st ? row_tma_launch<128, ROW_STEADY>(p, grid, s) : row_tma_launch<128, ROW_STAGE2>(p, grid, s);
-        case 256: return st ? row_tma_launch<256, ROW_STEADY>(p, grid, s) : row_tma_launch<256, ROW_STAGE2>(p, grid, s);
-        case 512: return st ? row_tma_launch<512, ROW_STEADY>(p, grid, s) : row_tma_launch<512, ROW_STAGE2>(p, grid, s);
-        case 1024: return st ? row_tma_launch<1024, ROW_STEADY>(p, grid, s) : row_tma_launch<1024, ROW_STAGE2>(p, grid, s);
+        case 128: return row_tma_dispatch<128>(mode, p, grid, s);
+        case 256: return row_tma_dispatch<256>(mode, p, grid, s);
+        case 512: return row_tma_dispatch<512>(mode, p, grid, s);
+        case 1024: return row_tma_dispatch<1024>(mode, p, grid, s);
         default: return cudaErrorInvalidValue;
     }
 }
