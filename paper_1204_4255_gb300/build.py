@@ -21,13 +21,15 @@ LIB = os.path.join(HERE, "libxsde.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 
-# (source, XSDE_REAL_BITS or None)
+# (source, XSDE_REAL_BITS or None[, XSDE_PART])
 UNITS = [
     ("api.cu", None),
     ("rk4ip_0d.cu", None),
     ("noise.cu", None),
-    ("rk4ip_1d.cu", 32),
-    ("rk4ip_1d.cu", 64),
+    ("rk4ip_1d.cu", 32, 0),
+    ("rk4ip_1d.cu", 32, 1),
+    ("rk4ip_1d.cu", 64, 0),
+    ("rk4ip_1d.cu", 64, 1),
     ("rk4ip_2d.cu", 32),
     ("rk4ip_2d.cu", 64),
     ("rk4ip_2d_tma.cu", None),
@@ -60,12 +62,15 @@ def up_to_date() -> bool:
 
 
 def _compile(unit, verbose: bool) -> str:
-    src, bits = unit
-    stem = os.path.splitext(src)[0] + (f"_f{bits}" if bits else "")
+    src, bits = unit[0], unit[1]
+    part = unit[2] if len(unit) > 2 else None
+    stem = os.path.splitext(src)[0] + (f"_f{bits}" if bits else "") + (f"_p{part}" if part is not None else "")
     obj = os.path.join(BUILD, stem + ".o")
     cmd = [nvcc(), *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
     if bits:
         cmd.insert(-4, f"-DXSDE_REAL_BITS={bits}")
+    if part is not None:
+        cmd.insert(-4, f"-DXSDE_PART={part}")
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -54,7 +54,9 @@ __device__ __forceinline__ void slot_sum3(double (&v)[3], int t, double *scratch
     }
 }
 
-template <typename R, int N, int E, int PPC>
+// NOISE: the problem has Wiener noise (a template flag, so deterministic runs
+// carry no generator code)
+template <typename R, int N, int E, int PPC, bool NOISE>
 __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R> p) {
     using V = cx<R>;
     constexpr int T = N / E;
@@ -146,7 +148,12 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
             const int j = t + m * T;
             R v = Vs[m];
             if (vtime) v = p.lt.V[(int64_t)sg * N + j];
-            pt[m] = point_term(p.lt, v, (uint32_t)j, gp, (uint32_t)sg);
+            if constexpr (NOISE) {
+                pt[m] = point_term(p.lt, v, (uint32_t)j, gp, (uint32_t)sg);
+            } else {
+                pt[m].dtV = p.lt.dt * v;
+                pt[m].na = mk<V>(R(0), R(0));
+            }
             x[1][m] = apply_N(x[0][m], pt[m], gdt);     // N(a)
         }
         // a_I = D a, k1 = D N(a)
@@ -187,7 +194,8 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
 template <typename R, int N, int E, int PPC> cudaError_t launch_ppc(const Params1D<R> &p, cudaStream_t s) {
     constexpr int T = N / E;
     const size_t smem = (size_t)N * sizeof(tw_t<R>) + (size_t)PPC * 2 * padded_len<N>() * sizeof(cx<R>);
-    auto kern = rk4ip_1d_kernel<R, N, E, PPC>;
+    const bool noise = p.lt.noise != NM_NONE;
+    auto kern = noise ? rk4ip_1d_kernel<R, N, E, PPC, true> : rk4ip_1d_kernel<R, N, E, PPC, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (p.npaths + PPC - 1) / PPC;
@@ -198,13 +206,15 @@ template <typename R, int N, int E, int PPC> cudaError_t launch_ppc(const Params
 // default paths per CTA for E elements per thread: fill 128 threads
 template <int N, int E> constexpr int default_ppc() { return N / E >= 128 ? 1 : 128 / (N / E); }
 
+}  // namespace
+
 // Launch shapes.  Variants 0-3 keep 8 elements per thread (radix-8 stages):
 // the default paths per CTA, a half, a quarter (at least one; more CTAs for
 // small ensembles) and twice as many (at most 256 threads, so no variant is
 // squeezed below 255 registers a thread).  Variants 4 and 5 spread a path over
 // more threads, 4 or 2 elements each (radix-4 or radix-2 stages): more warps
 // per path for few, long, latency-bound paths.
-template <typename R, int N> cudaError_t launch_n(int variant, const Params1D<R> &p, cudaStream_t s) {
+template <typename R, int N> cudaError_t launch_1d_n(int variant, const Params1D<R> &p, cudaStream_t s) {
     constexpr int P0 = default_ppc<N, 8>(), T = N / 8;
     constexpr int P1 = P0 >= 2 ? P0 / 2 : 1, P2 = P0 >= 4 ? P0 / 4 : 1;
     constexpr int P3 = 2 * P0 * T <= 256 ? 2 * P0 : P0;
@@ -218,30 +228,56 @@ template <typename R, int N> cudaError_t launch_n(int variant, const Params1D<R>
     }
 }
 
-}  // namespace
-
 template <typename R> cudaError_t launch_rk4ip_1d(int n, int variant, const Params1D<R> &p, cudaStream_t s) {
     switch (n) {
-        case 16: return launch_n<R, 16>(variant, p, s);
-        case 32: return launch_n<R, 32>(variant, p, s);
-        case 64: return launch_n<R, 64>(variant, p, s);
-        case 128: return launch_n<R, 128>(variant, p, s);
-        case 256: return launch_n<R, 256>(variant, p, s);
-        case 512: return launch_n<R, 512>(variant, p, s);
-        case 1024: return launch_n<R, 1024>(variant, p, s);
-        case 2048: return launch_n<R, 2048>(variant, p, s);
+        case 16: return launch_1d_n<R, 16>(variant, p, s);
+        case 32: return launch_1d_n<R, 32>(variant, p, s);
+        case 64: return launch_1d_n<R, 64>(variant, p, s);
+        case 128: return launch_1d_n<R, 128>(variant, p, s);
+        case 256: return launch_1d_n<R, 256>(variant, p, s);
+        case 512: return launch_1d_n<R, 512>(variant, p, s);
+        case 1024: return launch_1d_n<R, 1024>(variant, p, s);
+        case 2048: return launch_1d_n<R, 2048>(variant, p, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
-// XSDE_REAL_BITS selects one precision per translation unit (parallel builds)
+// Parallel builds: XSDE_REAL_BITS selects one precision and XSDE_PART one half
+// of the lengths per translation unit (part 0 also holds the dispatch).
+#define XSDE_1D_LOW(R)                                                                   \
+    template cudaError_t launch_1d_n<R, 16>(int, const Params1D<R> &, cudaStream_t);     \
+    template cudaError_t launch_1d_n<R, 32>(int, const Params1D<R> &, cudaStream_t);     \
+    template cudaError_t launch_1d_n<R, 64>(int, const Params1D<R> &, cudaStream_t);     \
+    template cudaError_t launch_1d_n<R, 128>(int, const Params1D<R> &, cudaStream_t);    \
+    template cudaError_t launch_1d_n<R, 256>(int, const Params1D<R> &, cudaStream_t);
+#define XSDE_1D_HIGH(X, R)                                                               \
+    X template cudaError_t launch_1d_n<R, 512>(int, const Params1D<R> &, cudaStream_t);  \
+    X template cudaError_t launch_1d_n<R, 1024>(int, const Params1D<R> &, cudaStream_t); \
+    X template cudaError_t launch_1d_n<R, 2048>(int, const Params1D<R> &, cudaStream_t);
+#define XSDE_1D_UNIT(R)                                                                  \
+    XSDE_1D_PART0(R)                                                                     \
+    XSDE_1D_PART1(R)
+
+#if !defined(XSDE_PART)
+#define XSDE_1D_PART0(R) XSDE_1D_LOW(R) template cudaError_t launch_rk4ip_1d<R>(int, int, const Params1D<R> &, cudaStream_t);
+#define XSDE_1D_PART1(R) XSDE_1D_HIGH(, R)
+#elif XSDE_PART == 0
+#define XSDE_1D_PART0(R) XSDE_1D_HIGH(extern, R) XSDE_1D_LOW(R) template cudaError_t launch_rk4ip_1d<R>(int, int, const Params1D<R> &, cudaStream_t);
+#define XSDE_1D_PART1(R)
+#else
+#define XSDE_1D_PART0(R)
+#define XSDE_1D_PART1(R) XSDE_1D_HIGH(, R)
+#endif
+
 #if !defined(XSDE_REAL_BITS) || XSDE_REAL_BITS == 32
+#if !defined(XSDE_PART) || XSDE_PART == 0
 int rk4ip_1d_variants() { return 6; }
 int rk4ip_1d_elems(int variant) { return variant == 4 ? 4 : variant == 5 ? 2 : 8; }
-template cudaError_t launch_rk4ip_1d<float>(int, int, const Params1D<float> &, cudaStream_t);
+#endif
+XSDE_1D_UNIT(float)
 #endif
 #if !defined(XSDE_REAL_BITS) || XSDE_REAL_BITS == 64
-template cudaError_t launch_rk4ip_1d<double>(int, int, const Params1D<double> &, cudaStream_t);
+XSDE_1D_UNIT(double)
 #endif
 
 }  // namespace xsde
