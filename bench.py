@@ -376,7 +376,8 @@ def run_gpu(args) -> None:
     psi = host_psi.to("cuda", non_blocking=True)
     torch.cuda.synchronize()
 
-    path_offset = rank * P
+    from paper_1204_4255_gb300.distributed import gather_per_path, shard
+    path_offset, _ = shard(P * world, rank, world)     # P instances per rank, global path indices
     step = [0]
 
     def one_step():
@@ -410,7 +411,8 @@ def run_gpu(args) -> None:
     prof = xsde.xsde_profile_report(prob.prob)
     xsde.xsde_profile(prob.prob, False)
     prob.synchronize()
-    norms = per_path[-1, :, 0].cpu().numpy()
+    pp_all = gather_per_path(per_path, [P] * world) if world > 1 else per_path   # untimed
+    norms = pp_all[-1, :, 0].cpu().numpy()
     ok = bool(np.all(np.isfinite(norms)) and np.max(np.abs(norms - 1.0)) < 1e-3)
 
     # max over ranks
