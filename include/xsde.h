@@ -262,9 +262,10 @@ int xsde_synchronize(xsde_problem *prob, void *stream);
  *     give each thread 4 or 2 points (radix-4 or radix-2 stages, so a path
  *     spreads over more warps) with the default paths per CTA for that shape;
  *     where a bound applies a variant repeats another;
- *   2D and 3D lattices (2 variants): 0 uses the fastest kernels available
- *     (the persistent TMA-pipelined complex64 passes where they apply: lines
- *     of 128..1024 points, columns of 128..512), 1 forces the generic passes;
+ *   2D and 3D lattices (3 variants): 0 uses the persistent TMA-pipelined
+ *     complex64 passes where they apply (lines of 128..1024 points, columns
+ *     of 128..512), 1 forces the generic passes, 2 uses the TMA row passes and
+ *     the generic column passes;
  *   0D lattices (1 variant).
  * Out-of-range variants report XSDE_EINVAL.  xsde_autotune picks one by
  * timing. */

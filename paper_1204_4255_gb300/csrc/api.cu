@@ -411,13 +411,13 @@ int run_3d(xsde_problem *p, void *psi, int64_t nsteps, int64_t npaths, uint64_t 
     bool tma_row = false, tma_col1 = false, tma_col0 = false;
     CUtensorMap map1A, map1B, map0A, map0B;
     if constexpr (std::is_same<R, float>::value) {
-        if (p->kernel_variant == 0 && (uintptr_t)psi % 16 == 0 && (uintptr_t)p->d_scratch % 16 == 0) {
+        if (p->kernel_variant != 1 && (uintptr_t)psi % 16 == 0 && (uintptr_t)p->d_scratch % 16 == 0) {
             tma_row = tma_rows_ok(g.n[2], npaths * g.n[0] * g.n[1]);
             // dimension 1: [npaths n0 n1][n2]; dimension 0: [npaths n0][n1 n2]
-            tma_col1 = tma_col_supported(g.n[1]) && g.n[2] % COL_TMA_C == 0 &&
+            tma_col1 = p->kernel_variant == 0 && tma_col_supported(g.n[1]) && g.n[2] % COL_TMA_C == 0 &&
                        encode_field_map(&map1A, psi, npaths * g.n[0] * g.n[1], g.n[2], g.n[1]) &&
                        encode_field_map(&map1B, p->d_scratch, npaths * g.n[0] * g.n[1], g.n[2], g.n[1]);
-            tma_col0 = tma_col_supported(g.n[0]) && encode_field_map(&map0A, psi, npaths * g.n[0],
+            tma_col0 = p->kernel_variant == 0 && tma_col_supported(g.n[0]) && encode_field_map(&map0A, psi, npaths * g.n[0],
                                                                        (int64_t)g.n[1] * g.n[2], g.n[0]) &&
                        encode_field_map(&map0B, p->d_scratch, npaths * g.n[0], (int64_t)g.n[1] * g.n[2], g.n[0]);
         }
@@ -543,9 +543,9 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
     bool tma_row = false, tma_col = false;
     CUtensorMap mapA, mapB;
     if constexpr (std::is_same<R, float>::value) {
-        if (p->kernel_variant == 0 && (uintptr_t)psi % 16 == 0 && (uintptr_t)p->d_scratch % 16 == 0) {
+        if (p->kernel_variant != 1 && (uintptr_t)psi % 16 == 0 && (uintptr_t)p->d_scratch % 16 == 0) {
             tma_row = tma_rows_ok(g.n[1], npaths * g.n[0]);
-            tma_col = tma_col_supported(g.n[0]) && g.n[1] % COL_TMA_C == 0 &&
+            tma_col = p->kernel_variant == 0 && tma_col_supported(g.n[0]) && g.n[1] % COL_TMA_C == 0 &&
                       encode_field_map(&mapA, psi, npaths * g.n[0], g.n[1], g.n[0]) &&
                       encode_field_map(&mapB, p->d_scratch, npaths * g.n[0], g.n[1], g.n[0]);
         }
@@ -640,7 +640,7 @@ int variants_for(const xsde_problem *p) {
     switch (p->grid.ndim) {
         case 1: return rk4ip_1d_variants();
         case 2:
-        case 3: return 2;
+        case 3: return 3;
         default: return 1;
     }
 }

@@ -300,9 +300,11 @@ def test_c64_pipelined_passes_3d_and_short_lines(shape):
                    psi0.astype(np.complex128), 3)
     fast, pp_f, pq_f = gpu_run(w, "c64", sample_every=3, path0=1, variant=0)
     gen, _, _ = gpu_run(w, "c64", sample_every=3, path0=1, variant=1)
+    mixed, _, _ = gpu_run(w, "c64", sample_every=3, path0=1, variant=2)   # TMA rows, generic columns
     ref, opp, opq = O.run_workload(w, sample_every=3, path0=1)
     assert np.max(rel_l2(fast.reshape(npaths, -1), ref.reshape(npaths, -1), axis=1)) < 1e-4
     assert np.max(rel_l2(fast.reshape(npaths, -1), gen.reshape(npaths, -1), axis=1)) < 1e-5
+    assert np.max(rel_l2(mixed.reshape(npaths, -1), gen.reshape(npaths, -1), axis=1)) < 1e-5
     assert np.max(np.abs(pp_f - opp) / np.abs(opp)) < 1e-4
     assert np.max(np.abs(pq_f - opq) / np.abs(opq)) < 1e-4
 
