@@ -137,7 +137,9 @@ def cpu_baseline(budget_s: float = 12.0) -> dict:
 def adjoint_cost(dtype: str = "c64", reps: int = 5) -> dict:
     """Control workload (1D GPE, 1024 points, V on a 1024 x 500 space-time grid,
     500 steps, checkpoints every 50): device time of loss + dL/dV through
-    xsde_adjoint over a plain 500-step forward run through xsde_integrate."""
+    xsde_adjoint over a plain 500-step forward run through xsde_integrate, each
+    with its fastest launch shape (the forward autotuned, the adjoint timed with
+    8 and 4 points per thread)."""
     import torch
     import workloads as W
     from paper_1204_4255_gb300 import xsde
@@ -149,26 +151,32 @@ def adjoint_cost(dtype: str = "c64", reps: int = 5) -> dict:
     P.set_operators(c2=w.c2, g=w.gnl, pot_kind=xsde.XSDE_POT_TABLE, V=V)
     p0 = torch.from_numpy(w.psi0).to(tdt).cuda()
     tg = torch.from_numpy(w.extra["target"]).to(tdt).cuda()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        fn()
+        fn()
+        torch.cuda.synchronize()
+        e[0].record()
+        for _ in range(reps):
+            fn()
+        e[1].record()
+        torch.cuda.synchronize()
+        return e[0].elapsed_time(e[1]) / reps
+
+    fwd_variant = P.autotune(p0, w.dt, 50)
     psi = p0.clone()
-    for _ in range(2):
-        P.integrate(psi, w.dt, w.nsteps)
-        xsde.adjoint(P, p0, tg, w.dt, w.nsteps, w.extra["ckpt_every"])
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    torch.cuda.synchronize()
-    e[0].record()
-    for _ in range(reps):
-        P.integrate(psi, w.dt, w.nsteps)
-    e[1].record()
-    e[2].record()
-    for _ in range(reps):
-        xsde.adjoint(P, p0, tg, w.dt, w.nsteps, w.extra["ckpt_every"])
-    e[3].record()
-    torch.cuda.synchronize()
+    tf = timed(lambda: P.integrate(psi, w.dt, w.nsteps))
+    adj = {}
+    for variant in (0, 4):
+        xsde.xsde_set_kernel_variant(P.prob, variant)
+        adj[variant] = timed(lambda: xsde.adjoint(P, p0, tg, w.dt, w.nsteps, w.extra["ckpt_every"]))
     P.synchronize()
     P.close()
-    tf, ta = e[0].elapsed_time(e[1]) / reps, e[2].elapsed_time(e[3]) / reps
+    best = min(adj, key=adj.get)
     return {"workload": "1D GPE 1024 pts, V(x,t) 1024x500, 500 steps, ckpt 50", "dtype": dtype,
-            "forward_ms": tf, "loss_and_gradient_ms": ta, "cost_ratio": ta / tf}
+            "forward_ms": tf, "forward_variant": fwd_variant, "loss_and_gradient_ms": adj[best],
+            "adjoint_variant": best, "cost_ratio": adj[best] / tf}
 
 
 def plain_vs_fused(P: int = 64, nsteps: int = 20) -> dict:

@@ -955,7 +955,9 @@ int xsde_adjoint(xsde_problem *p, const xsde_vector *psi0, const xsde_vector *ta
         q.nsteps = nsteps;
         q.K = K;
         q.Etab = static_cast<const V *>(p->d_E[0]);
-        q.tw = static_cast<const tw_t<R> *>(p->d_tw[0]);
+        // the problem's points-per-thread shape (the 2-point shape runs as 4)
+        const int elems = rk4ip_1d_elems(p->kernel_variant) == 8 ? 8 : 4;
+        q.tw = static_cast<const tw_t<R> *>(elems == 8 ? p->d_tw[0] : p->d_tw1d[0]);
         q.dx = grid_dx(g, 0);
         q.ckpt = static_cast<V *>(p->d_adj);
         q.interm = q.ckpt + (size_t)nck * npaths * g.npts;
@@ -966,7 +968,7 @@ int xsde_adjoint(xsde_problem *p, const xsde_vector *psi0, const xsde_vector *ta
         const int phases[3] = {ADJ_FORWARD, ADJ_RECOMPUTE, ADJ_REVERSE};
         for (int i = 0; i < (full ? 3 : 1); ++i) {
             q.phase = full ? phases[i] : ADJ_SEQUENTIAL;
-            XSDE_CUDA(timed(p, 1, s, [&] { return launch_adjoint_1d<R>(g.n[0], q, s); }), "xsde_adjoint launch");
+            XSDE_CUDA(timed(p, 1, s, [&] { return launch_adjoint_1d<R>(g.n[0], elems, q, s); }), "xsde_adjoint launch");
         }
         return XSDE_OK;
     };

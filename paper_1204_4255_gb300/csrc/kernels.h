@@ -153,7 +153,7 @@ template <typename R> struct AdjParams {
     double *dLdV;          // [nsteps][N], accumulated (zeroed by the caller)
     cx<R> *dLdpsi0;        // [npaths][N] or nullptr
 };
-template <typename R> cudaError_t launch_adjoint_1d(int n, const AdjParams<R> &p, cudaStream_t s);
+template <typename R> cudaError_t launch_adjoint_1d(int n, int elems, const AdjParams<R> &p, cudaStream_t s);
 
 // --------------------------------------------------------------------------
 // 0D: one thread per path (an ordinary SDE; D is a scalar factor).

@@ -264,8 +264,8 @@ __global__ void __launch_bounds__(N / E) rk4ip_adjoint_kernel(const AdjParams<R>
     }
 }
 
-template <typename R, int N> cudaError_t adj_launch(const AdjParams<R> &p, cudaStream_t s) {
-    constexpr int E = 8, T = N / E;
+template <typename R, int N, int E> cudaError_t adj_launch(const AdjParams<R> &p, cudaStream_t s) {
+    constexpr int T = N / E;
     const size_t smem = (size_t)N * sizeof(tw_t<R>) + (size_t)2 * padded_len<N>() * sizeof(cx<R>) +
                         (size_t)2 * ((T + 31) / 32) * sizeof(double);
     auto kern = rk4ip_adjoint_kernel<R, N, E>;
@@ -278,19 +278,25 @@ template <typename R, int N> cudaError_t adj_launch(const AdjParams<R> &p, cudaS
     return cudaGetLastError();
 }
 
+template <typename R, int N> cudaError_t adj_launch_e(int elems, const AdjParams<R> &p, cudaStream_t s) {
+    return elems == 4 ? adj_launch<R, N, 4>(p, s) : adj_launch<R, N, 8>(p, s);
+}
+
 }  // namespace
 
-template <typename R> cudaError_t launch_adjoint_1d(int n, const AdjParams<R> &p, cudaStream_t s) {
+// elems: points per thread, 8 (radix-8 plan) or 4 (radix-4 plan; p.tw must
+// hold that plan's table)
+template <typename R> cudaError_t launch_adjoint_1d(int n, int elems, const AdjParams<R> &p, cudaStream_t s) {
     switch (n) {
-        case 256: return adj_launch<R, 256>(p, s);
-        case 512: return adj_launch<R, 512>(p, s);
-        case 1024: return adj_launch<R, 1024>(p, s);
-        case 2048: return adj_launch<R, 2048>(p, s);
+        case 256: return adj_launch_e<R, 256>(elems, p, s);
+        case 512: return adj_launch_e<R, 512>(elems, p, s);
+        case 1024: return adj_launch_e<R, 1024>(elems, p, s);
+        case 2048: return adj_launch_e<R, 2048>(elems, p, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template cudaError_t launch_adjoint_1d<float>(int, const AdjParams<float> &, cudaStream_t);
-template cudaError_t launch_adjoint_1d<double>(int, const AdjParams<double> &, cudaStream_t);
+template cudaError_t launch_adjoint_1d<float>(int, int, const AdjParams<float> &, cudaStream_t);
+template cudaError_t launch_adjoint_1d<double>(int, int, const AdjParams<double> &, cudaStream_t);
 
 }  // namespace xsde

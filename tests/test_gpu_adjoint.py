@@ -30,7 +30,7 @@ def full_oracle():
     return w, L, dLdV
 
 
-def gpu_adjoint(w, dtype, ckpt=50, V=None, psi0=None, nsteps=None):
+def gpu_adjoint(w, dtype, ckpt=50, V=None, psi0=None, nsteps=None, variant=0):
     import torch
     from paper_1204_4255_gb300 import xsde
     P = make_problem(w, dtype) if V is None else None
@@ -38,6 +38,7 @@ def gpu_adjoint(w, dtype, ckpt=50, V=None, psi0=None, nsteps=None):
         w2 = W.Workload(w.name, w.n, w.xmin, w.xmax, w.c0, w.c2, w.gnl, w.pot_kind, w.omega, V, w.noise_kind,
                         w.noise_amp, w.seed, w.dt, w.nsteps, w.psi0, extra=w.extra)
         P = make_problem(w2, dtype)
+    xsde.xsde_set_kernel_variant(P.prob, variant)
     tdt = torch.complex64 if dtype == "c64" else torch.complex128
     src = w.psi0 if psi0 is None else psi0
     p0 = torch.from_numpy(np.ascontiguousarray(src)).to(tdt).cuda()
@@ -107,6 +108,21 @@ def test_sequential_and_parallel_recompute_agree(monkeypatch, npaths, k):
     tol = 0.0 if npaths == 1 else 1e-14
     assert abs(l_seq - l_par) <= tol
     assert np.max(np.abs(d_seq - d_par)) <= tol * np.max(np.abs(d_par))
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_adjoint_four_point_shape_agrees(full_oracle, dtype):
+    """The adjoint with 4 points per thread (radix-4 plan, twice the threads per
+    path) against the 8-point shape and the oracle."""
+    w, L, dLdV = full_oracle
+    l8, d8 = gpu_adjoint(w, dtype)
+    l4, d4 = gpu_adjoint(w, dtype, variant=4)
+    scale = np.max(np.abs(dLdV))
+    if dtype == "c128":
+        assert abs(l4 - L) < 1e-12 and np.max(np.abs(d4 - dLdV)) < 1e-10 * scale
+        assert np.max(np.abs(d4 - d8)) < 1e-12 * scale
+    else:
+        assert np.linalg.norm(d4 - dLdV) < 1e-4 * np.linalg.norm(dLdV)
 
 
 def test_adjoint_sums_over_paths():
