@@ -211,7 +211,10 @@ int xsde_integrate(xsde_problem *prob, xsde_vector *psi, double dt, int64_t nste
  * library owns that workspace).  When the stage inputs of all steps fit in
  * XSDE_ADJOINT_MAX_BYTES bytes of workspace (environment variable, default
  * 2 GiB) all segments are recomputed at once before the reverse sweep; else one
- * at a time during it, in a buffer of one segment.  Asynchronous on `stream`. */
+ * at a time during it, in a buffer of one segment.  Each path runs on one CTA
+ * with 8 points per thread, or 4 when the problem's kernel variant is one of
+ * the 1D 4- or 2-point shapes (xsde_set_kernel_variant).  Asynchronous on
+ * `stream`. */
 int xsde_adjoint(xsde_problem *prob, const xsde_vector *psi0, const xsde_vector *target, double dt, int64_t nsteps,
                  int32_t ckpt_every, double *loss, double *dLdV, void *dLdpsi0, void *stream);
 
