@@ -114,24 +114,33 @@ def workload(npaths: int, seed_offset: int = 0):
     return W.gpe_2d(n=N_GRID, npaths=npaths, seed=2 + seed_offset)
 
 
-def cpu_baseline(budget_s: float = 12.0) -> dict:
+def cpu_baseline(budget_s: float = 12.0, single_core_s: float = 6.0) -> dict:
     """The FP64 oracle as it stands on one instance of the workload, for as many
-    whole RK4IP steps as fit in about budget_s seconds (at least one)."""
+    whole RK4IP steps as fit in about budget_s seconds (at least one) on all host
+    cores, and likewise on one core for about single_core_s seconds."""
     from oracle import oracle as O
     w = workload(1)
     grid, ops = O.from_workload(w)
+
+    def run(threads, budget, cap):
+        O.set_threads(threads)
+        psi = w.psi0
+        steps, t0 = 0, time.perf_counter()
+        while True:
+            psi, _, _ = O.rk4ip(psi, grid, ops, w.dt, 1, step0=steps)
+            steps += 1
+            el = time.perf_counter() - t0
+            if el > budget or steps >= cap:
+                return steps, el
+
+    steps, el = run(os.cpu_count() or 1, budget_s, 50)
+    cores = O.get_threads()
+    steps1, el1 = run(1, single_core_s, 10)
     O.set_threads(os.cpu_count() or 1)
-    psi = w.psi0
-    steps, t0 = 0, time.perf_counter()
-    while True:
-        psi, _, _ = O.rk4ip(psi, grid, ops, w.dt, 1, step0=steps)
-        steps += 1
-        el = time.perf_counter() - t0
-        if el > budget_s or steps >= 50:
-            break
-    pts = w.npts * steps
-    return {"value": pts / el, "unit": UNIT, "cores": O.get_threads(), "kind": "oracle",
-            "sample": f"1 instance of 512x512, {steps} RK4IP steps, FP64, {el:.1f} s"}
+    return {"value": w.npts * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"1 instance of 512x512, {steps} RK4IP steps, FP64, {el:.1f} s",
+            "single_core": {"value": w.npts * steps1 / el1, "unit": UNIT,
+                            "sample": f"1 instance of 512x512, {steps1} RK4IP steps, FP64, {el1:.1f} s"}}
 
 
 def adjoint_cost(dtype: str = "c64", reps: int = 5) -> dict:
