@@ -311,3 +311,51 @@ def step_adjoint(a, lam, grid: Grid, ops: Ops, step: int, dt: float):
     lib.oracle_step_adjoint(ctypes.byref(grid._c()), ctypes.byref(ops._c()), _ptr(a), _ptr(lam), step, dt,
                             _ptr(out), _ptr(gV))
     return out, gV
+
+
+# --------------------------------------------------------------------------- #
+# Adaptive Cash-Karp 4(5) Runge-Kutta, interaction picture or explicit        #
+# --------------------------------------------------------------------------- #
+
+def _load_ark45(lib):
+    if not hasattr(lib, "_ark45_ready"):
+        dp, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+        lib.oracle_cash_karp.argtypes = [dp, dp, dp, dp]
+        lib.oracle_ark45.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Ops), dp, i64, dbl, dbl, dbl,
+                                     ctypes.c_int32, i64, dp, dp]
+        lib.oracle_ark45.restype = ctypes.c_int
+        lib._ark45_ready = True
+    return lib
+
+
+def cash_karp() -> dict:
+    """The oracle's Cash-Karp tableau: c [6], a [6, 5], b5 [6], b4 [6]."""
+    lib = _load_ark45(_load())
+    c, b5, b4 = np.zeros(6), np.zeros(6), np.zeros(6)
+    a = np.zeros((6, 5))
+    lib.oracle_cash_karp(_ptr(c), _ptr(a), _ptr(b5), _ptr(b4))
+    return {"c": c, "a": a, "b5": b5, "b4": b4}
+
+
+def ark45(psi: np.ndarray, grid: Grid, ops: Ops, t_end: float, tol: float, h0: float, picture: bool = True,
+          max_steps: int = 10 ** 7, threads: int | None = None):
+    """Adaptive Cash-Karp integration of every path of psi [npaths, *grid.shape]
+    from t = 0 to t_end, in the interaction picture (picture=True) or on the
+    explicit equation.  tol <= 0 takes fixed steps of h0.  Returns (psi_final,
+    accepted [npaths], rejected [npaths]); raises if a path ran out of
+    max_steps attempts."""
+    lib = _load_ark45(_load())
+    a = np.ascontiguousarray(psi, dtype=np.complex128).copy()
+    npaths = a.size // grid.npts
+    acc = np.zeros(npaths, dtype=np.int64)
+    rej = np.zeros(npaths, dtype=np.int64)
+    if threads is not None:
+        set_threads(threads)
+    gc, oc = grid._c(), ops._c()
+    rc = lib.oracle_ark45(ctypes.byref(gc), ctypes.byref(oc), _ptr(a), npaths, t_end, tol, h0,
+                          1 if picture else 0, max_steps, _ptr(acc), _ptr(rej))
+    if rc < 0:
+        raise ValueError("oracle_ark45 rejected its arguments")
+    if rc > 0:
+        raise RuntimeError("oracle_ark45: a path ran out of steps")
+    return a, acc, rej

@@ -725,3 +725,177 @@ int oracle_step_adjoint(const oracle_grid *g, const oracle_ops *ops, const doubl
     free(E); free(in.Vrow);
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Adaptive fourth-fifth order Runge-Kutta (Sec. 2.5: the Cash-Karp embedded */
+/* pair), in the interaction picture of Sec. 2.6 or on the explicit equation */
+/* ------------------------------------------------------------------------- */
+/*
+ * Deterministic equation df/dt = L f + g(f), g(f) = -i (V(x) + gnl |f|^2) f.
+ * One step of size h from t:
+ *   interaction picture (picture = 1): with f~(s) = exp(-L s) f(t + s), the
+ *     stages are k_i = h exp(-L c_i h) g(exp(L c_i h) Y_i), Y_i = f + sum_j a_ij k_j,
+ *     the fifth-order result is f~5 = f + sum_i b5_i k_i and the step ends with
+ *     f(t + h) = exp(L h) f~5 (the picture is re-centred at every step);
+ *   explicit (picture = 0): k_i = h (L Y_i + g(Y_i)), f(t + h) = f + sum_i b5_i k_i.
+ * Error estimate e = sum_i (b5_i - b4_i) k_i; err = max_j |e_j| / max_j |f5_j|
+ * (f5 the fifth-order result of the step, in the frame the stages use).  A
+ * step is accepted when err <= tol; either way the next size is
+ * h * clamp(0.9 (tol/err)^(1/5), 0.2, 5) (5 when err = 0), and a step that
+ * would pass t_end, or end within 1e-12 t_end of it, is set to end on t_end.  tol <= 0 selects fixed steps of
+ * h0 (never rejected; the last one shortened).
+ */
+
+/* Cash & Karp (1990), ACM TOMS 16, 201: nodes, coupling and the two weights */
+static const double CK_C[6] = {0.0, 1.0 / 5.0, 3.0 / 10.0, 3.0 / 5.0, 1.0, 7.0 / 8.0};
+static const double CK_A[6][5] = {
+    {0.0, 0.0, 0.0, 0.0, 0.0},
+    {1.0 / 5.0, 0.0, 0.0, 0.0, 0.0},
+    {3.0 / 40.0, 9.0 / 40.0, 0.0, 0.0, 0.0},
+    {3.0 / 10.0, -9.0 / 10.0, 6.0 / 5.0, 0.0, 0.0},
+    {-11.0 / 54.0, 5.0 / 2.0, -70.0 / 27.0, 35.0 / 27.0, 0.0},
+    {1631.0 / 55296.0, 175.0 / 512.0, 575.0 / 13824.0, 44275.0 / 110592.0, 253.0 / 4096.0}};
+static const double CK_B5[6] = {37.0 / 378.0, 0.0, 250.0 / 621.0, 125.0 / 594.0, 0.0, 512.0 / 1771.0};
+static const double CK_B4[6] = {2825.0 / 27648.0, 0.0, 18575.0 / 48384.0, 13525.0 / 55296.0, 277.0 / 14336.0,
+                                1.0 / 4.0};
+
+/* the tableau, for the tests: c[6], a[6][5] row-major, b5[6], b4[6] */
+void oracle_cash_karp(double *c, double *a, double *b5, double *b4)
+{
+    for (int i = 0; i < 6; i++) {
+        c[i] = CK_C[i];
+        b5[i] = CK_B5[i];
+        b4[i] = CK_B4[i];
+        for (int j = 0; j < 5; j++) a[i * 5 + j] = CK_A[i][j];
+    }
+}
+
+/* exp(L(k) tau) times u, in place (u in real space on entry and exit) */
+static void propagate(cplx *u, const oracle_grid *g, const oracle_ops *ops, double tau)
+{
+    if (tau == 0.0) return;
+    cplx c0 = ops->c0_re + I * ops->c0_im;
+    cplx c2 = ops->c2_re + I * ops->c2_im;
+    int64_t npts = grid_points(g);
+    fft_nd(u, g, 1, -1);
+    for (int64_t j = 0; j < npts; j++) u[j] *= cexp((c0 + c2 * ksq_at(g, j)) * tau);
+    fft_nd(u, g, 1, +1);
+}
+
+/* out = L u = iFFT(L(k) FFT(u)) */
+static void apply_L(cplx *out, const cplx *u, const oracle_grid *g, const oracle_ops *ops)
+{
+    cplx c0 = ops->c0_re + I * ops->c0_im;
+    cplx c2 = ops->c2_re + I * ops->c2_im;
+    int64_t npts = grid_points(g);
+    memcpy(out, u, (size_t)npts * sizeof(cplx));
+    fft_nd(out, g, 1, -1);
+    for (int64_t j = 0; j < npts; j++) out[j] *= c0 + c2 * ksq_at(g, j);
+    fft_nd(out, g, 1, +1);
+}
+
+/* g(u) = -i (V + gnl |u|^2) u */
+static void g_det(cplx *out, const cplx *u, const double *Vrow, const oracle_ops *ops, int64_t npts)
+{
+    for (int64_t j = 0; j < npts; j++) {
+        double mod2 = creal(u[j]) * creal(u[j]) + cimag(u[j]) * cimag(u[j]);
+        out[j] = -I * (Vrow[j] + ops->gnl * mod2) * u[j];
+    }
+}
+
+/* one path from t = 0 to t_end; returns 0, or 1 when max_steps attempts ran out */
+static int ark45_path(const oracle_grid *g, const oracle_ops *ops, const double *Vrow, cplx *y, double t_end,
+                      double tol, double h0, int picture, int64_t max_steps, int64_t *accepted,
+                      int64_t *rejected)
+{
+    int64_t npts = grid_points(g);
+    cplx *k = malloc((size_t)6 * npts * sizeof(cplx));
+    cplx *Y = malloc((size_t)npts * sizeof(cplx));
+    cplx *v = malloc((size_t)npts * sizeof(cplx));
+    cplx *Lv = malloc((size_t)npts * sizeof(cplx));
+    double t = 0.0, h = h0;
+    int64_t acc = 0, rej = 0;
+    int rc = 0;
+    while (t < t_end) {
+        if (acc + rej >= max_steps) { rc = 1; break; }
+        /* end exactly on t_end (a step within 1e-12 t_end of it is stretched) */
+        if (t + h > t_end || t_end - (t + h) <= 1e-12 * t_end) h = t_end - t;
+        for (int i = 0; i < 6; i++) {
+            cplx *ki = k + (size_t)i * npts;
+            for (int64_t j = 0; j < npts; j++) {
+                cplx s = y[j];
+                for (int m = 0; m < i; m++) s += CK_A[i][m] * k[(size_t)m * npts + j];
+                Y[j] = s;
+            }
+            if (picture) {
+                const double tau = CK_C[i] * h;
+                propagate(Y, g, ops, tau);
+                g_det(v, Y, Vrow, ops, npts);
+                propagate(v, g, ops, -tau);
+                for (int64_t j = 0; j < npts; j++) ki[j] = h * v[j];
+            } else {
+                g_det(v, Y, Vrow, ops, npts);
+                apply_L(Lv, Y, g, ops);
+                for (int64_t j = 0; j < npts; j++) ki[j] = h * (Lv[j] + v[j]);
+            }
+        }
+        double emax = 0.0, ymax = 0.0;
+        for (int64_t j = 0; j < npts; j++) {
+            cplx y5 = y[j], e = 0.0;
+            for (int i = 0; i < 6; i++) {
+                y5 += CK_B5[i] * k[(size_t)i * npts + j];
+                e += (CK_B5[i] - CK_B4[i]) * k[(size_t)i * npts + j];
+            }
+            Y[j] = y5;
+            if (cabs(e) > emax) emax = cabs(e);
+            if (cabs(y5) > ymax) ymax = cabs(y5);
+        }
+        const double err = ymax > 0.0 ? emax / ymax : 0.0;
+        if (tol <= 0.0 || err <= tol) {
+            t += h;
+            memcpy(y, Y, (size_t)npts * sizeof(cplx));
+            if (picture) propagate(y, g, ops, h);
+            acc++;
+        } else {
+            rej++;
+        }
+        if (tol > 0.0) {
+            double fac = err > 0.0 ? 0.9 * pow(tol / err, 0.2) : 5.0;
+            if (fac < 0.2) fac = 0.2;
+            if (fac > 5.0) fac = 5.0;
+            h *= fac;
+        } else {
+            h = h0;
+        }
+    }
+    *accepted = acc;
+    *rejected = rej;
+    free(k);
+    free(Y);
+    free(v);
+    free(Lv);
+    return rc;
+}
+
+/* Adaptive integration of every path to t_end (see the block comment above).
+ * Deterministic problems with a static potential only.  Returns 0, -1 for
+ * arguments it does not accept, 1 if some path ran out of max_steps attempts
+ * (its field is then the state it reached). */
+int oracle_ark45(const oracle_grid *g, const oracle_ops *ops, double *psi_in, int64_t npaths, double t_end,
+                 double tol, double h0, int32_t picture, int64_t max_steps, int64_t *accepted,
+                 int64_t *rejected)
+{
+    if (ops->noise_kind != NOISE_NONE || (ops->pot_kind == POT_TABLE && ops->V_nt != 1)) return -1;
+    if (!(t_end >= 0.0) || !(h0 > 0.0) || g->ndim < 1) return -1;
+    int64_t npts = grid_points(g);
+    double *Vrow = malloc((size_t)npts * sizeof(double));
+    for (int64_t j = 0; j < npts; j++) Vrow[j] = potential_at(g, ops, j, 0);
+    cplx *psi = (cplx *)psi_in;
+    int rc = 0;
+    #pragma omp parallel for schedule(dynamic) reduction(| : rc)
+    for (int64_t p = 0; p < npaths; p++)
+        rc |= ark45_path(g, ops, Vrow, psi + p * npts, t_end, tol, h0, picture, max_steps, accepted + p,
+                         rejected + p);
+    free(Vrow);
+    return rc;
+}

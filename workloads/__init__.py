@@ -245,3 +245,14 @@ def batched_instances(n3: int = 128, sizes2=(256, 512), count2: int = 32, sizes1
                                 w.omega, None, w.noise_kind, w.noise_amp, w.seed, dt, nsteps,
                                 np.concatenate([g.psi0 for g in group], axis=0)))
     return out
+
+
+def ip_scaling(n: int, box: float = 10.0, g: float = 10.0, t_end: float = 2 * math.pi) -> Workload:
+    """The interaction-picture scaling experiment: the dimensionless trapped GPE
+    (Eq. NonlinearSchrodingerEquationDimensionless, V = x^2/2, nonlinearity g)
+    on [-box, box) at n points, from the ground state of the linear problem
+    (Eq. InitialCondition, N = 1) to t_end (one trap period by default)."""
+    x = -box + np.arange(n) * (2 * box / n)
+    psi0 = (np.pi ** -0.25 * np.exp(-x ** 2 / 2)).astype(np.complex128)[None, :]
+    return Workload(f"ip_scaling_{n}", (n,), (-box,), (box,), 0j, -0.5j, g, POT_HARMONIC, (1.0,), None,
+                    NOISE_NONE, 0.0, 0, 0.0, 0, psi0, extra={"t_end": t_end})
