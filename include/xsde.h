@@ -56,7 +56,8 @@ typedef enum {
     XSDE_ECUDA = 3,         /* a CUDA runtime call failed */
     XSDE_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
     XSDE_ENONFINITE = 5,    /* the field became NaN/Inf */
-    XSDE_EUNSUPPORTED = 6   /* valid but not implemented (size, dtype, combination) */
+    XSDE_EUNSUPPORTED = 6,  /* valid but not implemented (size, dtype, combination) */
+    XSDE_ELIMIT = 7         /* an adaptive integration used up its step attempts */
 } xsde_status;
 
 typedef enum { XSDE_C64 = 1, XSDE_C128 = 2 } xsde_dtype;
@@ -218,6 +219,35 @@ int xsde_integrate(xsde_problem *prob, xsde_vector *psi, double dt, int64_t nste
 int xsde_adjoint(xsde_problem *prob, const xsde_vector *psi0, const xsde_vector *target, double dt, int64_t nsteps,
                  int32_t ckpt_every, double *loss, double *dLdV, void *dLdpsi0, void *stream);
 
+/* ---- adaptive integration --------------------------------------------------- */
+
+/* The adaptive fourth-fifth order Runge-Kutta of Sec. 2.5 (the Cash-Karp
+ * embedded pair), in the interaction picture of Sec. 2.6 (picture = 1: the
+ * linear part exp(L tau) applied exactly, the picture re-centred every step)
+ * or on the explicit equation (picture = 0: L f evaluated spectrally at every
+ * stage), the comparison of Fig. IPvsEX.  Each path advances from t = 0 to
+ * t_end with its own step size: the step's error estimate
+ * err = max_j |f5_j - f4_j| / max_j |f5_j| must be <= tol; the next step is
+ * h clamp(0.9 (tol/err)^(1/5), 0.2, 5); a step that would pass t_end, or end
+ * within 1e-12 t_end of it, ends on t_end; tol <= 0 takes fixed steps of h0. */
+typedef struct {
+    double t_end;       /* >= 0 */
+    double tol;         /* relative error per step; <= 0: fixed steps of h0 */
+    double h0;          /* first step, > 0 */
+    int32_t picture;    /* 1: interaction picture, 0: explicit */
+    int64_t max_steps;  /* step attempts per path (accepted + rejected), >= 1 */
+} xsde_adaptive;
+
+/* Integrate every path of psi (1D lattice of 64..2048 points, deterministic
+ * operators with a static potential, no sampling group; else
+ * XSDE_EUNSUPPORTED) as above, in place, asynchronously on `stream`.
+ * accepted / rejected (device, int64 [npaths]) receive each path's step
+ * counts.  A path that used up max_steps stops where it is and the next
+ * xsde_synchronize reports XSDE_ELIMIT.  Each path runs on one CTA; the six
+ * stage derivatives use the problem's workspace (6 fields). */
+int xsde_integrate_adaptive(xsde_problem *prob, xsde_vector *psi, const xsde_adaptive *spec, int64_t *accepted,
+                            int64_t *rejected, void *stream);
+
 /* As xsde_integrate (1D-3D lattices, no sampling group), computed the plain
  * unfused way, for comparison with the fused passes: every transform is a
  * cuFFT call over all paths and every other operation of the step (exp(L dt/2)
@@ -253,7 +283,8 @@ int xsde_integrate_static_scratch(xsde_problem *prob, xsde_vector *psi, double d
 
 /* Wait for `stream`, then report device-side errors of this problem's calls:
  * XSDE_ENONFINITE if a sampled field held NaN/Inf, XSDE_ETIMEOUT if a bounded
- * wait gave up.  Clears the device error word. */
+ * wait gave up, XSDE_ELIMIT if an adaptive path used up its step attempts.
+ * Clears the device error word. */
 int xsde_synchronize(xsde_problem *prob, void *stream);
 
 /* Kernel implementation for this problem, in [0, xsde_kernel_variants(prob)).

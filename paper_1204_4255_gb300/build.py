@@ -35,6 +35,7 @@ UNITS = [
     ("rk4ip_2d_tma.cu", None),
     ("rk4ip_adjoint.cu", None),
     ("plain.cu", None),
+    ("ark45_1d.cu", None),
 ]
 
 

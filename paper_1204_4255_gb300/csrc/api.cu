@@ -975,6 +975,65 @@ int xsde_adjoint(xsde_problem *p, const xsde_vector *psi0, const xsde_vector *ta
     return p->dtype == XSDE_C64 ? run(0.0f) : run(0.0);
 }
 
+int xsde_integrate_adaptive(xsde_problem *p, xsde_vector *psi, const xsde_adaptive *spec, int64_t *accepted,
+                            int64_t *rejected, void *stream) {
+    if (!p || !psi || !spec || !accepted || !rejected)
+        return fail(XSDE_EINVAL, "xsde_integrate_adaptive: NULL argument");
+    if (!p->have_ops) return fail(XSDE_EINVAL, "xsde_integrate_adaptive: operators not set");
+    if (psi->dtype != p->dtype) return fail(XSDE_EINVAL, "xsde_integrate_adaptive: field dtype differs");
+    if (!same_lattice(psi->grid, p->grid)) return fail(XSDE_EINVAL, "xsde_integrate_adaptive: field lattice differs");
+    const xsde_grid &g = p->grid;
+    if (g.ndim != 1 || g.n[0] < 64)
+        return fail(XSDE_EUNSUPPORTED, "xsde_integrate_adaptive: 1D lattices of 64..2048 points");
+    if (p->noise.kind != XSDE_NOISE_NONE)
+        return fail(XSDE_EUNSUPPORTED, "xsde_integrate_adaptive: deterministic problems only");
+    if (p->N.pot_kind == XSDE_POT_TABLE && p->N.V_nt != 1)
+        return fail(XSDE_EUNSUPPORTED, "xsde_integrate_adaptive: a time-dependent potential table");
+    if (p->samp.every > 0) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_adaptive: sampling groups");
+    if (!(spec->t_end >= 0.0) || !std::isfinite(spec->t_end) || !(spec->h0 > 0.0) || !std::isfinite(spec->h0) ||
+        !std::isfinite(spec->tol) || spec->max_steps < 1 || (spec->picture != 0 && spec->picture != 1))
+        return fail(XSDE_EINVAL, "xsde_integrate_adaptive: need t_end >= 0, h0 > 0, finite tol, max_steps >= 1");
+    const int64_t npaths = psi->npaths;
+    if (npaths > (int64_t)INT32_MAX) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_adaptive: too many paths");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != p->device) return fail(XSDE_EINVAL, "xsde_integrate_adaptive: wrong current device");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int n = g.n[0];
+    auto run = [&](auto zero) -> int {
+        using R = decltype(zero);
+        using V = cx<R>;
+        int rc = p->table_dt > 0.0 ? XSDE_OK : ensure_tables<V>(p, 1.0, s);   // the twiddle tables
+        if (rc != XSDE_OK) return rc;
+        if ((rc = ensure_scratch(p, (size_t)6 * npaths * n * sizeof(V), s)) != XSDE_OK) return rc;
+        AdaptiveParams<R> q;
+        Sampling sm;
+        fill_terms<R>(p, 1.0, npaths, 0, q.lt, sm);
+        q.psi = static_cast<V *>(psi->data);
+        q.npaths = npaths;
+        const int elems = ark45_1d_elems(n);
+        q.tw = static_cast<const tw_t<R> *>(elems == 8 ? p->d_tw[0] : p->d_tw1d[elems == 4 ? 0 : 1]);
+        q.kbuf = static_cast<V *>(p->d_scratch);
+        q.c0_re = p->L.c0_re;
+        q.c0_im = p->L.c0_im;
+        q.c2_re = p->L.c2_re;
+        q.c2_im = p->L.c2_im;
+        q.kscale = 2.0 * M_PI / (g.xmax[0] - g.xmin[0]);
+        q.gnl = p->N.g;
+        q.t_end = spec->t_end;
+        q.tol = spec->tol;
+        q.h0 = spec->h0;
+        q.picture = spec->picture;
+        q.max_steps = spec->max_steps;
+        q.accepted = accepted;
+        q.rejected = rejected;
+        q.status = p->d_status;
+        XSDE_CUDA(launch_ark45_1d<R>(n, q, s), "xsde_integrate_adaptive launch");
+        return XSDE_OK;
+    };
+    return p->dtype == XSDE_C64 ? run(0.0f) : run(0.0);
+}
+
 int xsde_integrate_plain(xsde_problem *p, xsde_vector *psi, double dt, int64_t nsteps, int64_t npaths,
                          int64_t path_offset, uint64_t step_offset, void *stream) {
     int rc = check_integrate("xsde_integrate_plain", p, psi, dt, nsteps, npaths, path_offset, step_offset);
@@ -1070,6 +1129,7 @@ int xsde_synchronize(xsde_problem *p, void *stream) {
     if (st) XSDE_CUDA(cudaMemset(p->d_status, 0, sizeof(int)), "xsde_synchronize: reset");
     if (st & ST_TIMEOUT) return fail(XSDE_ETIMEOUT, "a bounded device-side wait gave up");
     if (st & ST_NONFINITE) return fail(XSDE_ENONFINITE, "the field became non-finite");
+    if (st & ST_STEP_LIMIT) return fail(XSDE_ELIMIT, "an adaptive path used up its step attempts");
     return XSDE_OK;
 }
 

@@ -156,6 +156,30 @@ template <typename R> struct AdjParams {
 template <typename R> cudaError_t launch_adjoint_1d(int n, int elems, const AdjParams<R> &p, cudaStream_t s);
 
 // --------------------------------------------------------------------------
+// Adaptive Cash-Karp 4(5) Runge-Kutta on 1D lattices (ark45_1d.cu): one CTA
+// per path, each path with its own step size.
+// --------------------------------------------------------------------------
+enum { ST_STEP_LIMIT = 4 };   // a path used up its step attempts
+template <typename R> struct AdaptiveParams {
+    cx<R> *psi;            // [npaths][N] real space, in/out
+    int64_t npaths;
+    const tw_t<R> *tw;     // per-stage twiddles of the launch shape's radix plan
+    cx<R> *kbuf;           // [npaths][6][N] stage derivatives (workspace)
+    LocalTerm<R> lt;       // the static potential (noise off)
+    double c0_re, c0_im, c2_re, c2_im;   // L(k) = c0 + c2 k^2
+    double kscale;         // 2 pi / (xmax - xmin)
+    double gnl;
+    double t_end, tol, h0;
+    int picture;           // 1: interaction picture, 0: explicit
+    int64_t max_steps;     // step attempts per path
+    int64_t *accepted, *rejected;   // [npaths] (device)
+    int *status;
+};
+// points per thread of the launch shape for N (at least one warp per path)
+int ark45_1d_elems(int n);
+template <typename R> cudaError_t launch_ark45_1d(int n, const AdaptiveParams<R> &p, cudaStream_t s);
+
+// --------------------------------------------------------------------------
 // 0D: one thread per path (an ordinary SDE; D is a scalar factor).
 // --------------------------------------------------------------------------
 template <typename R> struct Params0D {

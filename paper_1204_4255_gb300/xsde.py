@@ -16,7 +16,7 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libxsde.so")
 
-XSDE_OK, XSDE_EINVAL, XSDE_ENOMEM, XSDE_ECUDA, XSDE_ETIMEOUT, XSDE_ENONFINITE, XSDE_EUNSUPPORTED = range(7)
+XSDE_OK, XSDE_EINVAL, XSDE_ENOMEM, XSDE_ECUDA, XSDE_ETIMEOUT, XSDE_ENONFINITE, XSDE_EUNSUPPORTED, XSDE_ELIMIT = range(8)
 XSDE_C64, XSDE_C128 = 1, 2
 XSDE_POT_NONE, XSDE_POT_HARMONIC, XSDE_POT_TABLE = 0, 1, 2
 XSDE_NOISE_NONE, XSDE_NOISE_WIENER_REAL, XSDE_NOISE_WIENER_COMPLEX = 0, 1, 2
@@ -32,6 +32,7 @@ EXPORTED = (
     "xsde_profile", "xsde_profile_report", "xsde_kernel_name", "xsde_set_kernel_variant",
     "xsde_integrate_static_scratch", "xsde_adjoint", "xsde_kernel_variants", "xsde_autotune",
     "xsde_batch_create", "xsde_batch_integrate", "xsde_batch_destroy", "xsde_integrate_plain",
+    "xsde_integrate_adaptive",
 )
 XSDE_BATCH_AUTOTUNE = 1
 XSDE_KERNEL_KINDS = 9
@@ -56,6 +57,11 @@ class xsde_nonlinear_op(ctypes.Structure):
 
 class xsde_sampling(ctypes.Structure):
     _fields_ = [("every", ctypes.c_int32), ("which", ctypes.c_int32)]
+
+
+class xsde_adaptive(ctypes.Structure):
+    _fields_ = [("t_end", ctypes.c_double), ("tol", ctypes.c_double), ("h0", ctypes.c_double),
+                ("picture", ctypes.c_int32), ("max_steps", ctypes.c_int64)]
 
 
 class xsde_batch_member(ctypes.Structure):
@@ -108,6 +114,7 @@ def load(path: str = LIB_PATH):
         "xsde_batch_integrate": (ctypes.c_int, [vp, dp, i64, u64, vp]),
         "xsde_batch_destroy": (None, [vp]),
         "xsde_integrate_plain": (ctypes.c_int, [vp, vp, dp, i64, i64, i64, u64, vp]),
+        "xsde_integrate_adaptive": (ctypes.c_int, [vp, vp, ctypes.POINTER(xsde_adaptive), vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -218,6 +225,13 @@ def xsde_integrate_plain(prob, vec, dt: float, nsteps: int, npaths: int, path_of
     """The unfused comparison step (cuFFT + elementwise kernels)."""
     _check(load().xsde_integrate_plain(prob, vec, dt, nsteps, npaths, path_offset, step_offset,
                                        ctypes.c_void_p(stream or None)))
+
+
+def xsde_integrate_adaptive(prob, vec, spec: xsde_adaptive, accepted_ptr: int, rejected_ptr: int,
+                            stream: int = 0) -> None:
+    """Adaptive Cash-Karp integration to spec.t_end (interaction picture or explicit)."""
+    _check(load().xsde_integrate_adaptive(prob, vec, ctypes.byref(spec), ctypes.c_void_p(accepted_ptr),
+                                          ctypes.c_void_p(rejected_ptr), ctypes.c_void_p(stream or None)))
 
 
 def xsde_integrate_static_scratch(prob, vec, dt: float, nsteps: int, npaths: int, path_offset: int = 0,
@@ -385,6 +399,21 @@ class Problem:
                                  _stream_handle(stream))
         finally:
             xsde_vector_free(vec)
+
+    def integrate_adaptive(self, psi, t_end: float, tol: float, h0: float, picture: bool = True,
+                           max_steps: int = 10 ** 7, stream=None):
+        """Adaptive integration of psi to t_end in place; returns (accepted,
+        rejected) step counts per path as int64 CUDA tensors."""
+        import torch
+        acc = torch.zeros(psi.shape[0], dtype=torch.int64, device=psi.device)
+        rej = torch.zeros(psi.shape[0], dtype=torch.int64, device=psi.device)
+        vec = self.wrap(psi)
+        try:
+            xsde_integrate_adaptive(self.prob, vec, xsde_adaptive(t_end, tol, h0, 1 if picture else 0, max_steps),
+                                    acc.data_ptr(), rej.data_ptr(), _stream_handle(stream))
+        finally:
+            xsde_vector_free(vec)
+        return acc, rej
 
     def synchronize(self, stream=None):
         xsde_synchronize(self.prob, _stream_handle(stream))

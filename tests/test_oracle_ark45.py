@@ -108,4 +108,4 @@ def test_step_count_scaling_with_resolution():
         ex.append(a_ex[0] + r_ex[0])
     assert max(ip) <= 1.5 * min(ip), ip
     for i in range(2):
-        assert 2.5 < ex[i + 1] / ex[i] < 5.5, ex
+        assert 3.5 < ex[i + 1] / ex[i] < 6.5, ex
