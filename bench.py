@@ -278,6 +278,39 @@ def config_figures() -> dict:
     return out
 
 
+def ip_vs_explicit(tol: float = 1e-6, t_end: float = 1.0) -> dict:
+    """Fig. IPvsEX: the adaptive Cash-Karp integrator (xsde_integrate_adaptive,
+    complex128) on the trapped GPE (V = x^2/2, g = 10, [-10, 10), ground state of
+    the linear problem) to t_end at tolerance tol, with and without the
+    interaction picture, at 64..2048 points (explicit up to 1024): step
+    attempts and device time."""
+    import torch
+    import workloads as W
+    from paper_1204_4255_gb300 import xsde
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"equation": "i psi_t = -1/2 psi_xx + 1/2 x^2 psi + 10 |psi|^2 psi, [-10,10), psi0 = pi^-1/4 exp(-x^2/2)",
+           "t_end": t_end, "tol": tol, "dtype": "c128", "points": {}}
+    for n in (64, 128, 256, 512, 1024, 2048):
+        w = W.ip_scaling(n, t_end=t_end)
+        row = {}
+        for picture in ((True, False) if n <= 1024 else (True,)):
+            P = xsde.Problem(w.n, w.xmin, w.xmax, "c128")
+            P.set_operators(c2=w.c2, g=w.gnl, pot_kind=xsde.XSDE_POT_HARMONIC, omega=(1.0, 0.0, 0.0))
+            psi = torch.from_numpy(w.psi0).cuda()
+            P.integrate_adaptive(psi.clone(), t_end, tol, 1e-3, picture=picture)   # warm
+            torch.cuda.synchronize()
+            e0.record()
+            acc, rej = P.integrate_adaptive(psi, t_end, tol, 1e-3, picture=picture)
+            e1.record()
+            torch.cuda.synchronize()
+            P.synchronize()
+            row["interaction_picture" if picture else "explicit"] = {
+                "steps": int(acc[0]), "rejected": int(rej[0]), "ms": e0.elapsed_time(e1)}
+            P.close()
+        out["points"][str(n)] = row
+    return out
+
+
 def batched_cost(reps: int = 3) -> dict:
     """Uneven instances advanced together (xsde_batch, autotuned, one CUDA graph
     replay per call): one 3D GPE 128^3, 32 2D GPEs at 256^2 and 32 at 512^2, and
@@ -482,6 +515,7 @@ def run_gpu(args) -> None:
         bat = batched_cost() if not args.no_batch else None
         plain = plain_vs_fused() if not args.no_batch else None
         others = config_figures() if not args.no_batch else None
+        ipex = ip_vs_explicit() if not args.no_batch else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -493,7 +527,7 @@ def run_gpu(args) -> None:
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "kernels_profiled_step": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]},
             "norm_check": ok, "adjoint": adj, "batched": bat, "plain_vs_fused": plain,
-            "other_workloads": others,
+            "other_workloads": others, "ip_vs_explicit": ipex,
         }
         print(json.dumps(line), flush=True)
     prob.close()
