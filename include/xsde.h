@@ -178,6 +178,14 @@ void xsde_problem_destroy(xsde_problem *prob);
  * noise; a potential table needs V != NULL and V_nt >= 1. */
 int xsde_set_operators(xsde_problem *prob, const xsde_linear_op *L, const xsde_nonlinear_op *N);
 
+/* Sample the same Brownian path at several step sizes (Sec. 2.5's strong
+ * convergence test): with substeps S (1..65536, default 1) the noise of global
+ * step n is built from the normals of the S finer steps S n .. S n + S - 1 --
+ * their Wiener increments summed -- so a run with step dt and S substeps sees
+ * the path of a run with step dt/S and substeps 1.  Global step indices times
+ * S must stay below 2^32.  Applies to every integrating call of the problem. */
+int xsde_set_noise_substeps(xsde_problem *prob, int32_t substeps);
+
 /* Register a sampling group for the following xsde_integrate calls.
  * per_path  (device, FP64): [nsamp][npaths][2] = (norm, energy)  if NORM|ENERGY
  * per_point (device, FP64): [nsamp][npts][2]  = (mean |psi|^2, mean |psi|^4)

@@ -50,6 +50,7 @@ class _Ops(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("pot_kind", ctypes.c_int32),
         ("noise_kind", ctypes.c_int32),
+        ("substeps", ctypes.c_int32),
     ]
 
 
@@ -133,6 +134,7 @@ class Ops:
     noise_kind: int = NOISE_NONE
     noise_amp: float = 0.0
     seed: int = 0
+    substeps: int = 1                 # noise of a step from this many finer steps
     _keep: list = field(default_factory=list, repr=False)
 
     def _c(self) -> _Ops:
@@ -155,6 +157,7 @@ class Ops:
         o.seed = self.seed
         o.pot_kind = self.pot_kind
         o.noise_kind = self.noise_kind
+        o.substeps = self.substeps
         return o
 
 

@@ -67,6 +67,9 @@ typedef struct {
     int32_t pot_kind;      /* 0 none, 1 harmonic, 2 table */
     int32_t noise_kind;    /* 0 none, 1 additive real, 2 additive complex,
                               3 multiplicative real */
+    int32_t substeps;      /* noise of step n from the finer steps S n .. S n + S - 1
+                              (the same Brownian path as steps S times shorter);
+                              values below 1 mean 1 */
 } oracle_ops;
 
 enum { POT_NONE = 0, POT_HARMONIC = 1, POT_TABLE = 2 };
@@ -328,11 +331,21 @@ static void fill_step_inputs(step_inputs *in, const oracle_grid *g, const oracle
     for (int64_t j = 0; j < npts; j++) in->Vrow[j] = potential_at(g, ops, j, step);
     if (ops->noise_kind == NOISE_NONE) return;
     double scale = 1.0 / sqrt(dt * grid_dV(g));   /* white noise per step: var 1/(dt dV) */
+    const int64_t S = ops->substeps > 1 ? ops->substeps : 1;
     #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < npaths * npts; i++) {
         int64_t p = i / npts, j = i % npts;
-        double z[2];
-        wiener_pair(ops->seed, j, path0 + p, step, z);
+        /* the Wiener increment of the step is the sum of the S finer steps'
+           increments: z = (sum of their standard normals) / sqrt(S) */
+        double z[2] = {0.0, 0.0};
+        for (int64_t f = 0; f < S; f++) {
+            double zf[2];
+            wiener_pair(ops->seed, j, path0 + p, S * step + f, zf);
+            z[0] += zf[0];
+            z[1] += zf[1];
+        }
+        z[0] /= sqrt((double)S);
+        z[1] /= sqrt((double)S);
         if (ops->noise_kind == NOISE_ADD_REAL) in->xi_a[i] = scale * z[0];
         else if (ops->noise_kind == NOISE_ADD_COMPLEX) in->xi_a[i] = scale * (z[0] + I * z[1]) / sqrt(2.0);
         else in->xi_m[i] = scale * z[0];

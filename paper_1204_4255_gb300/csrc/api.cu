@@ -72,6 +72,7 @@ struct xsde_problem {
     int *d_status = nullptr;
     int num_sms = 1;
     int kernel_variant = 0;   // see xsde_set_kernel_variant
+    int noise_substeps = 1;   // see xsde_set_noise_substeps
     uint64_t generation = 0;  // bumped by every call that changes what integrate launches
     void *d_adj = nullptr;    // adjoint checkpoints and stage inputs
     size_t adj_bytes = 0;
@@ -308,6 +309,7 @@ void fill_terms(const xsde_problem *p, double dt, int64_t npaths, int64_t path_o
     }
     lt.key = make_uint2((uint32_t)(p->noise.seed & 0xffffffffu), (uint32_t)(p->noise.seed >> 32));
     lt.path_offset = path_offset;
+    lt.substeps = p->noise_substeps;
 
     sm.every = p->samp.every;
     sm.which = p->samp.which;
@@ -612,7 +614,7 @@ int check_integrate(const char *who, xsde_problem *p, const xsde_vector *psi, do
     if (nsteps < 0) return fail(XSDE_EINVAL, "%s: nsteps < 0", who);
     if (path_offset < 0 || path_offset + npaths > (int64_t)UINT32_MAX + 1)
         return fail(XSDE_EINVAL, "%s: global path indices exceed 32 bits", who);
-    if (step_offset + (uint64_t)nsteps + 1 > (uint64_t)UINT32_MAX)
+    if ((step_offset + (uint64_t)nsteps + 1) * (uint64_t)p->noise_substeps > (uint64_t)UINT32_MAX)
         return fail(XSDE_EINVAL, "%s: global step indices exceed 32 bits", who);
     if (p->N.pot_kind == XSDE_POT_TABLE && p->N.V_nt > 1 && step_offset + (uint64_t)nsteps > (uint64_t)p->N.V_nt)
         return fail(XSDE_EINVAL, "%s: potential table has %lld rows, steps up to %llu needed", who,
@@ -844,6 +846,14 @@ int xsde_set_kernel_variant(xsde_problem *p, int variant) {
 }
 
 int xsde_kernel_variants(const xsde_problem *p) { return p ? variants_for(p) : 0; }
+
+int xsde_set_noise_substeps(xsde_problem *p, int32_t substeps) {
+    if (!p) return fail(XSDE_EINVAL, "xsde_set_noise_substeps: problem is NULL");
+    if (substeps < 1 || substeps > 65536) return fail(XSDE_EINVAL, "xsde_set_noise_substeps: %d", substeps);
+    if (p->noise_substeps != substeps) ++p->generation;
+    p->noise_substeps = substeps;
+    return XSDE_OK;
+}
 
 
 int xsde_profile(xsde_problem *p, int enable) {

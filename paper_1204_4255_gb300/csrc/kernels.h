@@ -34,6 +34,7 @@ template <typename R> struct LocalTerm {
     R nscale;             // amplitude * sqrt(dt/dV)   (complex noise: / sqrt 2)
     uint2 key;            // Philox key (seed_lo, seed_hi)
     int64_t path_offset;  // global index of local path 0
+    int substeps = 1;     // a step's noise is the mean of this many finer steps' (see point_term)
 };
 
 // Sampling group: FP64 per-path (norm, energy) and per-point (mean |psi|^2, |psi|^4).
@@ -238,7 +239,20 @@ __device__ __forceinline__ PointTerm<R> point_term(const LocalTerm<R> &lt, R Vra
     pt.dtV = lt.dt * Vraw;
     pt.na = mk<cx<R>>(R(0), R(0));
     if (lt.noise != NM_NONE) {
-        cx<R> z = wiener_pair<R>(lt.key, j, gpath, gstep);
+        // With substeps S the step's Wiener increment is the sum of those of S
+        // steps S times shorter (fine global steps S n .. S n + S - 1): the same
+        // Brownian path as a run with dt/S, normalised back to N(0, 1).
+        cx<R> z = wiener_pair<R>(lt.key, j, gpath, gstep * (uint32_t)lt.substeps);
+        if (lt.substeps > 1) {
+            for (int i = 1; i < lt.substeps; ++i) {
+                const cx<R> w = wiener_pair<R>(lt.key, j, gpath, gstep * (uint32_t)lt.substeps + (uint32_t)i);
+                z.x += w.x;
+                z.y += w.y;
+            }
+            const R r = R(1) / sqrt(R(lt.substeps));
+            z.x *= r;
+            z.y *= r;
+        }
         if (lt.noise == NM_MUL_REAL) pt.dtV += lt.nscale * z.x;
         else if (lt.noise == NM_ADD_REAL) pt.na = mk<cx<R>>(lt.nscale * z.x, R(0));
         else pt.na = mk<cx<R>>(lt.nscale * z.x, lt.nscale * z.y);

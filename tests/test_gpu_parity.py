@@ -318,3 +318,41 @@ def test_3d_gpe_128_cubed(dtype):
     tol = 1e-10 if dtype == "c128" else 1e-4
     assert rel_l2(got, ref) < tol
     assert np.allclose(pp, opp, rtol=tol, atol=0)
+
+
+# --------------------------------------------------------------------------- #
+# One Brownian path at several step sizes (noise substeps)                    #
+# --------------------------------------------------------------------------- #
+
+@pytest.mark.parametrize("case,S,dtype", [("tw_1d", 4, "c128"), ("tw_1d", 3, "c64"), ("kubo_0d", 8, "c128"),
+                                          ("gpe_2d_tma", 2, "c64"), ("gpe_3d", 2, "c128")])
+def test_noise_substeps_match_oracle(case, S, dtype):
+    if case == "tw_1d":
+        w = W.truncated_wigner(npaths=5, n=256, nsteps=12)
+    elif case == "kubo_0d":
+        w = W.kubo_oscillator(npaths=300, nsteps=40)
+    elif case == "gpe_2d_tma":
+        rng = np.random.default_rng(3)
+        x0 = -6 + np.arange(256) * 12 / 256
+        base = np.exp(-(x0[:, None] ** 2 + x0[None, :] ** 2) / 3)
+        psi0 = np.stack([base * np.exp(0.2j * rng.standard_normal((256, 256))) for _ in range(2)])
+        w = W.Workload("gpe2n", (256, 256), (-6.0, -6.0), (6.0, 6.0), 0j, -0.5j, 20.0, W.POT_HARMONIC,
+                       (1.0, 1.0), None, W.NOISE_ADD_COMPLEX, 0.05, 77, 5e-4, 6, psi0.astype(np.complex128))
+    else:
+        shape = (16, 16, 32)
+        axes = [-5 + np.arange(n) * 10 / n for n in shape]
+        X, Y, Z = np.meshgrid(*axes, indexing="ij")
+        psi0 = np.exp(-(X ** 2 + Y ** 2 + Z ** 2) / 4)[None].astype(np.complex128)
+        w = W.Workload("gpe3n", shape, (-5.0,) * 3, (5.0,) * 3, 0j, -0.5j, 3.0, W.POT_HARMONIC, (1.0, 1.0, 1.0),
+                       None, W.NOISE_MUL_REAL, 0.1, 55, 1e-3, 5, psi0)
+    got, _, _ = gpu_run(w, dtype, substeps=S, step_offset=3)
+    grid, ops = O.from_workload(w)
+    ops.substeps = S
+    ref, _, _ = O.rk4ip(w.psi0, grid, ops, w.dt, w.nsteps, step0=3)
+    tol = 1e-10 if dtype == "c128" else 1e-4
+    err = np.max(rel_l2(got.reshape(w.npaths, -1), ref.reshape(w.npaths, -1), axis=1))
+    assert err < tol, err
+    # and the substeps matter: the one-step path differs by far more than that
+    plain, _, _ = O.rk4ip(w.psi0, grid, O.from_workload(w)[1], w.dt, w.nsteps, step0=3)
+    diff = np.max(rel_l2(plain.reshape(w.npaths, -1), ref.reshape(w.npaths, -1), axis=1))
+    assert diff > 50 * err, (diff, err)

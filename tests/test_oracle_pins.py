@@ -356,3 +356,45 @@ def test_moments_sampling_matches_direct_means():
     m20 = np.abs(w.psi0) ** 2
     assert np.allclose(per_point[0, :, 0], m20.mean(axis=0), rtol=1e-13)
     assert np.allclose(per_path[-1, :, 0], m2.sum(axis=1) * w.dx(0), rtol=1e-13)
+
+
+# --------------------------------------------------------------------------- #
+# The same Brownian path at several step sizes (Sec. 2.5, strong convergence)  #
+# --------------------------------------------------------------------------- #
+
+@pytest.mark.parametrize("S", [2, 4])
+def test_substep_noise_is_the_sum_of_the_finer_increments(S):
+    """With S substeps, RK4IP on the OU process is the discrete closed form
+    driven by z_n = sum_{f<S} z(S n + f) / sqrt(S): the fine steps' normals."""
+    w = W.ornstein_uhlenbeck(npaths=8, nsteps=10, dt=0.02)
+    grid, ops = O.from_workload(w)
+    ops.substeps = S
+    out, _, _ = O.rk4ip(w.psi0, grid, ops, w.dt, w.nsteps)
+    th, s, dt = 1.0, 0.5, w.dt
+    c = (math.exp(-th * dt) + 4 * math.exp(-th * dt / 2) + 1) / 6
+    x = w.psi0.copy()
+    for n in range(w.nsteps):
+        z = sum(O.wiener_normals(w.seed, 1, 8, 0, S * n + f)[:, 0, 0] for f in range(S)) / math.sqrt(S)
+        x = math.exp(-th * dt) * x + c * s * math.sqrt(dt) * z
+    assert np.max(np.abs(out - x)) < 1e-13
+
+
+def test_strong_convergence_on_one_brownian_path():
+    """Kubo oscillator dz = i omega z dt + i beta z o dW (Stratonovich): the exact
+    solution along a path is z0 exp(i omega T + i beta W(T)).  Runs with steps
+    dt, dt/2, dt/4 (substeps 4, 2, 1 over the same fine path) approach it, the
+    error falling by at least 2 per halving; with the substeps ignored (every
+    run drawing its own path) they would not."""
+    T, dt_fine, npaths = 1.0, 1.0 / 256, 64
+    w = W.kubo_oscillator(npaths=npaths, nsteps=1)
+    grid, ops = O.from_workload(w)
+    om, beta, z0 = w.extra["omega"], w.extra["beta"], w.extra["z0"]
+    nfine = round(T / dt_fine)
+    Wt = sum(O.wiener_normals(w.seed, 1, npaths, 0, f)[:, 0, 0] for f in range(nfine)) * math.sqrt(dt_fine)
+    exact = z0 * np.exp(1j * om * T + 1j * beta * Wt)
+    errs = []
+    for S in (16, 8, 4):
+        ops.substeps = S
+        out, _, _ = O.rk4ip(w.psi0, grid, ops, S * dt_fine, nfine // S)
+        errs.append(np.mean(np.abs(out - exact)))
+    assert errs[0] / errs[1] > 2.0 and errs[1] / errs[2] > 2.0, errs
