@@ -51,6 +51,7 @@ class _Ops(ctypes.Structure):
         ("pot_kind", ctypes.c_int32),
         ("noise_kind", ctypes.c_int32),
         ("substeps", ctypes.c_int32),
+        ("scheme", ctypes.c_int32),
     ]
 
 
@@ -135,6 +136,7 @@ class Ops:
     noise_amp: float = 0.0
     seed: int = 0
     substeps: int = 1                 # noise of a step from this many finer steps
+    scheme: int = 0                   # 0 RK4IP, 1 semi-implicit midpoint (interaction picture)
     _keep: list = field(default_factory=list, repr=False)
 
     def _c(self) -> _Ops:
@@ -158,6 +160,7 @@ class Ops:
         o.pot_kind = self.pot_kind
         o.noise_kind = self.noise_kind
         o.substeps = self.substeps
+        o.scheme = self.scheme
         return o
 
 

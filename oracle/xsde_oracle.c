@@ -70,6 +70,8 @@ typedef struct {
     int32_t substeps;      /* noise of step n from the finer steps S n .. S n + S - 1
                               (the same Brownian path as steps S times shorter);
                               values below 1 mean 1 */
+    int32_t scheme;        /* 0: RK4IP; 1: semi-implicit midpoint in the interaction
+                              picture (see oracle_rk4ip) */
 } oracle_ops;
 
 enum { POT_NONE = 0, POT_HARMONIC = 1, POT_TABLE = 2 };
@@ -398,6 +400,8 @@ void oracle_observables(const oracle_grid *g, const oracle_ops *ops, const doubl
  *   k4  = N(D(a_I + k3))
  *   a  <- D(a_I + k1/6 + k2/3 + k3/3) + k4/6
  * with D = exp(L dt/2) applied in Fourier space and N = dt*g in real space.
+ * ops->scheme = 1 takes the semi-implicit midpoint step instead:
+ *   a_I = D(a);  m = a_I;  m <- a_I + N(m)/2 (three times);  a <- D(2 m - a_I).
  */
 
 /*
@@ -460,6 +464,24 @@ int oracle_rk4ip(const oracle_grid *g, const oracle_ops *ops, double *psi_in, in
         if (n == nsteps) break;
 
         fill_step_inputs(&in, g, ops, npaths, path0, step0 + n, dt);
+
+        if (ops->scheme == 1) {
+            /* semi-implicit midpoint in the interaction picture (Sec. 2.5's
+               semi-implicit method, Werner & Drummond 1997, with Sec. 2.6):
+               a_I = D(a); m <- a_I + N(m)/2 three times from m = a_I;
+               a <- D(2 m - a_I) */
+            memcpy(aI, a, sizeof(cplx) * m);
+            apply_D(aI, E, g, npaths);
+            memcpy(tmp, aI, sizeof(cplx) * m);
+            for (int it = 0; it < 3; it++) {
+                nonlinear(k1, tmp, ops, &in, npts, npaths, dt);
+                for (int64_t i = 0; i < m; i++) tmp[i] = aI[i] + 0.5 * k1[i];
+            }
+            for (int64_t i = 0; i < m; i++) tmp[i] = 2.0 * tmp[i] - aI[i];
+            apply_D(tmp, E, g, npaths);
+            memcpy(a, tmp, sizeof(cplx) * m);
+            continue;
+        }
 
         /* a_I = D(a) */
         memcpy(aI, a, sizeof(cplx) * m);

@@ -398,3 +398,61 @@ def test_strong_convergence_on_one_brownian_path():
         out, _, _ = O.rk4ip(w.psi0, grid, ops, S * dt_fine, nfine // S)
         errs.append(np.mean(np.abs(out - exact)))
     assert errs[0] / errs[1] > 2.0 and errs[1] / errs[2] > 2.0, errs
+
+
+# --------------------------------------------------------------------------- #
+# Semi-implicit midpoint in the interaction picture (Sec. 2.5, Sec. 2.6)      #
+# --------------------------------------------------------------------------- #
+
+def test_semi_implicit_is_second_order_on_the_soliton():
+    """Deterministic order 2 (error / 4 per halving of dt) on the exact soliton,
+    against RK4IP's order 4 on the same runs."""
+    w = W.nls_soliton()
+    grid, ops = O.from_workload(w)
+    x = w.coords(0)
+    T = 0.5
+    exact = (1 / np.cosh(x)) * np.exp(0.5j * T)
+    errs = {}
+    for scheme in (1, 0):
+        ops.scheme = scheme
+        errs[scheme] = []
+        for dt in (0.02, 0.01, 0.005):
+            out, _, _ = O.rk4ip(w.psi0, grid, ops, dt, round(T / dt))
+            errs[scheme].append(np.linalg.norm(out[0] - exact) / np.linalg.norm(exact))
+    si, rk = errs[1], errs[0]
+    for i in range(2):
+        assert 3.5 < si[i] / si[i + 1] < 4.6, si
+    assert rk[0] < si[0] / 100
+
+
+def test_semi_implicit_free_evolution_is_exact():
+    """g = 0: a <- D(2 a_I - a_I) = D(D(a)) = exp(L dt) a, the exact flow."""
+    n, L = 512, 40.0
+    x = -L + np.arange(n) * (2 * L / n)
+    w = W.Workload("free", (n,), (-L,), (L,), 0j, -0.5j, 0.0, W.POT_NONE, (0.0,), None, W.NOISE_NONE, 0.0, 0,
+                   0.1, 20, np.exp(-x ** 2 / 2).astype(np.complex128)[None])
+    grid, ops = O.from_workload(w)
+    ops.scheme = 1
+    out, _, _ = O.rk4ip(w.psi0, grid, ops, w.dt, w.nsteps)
+    exact = (1 + 2j) ** -0.5 * np.exp(-x ** 2 / (2 * (1 + 2j)))
+    assert np.linalg.norm(out[0] - exact) / np.linalg.norm(exact) < 1e-12
+
+
+def test_semi_implicit_strong_convergence_on_one_path():
+    """Kubo oscillator along one Brownian path per run (substeps): the
+    semi-implicit midpoint's error against the exact pathwise solution falls
+    at least linearly with dt (strong order 1, Stratonovich)."""
+    T, dt_fine, npaths = 1.0, 1.0 / 512, 256
+    w = W.kubo_oscillator(npaths=npaths, nsteps=1)
+    grid, ops = O.from_workload(w)
+    ops.scheme = 1
+    om, beta, z0 = w.extra["omega"], w.extra["beta"], w.extra["z0"]
+    nfine = round(T / dt_fine)
+    Wt = sum(O.wiener_normals(w.seed, 1, npaths, 0, f)[:, 0, 0] for f in range(nfine)) * math.sqrt(dt_fine)
+    exact = z0 * np.exp(1j * om * T + 1j * beta * Wt)
+    errs = []
+    for S in (32, 16, 8):
+        ops.substeps = S
+        out, _, _ = O.rk4ip(w.psi0, grid, ops, S * dt_fine, nfine // S)
+        errs.append(np.mean(np.abs(out - exact)))
+    assert errs[0] / errs[1] > 1.5 and errs[1] / errs[2] > 1.5 and errs[0] / errs[2] > 3.0, errs
