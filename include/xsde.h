@@ -178,6 +178,18 @@ void xsde_problem_destroy(xsde_problem *prob);
  * noise; a potential table needs V != NULL and V_nt >= 1. */
 int xsde_set_operators(xsde_problem *prob, const xsde_linear_op *L, const xsde_nonlinear_op *N);
 
+/* The fixed-step scheme of xsde_integrate (and of batches): RK4IP (default),
+ * or the semi-implicit midpoint step of Sec. 2.5's semi-implicit method in the
+ * interaction picture of Sec. 2.6 -- a_I = D(a); m = a_I; m <- a_I + N(m)/2
+ * three times; a <- D(2 m - a_I), with D = F^-1 exp(L dt/2) F and N = dt g with
+ * the step's noise: deterministic order 2, strong order 1 (Stratonovich).  The
+ * semi-implicit step runs on 0D and 1D lattices (one launch shape);
+ * xsde_integrate on other lattices, xsde_integrate_plain and xsde_adjoint
+ * report XSDE_EUNSUPPORTED for it. */
+#define XSDE_SCHEME_RK4IP 0
+#define XSDE_SCHEME_SEMI_IMPLICIT 1
+int xsde_set_scheme(xsde_problem *prob, int32_t scheme);
+
 /* Sample the same Brownian path at several step sizes (Sec. 2.5's strong
  * convergence test): with substeps S (1..65536, default 1) the noise of global
  * step n is built from the normals of the S finer steps S n .. S n + S - 1 --

@@ -73,6 +73,7 @@ struct xsde_problem {
     int num_sms = 1;
     int kernel_variant = 0;   // see xsde_set_kernel_variant
     int noise_substeps = 1;   // see xsde_set_noise_substeps
+    int scheme = XSDE_SCHEME_RK4IP;   // see xsde_set_scheme
     uint64_t generation = 0;  // bumped by every call that changes what integrate launches
     void *d_adj = nullptr;    // adjoint checkpoints and stage inputs
     size_t adj_bytes = 0;
@@ -505,6 +506,7 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
         q.lt = lt;
         q.sm = sm;
         q.status = p->d_status;
+        q.scheme = p->scheme;
         XSDE_CUDA(timed(p, 0, s, [&] { return launch_rk4ip_0d<R>(q, s); }), "rk4ip_0d launch");
         return XSDE_OK;
     }
@@ -515,11 +517,12 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
         q.nsteps = nsteps;
         q.step0 = step0;
         q.Etab = static_cast<const V *>(p->d_E[0]);
-        const int elems = rk4ip_1d_elems(p->kernel_variant);
+        const int elems = p->scheme == XSDE_SCHEME_RK4IP ? rk4ip_1d_elems(p->kernel_variant) : 8;
         q.tw = static_cast<const tw_t<R> *>(elems == 8 ? p->d_tw[0] : p->d_tw1d[elems == 4 ? 0 : 1]);
         q.lt = lt;
         q.sm = sm;
         q.status = p->d_status;
+        q.scheme = p->scheme;
         XSDE_CUDA(timed(p, 1, s, [&] { return launch_rk4ip_1d<R>(g.n[0], p->kernel_variant, q, s); }), "rk4ip_1d launch");
         return XSDE_OK;
     }
@@ -625,6 +628,8 @@ int check_integrate(const char *who, xsde_problem *p, const xsde_vector *psi, do
         return fail(XSDE_EUNSUPPORTED, "%s: at most 65535 paths per call on a 2D lattice", who);
     if (p->samp.every > 0 && nsteps / p->samp.every + 1 > (int64_t)INT32_MAX)
         return fail(XSDE_EINVAL, "%s: too many samples", who);
+    if (p->scheme != XSDE_SCHEME_RK4IP && p->grid.ndim > 1)
+        return fail(XSDE_EUNSUPPORTED, "%s: the semi-implicit scheme runs on 0D and 1D lattices", who);
     int dev = -1;
     cudaGetDevice(&dev);
     if (dev != p->device) return fail(XSDE_EINVAL, "%s: current device %d is not the problem's %d", who, dev, p->device);
@@ -847,6 +852,15 @@ int xsde_set_kernel_variant(xsde_problem *p, int variant) {
 
 int xsde_kernel_variants(const xsde_problem *p) { return p ? variants_for(p) : 0; }
 
+int xsde_set_scheme(xsde_problem *p, int32_t scheme) {
+    if (!p) return fail(XSDE_EINVAL, "xsde_set_scheme: problem is NULL");
+    if (scheme != XSDE_SCHEME_RK4IP && scheme != XSDE_SCHEME_SEMI_IMPLICIT)
+        return fail(XSDE_EINVAL, "xsde_set_scheme: unknown scheme %d", scheme);
+    if (p->scheme != scheme) ++p->generation;
+    p->scheme = scheme;
+    return XSDE_OK;
+}
+
 int xsde_set_noise_substeps(xsde_problem *p, int32_t substeps) {
     if (!p) return fail(XSDE_EINVAL, "xsde_set_noise_substeps: problem is NULL");
     if (substeps < 1 || substeps > 65536) return fail(XSDE_EINVAL, "xsde_set_noise_substeps: %d", substeps);
@@ -923,6 +937,7 @@ int xsde_adjoint(xsde_problem *p, const xsde_vector *psi0, const xsde_vector *ta
         return fail(XSDE_EINVAL, "xsde_adjoint: lattice differs");
     if (target->npaths != 1) return fail(XSDE_EINVAL, "xsde_adjoint: the target is a single field");
     if (p->noise.kind != XSDE_NOISE_NONE) return fail(XSDE_EUNSUPPORTED, "xsde_adjoint: deterministic problems only");
+    if (p->scheme != XSDE_SCHEME_RK4IP) return fail(XSDE_EUNSUPPORTED, "xsde_adjoint: the adjoint of RK4IP only");
     if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 1 || ckpt_every < 1)
         return fail(XSDE_EINVAL, "xsde_adjoint: need dt > 0, nsteps >= 1, ckpt_every >= 1");
     if (p->N.pot_kind == XSDE_POT_TABLE && p->N.V_nt > 1 && nsteps > p->N.V_nt)
@@ -1051,6 +1066,7 @@ int xsde_integrate_plain(xsde_problem *p, xsde_vector *psi, double dt, int64_t n
     const xsde_grid &g = p->grid;
     if (g.ndim == 0) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_plain: 0D problems have no transform");
     if (p->samp.every > 0) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_plain: sampling groups are not supported");
+    if (p->scheme != XSDE_SCHEME_RK4IP) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_plain: RK4IP only");
     if (npaths * g.npts > (int64_t)INT32_MAX)
         return fail(XSDE_EUNSUPPORTED, "xsde_integrate_plain: more than 2^31 points per call");
     cudaStream_t s = static_cast<cudaStream_t>(stream);

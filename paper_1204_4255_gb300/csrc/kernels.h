@@ -65,6 +65,7 @@ template <typename R> struct Params1D {
     LocalTerm<R> lt;
     Sampling sm;
     int *status;
+    int scheme = 0;        // 0 RK4IP, 1 semi-implicit midpoint (default launch shape only)
 };
 // variant v in [0, rk4ip_1d_variants()) sets the launch shape: elements per
 // thread rk4ip_1d_elems(v) (8, or 4 / 2 for variants 4 / 5, whose twiddle
@@ -192,6 +193,7 @@ template <typename R> struct Params0D {
     LocalTerm<R> lt;
     Sampling sm;
     int *status;
+    int scheme = 0;        // 0 RK4IP, 1 semi-implicit midpoint
 };
 template <typename R> cudaError_t launch_rk4ip_0d(const Params0D<R> &p, cudaStream_t s);
 

@@ -61,6 +61,14 @@ template <typename R> __global__ void __launch_bounds__(kThreads0D) rk4ip_0d_ker
         const uint64_t sg = p.step0 + n;
         const R v = vtime ? p.lt.V[sg] : Vstatic;
         const PointTerm<R> pt = point_term(p.lt, v, 0u, gp, (uint32_t)sg);
+        if (p.scheme == 1) {
+            // semi-implicit midpoint: a_I = D a; m <- a_I + N(m)/2 (three times); a <- D(2m - a_I)
+            const V aI = cmul(E, z);
+            V m = aI;
+            for (int it = 0; it < 3; ++it) m = caxpy(aI, half, apply_N(m, pt, gdt));
+            z = cmul(E, mk<V>(R(2) * m.x - aI.x, R(2) * m.y - aI.y));
+            continue;
+        }
         // a_I = D a, k1 = D N(a), k2, k3, k4 = N(D(a_I + k3)), a <- D(acc) + k4/6
         const V aI = cmul(E, z);
         const V k1 = cmul(E, apply_N(z, pt, gdt));

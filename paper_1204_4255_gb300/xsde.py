@@ -32,8 +32,9 @@ EXPORTED = (
     "xsde_profile", "xsde_profile_report", "xsde_kernel_name", "xsde_set_kernel_variant",
     "xsde_integrate_static_scratch", "xsde_adjoint", "xsde_kernel_variants", "xsde_autotune",
     "xsde_batch_create", "xsde_batch_integrate", "xsde_batch_destroy", "xsde_integrate_plain",
-    "xsde_integrate_adaptive", "xsde_set_noise_substeps",
+    "xsde_integrate_adaptive", "xsde_set_noise_substeps", "xsde_set_scheme",
 )
+XSDE_SCHEME_RK4IP, XSDE_SCHEME_SEMI_IMPLICIT = 0, 1
 XSDE_BATCH_AUTOTUNE = 1
 XSDE_KERNEL_KINDS = 9
 
@@ -116,6 +117,7 @@ def load(path: str = LIB_PATH):
         "xsde_integrate_plain": (ctypes.c_int, [vp, vp, dp, i64, i64, i64, u64, vp]),
         "xsde_integrate_adaptive": (ctypes.c_int, [vp, vp, ctypes.POINTER(xsde_adaptive), vp, vp, vp]),
         "xsde_set_noise_substeps": (ctypes.c_int, [vp, ctypes.c_int32]),
+        "xsde_set_scheme": (ctypes.c_int, [vp, ctypes.c_int32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -256,6 +258,10 @@ def xsde_synchronize(prob, stream: int = 0) -> None:
 
 def xsde_set_kernel_variant(prob, variant: int) -> None:
     _check(load().xsde_set_kernel_variant(prob, variant))
+
+
+def xsde_set_scheme(prob, scheme: int) -> None:
+    _check(load().xsde_set_scheme(prob, scheme))
 
 
 def xsde_set_noise_substeps(prob, substeps: int) -> None:

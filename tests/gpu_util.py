@@ -34,7 +34,7 @@ def make_problem(w, dtype: str):
 
 def gpu_run(w, dtype: str, nsteps: int | None = None, npaths: int | None = None, path0: int = 0,
             sample_every: int = 0, which: int = 15, step_offset: int = 0, psi0=None, problem=None,
-            variant: int = 0, substeps: int = 1):
+            variant: int = 0, substeps: int = 1, scheme: int = 0):
     """Integrate (a path subset of) a workload on the GPU.  Returns
     (psi [npaths, *n] complex128, per_path, per_point) as numpy arrays.
     variant 0 uses the fastest kernels available, 1 the generic ones."""
@@ -46,6 +46,7 @@ def gpu_run(w, dtype: str, nsteps: int | None = None, npaths: int | None = None,
     P = problem if problem is not None else make_problem(w, dtype)
     xsde.xsde_set_kernel_variant(P.prob, variant)
     xsde.xsde_set_noise_substeps(P.prob, substeps)
+    xsde.xsde_set_scheme(P.prob, scheme)
     tdt = torch.complex64 if dtype == "c64" else torch.complex128
     psi = torch.from_numpy(np.ascontiguousarray(src)).to(tdt).cuda().contiguous()
     per_path = per_point = None

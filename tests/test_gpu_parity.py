@@ -356,3 +356,44 @@ def test_noise_substeps_match_oracle(case, S, dtype):
     plain, _, _ = O.rk4ip(w.psi0, grid, O.from_workload(w)[1], w.dt, w.nsteps, step0=3)
     diff = np.max(rel_l2(plain.reshape(w.npaths, -1), ref.reshape(w.npaths, -1), axis=1))
     assert diff > 50 * err, (diff, err)
+
+
+# --------------------------------------------------------------------------- #
+# Semi-implicit midpoint scheme (0D and 1D)                                    #
+# --------------------------------------------------------------------------- #
+
+@pytest.mark.parametrize("case,dtype", [("soliton", "c128"), ("soliton", "c64"), ("tw", "c128"), ("tw", "c64"),
+                                        ("vtable", "c128"), ("kubo", "c128"), ("kubo", "c64"), ("ou", "c128")])
+def test_semi_implicit_matches_oracle(case, dtype):
+    if case == "soliton":
+        w = W.nls_soliton(nsteps=200)
+    elif case == "tw":
+        w = W.truncated_wigner(npaths=5, n=512, nsteps=40)
+    elif case == "vtable":
+        w = W.adjoint_control(n=256, nsteps=30)
+    elif case == "kubo":
+        w = W.kubo_oscillator(npaths=500, nsteps=200)
+    else:
+        w = W.ornstein_uhlenbeck(npaths=500, nsteps=200)
+    so = 0 if case == "vtable" else 2          # the table has one row per step
+    got, _, _ = gpu_run(w, dtype, scheme=1, substeps=2 if case == "tw" else 1, step_offset=so)
+    grid, ops = O.from_workload(w)
+    ops.scheme = 1
+    ops.substeps = 2 if case == "tw" else 1
+    ref, _, _ = O.rk4ip(w.psi0, grid, ops, w.dt, w.nsteps, step0=so)
+    tol = 1e-10 if dtype == "c128" else 1e-4
+    err = np.max(rel_l2(got.reshape(w.npaths, -1), ref.reshape(w.npaths, -1), axis=1))
+    assert err < tol, err
+
+
+def test_semi_implicit_rejected_on_2d():
+    import torch
+    from paper_1204_4255_gb300 import xsde
+    w = W.gpe_2d(n=64, nsteps=1)
+    P = make_problem(w, "c64")
+    xsde.xsde_set_scheme(P.prob, xsde.XSDE_SCHEME_SEMI_IMPLICIT)
+    psi = torch.from_numpy(w.psi0).to(torch.complex64).cuda()
+    with pytest.raises(xsde.XsdeError) as e:
+        P.integrate(psi, w.dt, 1)
+    assert e.value.status == xsde.XSDE_EUNSUPPORTED
+    P.close()
