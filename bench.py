@@ -311,6 +311,47 @@ def ip_vs_explicit(tol: float = 1e-6, t_end: float = 1.0) -> dict:
     return out
 
 
+def strong_convergence(npaths: int = 65536, T: float = 1.0, nfine: int = 1024) -> dict:
+    """Sec. 2.5's strong-convergence test on the Kubo oscillator (dz = i omega z
+    dt + i beta z o dW, complex128): runs with steps dt = T S / nfine and noise
+    substeps S follow one Brownian path per trajectory; mean |z - z_exact| at T,
+    z_exact = z0 exp(i omega T + i beta W(T)) with W(T) summed from the finest
+    normals (xsde_noise_normals), for RK4IP and the semi-implicit scheme."""
+    import math
+    import torch
+    import workloads as W
+    from paper_1204_4255_gb300 import xsde
+    w = W.kubo_oscillator(npaths=npaths)
+    om, beta, z0 = w.extra["omega"], w.extra["beta"], w.extra["z0"]
+    dt_f = T / nfine
+    P = xsde.Problem((), (), (), "c128")
+    P.set_operators(c0=w.c0, c2=w.c2, noise_kind=xsde.XSDE_NOISE_WIENER_REAL, seed=w.seed,
+                    coupling=xsde.XSDE_COUPLE_MULTIPLICATIVE, amplitude=w.noise_amp)
+    buf = torch.empty((npaths, 1), dtype=torch.complex128, device="cuda")
+    Wt = torch.zeros(npaths, dtype=torch.float64, device="cuda")
+    for f in range(nfine):
+        xsde.xsde_noise_normals(P.noise, xsde.XSDE_C128, 1, npaths, 0, f, buf.data_ptr())
+        Wt += buf[:, 0].real
+    exact = z0 * torch.exp(1j * (om * T + beta * math.sqrt(dt_f) * Wt))
+    out = {"workload": f"Kubo oscillator, {npaths} paths, T = {T}, finest step T/{nfine}", "dtype": "c128",
+           "errors": {}}
+    for scheme, name in ((xsde.XSDE_SCHEME_RK4IP, "rk4ip"), (xsde.XSDE_SCHEME_SEMI_IMPLICIT, "semi_implicit")):
+        xsde.xsde_set_scheme(P.prob, scheme)
+        row = {}
+        for S in (64, 32, 16, 8):
+            xsde.xsde_set_noise_substeps(P.prob, S)
+            psi = torch.full((npaths,), z0, dtype=torch.complex128, device="cuda")
+            P.integrate(psi, S * dt_f, nfine // S)
+            torch.cuda.synchronize()
+            row[f"dt=T/{nfine // S}"] = float((psi - exact).abs().mean())
+        errs = list(row.values())
+        row["order"] = math.log2(errs[0] / errs[-1]) / 3.0
+        out["errors"][name] = row
+    P.synchronize()
+    P.close()
+    return out
+
+
 def batched_cost(reps: int = 3) -> dict:
     """Uneven instances advanced together (xsde_batch, autotuned, one CUDA graph
     replay per call): one 3D GPE 128^3, 32 2D GPEs at 256^2 and 32 at 512^2, and
@@ -516,6 +557,7 @@ def run_gpu(args) -> None:
         plain = plain_vs_fused() if not args.no_batch else None
         others = config_figures() if not args.no_batch else None
         ipex = ip_vs_explicit() if not args.no_batch else None
+        strong = strong_convergence() if not args.no_batch else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -527,7 +569,7 @@ def run_gpu(args) -> None:
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "kernels_profiled_step": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]},
             "norm_check": ok, "adjoint": adj, "batched": bat, "plain_vs_fused": plain,
-            "other_workloads": others, "ip_vs_explicit": ipex,
+            "other_workloads": others, "ip_vs_explicit": ipex, "strong_convergence": strong,
         }
         print(json.dumps(line), flush=True)
     prob.close()
