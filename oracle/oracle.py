@@ -52,6 +52,7 @@ class _Ops(ctypes.Structure):
         ("noise_kind", ctypes.c_int32),
         ("substeps", ctypes.c_int32),
         ("scheme", ctypes.c_int32),
+        ("knl", ctypes.c_void_p),
     ]
 
 
@@ -78,6 +79,7 @@ def _load():
         lib.oracle_philox_batch.argtypes = [dp, dp, i64, dp]
         lib.oracle_wiener_normals.argtypes = [ctypes.c_uint64, i64, i64, i64, i64, dp]
         lib.oracle_observables.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Ops), dp, i64, i64, dp]
+        lib.oracle_nonlocal_potential.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Ops), dp, i64, dp]
         lib.oracle_rk4ip.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Ops), dp, i64, i64,
                                      ctypes.c_double, i64, i64, i32, dp, dp]
         lib.oracle_rk4ip.restype = ctypes.c_int
@@ -137,6 +139,7 @@ class Ops:
     seed: int = 0
     substeps: int = 1                 # noise of a step from this many finer steps
     scheme: int = 0                   # 0 RK4IP, 1 semi-implicit midpoint (interaction picture)
+    knl: np.ndarray | None = None     # non-local kernel in Fourier space [npts] complex, FFT order
     _keep: list = field(default_factory=list, repr=False)
 
     def _c(self) -> _Ops:
@@ -148,9 +151,10 @@ class Ops:
         om = list(self.omega) + [0.0] * (3 - len(self.omega))
         for d in range(3):
             o.omega[d] = om[d]
+        self._keep = []
         if self.V is not None:
             V = np.ascontiguousarray(self.V, dtype=np.float64)
-            self._keep = [V]
+            self._keep.append(V)
             o.V = V.ctypes.data
             o.V_nt = V.shape[0] if V.ndim == 2 else 1
         else:
@@ -161,6 +165,12 @@ class Ops:
         o.noise_kind = self.noise_kind
         o.substeps = self.substeps
         o.scheme = self.scheme
+        if self.knl is not None:
+            K = np.ascontiguousarray(self.knl, dtype=np.complex128).reshape(-1)
+            self._keep.append(K)
+            o.knl = K.ctypes.data
+        else:
+            o.knl = None
         return o
 
 
@@ -199,6 +209,16 @@ def observables(psi: np.ndarray, grid: Grid, ops: Ops, step: int = 0) -> np.ndar
     npaths = a.size // grid.npts
     out = np.empty((npaths, 2), dtype=np.float64)
     lib.oracle_observables(ctypes.byref(grid._c()), ctypes.byref(ops._c()), _ptr(a), npaths, step, _ptr(out))
+    return out
+
+
+def nonlocal_potential(psi: np.ndarray, grid: Grid, ops: Ops) -> np.ndarray:
+    """V_nl = iFFT(knl * FFT(|psi|^2)) per path: [npaths, *grid.shape] float64."""
+    lib = _load()
+    a = np.ascontiguousarray(psi, dtype=np.complex128)
+    npaths = a.size // grid.npts
+    out = np.empty((npaths,) + grid.shape, dtype=np.float64)
+    lib.oracle_nonlocal_potential(ctypes.byref(grid._c()), ctypes.byref(ops._c()), _ptr(a), npaths, _ptr(out))
     return out
 
 
@@ -243,7 +263,7 @@ def from_workload(w) -> tuple:
     grid = Grid(tuple(w.n), tuple(w.xmin), tuple(w.xmax))
     ops = Ops(c0=complex(w.c0), c2=complex(w.c2), gnl=w.gnl, pot_kind=w.pot_kind,
               omega=tuple(w.omega), V=w.V, noise_kind=w.noise_kind, noise_amp=w.noise_amp,
-              seed=w.seed)
+              seed=w.seed, knl=getattr(w, "knl", None))
     return grid, ops
 
 

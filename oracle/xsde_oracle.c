@@ -72,6 +72,9 @@ typedef struct {
                               values below 1 mean 1 */
     int32_t scheme;        /* 0: RK4IP; 1: semi-implicit midpoint in the interaction
                               picture (see oracle_rk4ip) */
+    const double *knl;     /* non-local kernel in Fourier space, [npts] complex in FFT
+                              order, or NULL: g gains -i V_nl psi with
+                              V_nl = iFFT(knl * FFT(|psi|^2)) (Example 5's convolution) */
 } oracle_ops;
 
 enum { POT_NONE = 0, POT_HARMONIC = 1, POT_TABLE = 2 };
@@ -308,28 +311,60 @@ typedef struct {
     double *Vrow;   /* potential of this step [npts] */
     cplx *xi_a;     /* additive noise of this step [npaths][npts] (or NULL) */
     double *xi_m;   /* multiplicative noise of this step [npaths][npts] (or NULL) */
+    const oracle_grid *g;   /* the lattice, for the non-local term */
 } step_inputs;
+
+/* V_nl of one path: the circular convolution of |u|^2 with the kernel whose
+   DFT is ops->knl, evaluated as iFFT(knl * FFT(|u|^2)) (Example 5) */
+static void nonlocal_potential(const oracle_grid *g, const oracle_ops *ops, const cplx *u, double *vnl)
+{
+    int64_t npts = grid_points(g);
+    const cplx *knl = (const cplx *)ops->knl;
+    cplx *rho = malloc(sizeof(cplx) * npts);
+    for (int64_t j = 0; j < npts; j++) rho[j] = creal(u[j]) * creal(u[j]) + cimag(u[j]) * cimag(u[j]);
+    fft_nd(rho, g, 1, -1);
+    for (int64_t j = 0; j < npts; j++) rho[j] *= knl[j];
+    fft_nd(rho, g, 1, +1);
+    for (int64_t j = 0; j < npts; j++) vnl[j] = creal(rho[j]);
+    free(rho);
+}
+
+/* the non-local potential of every path, for the tests: u, out [npaths][npts] */
+void oracle_nonlocal_potential(const oracle_grid *g, const oracle_ops *ops, const double *u, int64_t npaths,
+                               double *out)
+{
+    int64_t npts = grid_points(g);
+    for (int64_t p = 0; p < npaths; p++) nonlocal_potential(g, ops, (const cplx *)u + p * npts, out + p * npts);
+}
 
 /* out = N(u) = dt * g(x, t_n, u) for every path */
 static void nonlinear(cplx *out, const cplx *u, const oracle_ops *ops, const step_inputs *in,
                       int64_t npts, int64_t npaths, double dt)
 {
+    double *vnl = NULL;
+    if (ops->knl && in->g) {
+        vnl = malloc(sizeof(double) * npaths * npts);
+        for (int64_t p = 0; p < npaths; p++) nonlocal_potential(in->g, ops, u + p * npts, vnl + p * npts);
+    }
     #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < npaths * npts; i++) {
         int64_t j = i % npts;
         double mod2 = creal(u[i]) * creal(u[i]) + cimag(u[i]) * cimag(u[i]);
         double pot = in->Vrow[j] + ops->gnl * mod2;
+        if (vnl) pot += vnl[i];
         if (in->xi_m) pot += ops->noise_amp * in->xi_m[i];
         cplx gval = -I * pot * u[i];
         if (in->xi_a) gval += ops->noise_amp * in->xi_a[i];
         out[i] = dt * gval;
     }
+    free(vnl);
 }
 
 static void fill_step_inputs(step_inputs *in, const oracle_grid *g, const oracle_ops *ops,
                              int64_t npaths, int64_t path0, int64_t step, double dt)
 {
     int64_t npts = grid_points(g);
+    in->g = g;
     for (int64_t j = 0; j < npts; j++) in->Vrow[j] = potential_at(g, ops, j, step);
     if (ops->noise_kind == NOISE_NONE) return;
     double scale = 1.0 / sqrt(dt * grid_dV(g));   /* white noise per step: var 1/(dt dV) */
@@ -367,15 +402,18 @@ void oracle_observables(const oracle_grid *g, const oracle_ops *ops, const doubl
     int64_t npts = grid_points(g);
     double dV = grid_dV(g);
     cplx *spec = malloc(sizeof(cplx) * npaths * npts);
+    double *vnl = ops->knl ? malloc(sizeof(double) * npts) : NULL;
     memcpy(spec, psi, sizeof(cplx) * npaths * npts);
     fft_nd(spec, g, npaths, -1);
     for (int64_t p = 0; p < npaths; p++) {
         double norm = 0.0, e_lin = 0.0, e_loc = 0.0;
+        if (vnl) nonlocal_potential(g, ops, psi + p * npts, vnl);
         for (int64_t j = 0; j < npts; j++) {
             cplx u = psi[p * npts + j];
             double m2 = creal(u) * creal(u) + cimag(u) * cimag(u);
             norm += m2 * dV;
             e_loc += (potential_at(g, ops, j, step) * m2 + 0.5 * ops->gnl * m2 * m2) * dV;
+            if (vnl) e_loc += 0.5 * vnl[j] * m2 * dV;   /* pair interaction energy */
             cplx s = spec[p * npts + j];
             double s2 = creal(s) * creal(s) + cimag(s) * cimag(s);
             double hk = -ops->c0_im - ops->c2_im * ksq_at(g, j);    /* Re(i L(k)) */
@@ -385,6 +423,7 @@ void oracle_observables(const oracle_grid *g, const oracle_ops *ops, const doubl
         out[2 * p + 1] = e_lin + e_loc;
     }
     free(spec);
+    free(vnl);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -661,7 +700,7 @@ int oracle_adjoint(const oracle_grid *g, const oracle_ops *ops, const double *ps
                    const double *target_in, double dt, int64_t nsteps, double *loss, double *dLdV,
                    double *dLdpsi0)
 {
-    if (ops->noise_kind != NOISE_NONE || nsteps < 1) return -1;
+    if (ops->noise_kind != NOISE_NONE || nsteps < 1 || ops->knl) return -1;
     if (ops->pot_kind == POT_TABLE && ops->V_nt > 1 && nsteps > ops->V_nt) return -1;
     int64_t m = grid_points(g);
     double dV = grid_dV(g);
@@ -708,6 +747,7 @@ int oracle_adjoint(const oracle_grid *g, const oracle_ops *ops, const double *ps
 int oracle_step_tangent(const oracle_grid *g, const oracle_ops *ops, const double *a_in, const double *da_in,
                         const double *dVrow, int64_t step, double dt, double *da_out)
 {
+    if (ops->knl) return -1;
     int64_t m = grid_points(g);
     const cplx *a = (const cplx *)a_in, *da = (const cplx *)da_in;
     cplx *E = malloc(sizeof(cplx) * m);
@@ -745,6 +785,7 @@ int oracle_step_tangent(const oracle_grid *g, const oracle_ops *ops, const doubl
 int oracle_step_adjoint(const oracle_grid *g, const oracle_ops *ops, const double *a_in, const double *lam_in,
                         int64_t step, double dt, double *lam_out, double *gV)
 {
+    if (ops->knl) return -1;
     int64_t m = grid_points(g);
     cplx *E = malloc(sizeof(cplx) * m);
     half_step_factors(g, ops, dt, E);
@@ -920,7 +961,7 @@ int oracle_ark45(const oracle_grid *g, const oracle_ops *ops, double *psi_in, in
                  double tol, double h0, int32_t picture, int64_t max_steps, int64_t *accepted,
                  int64_t *rejected)
 {
-    if (ops->noise_kind != NOISE_NONE || (ops->pot_kind == POT_TABLE && ops->V_nt != 1)) return -1;
+    if (ops->noise_kind != NOISE_NONE || ops->knl || (ops->pot_kind == POT_TABLE && ops->V_nt != 1)) return -1;
     if (!(t_end >= 0.0) || !(h0 > 0.0) || g->ndim < 1) return -1;
     int64_t npts = grid_points(g);
     double *Vrow = malloc((size_t)npts * sizeof(double));

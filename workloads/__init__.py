@@ -14,11 +14,15 @@ The workloads follow the problems of XMDS2 (arXiv:1204.4255):
   * Ornstein-Uhlenbeck and Kubo-oscillator SDEs (Sec. 2.5, Wiener noise in
     Stratonovich form) as zero-dimensional problems;
   * the harmonic ground state of Eq. InitialCondition (Sec. 3.1) driven by a
-    space-time potential, for the adjoint.
+    space-time potential, for the adjoint;
+  * the charged condensate of Example 5 (Sec. 3.5): the trapped GPE with a
+    non-local, softened-Coulomb pair potential given by its Fourier kernel.
 
 Equation family shared by every workload (the reading used throughout):
     d psi/dt = L[psi] + g(x, t, psi),   L(k) = c0 + c2 |k|^2,
-    g = -i (V(x,t) + gnl |psi|^2 + alpha xi_r) psi + sigma xi_a.
+    g = -i (V(x,t) + V_nl[psi] + gnl |psi|^2 + alpha xi_r) psi + sigma xi_a,
+with V_nl the optional circular convolution of |psi|^2 with a pair potential,
+specified by its discrete Fourier kernel (Workload.knl).
 """
 from __future__ import annotations
 
@@ -52,6 +56,7 @@ class Workload:
     psi0: np.ndarray              # [npaths, *n] complex128
     sample_every: int = 0
     extra: dict = field(default_factory=dict)
+    knl: np.ndarray | None = None  # [*n] complex128 Fourier kernel of V_nl (FFT order), or None
 
     @property
     def npaths(self) -> int:
@@ -256,3 +261,40 @@ def ip_scaling(n: int, box: float = 10.0, g: float = 10.0, t_end: float = 2 * ma
     psi0 = (np.pi ** -0.25 * np.exp(-x ** 2 / 2)).astype(np.complex128)[None, :]
     return Workload(f"ip_scaling_{n}", (n,), (-box,), (box,), 0j, -0.5j, g, POT_HARMONIC, (1.0,), None,
                     NOISE_NONE, 0.0, 0, 0.0, 0, psi0, extra={"t_end": t_end})
+
+
+def convolution_kernel(n, xmin, xmax, f) -> np.ndarray:
+    """Fourier kernel khat [*n] (FFT order, complex128) of the lattice sum
+    V(x) = sum_x' f(x - x') rho(x') dV with periodic images: f sampled at the
+    minimum-image offsets (index j < n/2 at j dx, else at (j - n) dx) times dV,
+    transformed by the unnormalised forward DFT."""
+    n = tuple(n)
+    axes = []
+    for d in range(len(n)):
+        dx = (xmax[d] - xmin[d]) / n[d]
+        j = np.arange(n[d])
+        axes.append(np.where(j < n[d] // 2, j, j - n[d]) * dx)
+    off = np.meshgrid(*axes, indexing="ij")
+    dV = float(np.prod([(xmax[d] - xmin[d]) / n[d] for d in range(len(n))]))
+    return np.fft.fftn(f(*off) * dV).astype(np.complex128)
+
+
+def charged_bec(npaths: int = 1024, n: int = 1024, dt: float = 1e-4, nsteps: int = 1000, g: float = 10.0,
+                charge: float = 1.0, soft: float = 0.5, box: float = 20.0, seed: int = 9,
+                sample_every: int = 0) -> Workload:
+    """Example 5 (Sec. 3.5): the dimensionless trapped GPE (V = x^2/2, contact
+    nonlinearity g) of a charged condensate, whose particles also repel through
+    the softened Coulomb pair potential charge / sqrt((x - x')^2 + soft^2) on
+    [-box, box).  Each path starts from the linear ground state of
+    Eq. InitialCondition (unit norm), displaced by x0 uniform in [-1, 1] and
+    scaled in width by w uniform in [0.8, 1.25], so the paths are independent
+    instances of one problem."""
+    x = -box + np.arange(n) * (2 * box / n)
+    rng = np.random.default_rng(seed)
+    x0 = rng.uniform(-1.0, 1.0, npaths)
+    w = rng.uniform(0.8, 1.25, npaths)
+    psi0 = (np.pi ** -0.25 / np.sqrt(w)[:, None]) * np.exp(-((x[None, :] - x0[:, None]) / w[:, None]) ** 2 / 2)
+    knl = convolution_kernel((n,), (-box,), (box,), lambda d: charge / np.sqrt(d * d + soft * soft))
+    return Workload(f"charged_bec_{n}", (n,), (-box,), (box,), 0j, -0.5j, g, POT_HARMONIC, (1.0,), None,
+                    NOISE_NONE, 0.0, seed, dt, nsteps, psi0.astype(np.complex128), sample_every,
+                    extra={"charge": charge, "soft": soft}, knl=knl)
