@@ -278,6 +278,43 @@ def config_figures() -> dict:
     return out
 
 
+def nonlocal_cost(npaths: int = 4096, n: int = 1024, nsteps: int = 200) -> dict:
+    """Example 5's charged condensate (npaths paths x n points, softened Coulomb
+    pair potential, complex64 and complex128): device time of nsteps RK4IP
+    steps with the non-local term and with it removed, at the same launch
+    shape, after a warm-up call each.  The term adds a forward and an inverse
+    transform of one vector to each of the four N evaluations of a step (16
+    single-vector transforms per step instead of 8)."""
+    import torch
+    import workloads as W
+    from paper_1204_4255_gb300 import xsde
+    w = W.charged_bec(npaths=npaths, n=n, nsteps=nsteps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"workload": f"charged condensate {npaths} paths x {n} points, {nsteps} RK4IP steps", "unit": UNIT}
+    for dtype in ("c64", "c128"):
+        P = xsde.Problem(w.n, w.xmin, w.xmax, dtype)
+        P.set_operators(c0=w.c0, c2=w.c2, g=w.gnl, pot_kind=w.pot_kind, omega=(1.0, 0.0, 0.0))
+        src = torch.from_numpy(w.psi0).to(torch.complex64 if dtype == "c64" else torch.complex128).cuda()
+        res = {}
+        for label, khat in (("nonlocal", w.knl), ("local_only", None)):
+            P.set_nonlocal(khat)
+            psi = src.clone()
+            P.integrate(psi, w.dt, 5)
+            torch.cuda.synchronize()
+            e0.record()
+            P.integrate(psi, w.dt, nsteps, step_offset=5)
+            e1.record()
+            torch.cuda.synchronize()
+            P.synchronize()
+            ms = e0.elapsed_time(e1)
+            res[label] = {"value": npaths * n * nsteps / (ms / 1e3), "ms": ms}
+        res["cost_ratio"] = res["local_only"]["value"] / res["nonlocal"]["value"]
+        out[dtype] = res
+        P.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def ip_vs_explicit(tol: float = 1e-6, t_end: float = 1.0) -> dict:
     """Fig. IPvsEX: the adaptive Cash-Karp integrator (xsde_integrate_adaptive,
     complex128) on the trapped GPE (V = x^2/2, g = 10, [-10, 10), ground state of
@@ -558,6 +595,7 @@ def run_gpu(args) -> None:
         others = config_figures() if not args.no_batch else None
         ipex = ip_vs_explicit() if not args.no_batch else None
         strong = strong_convergence() if not args.no_batch else None
+        nonloc = nonlocal_cost() if not args.no_batch else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -570,6 +608,7 @@ def run_gpu(args) -> None:
             "clocks": clk.summary(), "kernels_profiled_step": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]},
             "norm_check": ok, "adjoint": adj, "batched": bat, "plain_vs_fused": plain,
             "other_workloads": others, "ip_vs_explicit": ipex, "strong_convergence": strong,
+            "nonlocal": nonloc,
         }
         print(json.dumps(line), flush=True)
     prob.close()

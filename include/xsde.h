@@ -198,6 +198,25 @@ int xsde_set_scheme(xsde_problem *prob, int32_t scheme);
  * S must stay below 2^32.  Applies to every integrating call of the problem. */
 int xsde_set_noise_substeps(xsde_problem *prob, int32_t substeps);
 
+/* Non-local pair potential (Example 5, Sec. 3.5: an interaction written as a
+ * convolution, evaluated with FFTs).  g gains -i V_nl psi with
+ *   V_nl = Re F^-1[ khat * F[|psi|^2] ],
+ * F the unnormalised forward DFT of the lattice and F^-1 its inverse (with the
+ * 1/npts), so that for khat = dx * DFT of a pair function f sampled at the
+ * periodic offsets, V_nl(x) = sum_x' f(x - x') |psi(x')|^2 dx.  Every
+ * evaluation of N in the step (four per RK4IP step) recomputes V_nl from its
+ * own argument.  khat: HOST pointer to npts complex numbers, interleaved
+ * (re, im) doubles in FFT order (index k at frequency k for k < npts/2, else
+ * k - npts); read during the call and copied to the device in the problem's
+ * precision.  NULL removes the term.  The call synchronises the device first,
+ * so no integration in flight sees a half-written kernel.  Energy moments add
+ * the pair energy 1/2 V_nl |psi|^2 dV.  1D lattices only (XSDE_EUNSUPPORTED
+ * elsewhere); runs with RK4IP on the default launch shape (the kernel variant
+ * is ignored), and xsde_integrate with the semi-implicit scheme,
+ * xsde_integrate_plain, xsde_integrate_adaptive and xsde_adjoint report
+ * XSDE_EUNSUPPORTED while it is set.  Non-finite entries: XSDE_EINVAL. */
+int xsde_set_nonlocal(xsde_problem *prob, const double *khat);
+
 /* Register a sampling group for the following xsde_integrate calls.
  * per_path  (device, FP64): [nsamp][npaths][2] = (norm, energy)  if NORM|ENERGY
  * per_point (device, FP64): [nsamp][npts][2]  = (mean |psi|^2, mean |psi|^4)

@@ -74,6 +74,8 @@ struct xsde_problem {
     int kernel_variant = 0;   // see xsde_set_kernel_variant
     int noise_substeps = 1;   // see xsde_set_noise_substeps
     int scheme = XSDE_SCHEME_RK4IP;   // see xsde_set_scheme
+    void *d_knl = nullptr;    // non-local kernel khat/npts in the problem's precision [npts]
+    bool nonlocal = false;    // see xsde_set_nonlocal
     uint64_t generation = 0;  // bumped by every call that changes what integrate launches
     void *d_adj = nullptr;    // adjoint checkpoints and stage inputs
     size_t adj_bytes = 0;
@@ -517,12 +519,13 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
         q.nsteps = nsteps;
         q.step0 = step0;
         q.Etab = static_cast<const V *>(p->d_E[0]);
-        const int elems = p->scheme == XSDE_SCHEME_RK4IP ? rk4ip_1d_elems(p->kernel_variant) : 8;
+        const int elems = p->scheme == XSDE_SCHEME_RK4IP && !p->nonlocal ? rk4ip_1d_elems(p->kernel_variant) : 8;
         q.tw = static_cast<const tw_t<R> *>(elems == 8 ? p->d_tw[0] : p->d_tw1d[elems == 4 ? 0 : 1]);
         q.lt = lt;
         q.sm = sm;
         q.status = p->d_status;
         q.scheme = p->scheme;
+        q.knl = p->nonlocal ? static_cast<const V *>(p->d_knl) : nullptr;
         XSDE_CUDA(timed(p, 1, s, [&] { return launch_rk4ip_1d<R>(g.n[0], p->kernel_variant, q, s); }), "rk4ip_1d launch");
         return XSDE_OK;
     }
@@ -630,6 +633,8 @@ int check_integrate(const char *who, xsde_problem *p, const xsde_vector *psi, do
         return fail(XSDE_EINVAL, "%s: too many samples", who);
     if (p->scheme != XSDE_SCHEME_RK4IP && p->grid.ndim > 1)
         return fail(XSDE_EUNSUPPORTED, "%s: the semi-implicit scheme runs on 0D and 1D lattices", who);
+    if (p->nonlocal && p->scheme != XSDE_SCHEME_RK4IP)
+        return fail(XSDE_EUNSUPPORTED, "%s: the non-local term runs with RK4IP only", who);
     int dev = -1;
     cudaGetDevice(&dev);
     if (dev != p->device) return fail(XSDE_EINVAL, "%s: current device %d is not the problem's %d", who, dev, p->device);
@@ -779,6 +784,7 @@ void xsde_problem_destroy(xsde_problem *p) {
     }
     cudaFree(p->d_tw1d[0]);
     cudaFree(p->d_tw1d[1]);
+    cudaFree(p->d_knl);
     cudaFree(p->d_scratch);
     cudaFree(p->d_adj);
     cudaFree(p->d_status);
@@ -861,6 +867,40 @@ int xsde_set_scheme(xsde_problem *p, int32_t scheme) {
     return XSDE_OK;
 }
 
+int xsde_set_nonlocal(xsde_problem *p, const double *khat) {
+    if (!p) return fail(XSDE_EINVAL, "xsde_set_nonlocal: problem is NULL");
+    if (!khat) {
+        if (p->nonlocal) ++p->generation;
+        p->nonlocal = false;
+        return XSDE_OK;
+    }
+    if (p->grid.ndim != 1) return fail(XSDE_EUNSUPPORTED, "xsde_set_nonlocal: 1D lattices only");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != p->device)
+        return fail(XSDE_EINVAL, "xsde_set_nonlocal: current device %d is not the problem's %d", dev, p->device);
+    const int64_t n = p->grid.npts;
+    for (int64_t i = 0; i < 2 * n; ++i)
+        if (!std::isfinite(khat[i])) return fail(XSDE_EINVAL, "xsde_set_nonlocal: non-finite kernel entry");
+    const bool f32 = p->dtype == XSDE_C64;
+    const size_t bytes = (size_t)n * (f32 ? sizeof(float2) : sizeof(double2));
+    // the transforms of the kernels are unnormalised: fold the inverse's 1/N in
+    std::vector<double> d(2 * n);
+    std::vector<float> f(f32 ? 2 * n : 0);
+    for (int64_t i = 0; i < 2 * n; ++i) {
+        d[i] = khat[i] / (double)n;
+        if (f32) f[i] = (float)d[i];
+    }
+    cudaError_t e = cudaDeviceSynchronize();   // no integration may still read the old kernel
+    if (e == cudaSuccess && !p->d_knl) e = cudaMalloc(&p->d_knl, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_knl, f32 ? (const void *)f.data() : (const void *)d.data(), bytes,
+                                         cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "xsde_set_nonlocal");
+    p->nonlocal = true;
+    ++p->generation;
+    return XSDE_OK;
+}
+
 int xsde_set_noise_substeps(xsde_problem *p, int32_t substeps) {
     if (!p) return fail(XSDE_EINVAL, "xsde_set_noise_substeps: problem is NULL");
     if (substeps < 1 || substeps > 65536) return fail(XSDE_EINVAL, "xsde_set_noise_substeps: %d", substeps);
@@ -938,6 +978,7 @@ int xsde_adjoint(xsde_problem *p, const xsde_vector *psi0, const xsde_vector *ta
     if (target->npaths != 1) return fail(XSDE_EINVAL, "xsde_adjoint: the target is a single field");
     if (p->noise.kind != XSDE_NOISE_NONE) return fail(XSDE_EUNSUPPORTED, "xsde_adjoint: deterministic problems only");
     if (p->scheme != XSDE_SCHEME_RK4IP) return fail(XSDE_EUNSUPPORTED, "xsde_adjoint: the adjoint of RK4IP only");
+    if (p->nonlocal) return fail(XSDE_EUNSUPPORTED, "xsde_adjoint: the non-local term has no adjoint here");
     if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 1 || ckpt_every < 1)
         return fail(XSDE_EINVAL, "xsde_adjoint: need dt > 0, nsteps >= 1, ckpt_every >= 1");
     if (p->N.pot_kind == XSDE_POT_TABLE && p->N.V_nt > 1 && nsteps > p->N.V_nt)
@@ -1015,6 +1056,7 @@ int xsde_integrate_adaptive(xsde_problem *p, xsde_vector *psi, const xsde_adapti
     if (p->N.pot_kind == XSDE_POT_TABLE && p->N.V_nt != 1)
         return fail(XSDE_EUNSUPPORTED, "xsde_integrate_adaptive: a time-dependent potential table");
     if (p->samp.every > 0) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_adaptive: sampling groups");
+    if (p->nonlocal) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_adaptive: the non-local term");
     if (!(spec->t_end >= 0.0) || !std::isfinite(spec->t_end) || !(spec->h0 > 0.0) || !std::isfinite(spec->h0) ||
         !std::isfinite(spec->tol) || spec->max_steps < 1 || (spec->picture != 0 && spec->picture != 1))
         return fail(XSDE_EINVAL, "xsde_integrate_adaptive: need t_end >= 0, h0 > 0, finite tol, max_steps >= 1");
@@ -1067,6 +1109,7 @@ int xsde_integrate_plain(xsde_problem *p, xsde_vector *psi, double dt, int64_t n
     if (g.ndim == 0) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_plain: 0D problems have no transform");
     if (p->samp.every > 0) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_plain: sampling groups are not supported");
     if (p->scheme != XSDE_SCHEME_RK4IP) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_plain: RK4IP only");
+    if (p->nonlocal) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_plain: the non-local term");
     if (npaths * g.npts > (int64_t)INT32_MAX)
         return fail(XSDE_EUNSUPPORTED, "xsde_integrate_plain: more than 2^31 points per call");
     cudaStream_t s = static_cast<cudaStream_t>(stream);

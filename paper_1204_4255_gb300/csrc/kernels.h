@@ -66,6 +66,8 @@ template <typename R> struct Params1D {
     Sampling sm;
     int *status;
     int scheme = 0;        // 0 RK4IP, 1 semi-implicit midpoint (default launch shape only)
+    const cx<R> *knl = nullptr;   // non-local kernel khat/N in FFT order [N], or none
+                                  // (RK4IP at the default launch shape only)
 };
 // variant v in [0, rk4ip_1d_variants()) sets the launch shape: elements per
 // thread rk4ip_1d_elems(v) (8, or 4 / 2 for variants 4 / 5, whose twiddle

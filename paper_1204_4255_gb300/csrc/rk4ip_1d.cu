@@ -54,12 +54,21 @@ __device__ __forceinline__ void slot_sum3(double (&v)[3], int t, double *scratch
     }
 }
 
+// the step's point term with the non-local potential vn added to V
+template <typename R> __device__ __forceinline__ PointTerm<R> with_vnl(PointTerm<R> pt, R dt, R vn) {
+    pt.dtV += dt * vn;
+    return pt;
+}
+
 // NOISE: the problem has Wiener noise (a template flag, so deterministic runs
 // carry no generator code)
+// NL: g carries the non-local potential V_nl = Re F^-1[khat F|psi|^2] of
+// XMDS2 Example 5 (Sec. 3.5): every evaluation of N transforms the density of
+// its argument forward and back once more (one vector, same exchange buffer)
 // SCHEME 1: the semi-implicit midpoint step in the interaction picture instead
 // of RK4IP (a_I = D a; m <- a_I + N(m)/2 three times from m = a_I;
 // a <- D(2 m - a_I): XMDS2 Sec. 2.5's semi-implicit method with Sec. 2.6)
-template <typename R, int N, int E, int PPC, bool NOISE, int SCHEME = 0>
+template <typename R, int N, int E, int PPC, bool NOISE, int SCHEME = 0, bool NL = false>
 __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R> p) {
     using V = cx<R>;
     constexpr int T = N / E;
@@ -100,12 +109,28 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
     const R gdt = p.lt.gdt;
     const R sixth = R(1) / R(6), third = R(1) / R(3), half = R(0.5);
 
+    // vn = V_nl of the slot's field u (khat is stored divided by N, so both
+    // transforms stay unnormalised)
+    auto nonlocal = [&](const V (&u)[E], R (&vn)[E]) {
+        V y[1][E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) y[0][m] = mk<V>(cabs2(u[m]), R(0));
+        fft<N, E, -1, 1>(y, t, sm1, L, sync, tw);
+#pragma unroll
+        for (int m = 0; m < E; ++m) y[0][m] = cmul(y[0][m], p.knl[t + m * T]);
+        fft<N, E, +1, 1>(y, t, sm1, L, sync, tw);
+#pragma unroll
+        for (int m = 0; m < E; ++m) vn[m] = y[0][m].x;
+    };
+    R vn[E];
+
     for (int64_t n = 0;; ++n) {
         // ---- sampling group (XMDS2 Sec. 2.5 moments over paths) ----------
         if (p.sm.every > 0 && n % p.sm.every == 0) {
             const int64_t s = n / p.sm.every;
             const uint64_t gs = p.step0 + n;
             double acc[3] = {0.0, 0.0, 0.0};   // norm, local energy, kinetic energy
+            if constexpr (NL) nonlocal(x[0], vn);
 #pragma unroll
             for (int m = 0; m < E; ++m) {
                 const int j = t + m * T;
@@ -114,6 +139,7 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
                 const double vv = (double)potential(p.lt, 1, idx, j, gs);
                 acc[0] += m2;
                 acc[1] += vv * m2 + 0.5 * p.sm.g * m2 * m2;
+                if constexpr (NL) acc[1] += 0.5 * (double)vn[m] * m2;   // pair energy, counted once
                 if (active && (p.sm.which & (MOM_MOD2 | MOM_MOD4)) && p.sm.per_point) {
                     double *pp = p.sm.per_point + 2 * (s * N + j);
                     atomicAdd(pp, m2 * p.sm.inv_paths);
@@ -146,6 +172,7 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
         // ---- one RK4IP step ----------------------------------------------
         const uint64_t sg = p.step0 + n;
         PointTerm<R> pt[E];
+        if constexpr (NL) nonlocal(x[0], vn);
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int j = t + m * T;
@@ -157,7 +184,7 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
                 pt[m].dtV = p.lt.dt * v;
                 pt[m].na = mk<V>(R(0), R(0));
             }
-            x[1][m] = apply_N(x[0][m], pt[m], gdt);     // N(a)
+            x[1][m] = apply_N(x[0][m], NL ? with_vnl(pt[m], p.lt.dt, vn[m]) : pt[m], gdt);     // N(a)
         }
         if constexpr (SCHEME == 1) {
             V y[1][E];
@@ -190,13 +217,34 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
         }
         fft<N, E, +1, 2>(x, t, sm2, L, sync, tw);
         // k2, k3 in real space; x[0] <- a_I + k3, x[1] <- a_I + k1/6 + k2/3 + k3/3
+        if constexpr (NL) {
+            // V_nl of each stage input needs the whole line: two passes over m
+            V w[E];
 #pragma unroll
-        for (int m = 0; m < E; ++m) {
-            const V aI = x[0][m], k1 = x[1][m];
-            const V k2 = apply_N(caxpy(aI, half, k1), pt[m], gdt);
-            const V k3 = apply_N(caxpy(aI, half, k2), pt[m], gdt);
-            x[0][m] = cadd(aI, k3);
-            x[1][m] = caxpy(caxpy(caxpy(aI, sixth, k1), third, k2), third, k3);
+            for (int m = 0; m < E; ++m) w[m] = caxpy(x[0][m], half, x[1][m]);
+            nonlocal(w, vn);
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const V k2 = apply_N(w[m], with_vnl(pt[m], p.lt.dt, vn[m]), gdt);
+                x[1][m] = caxpy(caxpy(x[0][m], sixth, x[1][m]), third, k2);
+                w[m] = caxpy(x[0][m], half, k2);
+            }
+            nonlocal(w, vn);
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const V k3 = apply_N(w[m], with_vnl(pt[m], p.lt.dt, vn[m]), gdt);
+                x[1][m] = caxpy(x[1][m], third, k3);
+                x[0][m] = cadd(x[0][m], k3);
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const V aI = x[0][m], k1 = x[1][m];
+                const V k2 = apply_N(caxpy(aI, half, k1), pt[m], gdt);
+                const V k3 = apply_N(caxpy(aI, half, k2), pt[m], gdt);
+                x[0][m] = cadd(aI, k3);
+                x[1][m] = caxpy(caxpy(caxpy(aI, sixth, k1), third, k2), third, k3);
+            }
         }
         fft<N, E, -1, 2>(x, t, sm2, L, sync, tw);
 #pragma unroll
@@ -206,8 +254,10 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
         }
         fft<N, E, +1, 2>(x, t, sm2, L, sync, tw);
         // k4 = N(D(a_I + k3)); a <- D(acc) + k4/6
+        if constexpr (NL) nonlocal(x[0], vn);
 #pragma unroll
-        for (int m = 0; m < E; ++m) x[0][m] = caxpy(x[1][m], sixth, apply_N(x[0][m], pt[m], gdt));
+        for (int m = 0; m < E; ++m)
+            x[0][m] = caxpy(x[1][m], sixth, apply_N(x[0][m], NL ? with_vnl(pt[m], p.lt.dt, vn[m]) : pt[m], gdt));
     }
 
     if (active) {
@@ -216,12 +266,13 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
     }
 }
 
-template <typename R, int N, int E, int PPC, int SCHEME = 0>
+template <typename R, int N, int E, int PPC, int SCHEME = 0, bool NL = false>
 cudaError_t launch_ppc(const Params1D<R> &p, cudaStream_t s) {
     constexpr int T = N / E;
     const size_t smem = (size_t)N * sizeof(tw_t<R>) + (size_t)PPC * 2 * padded_len<N>() * sizeof(cx<R>);
     const bool noise = p.lt.noise != NM_NONE;
-    auto kern = noise ? rk4ip_1d_kernel<R, N, E, PPC, true, SCHEME> : rk4ip_1d_kernel<R, N, E, PPC, false, SCHEME>;
+    auto kern = noise ? rk4ip_1d_kernel<R, N, E, PPC, true, SCHEME, NL>
+                      : rk4ip_1d_kernel<R, N, E, PPC, false, SCHEME, NL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (p.npaths + PPC - 1) / PPC;
@@ -245,6 +296,7 @@ template <typename R, int N> cudaError_t launch_1d_n(int variant, const Params1D
     constexpr int P1 = P0 >= 2 ? P0 / 2 : 1, P2 = P0 >= 4 ? P0 / 4 : 1;
     constexpr int P3 = 2 * P0 * T <= 256 ? 2 * P0 : P0;
     if (p.scheme == 1) return launch_ppc<R, N, 8, P0, 1>(p, s);   // one launch shape for the semi-implicit step
+    if (p.knl) return launch_ppc<R, N, 8, P0, 0, true>(p, s);       // and for the non-local term
     switch (variant) {
         case 1: return launch_ppc<R, N, 8, P1>(p, s);
         case 2: return launch_ppc<R, N, 8, P2>(p, s);

@@ -33,6 +33,7 @@ EXPORTED = (
     "xsde_integrate_static_scratch", "xsde_adjoint", "xsde_kernel_variants", "xsde_autotune",
     "xsde_batch_create", "xsde_batch_integrate", "xsde_batch_destroy", "xsde_integrate_plain",
     "xsde_integrate_adaptive", "xsde_set_noise_substeps", "xsde_set_scheme",
+    "xsde_set_nonlocal",
 )
 XSDE_SCHEME_RK4IP, XSDE_SCHEME_SEMI_IMPLICIT = 0, 1
 XSDE_BATCH_AUTOTUNE = 1
@@ -118,6 +119,7 @@ def load(path: str = LIB_PATH):
         "xsde_integrate_adaptive": (ctypes.c_int, [vp, vp, ctypes.POINTER(xsde_adaptive), vp, vp, vp]),
         "xsde_set_noise_substeps": (ctypes.c_int, [vp, ctypes.c_int32]),
         "xsde_set_scheme": (ctypes.c_int, [vp, ctypes.c_int32]),
+        "xsde_set_nonlocal": (ctypes.c_int, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -264,6 +266,16 @@ def xsde_set_scheme(prob, scheme: int) -> None:
     _check(load().xsde_set_scheme(prob, scheme))
 
 
+def xsde_set_nonlocal(prob, khat) -> None:
+    """khat: None, or npts complex values in FFT order (host; copied)."""
+    if khat is None:
+        _check(load().xsde_set_nonlocal(prob, None))
+        return
+    import numpy as np
+    k = np.ascontiguousarray(np.asarray(khat, dtype=np.complex128).reshape(-1))
+    _check(load().xsde_set_nonlocal(prob, k.ctypes.data))
+
+
 def xsde_set_noise_substeps(prob, substeps: int) -> None:
     _check(load().xsde_set_noise_substeps(prob, substeps))
 
@@ -365,6 +377,11 @@ class Problem:
         N.coupling = coupling
         N.amplitude = amplitude
         xsde_set_operators(self.prob, L, N)
+
+    def set_nonlocal(self, khat=None):
+        """Non-local pair potential from its Fourier kernel khat [npts] (host,
+        FFT order; copied), or None to remove it."""
+        xsde_set_nonlocal(self.prob, khat)
 
     def moments(self, every: int, which: int, per_path=None, per_point=None):
         spec = xsde_sampling(every, which)

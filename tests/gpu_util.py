@@ -29,6 +29,8 @@ def make_problem(w, dtype: str):
     kind, coupling = api_noise(w)
     P.set_operators(c0=w.c0, c2=w.c2, g=w.gnl, pot_kind=w.pot_kind, omega=tuple(w.omega) + (0.0,) * (3 - len(w.omega)),
                     V=V, noise_kind=kind, seed=w.seed, coupling=coupling, amplitude=w.noise_amp)
+    if getattr(w, "knl", None) is not None:
+        P.set_nonlocal(w.knl)
     return P
 
 

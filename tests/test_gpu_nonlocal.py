@@ -1,0 +1,126 @@
+"""GPU parity of the non-local term (Example 5, Sec. 3.5: a pair potential
+applied as an FFT convolution of |psi|^2) through the C-ABI against the FP64
+oracle: every 1D length, both precisions, ragged path counts, noise, a
+time-dependent potential table, the energy moment with the pair term, the
+contact-interaction limit, the full-size ensemble on sampled paths, and the
+calls that reject the term.
+
+Tolerances: complex128 within 1e-10 relative L2 of the oracle, complex64
+within 1e-4 (the fixed-step bar of the other parity tests)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import oracle as O
+from gpu_util import gpu_run, make_problem, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c128": 1e-10, "c64": 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1204_4255_gb300 import build, xsde
+    build.build()
+    xsde.load()
+
+
+@pytest.mark.parametrize("n", [16, 32, 64, 128, 256, 512, 1024, 2048])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_charged_condensate_matches_the_oracle(n, dtype):
+    w = W.charged_bec(npaths=5, n=n, dt=1e-3, nsteps=100)
+    got, pp, pq = gpu_run(w, dtype, sample_every=50)
+    ref, opp, opq = O.run_workload(w, sample_every=50)
+    tol = TOL[dtype]
+    assert np.max(rel_l2(got, ref, axis=1)) < tol
+    assert np.max(np.abs(pp - opp) / np.abs(opp)) < tol     # norm and energy with the pair term
+    assert np.max(np.abs(pq - opq) / np.maximum(np.abs(opq), 1e-3 * np.abs(opq).max())) < tol
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_noisy_ensemble_with_the_pair_potential(dtype):
+    w = W.truncated_wigner(npaths=7, n=256, nsteps=60)
+    w.knl = W.convolution_kernel(w.n, w.xmin, w.xmax, lambda d: 0.05 / np.sqrt(d * d + 1.0))
+    got, pp, _ = gpu_run(w, dtype, sample_every=30, path0=3, npaths=7)
+    ref, opp, _ = O.run_workload(w, sample_every=30, path0=3, npaths=7)
+    assert np.max(rel_l2(got, ref, axis=1)) < TOL[dtype]
+    assert np.max(np.abs(pp - opp) / np.abs(opp)) < TOL[dtype]
+
+
+def test_time_dependent_table_with_the_pair_potential():
+    w = W.adjoint_control(n=256, nsteps=40)
+    w.knl = W.convolution_kernel(w.n, w.xmin, w.xmax, lambda d: 0.5 * np.exp(-d * d))
+    got, _, _ = gpu_run(w, "c128", step_offset=0)
+    ref, _, _ = O.run_workload(w)
+    assert rel_l2(got, ref) < 1e-10
+
+
+def test_constant_kernel_equals_the_contact_interaction():
+    w = W.charged_bec(npaths=4, n=512, dt=1e-3, nsteps=50)
+    c = 0.8
+    w.knl = np.full(w.npts, c, dtype=np.complex128)
+    got, _, _ = gpu_run(w, "c128")
+    w.knl, w.gnl = None, w.gnl + c
+    want, _, _ = gpu_run(w, "c128")
+    assert rel_l2(got, want) < 1e-12
+
+
+def test_removing_the_kernel_restores_the_local_run():
+    import torch
+    w = W.charged_bec(npaths=3, n=256, dt=1e-3, nsteps=30)
+    P = make_problem(w, "c128")
+    P.set_nonlocal(None)
+    got, _, _ = gpu_run(w, "c128", problem=P)
+    P.close()
+    w.knl = None
+    ref, _, _ = O.run_workload(w)
+    assert rel_l2(got, ref) < 1e-10
+
+
+def test_full_size_ensemble_on_sampled_paths():
+    """The 1024-point, 4096-path charged condensate for 200 steps: paths
+    sampled across the ensemble (first, CTA boundaries, last) against the
+    oracle, every path's norm conserved to the method's accuracy."""
+    w = W.charged_bec(npaths=4096, n=1024, dt=1e-4, nsteps=200)
+    got, _, _ = gpu_run(w, "c64")
+    for p in (0, 1, 2047, 4095):
+        ref, _, _ = O.run_workload(w, path0=p, npaths=1)
+        assert rel_l2(got[p], ref[0]) < 1e-4, p
+    dx = w.dx(0)
+    n0 = np.sum(np.abs(w.psi0) ** 2, axis=1) * dx
+    n1 = np.sum(np.abs(got) ** 2, axis=1) * dx
+    assert np.max(np.abs(n1 - n0)) < 1e-4
+
+
+def test_calls_that_reject_the_term():
+    import torch
+    from paper_1204_4255_gb300 import xsde
+    w = W.charged_bec(npaths=2, n=256, dt=1e-3, nsteps=4)
+    P = make_problem(w, "c128")
+    psi = torch.from_numpy(np.ascontiguousarray(w.psi0)).cuda()
+    xsde.xsde_set_scheme(P.prob, xsde.XSDE_SCHEME_SEMI_IMPLICIT)
+    with pytest.raises(xsde.XsdeError) as e:
+        P.integrate(psi, w.dt, 4)
+    assert e.value.status == xsde.XSDE_EUNSUPPORTED
+    xsde.xsde_set_scheme(P.prob, xsde.XSDE_SCHEME_RK4IP)
+    with pytest.raises(xsde.XsdeError) as e:
+        P.integrate_plain(psi, w.dt, 4)
+    assert e.value.status == xsde.XSDE_EUNSUPPORTED
+    with pytest.raises(xsde.XsdeError) as e:
+        P.integrate_adaptive(psi, 0.01, 1e-6, 1e-3)
+    assert e.value.status == xsde.XSDE_EUNSUPPORTED
+    bad = w.knl.copy()
+    bad[3] = np.nan
+    with pytest.raises(xsde.XsdeError) as e:
+        P.set_nonlocal(bad)
+    assert e.value.status == xsde.XSDE_EINVAL
+    P.integrate(psi, w.dt, 4)      # the old kernel is still in place
+    P.synchronize()
+    P.close()
+    w2 = W.gpe_2d(n=64, nsteps=2, npaths=1)
+    P2 = make_problem(w2, "c64")
+    with pytest.raises(xsde.XsdeError) as e:
+        P2.set_nonlocal(np.ones(w2.npts, dtype=np.complex128))
+    assert e.value.status == xsde.XSDE_EUNSUPPORTED
+    P2.close()
