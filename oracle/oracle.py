@@ -35,6 +35,7 @@ class _Grid(ctypes.Structure):
         ("n", ctypes.c_int32 * 3),
         ("xmin", ctypes.c_double * 3),
         ("xmax", ctypes.c_double * 3),
+        ("basis", ctypes.c_int32 * 3),
     ]
 
 
@@ -97,10 +98,13 @@ def _ptr(a: np.ndarray | None):
 
 @dataclass
 class Grid:
-    """Periodic tensor-product lattice; dimension ndim-1 is contiguous."""
+    """Tensor-product lattice; dimension ndim-1 is contiguous.  basis[d]: 0
+    Fourier (periodic), 1 cosine (even about both ends), 2 sine (odd); () = all
+    Fourier."""
     n: tuple = ()
     xmin: tuple = ()
     xmax: tuple = ()
+    basis: tuple = ()
 
     @property
     def ndim(self) -> int:
@@ -121,6 +125,7 @@ class Grid:
             g.n[d] = self.n[d]
             g.xmin[d] = self.xmin[d]
             g.xmax[d] = self.xmax[d]
+            g.basis[d] = self.basis[d] if d < len(self.basis) else 0
         return g
 
 
@@ -260,7 +265,7 @@ def rk4ip(psi: np.ndarray, grid: Grid, ops: Ops, dt: float, nsteps: int, *, path
 
 def from_workload(w) -> tuple:
     """(Grid, Ops) for a workloads.Workload."""
-    grid = Grid(tuple(w.n), tuple(w.xmin), tuple(w.xmax))
+    grid = Grid(tuple(w.n), tuple(w.xmin), tuple(w.xmax), tuple(getattr(w, "basis", ()) or ()))
     ops = Ops(c0=complex(w.c0), c2=complex(w.c2), gnl=w.gnl, pot_kind=w.pot_kind,
               omega=tuple(w.omega), V=w.V, noise_kind=w.noise_kind, noise_amp=w.noise_amp,
               seed=w.seed, knl=getattr(w, "knl", None))

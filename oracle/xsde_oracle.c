@@ -19,10 +19,19 @@
  *     with the picture re-centred every step so that only exp(L dt/2) is needed.
  *   - norm and energy by equal-weight quadrature (Sec. 2.4, Fourier case) and
  *     per-point ensemble moments over paths (Sec. 2.5, multiple paths).
+ *   - the cosine and sine bases of Sec. 2.1 (Example 3 halves a symmetric
+ *     problem's grid with the cosine transform): per dimension, the DCT-II /
+ *     DST-II written out as sums of cosines / sines and their exact inverses.
  *
  * Conventions (the readings where the paper is silent):
  *   - lattice x_j = xmin + j*dx on [xmin, xmax), dx = (xmax-xmin)/N;
  *     k_j = 2*pi/(xmax-xmin) * (j < N/2 ? j : j-N);
+ *   - cosine / sine dimensions: cell-centred points x_j = xmin + (j + 1/2) dx
+ *     (even / odd reflection about both ends), modes cos(k_n (x - xmin)) with
+ *     k_n = pi n/(xmax-xmin), n = 0..N-1, and sin(k_n (x - xmin)) with
+ *     k_n = pi (n+1)/(xmax-xmin); forward transforms unnormalised,
+ *     X_n = sum_j x_j cos(pi n (j+1/2)/N) (sin(pi (n+1) (j+1/2)/N)), and the
+ *     inverses exact (so D = C^-1 exp(L dt/2) C);
  *   - array layout [path][n0][n1][n2], the last grid dimension contiguous;
  *   - L(k) = c0 + c2*|k|^2;
  *     g(x,t,psi) = -i*(V(x,t) + gnl*|psi|^2 + alpha*xi_r)*psi + sigma*xi_a,
@@ -47,13 +56,17 @@
 typedef double complex cplx;
 
 #define TWO_PI 6.283185307179586476925286766559
+#define PI 3.1415926535897932384626433832795
 
 typedef struct {
     int32_t ndim;      /* 0 (a single point: an ordinary SDE) .. 3 */
     int32_t n[3];      /* points per dimension, powers of two */
     double xmin[3];
     double xmax[3];
+    int32_t basis[3];  /* per dimension: 0 Fourier (periodic), 1 cosine (even), 2 sine (odd) */
 } oracle_grid;
+
+enum { BASIS_FOURIER = 0, BASIS_COS = 1, BASIS_SIN = 2 };
 
 typedef struct {
     double c0_re, c0_im;   /* L(k) = c0 + c2 |k|^2 */
@@ -114,14 +127,32 @@ static void unflatten(const oracle_grid *g, int64_t j, int idx[3])
 
 static double coord_x(const oracle_grid *g, int d, int i)
 {
-    return g->xmin[d] + i * grid_dx(g, d);
+    double off = g->basis[d] == BASIS_FOURIER ? 0.0 : 0.5;
+    return g->xmin[d] + (i + off) * grid_dx(g, d);
 }
 
 static double coord_k(const oracle_grid *g, int d, int i)
 {
     int n = g->n[d];
+    if (g->basis[d] == BASIS_COS) return PI * i / (g->xmax[d] - g->xmin[d]);
+    if (g->basis[d] == BASIS_SIN) return PI * (i + 1) / (g->xmax[d] - g->xmin[d]);
     int m = (i < n / 2) ? i : i - n;
     return TWO_PI / (g->xmax[d] - g->xmin[d]) * m;
+}
+
+/* weight of spectral point j in Parseval's sum: sum_x |u|^2 = sum_k w_k |U_k|^2 / npts.
+   Fourier modes weigh 1; a cosine or sine dimension weighs 2, except its mode that
+   has no partner (the constant cosine, the highest sine) */
+static double spectral_weight(const oracle_grid *g, int64_t j)
+{
+    int idx[3];
+    unflatten(g, j, idx);
+    double w = 1.0;
+    for (int d = 0; d < g->ndim; d++) {
+        if (g->basis[d] == BASIS_COS && idx[d] != 0) w *= 2.0;
+        if (g->basis[d] == BASIS_SIN && idx[d] != g->n[d] - 1) w *= 2.0;
+    }
+    return w;
 }
 
 static double ksq_at(const oracle_grid *g, int64_t j)
@@ -172,6 +203,44 @@ static void fft_line(cplx *x, int n, int sign)
     }
 }
 
+/* DCT-II (sign -1) of one line, or its inverse (sign +1), as plain sums */
+static void dct_line(cplx *x, int n, int sign)
+{
+    cplx *y = malloc(sizeof(cplx) * n);
+    for (int a = 0; a < n; a++) {
+        cplx acc = 0.0;
+        if (sign < 0) {           /* X_a = sum_j x_j cos(pi a (j + 1/2) / n) */
+            for (int j = 0; j < n; j++) acc += x[j] * cos(PI * a * (j + 0.5) / n);
+        } else {                  /* x_a = (X_0 + 2 sum_{m>0} X_m cos(pi m (a + 1/2) / n)) / n */
+            acc = x[0];
+            for (int m = 1; m < n; m++) acc += 2.0 * x[m] * cos(PI * m * (a + 0.5) / n);
+            acc /= n;
+        }
+        y[a] = acc;
+    }
+    memcpy(x, y, sizeof(cplx) * n);
+    free(y);
+}
+
+/* DST-II (sign -1) of one line, or its inverse (sign +1), as plain sums */
+static void dst_line(cplx *x, int n, int sign)
+{
+    cplx *y = malloc(sizeof(cplx) * n);
+    for (int a = 0; a < n; a++) {
+        cplx acc = 0.0;
+        if (sign < 0) {           /* X_a = sum_j x_j sin(pi (a + 1) (j + 1/2) / n) */
+            for (int j = 0; j < n; j++) acc += x[j] * sin(PI * (a + 1) * (j + 0.5) / n);
+        } else {                  /* x_a = (sum_{m<n-1} 2 X_m sin(..) + X_{n-1} sin(..)) / n */
+            for (int m = 0; m < n; m++)
+                acc += (m == n - 1 ? 1.0 : 2.0) * x[m] * sin(PI * (m + 1) * (a + 0.5) / n);
+            acc /= n;
+        }
+        y[a] = acc;
+    }
+    memcpy(x, y, sizeof(cplx) * n);
+    free(y);
+}
+
 /* Transform every line of every dimension of nbatch stacked arrays. */
 static void fft_nd(cplx *data, const oracle_grid *g, int64_t nbatch, int sign)
 {
@@ -190,7 +259,9 @@ static void fft_nd(cplx *data, const oracle_grid *g, int64_t nbatch, int sign)
             cplx *base = data + b * npts + o * stride * n + s;
             cplx *tmp = malloc(sizeof(cplx) * n);
             for (int i = 0; i < n; i++) tmp[i] = base[i * stride];
-            fft_line(tmp, n, sign);
+            if (g->basis[d] == BASIS_COS) dct_line(tmp, n, sign);
+            else if (g->basis[d] == BASIS_SIN) dst_line(tmp, n, sign);
+            else fft_line(tmp, n, sign);
             for (int i = 0; i < n; i++) base[i * stride] = tmp[i];
             free(tmp);
         }
@@ -417,7 +488,7 @@ void oracle_observables(const oracle_grid *g, const oracle_ops *ops, const doubl
             cplx s = spec[p * npts + j];
             double s2 = creal(s) * creal(s) + cimag(s) * cimag(s);
             double hk = -ops->c0_im - ops->c2_im * ksq_at(g, j);    /* Re(i L(k)) */
-            e_lin += hk * s2 * dV / npts;
+            e_lin += hk * spectral_weight(g, j) * s2 * dV / npts;
         }
         out[2 * p] = norm;
         out[2 * p + 1] = e_lin + e_loc;
@@ -458,8 +529,11 @@ int oracle_rk4ip(const oracle_grid *g, const oracle_ops *ops, double *psi_in, in
                  double *per_path, double *per_point)
 {
     if (g->ndim < 0 || g->ndim > 3 || npaths < 1 || nsteps < 0) return -1;
-    for (int d = 0; d < g->ndim; d++)
+    for (int d = 0; d < g->ndim; d++) {
         if (g->n[d] < 1 || (g->n[d] & (g->n[d] - 1))) return -1;
+        if (g->basis[d] < BASIS_FOURIER || g->basis[d] > BASIS_SIN) return -1;
+        if (ops->knl && g->basis[d] != BASIS_FOURIER) return -1;   /* a circular convolution */
+    }
     if (ops->pot_kind == POT_TABLE && ops->V_nt > 1 && step0 + nsteps > ops->V_nt) return -1;
 
     cplx *a = (cplx *)psi_in;

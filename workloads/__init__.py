@@ -16,7 +16,9 @@ The workloads follow the problems of XMDS2 (arXiv:1204.4255):
   * the harmonic ground state of Eq. InitialCondition (Sec. 3.1) driven by a
     space-time potential, for the adjoint;
   * the charged condensate of Example 5 (Sec. 3.5): the trapped GPE with a
-    non-local, softened-Coulomb pair potential given by its Fourier kernel.
+    non-local, softened-Coulomb pair potential given by its Fourier kernel;
+  * the reflection-symmetric trapped GPE of Example 3 (Sec. 3.3) on half the
+    domain with the cosine (or, for odd states, sine) basis, in 1D and in 2D.
 
 Equation family shared by every workload (the reading used throughout):
     d psi/dt = L[psi] + g(x, t, psi),   L(k) = c0 + c2 |k|^2,
@@ -57,6 +59,12 @@ class Workload:
     sample_every: int = 0
     extra: dict = field(default_factory=dict)
     knl: np.ndarray | None = None  # [*n] complex128 Fourier kernel of V_nl (FFT order), or None
+    basis: tuple = ()              # per dimension 0 Fourier, 1 cosine, 2 sine; () = all Fourier
+
+    def coords_of(self, d: int) -> np.ndarray:
+        """Lattice points of dimension d (cell-centred for cosine / sine dimensions)."""
+        off = 0.5 if d < len(self.basis) and self.basis[d] else 0.0
+        return self.xmin[d] + (np.arange(self.n[d]) + off) * self.dx(d)
 
     @property
     def npaths(self) -> int:
@@ -298,3 +306,46 @@ def charged_bec(npaths: int = 1024, n: int = 1024, dt: float = 1e-4, nsteps: int
     return Workload(f"charged_bec_{n}", (n,), (-box,), (box,), 0j, -0.5j, g, POT_HARMONIC, (1.0,), None,
                     NOISE_NONE, 0.0, seed, dt, nsteps, psi0.astype(np.complex128), sample_every,
                     extra={"charge": charge, "soft": soft}, knl=knl)
+
+
+BASIS_FOURIER, BASIS_COS, BASIS_SIN = 0, 1, 2
+
+
+def symmetric_gpe(npaths: int = 4096, n: int = 256, L: float = 7.0, g: float = 10.0, dt: float = 1e-3,
+                  nsteps: int = 1000, odd: bool = False, seed: int = 11, sample_every: int = 0) -> Workload:
+    """Example 3 (Sec. 3.3) in one dimension: the dimensionless trapped GPE
+    (Eq. NonlinearSchrodingerEquationDimensionless, V = x^2/2, nonlinearity g)
+    is symmetric about x = 0, so only (0, L) is simulated, on n cell-centred
+    points with the cosine basis (even states).  Path p starts from the ground
+    state of Eq. InitialCondition with N_p atoms, N_p uniform in [0.5, 2]
+    (odd=True: the sine basis and the first odd trap state
+    sqrt(2 N_p) pi^-1/4 x exp(-x^2/2))."""
+    dx = L / n
+    x = (np.arange(n) + 0.5) * dx
+    rng = np.random.default_rng(seed)
+    atoms = rng.uniform(0.5, 2.0, npaths)
+    shape = math.sqrt(2.0) * x * np.exp(-x ** 2 / 2) if odd else np.exp(-x ** 2 / 2)
+    psi0 = np.sqrt(atoms)[:, None] * np.pi ** -0.25 * shape[None, :]
+    basis = (BASIS_SIN if odd else BASIS_COS,)
+    return Workload(f"symmetric_gpe_{'sine' if odd else 'cosine'}_{n}", (n,), (0.0,), (L,), 0j, -0.5j, g,
+                    POT_HARMONIC, (1.0,), None, NOISE_NONE, 0.0, seed, dt, nsteps, psi0.astype(np.complex128),
+                    sample_every, basis=basis)
+
+
+def symmetric_gpe_2d(npaths: int = 64, n0: int = 256, n1: int = 512, L: float = 7.0, g: float = 20.0,
+                     dt: float = 1e-4, nsteps: int = 1000, seed: int = 12) -> Workload:
+    """Example 3 (Sec. 3.3) with Example 2's second dimension: the 2D trapped
+    GPE on x in (0, L) with the cosine basis (n0 cell-centred points) and y in
+    [-L, L) Fourier (n1 points).  Path p: the 2D harmonic ground state with
+    N_p atoms (uniform in [0.5, 2]), displaced in y by U[-1, 1] so the paths
+    are independent instances."""
+    x = (np.arange(n0) + 0.5) * (L / n0)
+    y = -L + np.arange(n1) * (2 * L / n1)
+    rng = np.random.default_rng(seed)
+    atoms = rng.uniform(0.5, 2.0, npaths)
+    y0 = rng.uniform(-1.0, 1.0, npaths)
+    psi0 = np.empty((npaths, n0, n1), dtype=np.complex128)
+    for p in range(npaths):
+        psi0[p] = math.sqrt(atoms[p]) / math.sqrt(math.pi) * np.exp(-x[:, None] ** 2 / 2 - (y[None, :] - y0[p]) ** 2 / 2)
+    return Workload(f"symmetric_gpe_2d_{n0}x{n1}", (n0, n1), (0.0, -L), (L, L), 0j, -0.5j, g, POT_HARMONIC,
+                    (1.0, 1.0), None, NOISE_NONE, 0.0, seed, dt, nsteps, psi0, basis=(BASIS_COS, BASIS_FOURIER))
