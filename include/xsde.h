@@ -132,6 +132,28 @@ void xsde_grid_destroy(xsde_grid *grid);
 /* number of lattice points (product of npts; 1 for ndim = 0) */
 int64_t xsde_grid_points(const xsde_grid *grid);
 
+/* Spectral basis per dimension (Sec. 2.1; Example 3, Sec. 3.3, halves a
+ * reflection-symmetric problem's grid with the cosine basis).  A cosine (sine)
+ * dimension of n points on (xmin, xmax) is cell-centred, x_j = xmin + (j+1/2)dx,
+ * even (odd) about both ends, with modes cos / sin(k (x - xmin)) at
+ * k = pi m/(xmax - xmin), m = 0..n-1 (cosine) or 1..n (sine): the DCT-II /
+ * DST-II lattice.  The library transforms such a dimension as the even (odd)
+ * extension of its n points, a 2n-point Fourier line over the doubled domain,
+ * whose modes are exactly these; fields store the n points only.  basis: ndim
+ * entries of XSDE_BASIS_*, read during the call; the default is all Fourier.
+ * Set it before creating problems, fields or noise from the grid (they copy
+ * it).  Runs on 1D lattices and on dimension 0 of 2D lattices (dimension 1
+ * Fourier), at most 1024 points along the cosine / sine dimension; other
+ * lattices, xsde_integrate_plain, xsde_integrate_adaptive, xsde_adjoint,
+ * xsde_integrate_static_scratch and xsde_set_nonlocal report XSDE_EUNSUPPORTED
+ * for such a problem.  Kernel variants are ignored (one launch shape; 2D keeps
+ * the generic column pass).  Energy moments use the basis's Parseval weights.
+ * Errors: XSDE_EINVAL for a NULL grid or basis, or an unknown value. */
+#define XSDE_BASIS_FOURIER 0
+#define XSDE_BASIS_COS 1
+#define XSDE_BASIS_SIN 2
+int xsde_grid_set_basis(xsde_grid *grid, const int32_t *basis);
+
 /* ---- fields (Sec. 3.1 "vectors") ---------------------------------------- */
 
 /* Allocate a device field of npaths x npts complex values (ncomp must be 1).

@@ -37,6 +37,7 @@ struct xsde_grid {
     int n[3];
     double xmin[3], xmax[3];
     int64_t npts;
+    int basis[3];   // XSDE_BASIS_* per dimension (xsde_grid_set_basis)
 };
 
 struct xsde_vector {
@@ -172,9 +173,19 @@ double grid_dV(const xsde_grid &g) {
     for (int d = 0; d < g.ndim; ++d) v *= grid_dx(g, d);
     return v;
 }
+// Length of the transform along dimension d: a cosine / sine dimension of n
+// stored points is transformed as its even / odd extension of 2n points over
+// the doubled domain, whose Fourier modes are the cosines / sines pi m/L.
+int tlen(const xsde_grid &g, int d) { return g.basis[d] != XSDE_BASIS_FOURIER ? 2 * g.n[d] : g.n[d]; }
+bool any_basis(const xsde_grid &g) {
+    for (int d = 0; d < g.ndim; ++d)
+        if (g.basis[d] != XSDE_BASIS_FOURIER) return true;
+    return false;
+}
 double kval(const xsde_grid &g, int d, int i) {
-    const int n = g.n[d];
-    return 2.0 * M_PI / (g.xmax[d] - g.xmin[d]) * (i < n / 2 ? i : i - n);
+    const int n = tlen(g, d);
+    const double len = (g.xmax[d] - g.xmin[d]) * (n == g.n[d] ? 1.0 : 2.0);
+    return 2.0 * M_PI / len * (i < n / 2 ? i : i - n);
 }
 
 // value -> hi (nearest) and lo (nearest to the remainder); FP64 keeps lo = 0
@@ -240,22 +251,24 @@ template <typename V> int ensure_tables(xsde_problem *p, double dt, cudaStream_t
     const std::complex<double> c0(p->L.c0_re, p->L.c0_im), c2(p->L.c2_re, p->L.c2_im);
     int rc;
     for (int d = 0; d < g.ndim; ++d)
-        if ((rc = upload_twiddles<decltype(V::x)>(g.n[d], &p->d_tw[d], s)) != XSDE_OK) return rc;
+        if ((rc = upload_twiddles<decltype(V::x)>(tlen(g, d), &p->d_tw[d], s)) != XSDE_OK) return rc;
     if (g.ndim == 1) {
+        const int n = tlen(g, 0);
         // the radix-4 and radix-2 plans of the 4- and 2-element launch shapes
-        if ((rc = upload_twiddles<decltype(V::x), 4>(g.n[0], &p->d_tw1d[0], s)) != XSDE_OK) return rc;
-        if ((rc = upload_twiddles<decltype(V::x), 2>(g.n[0], &p->d_tw1d[1], s)) != XSDE_OK) return rc;
-        std::vector<std::complex<double>> e(g.n[0]);
-        for (int i = 0; i < g.n[0]; ++i) {
+        if ((rc = upload_twiddles<decltype(V::x), 4>(n, &p->d_tw1d[0], s)) != XSDE_OK) return rc;
+        if ((rc = upload_twiddles<decltype(V::x), 2>(n, &p->d_tw1d[1], s)) != XSDE_OK) return rc;
+        std::vector<std::complex<double>> e(n);
+        for (int i = 0; i < n; ++i) {
             const double k = kval(g, 0, i);
-            e[i] = std::exp((c0 + c2 * (k * k)) * (0.5 * dt)) / (double)g.n[0];
+            e[i] = std::exp((c0 + c2 * (k * k)) * (0.5 * dt)) / (double)n;
         }
         if ((rc = upload<V>(e, &p->d_E[0], s)) != XSDE_OK) return rc;
     } else if (g.ndim == 2) {
-        std::vector<std::complex<double>> e0(g.n[0]), e1(g.n[1]);
-        for (int i = 0; i < g.n[0]; ++i) {
+        const int n0 = tlen(g, 0);
+        std::vector<std::complex<double>> e0(n0), e1(g.n[1]);
+        for (int i = 0; i < n0; ++i) {
             const double k = kval(g, 0, i);
-            e0[i] = std::exp((c0 + c2 * (k * k)) * (0.5 * dt)) / ((double)g.n[0] * g.n[1]);
+            e0[i] = std::exp((c0 + c2 * (k * k)) * (0.5 * dt)) / ((double)n0 * g.n[1]);
         }
         for (int i = 0; i < g.n[1]; ++i) {
             const double k = kval(g, 1, i);
@@ -289,7 +302,8 @@ void fill_terms(const xsde_problem *p, double dt, int64_t npaths, int64_t path_o
     lt.pot = p->N.pot_kind;
     for (int d = 0; d < 3; ++d) {
         lt.hw2[d] = (R)(d < g.ndim ? 0.5 * p->N.omega[d] * p->N.omega[d] : 0.0);
-        lt.xmin[d] = (R)(d < g.ndim ? g.xmin[d] : 0.0);
+        // cosine / sine lattices are cell-centred: x_j = xmin + (j + 1/2) dx
+        lt.xmin[d] = (R)(d < g.ndim ? g.xmin[d] + (g.basis[d] ? 0.5 * grid_dx(g, d) : 0.0) : 0.0);
         lt.dx[d] = (R)(d < g.ndim ? grid_dx(g, d) : 0.0);
     }
     lt.V = static_cast<const R *>(p->N.V);
@@ -322,7 +336,8 @@ void fill_terms(const xsde_problem *p, double dt, int64_t npaths, int64_t path_o
     sm.inv_paths = 1.0 / (double)npaths;
     sm.h0 = -p->L.c0_im;
     sm.h2 = -p->L.c2_im;
-    for (int d = 0; d < 3; ++d) sm.kscale[d] = d < g.ndim ? 2.0 * M_PI / (g.xmax[d] - g.xmin[d]) : 0.0;
+    for (int d = 0; d < 3; ++d)
+        sm.kscale[d] = d < g.ndim ? (g.basis[d] ? M_PI : 2.0 * M_PI) / (g.xmax[d] - g.xmin[d]) : 0.0;
     sm.g = p->N.g;
 }
 
@@ -519,14 +534,17 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
         q.nsteps = nsteps;
         q.step0 = step0;
         q.Etab = static_cast<const V *>(p->d_E[0]);
-        const int elems = p->scheme == XSDE_SCHEME_RK4IP && !p->nonlocal ? rk4ip_1d_elems(p->kernel_variant) : 8;
+        const bool shape0 = p->scheme != XSDE_SCHEME_RK4IP || p->nonlocal || g.basis[0] != XSDE_BASIS_FOURIER;
+        const int elems = shape0 ? 8 : rk4ip_1d_elems(p->kernel_variant);
         q.tw = static_cast<const tw_t<R> *>(elems == 8 ? p->d_tw[0] : p->d_tw1d[elems == 4 ? 0 : 1]);
         q.lt = lt;
         q.sm = sm;
         q.status = p->d_status;
         q.scheme = p->scheme;
         q.knl = p->nonlocal ? static_cast<const V *>(p->d_knl) : nullptr;
-        XSDE_CUDA(timed(p, 1, s, [&] { return launch_rk4ip_1d<R>(g.n[0], p->kernel_variant, q, s); }), "rk4ip_1d launch");
+        q.mirror = g.basis[0];
+        XSDE_CUDA(timed(p, 1, s, [&] { return launch_rk4ip_1d<R>(tlen(g, 0), p->kernel_variant, q, s); }),
+                  "rk4ip_1d launch");
         return XSDE_OK;
     }
     if (g.ndim == 3) return run_3d<R>(p, psi, nsteps, npaths, step0, lt, sm, s);
@@ -546,14 +564,16 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
     q.lt = lt;
     q.sm = sm;
     q.status = p->d_status;
+    q.mirror0 = g.basis[0];
     const int S = sm.every;
     // complex64 lattices the persistent TMA passes cover take the hot modes there
+    // (a cosine / sine dimension 0 keeps the generic column pass)
     bool tma_row = false, tma_col = false;
     CUtensorMap mapA, mapB;
     if constexpr (std::is_same<R, float>::value) {
         if (p->kernel_variant != 1 && (uintptr_t)psi % 16 == 0 && (uintptr_t)p->d_scratch % 16 == 0) {
             tma_row = tma_rows_ok(g.n[1], npaths * g.n[0]);
-            tma_col = p->kernel_variant == 0 && tma_col_supported(g.n[0]) && g.n[1] % COL_TMA_C == 0 &&
+            tma_col = p->kernel_variant == 0 && !q.mirror0 && tma_col_supported(g.n[0]) && g.n[1] % COL_TMA_C == 0 &&
                       encode_field_map(&mapA, psi, npaths * g.n[0], g.n[1], g.n[0]) &&
                       encode_field_map(&mapB, p->d_scratch, npaths * g.n[0], g.n[1], g.n[0]);
         }
@@ -602,7 +622,8 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
 bool same_lattice(const xsde_grid &a, const xsde_grid &b) {
     if (a.ndim != b.ndim) return false;
     for (int d = 0; d < a.ndim; ++d)
-        if (a.n[d] != b.n[d] || a.xmin[d] != b.xmin[d] || a.xmax[d] != b.xmax[d]) return false;
+        if (a.n[d] != b.n[d] || a.xmin[d] != b.xmin[d] || a.xmax[d] != b.xmax[d] || a.basis[d] != b.basis[d])
+            return false;
     return true;
 }
 
@@ -635,6 +656,16 @@ int check_integrate(const char *who, xsde_problem *p, const xsde_vector *psi, do
         return fail(XSDE_EUNSUPPORTED, "%s: the semi-implicit scheme runs on 0D and 1D lattices", who);
     if (p->nonlocal && p->scheme != XSDE_SCHEME_RK4IP)
         return fail(XSDE_EUNSUPPORTED, "%s: the non-local term runs with RK4IP only", who);
+    if (any_basis(p->grid)) {
+        const xsde_grid &g = p->grid;
+        if (g.ndim == 3) return fail(XSDE_EUNSUPPORTED, "%s: cosine / sine bases on 1D and 2D lattices only", who);
+        if (g.ndim == 2 && g.basis[1] != XSDE_BASIS_FOURIER)
+            return fail(XSDE_EUNSUPPORTED, "%s: on a 2D lattice only dimension 0 may be cosine / sine", who);
+        if (g.n[0] > 1024)
+            return fail(XSDE_EUNSUPPORTED, "%s: a cosine / sine dimension has at most 1024 points", who);
+        if (g.ndim == 2 && p->scheme != XSDE_SCHEME_RK4IP)
+            return fail(XSDE_EUNSUPPORTED, "%s: the semi-implicit scheme runs on 0D and 1D lattices", who);
+    }
     int dev = -1;
     cudaGetDevice(&dev);
     if (dev != p->device) return fail(XSDE_EINVAL, "%s: current device %d is not the problem's %d", who, dev, p->device);
@@ -689,6 +720,16 @@ int xsde_grid_create(int ndim, const int32_t *npts, const double *xmin, const do
 }
 
 void xsde_grid_destroy(xsde_grid *grid) { delete grid; }
+
+int xsde_grid_set_basis(xsde_grid *grid, const int32_t *basis) {
+    if (!grid) return fail(XSDE_EINVAL, "xsde_grid_set_basis: grid is NULL");
+    if (grid->ndim > 0 && !basis) return fail(XSDE_EINVAL, "xsde_grid_set_basis: basis is NULL");
+    for (int d = 0; d < grid->ndim; ++d)
+        if (basis[d] < XSDE_BASIS_FOURIER || basis[d] > XSDE_BASIS_SIN)
+            return fail(XSDE_EINVAL, "xsde_grid_set_basis: basis[%d] = %d", d, basis[d]);
+    for (int d = 0; d < grid->ndim; ++d) grid->basis[d] = basis[d];
+    return XSDE_OK;
+}
 
 int64_t xsde_grid_points(const xsde_grid *grid) { return grid ? grid->npts : 0; }
 
@@ -874,7 +915,8 @@ int xsde_set_nonlocal(xsde_problem *p, const double *khat) {
         p->nonlocal = false;
         return XSDE_OK;
     }
-    if (p->grid.ndim != 1) return fail(XSDE_EUNSUPPORTED, "xsde_set_nonlocal: 1D lattices only");
+    if (p->grid.ndim != 1 || any_basis(p->grid))
+        return fail(XSDE_EUNSUPPORTED, "xsde_set_nonlocal: 1D Fourier lattices only (a circular convolution)");
     int dev = -1;
     cudaGetDevice(&dev);
     if (dev != p->device)
@@ -979,6 +1021,7 @@ int xsde_adjoint(xsde_problem *p, const xsde_vector *psi0, const xsde_vector *ta
     if (p->noise.kind != XSDE_NOISE_NONE) return fail(XSDE_EUNSUPPORTED, "xsde_adjoint: deterministic problems only");
     if (p->scheme != XSDE_SCHEME_RK4IP) return fail(XSDE_EUNSUPPORTED, "xsde_adjoint: the adjoint of RK4IP only");
     if (p->nonlocal) return fail(XSDE_EUNSUPPORTED, "xsde_adjoint: the non-local term has no adjoint here");
+    if (any_basis(g)) return fail(XSDE_EUNSUPPORTED, "xsde_adjoint: Fourier lattices only");
     if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 1 || ckpt_every < 1)
         return fail(XSDE_EINVAL, "xsde_adjoint: need dt > 0, nsteps >= 1, ckpt_every >= 1");
     if (p->N.pot_kind == XSDE_POT_TABLE && p->N.V_nt > 1 && nsteps > p->N.V_nt)
@@ -1057,6 +1100,7 @@ int xsde_integrate_adaptive(xsde_problem *p, xsde_vector *psi, const xsde_adapti
         return fail(XSDE_EUNSUPPORTED, "xsde_integrate_adaptive: a time-dependent potential table");
     if (p->samp.every > 0) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_adaptive: sampling groups");
     if (p->nonlocal) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_adaptive: the non-local term");
+    if (any_basis(p->grid)) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_adaptive: Fourier lattices only");
     if (!(spec->t_end >= 0.0) || !std::isfinite(spec->t_end) || !(spec->h0 > 0.0) || !std::isfinite(spec->h0) ||
         !std::isfinite(spec->tol) || spec->max_steps < 1 || (spec->picture != 0 && spec->picture != 1))
         return fail(XSDE_EINVAL, "xsde_integrate_adaptive: need t_end >= 0, h0 > 0, finite tol, max_steps >= 1");
@@ -1110,6 +1154,7 @@ int xsde_integrate_plain(xsde_problem *p, xsde_vector *psi, double dt, int64_t n
     if (p->samp.every > 0) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_plain: sampling groups are not supported");
     if (p->scheme != XSDE_SCHEME_RK4IP) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_plain: RK4IP only");
     if (p->nonlocal) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_plain: the non-local term");
+    if (any_basis(p->grid)) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_plain: Fourier lattices only");
     if (npaths * g.npts > (int64_t)INT32_MAX)
         return fail(XSDE_EUNSUPPORTED, "xsde_integrate_plain: more than 2^31 points per call");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1707,6 +1752,7 @@ extern "C" int xsde_integrate_static_scratch(xsde_problem *p, xsde_vector *psi, 
     if (!p->have_ops) return fail(XSDE_EINVAL, "xsde_integrate_static_scratch: operators not set");
     if (p->grid.ndim != 2)
         return fail(XSDE_EUNSUPPORTED, "xsde_integrate_static_scratch: only 2D lattices use a scratch field");
+    if (any_basis(p->grid)) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_static_scratch: Fourier lattices only");
     if (psi->dtype != p->dtype) return fail(XSDE_EINVAL, "xsde_integrate_static_scratch: field dtype differs");
     if (!same_lattice(psi->grid, p->grid)) return fail(XSDE_EINVAL, "xsde_integrate_static_scratch: lattice differs");
     if (npaths != psi->npaths) return fail(XSDE_EINVAL, "xsde_integrate_static_scratch: npaths differs from the field");

@@ -88,10 +88,16 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
     for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = p.tw[i];
     __syncthreads();
 
+    // Cosine / sine lattices (XMDS2 Sec. 2.1) run as the even / odd extension
+    // of their NS = N/2 stored points over the reflection at the lower end: the
+    // image point j >= NS is stored point N-1-j, negated for the sine basis.
+    // The extension's transforms diagonalise exactly the cosine / sine modes.
+    const int mir = p.mirror;
+    const int NS = mir ? N / 2 : N;
     const int64_t lp = (int64_t)blockIdx.x * PPC + slot;
     const bool active = lp < p.npaths;
     const uint32_t gp = (uint32_t)(p.lt.path_offset + lp);
-    V *psi = p.psi + lp * N;
+    V *psi = p.psi + lp * NS;
     const bool vtime = p.lt.pot == PM_TABLE && p.lt.V_nt > 1;
 
     V x[2][E];
@@ -100,11 +106,13 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int j = t + m * T;
-        x[0][m] = active ? psi[j] : mk<V>(R(0), R(0));
+        const int pj = mir && j >= NS ? N - 1 - j : j;
+        x[0][m] = active ? psi[pj] : mk<V>(R(0), R(0));
+        if (mir == 2 && j >= NS) x[0][m] = mk<V>(-x[0][m].x, -x[0][m].y);
         Ek[m] = p.Etab[j];
         El[m] = p.Etab[N + j];
-        const int idx[3] = {j, 0, 0};
-        Vs[m] = vtime ? R(0) : potential(p.lt, 1, idx, j, 0);
+        const int idx[3] = {pj, 0, 0};
+        Vs[m] = vtime ? R(0) : potential(p.lt, 1, idx, pj, 0);
     }
     const R gdt = p.lt.gdt;
     const R sixth = R(1) / R(6), third = R(1) / R(3), half = R(0.5);
@@ -134,6 +142,7 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
 #pragma unroll
             for (int m = 0; m < E; ++m) {
                 const int j = t + m * T;
+                if (j >= NS) continue;   // image points of a cosine / sine lattice
                 const int idx[3] = {j, 0, 0};
                 const double m2 = (double)cabs2(x[0][m]);
                 const double vv = (double)potential(p.lt, 1, idx, j, gs);
@@ -141,7 +150,7 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
                 acc[1] += vv * m2 + 0.5 * p.sm.g * m2 * m2;
                 if constexpr (NL) acc[1] += 0.5 * (double)vn[m] * m2;   // pair energy, counted once
                 if (active && (p.sm.which & (MOM_MOD2 | MOM_MOD4)) && p.sm.per_point) {
-                    double *pp = p.sm.per_point + 2 * (s * N + j);
+                    double *pp = p.sm.per_point + 2 * (s * NS + j);
                     atomicAdd(pp, m2 * p.sm.inv_paths);
                     atomicAdd(pp + 1, m2 * m2 * p.sm.inv_paths);
                 }
@@ -156,6 +165,7 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
                 const double k = p.sm.kscale[0] * (kj < N / 2 ? kj : kj - N);
                 acc[2] += (p.sm.h0 + p.sm.h2 * k * k) * (double)cabs2(y[0][m]);
             }
+            if (mir) acc[2] *= 0.5;   // the extension holds the stored half twice
             slot_sum3<T>(acc, t, reinterpret_cast<double *>(bufB), sync);
             if (t == 0 && active) {
                 const double norm = acc[0] * p.sm.dV;
@@ -176,10 +186,12 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int j = t + m * T;
+            const int pj = mir && j >= NS ? N - 1 - j : j;
             R v = Vs[m];
-            if (vtime) v = p.lt.V[(int64_t)sg * N + j];
+            if (vtime) v = p.lt.V[(int64_t)sg * NS + pj];
             if constexpr (NOISE) {
-                pt[m] = point_term(p.lt, v, (uint32_t)j, gp, (uint32_t)sg);
+                pt[m] = point_term(p.lt, v, (uint32_t)pj, gp, (uint32_t)sg);
+                if (mir == 2 && j >= NS) pt[m].na = mk<V>(-pt[m].na.x, -pt[m].na.y);   // odd image
             } else {
                 pt[m].dtV = p.lt.dt * v;
                 pt[m].na = mk<V>(R(0), R(0));
@@ -262,7 +274,8 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
 
     if (active) {
 #pragma unroll
-        for (int m = 0; m < E; ++m) psi[t + m * T] = x[0][m];
+        for (int m = 0; m < E; ++m)
+            if (t + m * T < NS) psi[t + m * T] = x[0][m];
     }
 }
 
@@ -297,6 +310,7 @@ template <typename R, int N> cudaError_t launch_1d_n(int variant, const Params1D
     constexpr int P3 = 2 * P0 * T <= 256 ? 2 * P0 : P0;
     if (p.scheme == 1) return launch_ppc<R, N, 8, P0, 1>(p, s);   // one launch shape for the semi-implicit step
     if (p.knl) return launch_ppc<R, N, 8, P0, 0, true>(p, s);       // and for the non-local term
+    if (p.mirror) return launch_ppc<R, N, 8, P0>(p, s);             // and for cosine / sine lattices
     switch (variant) {
         case 1: return launch_ppc<R, N, 8, P1>(p, s);
         case 2: return launch_ppc<R, N, 8, P2>(p, s);

@@ -231,8 +231,18 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
     const int col = blockIdx.x * C + c;
     const int64_t path = blockIdx.y;
     const int n1 = p.n1;
-    const int64_t base = path * (int64_t)N0 * n1 + col;
+    // a cosine / sine dimension 0 (XMDS2 Sec. 2.1) of NS stored rows is
+    // transformed as its even / odd extension: row j >= NS is the image of
+    // stored row N0-1-j (negated for the sine basis) and is not written back
+    const int mir = p.mirror0;
+    const int NS = mir ? N0 / 2 : N0;
+    const int64_t base = path * (int64_t)NS * n1 + col;
     const bool sample = p.sample_slot >= 0;
+    auto at = [&](int j) -> int64_t { return base + (int64_t)(mir && j >= NS ? N0 - 1 - j : j) * n1; };
+    auto load = [&](const V *f, int j) -> V {
+        const V v = f[at(j)];
+        return (mir == 2 && j >= NS) ? mk<V>(-v.x, -v.y) : v;
+    };
 
     auto kinetic = [&](const V (&f)[E]) {
         // sum_k Re(i L(k)) |F psi|^2 dV / N, accumulated into the energy of this path.
@@ -257,7 +267,7 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
             const double k0 = p.sm.kscale[0] * (kj < N0 / 2 ? kj : kj - N0);
             s += (p.sm.h0 + p.sm.h2 * (k0 * k0 + kc2)) * (double)cabs2(f[m]);
         }
-        s *= w;
+        s *= mir ? 0.5 * w : w;   // an extension holds the stored half twice
         s = warp_sum(s);
         __syncthreads();
         if ((threadIdx.x & 31) == 0) scratch[threadIdx.x >> 5] = s;
@@ -274,21 +284,21 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
     if constexpr (MODE == COL_SPECTRAL || MODE == COL_FFT_FWD) {
         V y[1][E];
 #pragma unroll
-        for (int m = 0; m < E; ++m) y[0][m] = p.B[base + (int64_t)(t + m * T) * n1];
+        for (int m = 0; m < E; ++m) y[0][m] = load(p.B, t + m * T);
         fft<N0, E, -1, 1>(y, t, sm1, L, sync, tw);
         if constexpr (MODE == COL_SPECTRAL) {
             kinetic(y[0]);
         } else {
 #pragma unroll
-            for (int m = 0; m < E; ++m) p.B[base + (int64_t)(t + m * T) * n1] = y[0][m];
+            for (int m = 0; m < E; ++m) p.B[base + (int64_t)(t + m * T) * n1] = y[0][m];   // 3D only (no mirror)
         }
         return;
     } else {
         V x[2][E];
 #pragma unroll
         for (int m = 0; m < E; ++m) {
-            x[0][m] = p.A[base + (int64_t)(t + m * T) * n1];
-            x[1][m] = p.B[base + (int64_t)(t + m * T) * n1];
+            x[0][m] = load(p.A, t + m * T);
+            x[1][m] = load(p.B, t + m * T);
         }
         fft<N0, E, -1, 2>(x, t, sm2, L, sync, tw);
         if (sample) kinetic(x[0]);
@@ -301,6 +311,7 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
         fft<N0, E, +1, 2>(x, t, sm2, L, sync, tw);
 #pragma unroll
         for (int m = 0; m < E; ++m) {
+            if (t + m * T >= NS) continue;
             p.A[base + (int64_t)(t + m * T) * n1] = x[0][m];
             p.B[base + (int64_t)(t + m * T) * n1] = x[1][m];
         }
@@ -370,7 +381,8 @@ template <typename R> cudaError_t launch_row_pass(int mode, const Params2D<R> &p
 }
 
 template <typename R> cudaError_t launch_col_pass(int mode, const Params2D<R> &p, cudaStream_t s) {
-    switch (p.n0) {
+    if (p.mirror0 && (p.ndim != 2 || mode == COL_FFT_FWD)) return cudaErrorInvalidValue;
+    switch (p.mirror0 ? 2 * p.n0 : p.n0) {
         case 16: return col_mode<R, 16>(mode, p, s);
         case 32: return col_mode<R, 32>(mode, p, s);
         case 64: return col_mode<R, 64>(mode, p, s);

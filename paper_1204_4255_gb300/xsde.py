@@ -33,8 +33,9 @@ EXPORTED = (
     "xsde_integrate_static_scratch", "xsde_adjoint", "xsde_kernel_variants", "xsde_autotune",
     "xsde_batch_create", "xsde_batch_integrate", "xsde_batch_destroy", "xsde_integrate_plain",
     "xsde_integrate_adaptive", "xsde_set_noise_substeps", "xsde_set_scheme",
-    "xsde_set_nonlocal",
+    "xsde_set_nonlocal", "xsde_grid_set_basis",
 )
+XSDE_BASIS_FOURIER, XSDE_BASIS_COS, XSDE_BASIS_SIN = 0, 1, 2
 XSDE_SCHEME_RK4IP, XSDE_SCHEME_SEMI_IMPLICIT = 0, 1
 XSDE_BATCH_AUTOTUNE = 1
 XSDE_KERNEL_KINDS = 9
@@ -120,6 +121,7 @@ def load(path: str = LIB_PATH):
         "xsde_set_noise_substeps": (ctypes.c_int, [vp, ctypes.c_int32]),
         "xsde_set_scheme": (ctypes.c_int, [vp, ctypes.c_int32]),
         "xsde_set_nonlocal": (ctypes.c_int, [vp, vp]),
+        "xsde_grid_set_basis": (ctypes.c_int, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -149,6 +151,11 @@ def xsde_grid_create(npts, xmin, xmax) -> ctypes.c_void_p:
     _check(load().xsde_grid_create(nd, _arr(ctypes.c_int32, npts), _arr(ctypes.c_double, xmin),
                                    _arr(ctypes.c_double, xmax), ctypes.byref(out)))
     return out
+
+
+def xsde_grid_set_basis(grid, basis) -> None:
+    """basis: one XSDE_BASIS_* per dimension."""
+    _check(load().xsde_grid_set_basis(grid, _arr(ctypes.c_int32, basis)))
 
 
 def xsde_grid_destroy(grid) -> None:
@@ -347,10 +354,12 @@ def _stream_handle(stream) -> int:
 class Problem:
     """A lattice + precision + operators (one xsde_problem handle)."""
 
-    def __init__(self, npts, xmin, xmax, dtype: str = "c64"):
+    def __init__(self, npts, xmin, xmax, dtype: str = "c64", basis=()):
         self.shape = tuple(int(n) for n in npts)
         self.dtype_code = XSDE_C64 if dtype == "c64" else XSDE_C128
         self.grid = xsde_grid_create(self.shape, xmin, xmax)
+        if basis and any(basis):
+            xsde_grid_set_basis(self.grid, tuple(basis))
         self.prob = xsde_problem_create(self.grid, self.dtype_code)
         self.noise = None
         self._keep = []

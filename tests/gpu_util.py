@@ -22,7 +22,7 @@ def api_noise(w):
 def make_problem(w, dtype: str):
     import torch
     from paper_1204_4255_gb300 import xsde
-    P = xsde.Problem(w.n, w.xmin, w.xmax, dtype)
+    P = xsde.Problem(w.n, w.xmin, w.xmax, dtype, basis=getattr(w, "basis", ()))
     V = None
     if w.V is not None:
         V = torch.from_numpy(np.ascontiguousarray(w.V)).to(torch.float32 if dtype == "c64" else torch.float64).cuda()
