@@ -137,14 +137,13 @@ int64_t xsde_grid_points(const xsde_grid *grid);
  * dimension of n points on (xmin, xmax) is cell-centred, x_j = xmin + (j+1/2)dx,
  * even (odd) about both ends, with modes cos / sin(k (x - xmin)) at
  * k = pi m/(xmax - xmin), m = 0..n-1 (cosine) or 1..n (sine): the DCT-II /
- * DST-II lattice.  The library transforms such a dimension as the even (odd)
- * extension of its n points, a 2n-point Fourier line over the doubled domain,
- * whose modes are exactly these; fields store the n points only.  basis: ndim
- * entries of XSDE_BASIS_*, read during the call; the default is all Fourier.
- * Set it before creating problems, fields or noise from the grid (they copy
- * it).  Runs on 1D lattices and on dimension 0 of 2D lattices (dimension 1
- * Fourier), at most 1024 points along the cosine / sine dimension; other
- * lattices, xsde_integrate_plain, xsde_integrate_adaptive, xsde_adjoint,
+ * DST-II lattice.  The library evaluates these transforms with n-point FFTs
+ * of the points taken in even-odd order (Makhoul's algorithm) and one pairing
+ * of mode k with n-k.  basis: ndim entries of XSDE_BASIS_*, read during the
+ * call; the default is all Fourier.  Set it before creating problems, fields
+ * or noise from the grid (they copy it).  Runs on 1D lattices and on
+ * dimension 0 of 2D lattices (dimension 1 Fourier); other lattices,
+ * xsde_integrate_plain, xsde_integrate_adaptive, xsde_adjoint,
  * xsde_integrate_static_scratch and xsde_set_nonlocal report XSDE_EUNSUPPORTED
  * for such a problem.  Kernel variants are ignored (one launch shape; 2D keeps
  * the generic column pass).  Energy moments use the basis's Parseval weights.

@@ -76,6 +76,7 @@ struct xsde_problem {
     int noise_substeps = 1;   // see xsde_set_noise_substeps
     int scheme = XSDE_SCHEME_RK4IP;   // see xsde_set_scheme
     void *d_knl = nullptr;    // non-local kernel khat/npts in the problem's precision [npts]
+    void *d_B = nullptr;      // cosine / sine dimension 0: the B table of its pair step
     bool nonlocal = false;    // see xsde_set_nonlocal
     uint64_t generation = 0;  // bumped by every call that changes what integrate launches
     void *d_adj = nullptr;    // adjoint checkpoints and stage inputs
@@ -173,19 +174,38 @@ double grid_dV(const xsde_grid &g) {
     for (int d = 0; d < g.ndim; ++d) v *= grid_dx(g, d);
     return v;
 }
-// Length of the transform along dimension d: a cosine / sine dimension of n
-// stored points is transformed as its even / odd extension of 2n points over
-// the doubled domain, whose Fourier modes are the cosines / sines pi m/L.
-int tlen(const xsde_grid &g, int d) { return g.basis[d] != XSDE_BASIS_FOURIER ? 2 * g.n[d] : g.n[d]; }
 bool any_basis(const xsde_grid &g) {
     for (int d = 0; d < g.ndim; ++d)
         if (g.basis[d] != XSDE_BASIS_FOURIER) return true;
     return false;
 }
+// wavenumber of spectral index i along d: Fourier k = 2 pi m/L (m = i or i - n);
+// cosine k = pi i/L; sine k = pi (i+1)/L
 double kval(const xsde_grid &g, int d, int i) {
-    const int n = tlen(g, d);
-    const double len = (g.xmax[d] - g.xmin[d]) * (n == g.n[d] ? 1.0 : 2.0);
+    const int n = g.n[d];
+    const double len = g.xmax[d] - g.xmin[d];
+    if (g.basis[d] == XSDE_BASIS_COS) return M_PI * i / len;
+    if (g.basis[d] == XSDE_BASIS_SIN) return M_PI * (i + 1) / len;
     return 2.0 * M_PI / len * (i < n / 2 ? i : i - n);
+}
+
+// A cosine / sine dimension applies the diagonal factors f of its modes
+// through the FFT of its even-odd ordered points: U_k = A_k V_k + B_k V_{n-k},
+// A_k = (F_k + F_{n-k})/2, B_k = exp(i pi k/n) (F_k - F_{n-k})/2 (A_0 = F_0,
+// B_0 = 0) with F the cosine factors in mode order, or for the sine basis the
+// sine factors reversed (F_k = f_{n-1-k}).
+void trig_pair_tables(int basis, const std::vector<std::complex<double>> &f, std::vector<std::complex<double>> &A,
+                      std::vector<std::complex<double>> &B) {
+    const int n = (int)f.size();
+    std::vector<std::complex<double>> F(n);
+    for (int k = 0; k < n; ++k) F[k] = basis == XSDE_BASIS_SIN ? f[n - 1 - k] : f[k];
+    A.assign(n, 0.0);
+    B.assign(n, 0.0);
+    A[0] = F[0];
+    for (int k = 1; k < n; ++k) {
+        A[k] = 0.5 * (F[k] + F[n - k]);
+        B[k] = 0.5 * std::polar(1.0, M_PI * k / n) * (F[k] - F[n - k]);
+    }
 }
 
 // value -> hi (nearest) and lo (nearest to the remainder); FP64 keeps lo = 0
@@ -251,9 +271,9 @@ template <typename V> int ensure_tables(xsde_problem *p, double dt, cudaStream_t
     const std::complex<double> c0(p->L.c0_re, p->L.c0_im), c2(p->L.c2_re, p->L.c2_im);
     int rc;
     for (int d = 0; d < g.ndim; ++d)
-        if ((rc = upload_twiddles<decltype(V::x)>(tlen(g, d), &p->d_tw[d], s)) != XSDE_OK) return rc;
+        if ((rc = upload_twiddles<decltype(V::x)>(g.n[d], &p->d_tw[d], s)) != XSDE_OK) return rc;
     if (g.ndim == 1) {
-        const int n = tlen(g, 0);
+        const int n = g.n[0];
         // the radix-4 and radix-2 plans of the 4- and 2-element launch shapes
         if ((rc = upload_twiddles<decltype(V::x), 4>(n, &p->d_tw1d[0], s)) != XSDE_OK) return rc;
         if ((rc = upload_twiddles<decltype(V::x), 2>(n, &p->d_tw1d[1], s)) != XSDE_OK) return rc;
@@ -262,13 +282,26 @@ template <typename V> int ensure_tables(xsde_problem *p, double dt, cudaStream_t
             const double k = kval(g, 0, i);
             e[i] = std::exp((c0 + c2 * (k * k)) * (0.5 * dt)) / (double)n;
         }
-        if ((rc = upload<V>(e, &p->d_E[0], s)) != XSDE_OK) return rc;
+        if (g.basis[0] != XSDE_BASIS_FOURIER) {
+            std::vector<std::complex<double>> A, B;
+            trig_pair_tables(g.basis[0], e, A, B);
+            if ((rc = upload<V>(A, &p->d_E[0], s)) != XSDE_OK) return rc;
+            if ((rc = upload<V>(B, &p->d_B, s)) != XSDE_OK) return rc;
+        } else if ((rc = upload<V>(e, &p->d_E[0], s)) != XSDE_OK) {
+            return rc;
+        }
     } else if (g.ndim == 2) {
-        const int n0 = tlen(g, 0);
+        const int n0 = g.n[0];
         std::vector<std::complex<double>> e0(n0), e1(g.n[1]);
         for (int i = 0; i < n0; ++i) {
             const double k = kval(g, 0, i);
             e0[i] = std::exp((c0 + c2 * (k * k)) * (0.5 * dt)) / ((double)n0 * g.n[1]);
+        }
+        if (g.basis[0] != XSDE_BASIS_FOURIER) {
+            std::vector<std::complex<double>> A, B;
+            trig_pair_tables(g.basis[0], e0, A, B);
+            e0 = A;
+            if ((rc = upload<V>(B, &p->d_B, s)) != XSDE_OK) return rc;
         }
         for (int i = 0; i < g.n[1]; ++i) {
             const double k = kval(g, 1, i);
@@ -542,8 +575,9 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
         q.status = p->d_status;
         q.scheme = p->scheme;
         q.knl = p->nonlocal ? static_cast<const V *>(p->d_knl) : nullptr;
-        q.mirror = g.basis[0];
-        XSDE_CUDA(timed(p, 1, s, [&] { return launch_rk4ip_1d<R>(tlen(g, 0), p->kernel_variant, q, s); }),
+        q.basis = g.basis[0];
+        q.Btab = static_cast<const V *>(p->d_B);
+        XSDE_CUDA(timed(p, 1, s, [&] { return launch_rk4ip_1d<R>(g.n[0], p->kernel_variant, q, s); }),
                   "rk4ip_1d launch");
         return XSDE_OK;
     }
@@ -564,7 +598,8 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
     q.lt = lt;
     q.sm = sm;
     q.status = p->d_status;
-    q.mirror0 = g.basis[0];
+    q.basis0 = g.basis[0];
+    q.B0 = static_cast<const V *>(p->d_B);
     const int S = sm.every;
     // complex64 lattices the persistent TMA passes cover take the hot modes there
     // (a cosine / sine dimension 0 keeps the generic column pass)
@@ -573,7 +608,7 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
     if constexpr (std::is_same<R, float>::value) {
         if (p->kernel_variant != 1 && (uintptr_t)psi % 16 == 0 && (uintptr_t)p->d_scratch % 16 == 0) {
             tma_row = tma_rows_ok(g.n[1], npaths * g.n[0]);
-            tma_col = p->kernel_variant == 0 && !q.mirror0 && tma_col_supported(g.n[0]) && g.n[1] % COL_TMA_C == 0 &&
+            tma_col = p->kernel_variant == 0 && !q.basis0 && tma_col_supported(g.n[0]) && g.n[1] % COL_TMA_C == 0 &&
                       encode_field_map(&mapA, psi, npaths * g.n[0], g.n[1], g.n[0]) &&
                       encode_field_map(&mapB, p->d_scratch, npaths * g.n[0], g.n[1], g.n[0]);
         }
@@ -661,8 +696,6 @@ int check_integrate(const char *who, xsde_problem *p, const xsde_vector *psi, do
         if (g.ndim == 3) return fail(XSDE_EUNSUPPORTED, "%s: cosine / sine bases on 1D and 2D lattices only", who);
         if (g.ndim == 2 && g.basis[1] != XSDE_BASIS_FOURIER)
             return fail(XSDE_EUNSUPPORTED, "%s: on a 2D lattice only dimension 0 may be cosine / sine", who);
-        if (g.n[0] > 1024)
-            return fail(XSDE_EUNSUPPORTED, "%s: a cosine / sine dimension has at most 1024 points", who);
         if (g.ndim == 2 && p->scheme != XSDE_SCHEME_RK4IP)
             return fail(XSDE_EUNSUPPORTED, "%s: the semi-implicit scheme runs on 0D and 1D lattices", who);
     }
@@ -826,6 +859,7 @@ void xsde_problem_destroy(xsde_problem *p) {
     cudaFree(p->d_tw1d[0]);
     cudaFree(p->d_tw1d[1]);
     cudaFree(p->d_knl);
+    cudaFree(p->d_B);
     cudaFree(p->d_scratch);
     cudaFree(p->d_adj);
     cudaFree(p->d_status);

@@ -68,8 +68,9 @@ template <typename R> struct Params1D {
     int scheme = 0;        // 0 RK4IP, 1 semi-implicit midpoint (default launch shape only)
     const cx<R> *knl = nullptr;   // non-local kernel khat/N in FFT order [N], or none
                                   // (RK4IP at the default launch shape only)
-    int mirror = 0;        // 0 Fourier; 1 / 2: cosine / sine lattice of N/2 stored points
-                           // run as its even / odd extension (default launch shape only)
+    int basis = 0;         // 0 Fourier; 1 / 2 cosine / sine lattice (default launch shape
+                           // only): Etab holds A and Btab B of U_k = A_k V_k + B_k V_{N-k}
+    const cx<R> *Btab = nullptr;   // hi [N] then lo [N]
 };
 // variant v in [0, rk4ip_1d_variants()) sets the launch shape: elements per
 // thread rk4ip_1d_elems(v) (8, or 4 / 2 for variants 4 / 5, whose twiddle
@@ -120,9 +121,11 @@ template <typename R> struct Params2D {
     int ndim = 2;
     int nmid = 1;
     int kinner = 0;
-    // 2D cosine / sine dimension 0: n0 stored rows, the column pass transforms
-    // the even (1) / odd (2) extension of length 2 n0 (generic column kernel)
-    int mirror0 = 0;
+    // 2D cosine (1) / sine (2) dimension 0 (generic column kernel): rows are
+    // gathered in the even-odd order, E0 holds A and B0 B of
+    // U_k = A_k V_k + B_k V_{n0-k} (hi [n0] then lo [n0] each)
+    int basis0 = 0;
+    const cx<R> *B0 = nullptr;
 };
 template <typename R> cudaError_t launch_row_pass(int mode, const Params2D<R> &p, cudaStream_t s);
 template <typename R> cudaError_t launch_col_pass(int mode, const Params2D<R> &p, cudaStream_t s);

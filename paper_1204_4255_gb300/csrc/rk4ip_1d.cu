@@ -68,7 +68,8 @@ template <typename R> __device__ __forceinline__ PointTerm<R> with_vnl(PointTerm
 // SCHEME 1: the semi-implicit midpoint step in the interaction picture instead
 // of RK4IP (a_I = D a; m <- a_I + N(m)/2 three times from m = a_I;
 // a <- D(2 m - a_I): XMDS2 Sec. 2.5's semi-implicit method with Sec. 2.6)
-template <typename R, int N, int E, int PPC, bool NOISE, int SCHEME = 0, bool NL = false>
+// TRIG: a cosine or sine lattice (XMDS2 Sec. 2.1; p.basis 1 / 2), see below
+template <typename R, int N, int E, int PPC, bool NOISE, int SCHEME = 0, bool NL = false, bool TRIG = false>
 __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R> p) {
     using V = cx<R>;
     constexpr int T = N / E;
@@ -88,32 +89,69 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
     for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = p.tw[i];
     __syncthreads();
 
-    // Cosine / sine lattices (XMDS2 Sec. 2.1) run as the even / odd extension
-    // of their NS = N/2 stored points over the reflection at the lower end: the
-    // image point j >= NS is stored point N-1-j, negated for the sine basis.
-    // The extension's transforms diagonalise exactly the cosine / sine modes.
-    const int mir = p.mirror;
-    const int NS = mir ? N / 2 : N;
+    // Cosine / sine lattices (TRIG).  The N cell-centred points are held in
+    // the even-odd order of the DCT-II's evaluation by an N-point FFT
+    // (Makhoul, IEEE TASSP 1980): register slot s holds point 2s for s < N/2
+    // and point 2N-1-2s above.  The FFT of the slots, V, gives the cosine
+    // spectrum X_k = (w_k V_k + conj(w_k) V_{N-k})/2, w_k = exp(-i pi k/2N), and
+    // D = C^-1 diag(E) C becomes U_k = A_k V_k + B_k V_{N-k} between the two
+    // FFTs (A, B from the host; one exchange pairs k with N-k).  A sine
+    // lattice is the cosine one of (-1)^j psi_j with its modes reversed: its
+    // odd points (slots s >= N/2) are held negated, and so is their additive
+    // noise.  Real-space work at slot s uses point point_of(s).
+    const int bas = TRIG ? p.basis : 0;
+    auto point_of = [&](int s) -> int { return !TRIG ? s : (s < N / 2 ? 2 * s : 2 * N - 1 - 2 * s); };
+    auto negated = [&](int s) -> bool { return TRIG && bas == 2 && s >= N / 2; };
     const int64_t lp = (int64_t)blockIdx.x * PPC + slot;
     const bool active = lp < p.npaths;
     const uint32_t gp = (uint32_t)(p.lt.path_offset + lp);
-    V *psi = p.psi + lp * NS;
+    V *psi = p.psi + lp * N;
     const bool vtime = p.lt.pot == PM_TABLE && p.lt.V_nt > 1;
 
     V x[2][E];
-    V Ek[E], El[E];
+    V Ek[E], El[E];   // exp(L dt/2)/N (Fourier) or A (TRIG), hi and lo; B is read through L1
     R Vs[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int j = t + m * T;
-        const int pj = mir && j >= NS ? N - 1 - j : j;
+        const int pj = point_of(j);
         x[0][m] = active ? psi[pj] : mk<V>(R(0), R(0));
-        if (mir == 2 && j >= NS) x[0][m] = mk<V>(-x[0][m].x, -x[0][m].y);
+        if (negated(j)) x[0][m] = mk<V>(-x[0][m].x, -x[0][m].y);
         Ek[m] = p.Etab[j];
         El[m] = p.Etab[N + j];
         const int idx[3] = {pj, 0, 0};
         Vs[m] = vtime ? R(0) : potential(p.lt, 1, idx, pj, 0);
     }
+
+    // exp(L dt/2) in the lattice's spectral basis, on NV transformed vectors
+    auto kmul = [&](auto &v) {
+        constexpr int NV = sizeof(v) / sizeof(v[0]);
+        if constexpr (TRIG) {
+            V *const *smv = NV == 2 ? sm2 : sm1;
+#pragma unroll
+            for (int m = 0; m < E; ++m)
+#pragma unroll
+                for (int iv = 0; iv < NV; ++iv) smv[iv][L(t + m * T)] = v[iv][m];
+            sync();
+            V q[NV][E];
+#pragma unroll
+            for (int m = 0; m < E; ++m)
+#pragma unroll
+                for (int iv = 0; iv < NV; ++iv) q[iv][m] = smv[iv][L((N - t - m * T) & (N - 1))];
+            sync();
+#pragma unroll
+            for (int m = 0; m < E; ++m)
+#pragma unroll
+                for (int iv = 0; iv < NV; ++iv)
+                    v[iv][m] = cadd(cmul_hilo(v[iv][m], Ek[m], El[m]),
+                                    cmul_hilo(q[iv][m], __ldg(p.Btab + t + m * T), __ldg(p.Btab + N + t + m * T)));
+        } else {
+#pragma unroll
+            for (int m = 0; m < E; ++m)
+#pragma unroll
+                for (int iv = 0; iv < NV; ++iv) v[iv][m] = cmul_hilo(v[iv][m], Ek[m], El[m]);
+        }
+    };
     const R gdt = p.lt.gdt;
     const R sixth = R(1) / R(6), third = R(1) / R(3), half = R(0.5);
 
@@ -141,8 +179,7 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
             if constexpr (NL) nonlocal(x[0], vn);
 #pragma unroll
             for (int m = 0; m < E; ++m) {
-                const int j = t + m * T;
-                if (j >= NS) continue;   // image points of a cosine / sine lattice
+                const int j = point_of(t + m * T);
                 const int idx[3] = {j, 0, 0};
                 const double m2 = (double)cabs2(x[0][m]);
                 const double vv = (double)potential(p.lt, 1, idx, j, gs);
@@ -150,7 +187,7 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
                 acc[1] += vv * m2 + 0.5 * p.sm.g * m2 * m2;
                 if constexpr (NL) acc[1] += 0.5 * (double)vn[m] * m2;   // pair energy, counted once
                 if (active && (p.sm.which & (MOM_MOD2 | MOM_MOD4)) && p.sm.per_point) {
-                    double *pp = p.sm.per_point + 2 * (s * NS + j);
+                    double *pp = p.sm.per_point + 2 * (s * N + j);
                     atomicAdd(pp, m2 * p.sm.inv_paths);
                     atomicAdd(pp + 1, m2 * m2 * p.sm.inv_paths);
                 }
@@ -159,13 +196,32 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
 #pragma unroll
             for (int m = 0; m < E; ++m) y[0][m] = x[0][m];
             fft<N, E, -1, 1>(y, t, sm1, L, sync, tw);
+            if constexpr (TRIG) {
+                // cosine spectrum X_k from the pair (k, N-k); Parseval weight 2
+                // for every mode but k = 0; sine mode N-1-k sits at k
 #pragma unroll
-            for (int m = 0; m < E; ++m) {
-                const int kj = t + m * T;
-                const double k = p.sm.kscale[0] * (kj < N / 2 ? kj : kj - N);
-                acc[2] += (p.sm.h0 + p.sm.h2 * k * k) * (double)cabs2(y[0][m]);
+                for (int m = 0; m < E; ++m) bufA[L(t + m * T)] = y[0][m];
+                sync();
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    const int kj = t + m * T;
+                    const V yq = bufA[L((N - kj) & (N - 1))];
+                    double sn, cs;
+                    sincospi(-(double)kj / (2.0 * N), &sn, &cs);
+                    const double xr = 0.5 * (cs * ((double)y[0][m].x + (double)yq.x) - sn * ((double)y[0][m].y - (double)yq.y));
+                    const double xi = 0.5 * (cs * ((double)y[0][m].y + (double)yq.y) + sn * ((double)y[0][m].x - (double)yq.x));
+                    const double k = p.sm.kscale[0] * (bas == 1 ? kj : N - kj);
+                    acc[2] += (kj == 0 ? 1.0 : 2.0) * (p.sm.h0 + p.sm.h2 * k * k) * (xr * xr + xi * xi);
+                }
+                sync();
+            } else {
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    const int kj = t + m * T;
+                    const double k = p.sm.kscale[0] * (kj < N / 2 ? kj : kj - N);
+                    acc[2] += (p.sm.h0 + p.sm.h2 * k * k) * (double)cabs2(y[0][m]);
+                }
             }
-            if (mir) acc[2] *= 0.5;   // the extension holds the stored half twice
             slot_sum3<T>(acc, t, reinterpret_cast<double *>(bufB), sync);
             if (t == 0 && active) {
                 const double norm = acc[0] * p.sm.dV;
@@ -186,12 +242,12 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int j = t + m * T;
-            const int pj = mir && j >= NS ? N - 1 - j : j;
+            const int pj = point_of(j);
             R v = Vs[m];
-            if (vtime) v = p.lt.V[(int64_t)sg * NS + pj];
+            if (vtime) v = p.lt.V[(int64_t)sg * N + pj];
             if constexpr (NOISE) {
                 pt[m] = point_term(p.lt, v, (uint32_t)pj, gp, (uint32_t)sg);
-                if (mir == 2 && j >= NS) pt[m].na = mk<V>(-pt[m].na.x, -pt[m].na.y);   // odd image
+                if (negated(j)) pt[m].na = mk<V>(-pt[m].na.x, -pt[m].na.y);
             } else {
                 pt[m].dtV = p.lt.dt * v;
                 pt[m].na = mk<V>(R(0), R(0));
@@ -203,8 +259,7 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
 #pragma unroll
             for (int m = 0; m < E; ++m) y[0][m] = x[0][m];
             fft<N, E, -1, 1>(y, t, sm1, L, sync, tw);
-#pragma unroll
-            for (int m = 0; m < E; ++m) y[0][m] = cmul_hilo(y[0][m], Ek[m], El[m]);
+            kmul(y);
             fft<N, E, +1, 1>(y, t, sm1, L, sync, tw);       // a_I
 #pragma unroll
             for (int m = 0; m < E; ++m) {
@@ -213,8 +268,7 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
                 y[0][m] = mk<V>(R(2) * mid.x - y[0][m].x, R(2) * mid.y - y[0][m].y);
             }
             fft<N, E, -1, 1>(y, t, sm1, L, sync, tw);
-#pragma unroll
-            for (int m = 0; m < E; ++m) y[0][m] = cmul_hilo(y[0][m], Ek[m], El[m]);
+            kmul(y);
             fft<N, E, +1, 1>(y, t, sm1, L, sync, tw);
 #pragma unroll
             for (int m = 0; m < E; ++m) x[0][m] = y[0][m];
@@ -222,11 +276,7 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
         }
         // a_I = D a, k1 = D N(a)
         fft<N, E, -1, 2>(x, t, sm2, L, sync, tw);
-#pragma unroll
-        for (int m = 0; m < E; ++m) {
-            x[0][m] = cmul_hilo(x[0][m], Ek[m], El[m]);
-            x[1][m] = cmul_hilo(x[1][m], Ek[m], El[m]);
-        }
+        kmul(x);
         fft<N, E, +1, 2>(x, t, sm2, L, sync, tw);
         // k2, k3 in real space; x[0] <- a_I + k3, x[1] <- a_I + k1/6 + k2/3 + k3/3
         if constexpr (NL) {
@@ -259,11 +309,7 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
             }
         }
         fft<N, E, -1, 2>(x, t, sm2, L, sync, tw);
-#pragma unroll
-        for (int m = 0; m < E; ++m) {
-            x[0][m] = cmul_hilo(x[0][m], Ek[m], El[m]);
-            x[1][m] = cmul_hilo(x[1][m], Ek[m], El[m]);
-        }
+        kmul(x);
         fft<N, E, +1, 2>(x, t, sm2, L, sync, tw);
         // k4 = N(D(a_I + k3)); a <- D(acc) + k4/6
         if constexpr (NL) nonlocal(x[0], vn);
@@ -274,18 +320,20 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
 
     if (active) {
 #pragma unroll
-        for (int m = 0; m < E; ++m)
-            if (t + m * T < NS) psi[t + m * T] = x[0][m];
+        for (int m = 0; m < E; ++m) {
+            const int j = t + m * T;
+            psi[point_of(j)] = negated(j) ? mk<V>(-x[0][m].x, -x[0][m].y) : x[0][m];
+        }
     }
 }
 
-template <typename R, int N, int E, int PPC, int SCHEME = 0, bool NL = false>
+template <typename R, int N, int E, int PPC, int SCHEME = 0, bool NL = false, bool TRIG = false>
 cudaError_t launch_ppc(const Params1D<R> &p, cudaStream_t s) {
     constexpr int T = N / E;
     const size_t smem = (size_t)N * sizeof(tw_t<R>) + (size_t)PPC * 2 * padded_len<N>() * sizeof(cx<R>);
     const bool noise = p.lt.noise != NM_NONE;
-    auto kern = noise ? rk4ip_1d_kernel<R, N, E, PPC, true, SCHEME, NL>
-                      : rk4ip_1d_kernel<R, N, E, PPC, false, SCHEME, NL>;
+    auto kern = noise ? rk4ip_1d_kernel<R, N, E, PPC, true, SCHEME, NL, TRIG>
+                      : rk4ip_1d_kernel<R, N, E, PPC, false, SCHEME, NL, TRIG>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (p.npaths + PPC - 1) / PPC;
@@ -308,9 +356,10 @@ template <typename R, int N> cudaError_t launch_1d_n(int variant, const Params1D
     constexpr int P0 = default_ppc<N, 8>(), T = N / 8;
     constexpr int P1 = P0 >= 2 ? P0 / 2 : 1, P2 = P0 >= 4 ? P0 / 4 : 1;
     constexpr int P3 = 2 * P0 * T <= 256 ? 2 * P0 : P0;
-    if (p.scheme == 1) return launch_ppc<R, N, 8, P0, 1>(p, s);   // one launch shape for the semi-implicit step
+    if (p.basis)   // one launch shape for cosine / sine lattices,
+        return p.scheme == 1 ? launch_ppc<R, N, 8, P0, 1, false, true>(p, s) : launch_ppc<R, N, 8, P0, 0, false, true>(p, s);
+    if (p.scheme == 1) return launch_ppc<R, N, 8, P0, 1>(p, s);   // for the semi-implicit step
     if (p.knl) return launch_ppc<R, N, 8, P0, 0, true>(p, s);       // and for the non-local term
-    if (p.mirror) return launch_ppc<R, N, 8, P0>(p, s);             // and for cosine / sine lattices
     switch (variant) {
         case 1: return launch_ppc<R, N, 8, P1>(p, s);
         case 2: return launch_ppc<R, N, 8, P2>(p, s);

@@ -212,7 +212,7 @@ template <typename R, int N0> struct ColCfg {
     static_assert(THREADS % 32 == 0, "column tiles are whole warps");
 };
 
-template <typename R, int N0, int MODE>
+template <typename R, int N0, int MODE, bool TRIG = false>
 __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const Params2D<R> p) {
     using V = cx<R>;
     using Cfg = ColCfg<R, N0>;
@@ -231,20 +231,37 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
     const int col = blockIdx.x * C + c;
     const int64_t path = blockIdx.y;
     const int n1 = p.n1;
-    // a cosine / sine dimension 0 (XMDS2 Sec. 2.1) of NS stored rows is
-    // transformed as its even / odd extension: row j >= NS is the image of
-    // stored row N0-1-j (negated for the sine basis) and is not written back
-    const int mir = p.mirror0;
-    const int NS = mir ? N0 / 2 : N0;
-    const int64_t base = path * (int64_t)NS * n1 + col;
+    const int64_t base = path * (int64_t)N0 * n1 + col;
     const bool sample = p.sample_slot >= 0;
-    auto at = [&](int j) -> int64_t { return base + (int64_t)(mir && j >= NS ? N0 - 1 - j : j) * n1; };
-    auto load = [&](const V *f, int j) -> V {
-        const V v = f[at(j)];
-        return (mir == 2 && j >= NS) ? mk<V>(-v.x, -v.y) : v;
+    // A cosine / sine dimension 0 (TRIG; XMDS2 Sec. 2.1) gathers its rows in the
+    // even-odd order of the DCT-II's evaluation by an N0-point FFT (slot s holds
+    // row 2s below N0/2, row 2 N0-1-2s above; odd rows negated for the sine
+    // basis); between the FFTs one exchange pairs k with N0-k and
+    // U_k = A_k V_k + B_k V_{N0-k} applies exp(L dt/2) in the cosine / sine basis.
+    const int bas = TRIG ? p.basis0 : 0;
+    auto row_of = [&](int s) -> int { return !TRIG ? s : (s < N0 / 2 ? 2 * s : 2 * N0 - 1 - 2 * s); };
+    auto at = [&](int s) -> int64_t { return base + (int64_t)row_of(s) * n1; };
+    auto load = [&](const V *f, int s) -> V {
+        const V v = f[at(s)];
+        return (TRIG && bas == 2 && s >= N0 / 2) ? mk<V>(-v.x, -v.y) : v;
+    };
+    auto store = [&](V *f, int s, V v) { f[at(s)] = (TRIG && bas == 2 && s >= N0 / 2) ? mk<V>(-v.x, -v.y) : v; };
+    // partner values V_{N0-k} of the transformed vectors (TRIG)
+    auto partners = [&](auto &v, auto &q) {
+        constexpr int NV = sizeof(v) / sizeof(v[0]);
+#pragma unroll
+        for (int m = 0; m < E; ++m)
+#pragma unroll
+            for (int iv = 0; iv < NV; ++iv) sm2[iv][L(t + m * T)] = v[iv][m];
+        sync();
+#pragma unroll
+        for (int m = 0; m < E; ++m)
+#pragma unroll
+            for (int iv = 0; iv < NV; ++iv) q[iv][m] = sm2[iv][L((N0 - t - m * T) & (N0 - 1))];
+        sync();
     };
 
-    auto kinetic = [&](const V (&f)[E]) {
+    auto kinetic = [&](const V (&f)[E], const V (&fq)[E]) {
         // sum_k Re(i L(k)) |F psi|^2 dV / N, accumulated into the energy of this path.
         // The column index is k1 (2D) or the pair (k1, k2) = (col / kinner, col % kinner) (3D).
         double kc2;
@@ -264,10 +281,21 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int kj = t + m * T;
-            const double k0 = p.sm.kscale[0] * (kj < N0 / 2 ? kj : kj - N0);
-            s += (p.sm.h0 + p.sm.h2 * (k0 * k0 + kc2)) * (double)cabs2(f[m]);
+            if constexpr (TRIG) {
+                // cosine spectrum from the pair, Parseval weight 2 but at k = 0;
+                // sine mode N0-1-k sits at k
+                double sn, cs;
+                sincospi(-(double)kj / (2.0 * N0), &sn, &cs);
+                const double xr = 0.5 * (cs * ((double)f[m].x + (double)fq[m].x) - sn * ((double)f[m].y - (double)fq[m].y));
+                const double xi = 0.5 * (cs * ((double)f[m].y + (double)fq[m].y) + sn * ((double)f[m].x - (double)fq[m].x));
+                const double k0 = p.sm.kscale[0] * (bas == 1 ? kj : N0 - kj);
+                s += (kj == 0 ? 1.0 : 2.0) * (p.sm.h0 + p.sm.h2 * (k0 * k0 + kc2)) * (xr * xr + xi * xi);
+            } else {
+                const double k0 = p.sm.kscale[0] * (kj < N0 / 2 ? kj : kj - N0);
+                s += (p.sm.h0 + p.sm.h2 * (k0 * k0 + kc2)) * (double)cabs2(f[m]);
+            }
         }
-        s *= mir ? 0.5 * w : w;   // an extension holds the stored half twice
+        s *= w;
         s = warp_sum(s);
         __syncthreads();
         if ((threadIdx.x & 31) == 0) scratch[threadIdx.x >> 5] = s;
@@ -287,10 +315,12 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
         for (int m = 0; m < E; ++m) y[0][m] = load(p.B, t + m * T);
         fft<N0, E, -1, 1>(y, t, sm1, L, sync, tw);
         if constexpr (MODE == COL_SPECTRAL) {
-            kinetic(y[0]);
+            V yq[1][E];
+            if constexpr (TRIG) partners(y, yq);
+            kinetic(y[0], yq[0]);
         } else {
 #pragma unroll
-            for (int m = 0; m < E; ++m) p.B[base + (int64_t)(t + m * T) * n1] = y[0][m];   // 3D only (no mirror)
+            for (int m = 0; m < E; ++m) p.B[base + (int64_t)(t + m * T) * n1] = y[0][m];   // 3D only
         }
         return;
     } else {
@@ -301,19 +331,26 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
             x[1][m] = load(p.B, t + m * T);
         }
         fft<N0, E, -1, 2>(x, t, sm2, L, sync, tw);
-        if (sample) kinetic(x[0]);
+        V xq[2][E];
+        if constexpr (TRIG) partners(x, xq);
+        if (sample) kinetic(x[0], xq[0]);
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const V eh = __ldg(p.E0 + t + m * T), el = __ldg(p.E0 + N0 + t + m * T);
-            x[0][m] = cmul_hilo(x[0][m], eh, el);
-            x[1][m] = cmul_hilo(x[1][m], eh, el);
+            if constexpr (TRIG) {
+                const V bh = __ldg(p.B0 + t + m * T), bl = __ldg(p.B0 + N0 + t + m * T);
+                x[0][m] = cadd(cmul_hilo(x[0][m], eh, el), cmul_hilo(xq[0][m], bh, bl));
+                x[1][m] = cadd(cmul_hilo(x[1][m], eh, el), cmul_hilo(xq[1][m], bh, bl));
+            } else {
+                x[0][m] = cmul_hilo(x[0][m], eh, el);
+                x[1][m] = cmul_hilo(x[1][m], eh, el);
+            }
         }
         fft<N0, E, +1, 2>(x, t, sm2, L, sync, tw);
 #pragma unroll
         for (int m = 0; m < E; ++m) {
-            if (t + m * T >= NS) continue;
-            p.A[base + (int64_t)(t + m * T) * n1] = x[0][m];
-            p.B[base + (int64_t)(t + m * T) * n1] = x[1][m];
+            store(p.A, t + m * T, x[0][m]);
+            store(p.B, t + m * T, x[1][m]);
         }
     }
 }
@@ -346,6 +383,8 @@ template <typename R, int N0, int MODE> cudaError_t col_launch(const Params2D<R>
     using Cfg = ColCfg<R, N0>;
     const size_t smem = (size_t)2 * N0 * Cfg::C * sizeof(cx<R>) + (Cfg::THREADS / 32 + 1) * sizeof(double);
     auto kern = col_pass_kernel<R, N0, MODE>;
+    if constexpr (MODE != COL_FFT_FWD)
+        if (p.basis0) kern = col_pass_kernel<R, N0, MODE, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(p.n1 / Cfg::C), (unsigned)p.npaths);
@@ -381,8 +420,8 @@ template <typename R> cudaError_t launch_row_pass(int mode, const Params2D<R> &p
 }
 
 template <typename R> cudaError_t launch_col_pass(int mode, const Params2D<R> &p, cudaStream_t s) {
-    if (p.mirror0 && (p.ndim != 2 || mode == COL_FFT_FWD)) return cudaErrorInvalidValue;
-    switch (p.mirror0 ? 2 * p.n0 : p.n0) {
+    if (p.basis0 && (p.ndim != 2 || mode == COL_FFT_FWD)) return cudaErrorInvalidValue;
+    switch (p.n0) {
         case 16: return col_mode<R, 16>(mode, p, s);
         case 32: return col_mode<R, 32>(mode, p, s);
         case 64: return col_mode<R, 64>(mode, p, s);
