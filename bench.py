@@ -22,6 +22,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -360,6 +361,32 @@ def half_domain_cost(nsteps: int = 200) -> dict:
     return out
 
 
+# algorithmic FLOPs per point-step: 8 transforms of 5 log2(N_tot) each, plus
+# the pointwise stage work (about 100), the FFT count convention of the
+# roofline for arithmetic-bound runs
+def fft_flops_per_pt_step(n_tot: int) -> float:
+    return 8 * 5 * math.log2(n_tot) + 100
+
+
+def arithmetic_rooflines(others, plain) -> dict:
+    """FMA-pipe fractions of the arithmetic-bound runs: the 1D whole-run kernel
+    (truncated Wigner, FP32) and the complex128 2D passes (FP64), against the
+    FP32 / FP64 FMA throughput measured on this GPU (xsde_measure_fma_peaks)."""
+    from paper_1204_4255_gb300 import xsde
+    f32, f64 = xsde.xsde_measure_fma_peaks()
+    out = {"fp32_fma_tflops": f32, "fp64_fma_tflops": f64, "flops_model": "8 * 5 log2(N_tot) + 100 per pt-step"}
+    if others:
+        tw = others["truncated_wigner_4096x1024_4000_steps_moments_every_100"]["c64"]["value"]
+        a = tw * fft_flops_per_pt_step(1024) / 1e12
+        out["truncated_wigner_1d_c64"] = {"achieved_tflops": a, "peak_tflops": f32, "frac": a / f32, "bound": "alu"}
+    if plain:
+        v = plain["fused_c128"]["value"]
+        a = v * fft_flops_per_pt_step(512 * 512) / 1e12
+        out["gpe_2d_64x512x512_fused_c128"] = {"achieved_tflops": a, "peak_tflops": f64, "frac": a / f64,
+                                               "bound": "alu"}
+    return out
+
+
 def ip_vs_explicit(tol: float = 1e-6, t_end: float = 1.0) -> dict:
     """Fig. IPvsEX: the adaptive Cash-Karp integrator (xsde_integrate_adaptive,
     complex128) on the trapped GPE (V = x^2/2, g = 10, [-10, 10), ground state of
@@ -642,6 +669,7 @@ def run_gpu(args) -> None:
         strong = strong_convergence() if not args.no_batch else None
         nonloc = nonlocal_cost() if not args.no_batch else None
         halfdom = half_domain_cost() if not args.no_batch else None
+        arith = arithmetic_rooflines(others, plain) if not args.no_batch else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -654,12 +682,52 @@ def run_gpu(args) -> None:
             "clocks": clk.summary(), "kernels_profiled_step": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]},
             "norm_check": ok, "adjoint": adj, "batched": bat, "plain_vs_fused": plain,
             "other_workloads": others, "ip_vs_explicit": ipex, "strong_convergence": strong,
-            "nonlocal": nonloc, "half_domain": halfdom,
+            "nonlocal": nonloc, "half_domain": halfdom, "arithmetic_rooflines": arith,
         }
         print(json.dumps(line), flush=True)
     prob.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_case(name: str) -> None:
+    """One workload, one warm-up call and one timed call of `nsteps` RK4IP
+    steps, for kernel profiles (ncu captures of a single kernel): tw1d (the
+    truncated-Wigner 1D ensemble, 4096 x 1024, complex64, 100 steps), gpe3d
+    (the 128^3 GPE, one instance, complex64, 10 steps, autotuned), charged
+    (Example 5's non-local condensate, 4096 x 1024, complex64, 100 steps) and
+    example3 (64 x (256 cosine x 512 Fourier), complex64, 20 steps)."""
+    import torch
+    import workloads as W
+    from paper_1204_4255_gb300 import xsde
+    cases = {
+        "tw1d": (lambda: W.truncated_wigner(nsteps=100), 100),
+        "gpe3d": (lambda: W.gpe_3d(nsteps=10), 10),
+        "charged": (lambda: W.charged_bec(npaths=4096, n=1024, nsteps=100), 100),
+        "example3": (lambda: W.symmetric_gpe_2d(npaths=64, nsteps=20), 20),
+    }
+    w, nsteps = cases[name][0](), cases[name][1]
+    kind = {W.NOISE_NONE: xsde.XSDE_NOISE_NONE, W.NOISE_ADD_COMPLEX: xsde.XSDE_NOISE_WIENER_COMPLEX}[w.noise_kind]
+    P = xsde.Problem(w.n, w.xmin, w.xmax, "c64", basis=w.basis)
+    P.set_operators(c0=w.c0, c2=w.c2, g=w.gnl, pot_kind=w.pot_kind,
+                    omega=tuple(w.omega) + (0.0,) * (3 - len(w.omega)), noise_kind=kind, seed=w.seed,
+                    amplitude=w.noise_amp)
+    if w.knl is not None:
+        P.set_nonlocal(w.knl)
+    psi = torch.from_numpy(w.psi0).to(torch.complex64).cuda()
+    if name == "gpe3d":
+        P.autotune(psi.clone(), w.dt, nsteps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    P.integrate(psi, w.dt, nsteps)
+    torch.cuda.synchronize()
+    e0.record()
+    P.integrate(psi, w.dt, nsteps, step_offset=nsteps)
+    e1.record()
+    torch.cuda.synchronize()
+    P.synchronize()
+    ms = e0.elapsed_time(e1)
+    print(json.dumps({"case": name, "ms": ms, "pt_steps_per_s": w.npaths * w.npts * nsteps / (ms / 1e3)}))
+    P.close()
 
 
 def main():
@@ -675,8 +743,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched and plain-vs-fused figures")
+    ap.add_argument("--case", choices=["tw1d", "gpe3d", "charged", "example3"],
+                    help="run one workload once (for kernel profiles) instead of the bench")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.case:
+        run_case(args.case)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -238,6 +238,15 @@ int xsde_set_noise_substeps(xsde_problem *prob, int32_t substeps);
  * XSDE_EUNSUPPORTED while it is set.  Non-finite entries: XSDE_EINVAL. */
 int xsde_set_nonlocal(xsde_problem *prob, const double *khat);
 
+/* Diagnostics: dense fused-multiply-add throughput of the current device's
+ * FP32 and FP64 pipes in TFLOP/s (8 independent FMA chains per thread, 64
+ * warps per SM, timed with CUDA events after a warm-up launch; about 20 ms
+ * each, synchronous, on the default stream).  These are the denominators of
+ * the roofline fractions of arithmetic-bound kernels (the 1D whole-run kernel,
+ * the complex128 passes).  Either pointer may be NULL to skip that pipe (not
+ * both: XSDE_EINVAL); XSDE_ECUDA on a launch failure. */
+int xsde_measure_fma_peaks(double *fp32_tflops, double *fp64_tflops);
+
 /* Register a sampling group for the following xsde_integrate calls.
  * per_path  (device, FP64): [nsamp][npaths][2] = (norm, energy)  if NORM|ENERGY
  * per_point (device, FP64): [nsamp][npts][2]  = (mean |psi|^2, mean |psi|^4)

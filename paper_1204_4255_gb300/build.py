@@ -36,6 +36,7 @@ UNITS = [
     ("rk4ip_adjoint.cu", None),
     ("plain.cu", None),
     ("ark45_1d.cu", None),
+    ("peaks.cu", None),
 ]
 
 

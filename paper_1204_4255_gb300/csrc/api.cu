@@ -977,6 +977,13 @@ int xsde_set_nonlocal(xsde_problem *p, const double *khat) {
     return XSDE_OK;
 }
 
+int xsde_measure_fma_peaks(double *fp32_tflops, double *fp64_tflops) {
+    if (!fp32_tflops && !fp64_tflops) return fail(XSDE_EINVAL, "xsde_measure_fma_peaks: no output");
+    if (measure_fma_peaks(fp32_tflops, fp64_tflops) != 0)
+        return fail(XSDE_ECUDA, "xsde_measure_fma_peaks: %s", cudaGetErrorString(cudaGetLastError()));
+    return XSDE_OK;
+}
+
 int xsde_set_noise_substeps(xsde_problem *p, int32_t substeps) {
     if (!p) return fail(XSDE_EINVAL, "xsde_set_noise_substeps: problem is NULL");
     if (substeps < 1 || substeps > 65536) return fail(XSDE_EINVAL, "xsde_set_noise_substeps: %d", substeps);

@@ -76,6 +76,8 @@ template <typename R> struct Params1D {
 // thread rk4ip_1d_elems(v) (8, or 4 / 2 for variants 4 / 5, whose twiddle
 // table follows the radix-4 / radix-2 plan) and paths per CTA (variants 0-3:
 // the default filling 128 threads, a half, a quarter, twice)
+// FP32 / FP64 FMA throughput of the current device (TFLOP/s); 0 or -1
+int measure_fma_peaks(double *fp32_tflops, double *fp64_tflops);
 int rk4ip_1d_variants();
 int rk4ip_1d_elems(int variant);
 template <typename R> cudaError_t launch_rk4ip_1d(int n, int variant, const Params1D<R> &p, cudaStream_t s);

@@ -33,7 +33,7 @@ EXPORTED = (
     "xsde_integrate_static_scratch", "xsde_adjoint", "xsde_kernel_variants", "xsde_autotune",
     "xsde_batch_create", "xsde_batch_integrate", "xsde_batch_destroy", "xsde_integrate_plain",
     "xsde_integrate_adaptive", "xsde_set_noise_substeps", "xsde_set_scheme",
-    "xsde_set_nonlocal", "xsde_grid_set_basis",
+    "xsde_set_nonlocal", "xsde_grid_set_basis", "xsde_measure_fma_peaks",
 )
 XSDE_BASIS_FOURIER, XSDE_BASIS_COS, XSDE_BASIS_SIN = 0, 1, 2
 XSDE_SCHEME_RK4IP, XSDE_SCHEME_SEMI_IMPLICIT = 0, 1
@@ -122,6 +122,7 @@ def load(path: str = LIB_PATH):
         "xsde_set_scheme": (ctypes.c_int, [vp, ctypes.c_int32]),
         "xsde_set_nonlocal": (ctypes.c_int, [vp, vp]),
         "xsde_grid_set_basis": (ctypes.c_int, [vp, vp]),
+        "xsde_measure_fma_peaks": (ctypes.c_int, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -156,6 +157,13 @@ def xsde_grid_create(npts, xmin, xmax) -> ctypes.c_void_p:
 def xsde_grid_set_basis(grid, basis) -> None:
     """basis: one XSDE_BASIS_* per dimension."""
     _check(load().xsde_grid_set_basis(grid, _arr(ctypes.c_int32, basis)))
+
+
+def xsde_measure_fma_peaks() -> tuple:
+    """(FP32, FP64) FMA throughput of the current device in TFLOP/s."""
+    f32, f64 = ctypes.c_double(), ctypes.c_double()
+    _check(load().xsde_measure_fma_peaks(ctypes.byref(f32), ctypes.byref(f64)))
+    return f32.value, f64.value
 
 
 def xsde_grid_destroy(grid) -> None:
