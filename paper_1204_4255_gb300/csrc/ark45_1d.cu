@@ -74,7 +74,7 @@ template <typename R, int N, int E>
 __global__ void __launch_bounds__(N / E) ark45_1d_kernel(const AdaptiveParams<R> p) {
     using V = cx<R>;
     constexpr int T = N / E;
-    constexpr int BUF = padded_len<N>();
+    constexpr int BUF = line_len<V, N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     tw_t<R> *tws = reinterpret_cast<tw_t<R> *>(smem_raw);
     V *buf = reinterpret_cast<V *>(tws + N);
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(N / E) ark45_1d_kernel(const AdaptiveParams<R>
     V *const sm1[1] = {buf};
     const SyncBlock sync{};
     const TwiddleTable<tw_t<R>> tw{tws};
-    const PaddedLine L{};
+    const LineLayout<V> L{};
     const int t = threadIdx.x;
     const int64_t path = blockIdx.x;
 
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(N / E) ark45_1d_kernel(const AdaptiveParams<R>
 
 template <typename R, int N> cudaError_t ark_launch(const AdaptiveParams<R> &p, cudaStream_t s) {
     constexpr int E = N >= 256 ? 8 : (N == 128 ? 4 : 2), T = N / E;
-    const size_t smem = (size_t)N * sizeof(tw_t<R>) + (size_t)padded_len<N>() * sizeof(cx<R>) + 64 * sizeof(double);
+    const size_t smem = (size_t)N * sizeof(tw_t<R>) + (size_t)line_len<cx<R>, N>() * sizeof(cx<R>) + 64 * sizeof(double);
     auto kern = ark45_1d_kernel<R, N, E>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

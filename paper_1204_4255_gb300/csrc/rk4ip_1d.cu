@@ -73,7 +73,7 @@ template <typename R, int N, int E, int PPC, bool NOISE, int SCHEME = 0, bool NL
 __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R> p) {
     using V = cx<R>;
     constexpr int T = N / E;
-    constexpr int BUF = padded_len<N>();
+    constexpr int BUF = line_len<V, N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     tw_t<R> *tws = reinterpret_cast<tw_t<R> *>(smem_raw);
     const int slot = threadIdx.x / T;
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
     V *const sm1[1] = {bufA};
     const SlotSync<T, PPC> sync{slot};
     const TwiddleTable<tw_t<R>> tw{tws};
-    const PaddedLine L{};
+    const LineLayout<V> L{};
 
     for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = p.tw[i];
     __syncthreads();
@@ -274,43 +274,48 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
             for (int m = 0; m < E; ++m) x[0][m] = y[0][m];
             continue;
         }
-        // a_I = D a, k1 = D N(a)
-        fft<N, E, -1, 2>(x, t, sm2, L, sync, tw);
-        kmul(x);
-        fft<N, E, +1, 2>(x, t, sm2, L, sync, tw);
-        // k2, k3 in real space; x[0] <- a_I + k3, x[1] <- a_I + k1/6 + k2/3 + k3/3
-        if constexpr (NL) {
-            // V_nl of each stage input needs the whole line: two passes over m
-            V w[E];
+        // a_I = D a and k1 = D N(a) (h = 0), then the k2/k3 stage and
+        // D(a_I + k3), D(acc) (h = 1).  The half-step loop stays rolled so the
+        // step's code holds one copy of the two-vector transforms (the
+        // instruction cache keeps the whole step).
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1) {
+                // k2, k3 in real space; x[0] <- a_I + k3, x[1] <- a_I + k1/6 + k2/3 + k3/3
+                if constexpr (NL) {
+                    // V_nl of each stage input needs the whole line: two passes over m
+                    V w[E];
 #pragma unroll
-            for (int m = 0; m < E; ++m) w[m] = caxpy(x[0][m], half, x[1][m]);
-            nonlocal(w, vn);
+                    for (int m = 0; m < E; ++m) w[m] = caxpy(x[0][m], half, x[1][m]);
+                    nonlocal(w, vn);
 #pragma unroll
-            for (int m = 0; m < E; ++m) {
-                const V k2 = apply_N(w[m], with_vnl(pt[m], p.lt.dt, vn[m]), gdt);
-                x[1][m] = caxpy(caxpy(x[0][m], sixth, x[1][m]), third, k2);
-                w[m] = caxpy(x[0][m], half, k2);
+                    for (int m = 0; m < E; ++m) {
+                        const V k2 = apply_N(w[m], with_vnl(pt[m], p.lt.dt, vn[m]), gdt);
+                        x[1][m] = caxpy(caxpy(x[0][m], sixth, x[1][m]), third, k2);
+                        w[m] = caxpy(x[0][m], half, k2);
+                    }
+                    nonlocal(w, vn);
+#pragma unroll
+                    for (int m = 0; m < E; ++m) {
+                        const V k3 = apply_N(w[m], with_vnl(pt[m], p.lt.dt, vn[m]), gdt);
+                        x[1][m] = caxpy(x[1][m], third, k3);
+                        x[0][m] = cadd(x[0][m], k3);
+                    }
+                } else {
+#pragma unroll
+                    for (int m = 0; m < E; ++m) {
+                        const V aI = x[0][m], k1 = x[1][m];
+                        const V k2 = apply_N(caxpy(aI, half, k1), pt[m], gdt);
+                        const V k3 = apply_N(caxpy(aI, half, k2), pt[m], gdt);
+                        x[0][m] = cadd(aI, k3);
+                        x[1][m] = caxpy(caxpy(caxpy(aI, sixth, k1), third, k2), third, k3);
+                    }
+                }
             }
-            nonlocal(w, vn);
-#pragma unroll
-            for (int m = 0; m < E; ++m) {
-                const V k3 = apply_N(w[m], with_vnl(pt[m], p.lt.dt, vn[m]), gdt);
-                x[1][m] = caxpy(x[1][m], third, k3);
-                x[0][m] = cadd(x[0][m], k3);
-            }
-        } else {
-#pragma unroll
-            for (int m = 0; m < E; ++m) {
-                const V aI = x[0][m], k1 = x[1][m];
-                const V k2 = apply_N(caxpy(aI, half, k1), pt[m], gdt);
-                const V k3 = apply_N(caxpy(aI, half, k2), pt[m], gdt);
-                x[0][m] = cadd(aI, k3);
-                x[1][m] = caxpy(caxpy(caxpy(aI, sixth, k1), third, k2), third, k3);
-            }
+            fft<N, E, -1, 2>(x, t, sm2, L, sync, tw);
+            kmul(x);
+            fft<N, E, +1, 2>(x, t, sm2, L, sync, tw);
         }
-        fft<N, E, -1, 2>(x, t, sm2, L, sync, tw);
-        kmul(x);
-        fft<N, E, +1, 2>(x, t, sm2, L, sync, tw);
         // k4 = N(D(a_I + k3)); a <- D(acc) + k4/6
         if constexpr (NL) nonlocal(x[0], vn);
 #pragma unroll
@@ -330,7 +335,7 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
 template <typename R, int N, int E, int PPC, int SCHEME = 0, bool NL = false, bool TRIG = false>
 cudaError_t launch_ppc(const Params1D<R> &p, cudaStream_t s) {
     constexpr int T = N / E;
-    const size_t smem = (size_t)N * sizeof(tw_t<R>) + (size_t)PPC * 2 * padded_len<N>() * sizeof(cx<R>);
+    const size_t smem = (size_t)N * sizeof(tw_t<R>) + (size_t)PPC * 2 * line_len<cx<R>, N>() * sizeof(cx<R>);
     const bool noise = p.lt.noise != NM_NONE;
     auto kern = noise ? rk4ip_1d_kernel<R, N, E, PPC, true, SCHEME, NL, TRIG>
                       : rk4ip_1d_kernel<R, N, E, PPC, false, SCHEME, NL, TRIG>;

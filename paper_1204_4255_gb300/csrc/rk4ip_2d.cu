@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(RowCfg<N1>::THREADS) row_pass_kernel(const Par
     using V = cx<R>;
     using Cfg = RowCfg<N1>;
     constexpr int E = Cfg::E, T = Cfg::T, LINES = Cfg::LINES;
-    constexpr int BUF = padded_len<N1>();
+    constexpr int BUF = line_len<V, N1>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *smem = reinterpret_cast<V *>(smem_raw);
     const int line = threadIdx.x / T;
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(RowCfg<N1>::THREADS) row_pass_kernel(const Par
     double *scratch = reinterpret_cast<double *>(smem + LINES * 2 * BUF);
     const SyncBlock sync{};
     const TwiddleLdg<tw_t<R>> tw{p.tw1};
-    const PaddedLine L{};
+    const LineLayout<V> L{};
 
     const int64_t nrows = p.npaths * (int64_t)p.n0;
     const int64_t row = (int64_t)blockIdx.x * LINES + line;
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
 
 template <typename R, int N1, int MODE> cudaError_t row_launch(const Params2D<R> &p, cudaStream_t s) {
     using Cfg = RowCfg<N1>;
-    const size_t smem = (size_t)Cfg::LINES * 2 * padded_len<N1>() * sizeof(cx<R>) +
+    const size_t smem = (size_t)Cfg::LINES * 2 * line_len<cx<R>, N1>() * sizeof(cx<R>) +
                         (size_t)Cfg::LINES * (Cfg::T / 32 + 1) * 2 * sizeof(double);
     auto kern = row_pass_kernel<R, N1, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

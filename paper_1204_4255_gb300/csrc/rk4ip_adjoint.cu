@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(N / E) rk4ip_adjoint_kernel(const AdjParams<R>
     using V = cx<R>;
     using M = AdjMath<R>;
     constexpr int T = N / E;
-    constexpr int BUF = padded_len<N>();
+    constexpr int BUF = line_len<V, N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     tw_t<R> *tws = reinterpret_cast<tw_t<R> *>(smem_raw);
     V *bufA = reinterpret_cast<V *>(tws + N);
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(N / E) rk4ip_adjoint_kernel(const AdjParams<R>
     V *const sm2[2] = {bufA, bufB};
     const SyncBlock sync{};
     const TwiddleTable<tw_t<R>> tw{tws};
-    const PaddedLine L{};
+    const LineLayout<V> L{};
     const int t = threadIdx.x;
     const int64_t path = blockIdx.x;
 
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(N / E) rk4ip_adjoint_kernel(const AdjParams<R>
 
 template <typename R, int N, int E> cudaError_t adj_launch(const AdjParams<R> &p, cudaStream_t s) {
     constexpr int T = N / E;
-    const size_t smem = (size_t)N * sizeof(tw_t<R>) + (size_t)2 * padded_len<N>() * sizeof(cx<R>) +
+    const size_t smem = (size_t)N * sizeof(tw_t<R>) + (size_t)2 * line_len<cx<R>, N>() * sizeof(cx<R>) +
                         (size_t)2 * ((T + 31) / 32) * sizeof(double);
     auto kern = rk4ip_adjoint_kernel<R, N, E>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
