@@ -358,13 +358,17 @@ int xsde_synchronize(xsde_problem *prob, void *stream);
 
 /* Kernel implementation for this problem, in [0, xsde_kernel_variants(prob)).
  * All variants compute the same scheme; they differ in launch shape:
- *   1D lattices (6 variants): variants 0-3 give each thread 8 points of a
+ *   1D lattices (7 variants): variants 0-3 give each thread 8 points of a
  *     path (radix-8 stages) and one CTA the default number of paths (filling
  *     128 threads; one path for N >= 1024), a half (1), a quarter (2, at least
  *     one path) or twice (3, at most 256 threads) as many; variants 4 and 5
  *     give each thread 4 or 2 points (radix-4 or radix-2 stages, so a path
  *     spreads over more warps) with the default paths per CTA for that shape;
- *     where a bound applies a variant repeats another;
+ *     variant 0 is compiled for 512 resident threads per SM in complex64 (at
+ *     most 128 registers a thread, a few values spilled: more warps to hide
+ *     the exchanges' latency) and with all its registers in complex128;
+ *     variant 6 is variant 0 with the other choice; where a bound applies a
+ *     variant repeats another;
  *   2D and 3D lattices (3 variants): 0 uses the persistent TMA-pipelined
  *     complex64 passes where they apply (lines of 128..1024 points, columns
  *     of 128..512), 1 forces the generic passes, 2 uses the TMA row passes and

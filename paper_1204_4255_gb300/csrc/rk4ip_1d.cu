@@ -69,8 +69,10 @@ template <typename R> __device__ __forceinline__ PointTerm<R> with_vnl(PointTerm
 // of RK4IP (a_I = D a; m <- a_I + N(m)/2 three times from m = a_I;
 // a <- D(2 m - a_I): XMDS2 Sec. 2.5's semi-implicit method with Sec. 2.6)
 // TRIG: a cosine or sine lattice (XMDS2 Sec. 2.1; p.basis 1 / 2), see below
-template <typename R, int N, int E, int PPC, bool NOISE, int SCHEME = 0, bool NL = false, bool TRIG = false>
-__global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R> p) {
+// MINB: CTAs per SM the register allocation must allow (1: no cap)
+template <typename R, int N, int E, int PPC, bool NOISE, int SCHEME = 0, bool NL = false, bool TRIG = false,
+          int MINB = 1>
+__global__ void __launch_bounds__(PPC *(N / E), MINB) rk4ip_1d_kernel(const Params1D<R> p) {
     using V = cx<R>;
     constexpr int T = N / E;
     constexpr int BUF = line_len<V, N>();
@@ -332,13 +334,13 @@ __global__ void __launch_bounds__(PPC *(N / E)) rk4ip_1d_kernel(const Params1D<R
     }
 }
 
-template <typename R, int N, int E, int PPC, int SCHEME = 0, bool NL = false, bool TRIG = false>
+template <typename R, int N, int E, int PPC, int SCHEME = 0, bool NL = false, bool TRIG = false, int MINB = 1>
 cudaError_t launch_ppc(const Params1D<R> &p, cudaStream_t s) {
     constexpr int T = N / E;
     const size_t smem = (size_t)N * sizeof(tw_t<R>) + (size_t)PPC * 2 * line_len<cx<R>, N>() * sizeof(cx<R>);
     const bool noise = p.lt.noise != NM_NONE;
-    auto kern = noise ? rk4ip_1d_kernel<R, N, E, PPC, true, SCHEME, NL, TRIG>
-                      : rk4ip_1d_kernel<R, N, E, PPC, false, SCHEME, NL, TRIG>;
+    auto kern = noise ? rk4ip_1d_kernel<R, N, E, PPC, true, SCHEME, NL, TRIG, MINB>
+                      : rk4ip_1d_kernel<R, N, E, PPC, false, SCHEME, NL, TRIG, MINB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (p.npaths + PPC - 1) / PPC;
@@ -363,7 +365,13 @@ template <typename R, int N> cudaError_t launch_1d_n(int variant, const Params1D
     constexpr int P3 = 2 * P0 * T <= 256 ? 2 * P0 : P0;
     if (p.basis)   // one launch shape for cosine / sine lattices,
         return p.scheme == 1 ? launch_ppc<R, N, 8, P0, 1, false, true>(p, s) : launch_ppc<R, N, 8, P0, 0, false, true>(p, s);
-    if (p.scheme == 1) return launch_ppc<R, N, 8, P0, 1>(p, s);   // for the semi-implicit step
+    // 512 resident threads per SM cap a thread at 128 registers: the complex64
+    // transforms gain more from the extra warps than they lose to the few
+    // spilled values; complex128 keeps all its registers.  Variant 6 takes
+    // the other choice.
+    constexpr int CAP = P0 * T < 512 ? 512 / (P0 * T) : 1;
+    constexpr int MB0 = sizeof(R) == 4 ? CAP : 1, MB6 = sizeof(R) == 4 ? 1 : CAP;
+    if (p.scheme == 1) return launch_ppc<R, N, 8, P0, 1, false, false, MB0>(p, s);   // for the semi-implicit step
     if (p.knl) return launch_ppc<R, N, 8, P0, 0, true>(p, s);       // and for the non-local term
     switch (variant) {
         case 1: return launch_ppc<R, N, 8, P1>(p, s);
@@ -371,7 +379,8 @@ template <typename R, int N> cudaError_t launch_1d_n(int variant, const Params1D
         case 3: return launch_ppc<R, N, 8, P3>(p, s);
         case 4: return launch_ppc<R, N, 4, default_ppc<N, 4>()>(p, s);
         case 5: return launch_ppc<R, N, 2, default_ppc<N, 2>()>(p, s);
-        default: return launch_ppc<R, N, 8, P0>(p, s);
+        case 6: return launch_ppc<R, N, 8, P0, 0, false, false, MB6>(p, s);
+        default: return launch_ppc<R, N, 8, P0, 0, false, false, MB0>(p, s);
     }
 }
 
@@ -418,7 +427,7 @@ template <typename R> cudaError_t launch_rk4ip_1d(int n, int variant, const Para
 
 #if !defined(XSDE_REAL_BITS) || XSDE_REAL_BITS == 32
 #if !defined(XSDE_PART) || XSDE_PART == 0
-int rk4ip_1d_variants() { return 6; }
+int rk4ip_1d_variants() { return 7; }
 int rk4ip_1d_elems(int variant) { return variant == 4 ? 4 : variant == 5 ? 2 : 8; }
 #endif
 XSDE_1D_UNIT(float)

@@ -185,7 +185,7 @@ def test_1d_variants_agree(dtype, n):
     P = make_problem(w, dtype)
     nv = xsde.xsde_kernel_variants(P.prob)
     P.close()
-    assert nv == 6
+    assert nv == 7
     outs = _run_each([w] * nv, dtype, 20, variants=list(range(nv)))
     ref, _, _ = O.run_workload(w, nsteps=20)
     close, tol = (1e-12, 1e-10) if dtype == "c128" else (1e-5, 1e-4)
