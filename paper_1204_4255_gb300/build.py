@@ -21,21 +21,36 @@ LIB = os.path.join(HERE, "libxsde.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 
-# (source, XSDE_REAL_BITS or None[, XSDE_PART])
+# (source, XSDE_REAL_BITS or None[, XSDE_PART]), the longest compiles first
 UNITS = [
+    ("rk4ip_2d.cu", 64, 1),
+    ("rk4ip_2d.cu", 32, 1),
+    ("rk4ip_adjoint.cu", 32),
+    ("rk4ip_adjoint.cu", 64),
+    ("rk4ip_2d.cu", 64, 0),
+    ("rk4ip_2d.cu", 32, 0),
+    ("rk4ip_1d.cu", 32, 6),
+    ("rk4ip_1d.cu", 32, 4),
+    ("rk4ip_1d.cu", 32, 5),
+    ("rk4ip_1d.cu", 32, 7),
+    ("rk4ip_1d.cu", 32, 3),
+    ("rk4ip_1d.cu", 32, 2),
+    ("rk4ip_1d.cu", 32, 1),
+    ("rk4ip_1d.cu", 32, 0),
+    ("rk4ip_1d.cu", 64, 6),
+    ("rk4ip_1d.cu", 64, 7),
+    ("rk4ip_1d.cu", 64, 5),
+    ("rk4ip_1d.cu", 64, 4),
+    ("rk4ip_1d.cu", 64, 3),
+    ("rk4ip_1d.cu", 64, 2),
+    ("rk4ip_1d.cu", 64, 1),
+    ("rk4ip_1d.cu", 64, 0),
+    ("rk4ip_2d_tma.cu", None),
+    ("ark45_1d.cu", None),
+    ("plain.cu", None),
     ("api.cu", None),
     ("rk4ip_0d.cu", None),
     ("noise.cu", None),
-    ("rk4ip_1d.cu", 32, 0),
-    ("rk4ip_1d.cu", 32, 1),
-    ("rk4ip_1d.cu", 64, 0),
-    ("rk4ip_1d.cu", 64, 1),
-    ("rk4ip_2d.cu", 32),
-    ("rk4ip_2d.cu", 64),
-    ("rk4ip_2d_tma.cu", None),
-    ("rk4ip_adjoint.cu", None),
-    ("plain.cu", None),
-    ("ark45_1d.cu", None),
     ("peaks.cu", None),
 ]
 

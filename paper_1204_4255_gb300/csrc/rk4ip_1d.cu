@@ -274,55 +274,55 @@ __global__ void __launch_bounds__(PPC *(N / E), MINB) rk4ip_1d_kernel(const Para
             fft<N, E, +1, 1>(y, t, sm1, L, sync, tw);
 #pragma unroll
             for (int m = 0; m < E; ++m) x[0][m] = y[0][m];
-            continue;
-        }
-        // a_I = D a and k1 = D N(a) (h = 0), then the k2/k3 stage and
-        // D(a_I + k3), D(acc) (h = 1).  The half-step loop stays rolled so the
-        // step's code holds one copy of the two-vector transforms (the
-        // instruction cache keeps the whole step).
+        } else {
+            // a_I = D a and k1 = D N(a) (h = 0), then the k2/k3 stage and
+            // D(a_I + k3), D(acc) (h = 1).  The half-step loop stays rolled so the
+            // step's code holds one copy of the two-vector transforms (the
+            // instruction cache keeps the whole step).
 #pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
-            if (h == 1) {
-                // k2, k3 in real space; x[0] <- a_I + k3, x[1] <- a_I + k1/6 + k2/3 + k3/3
-                if constexpr (NL) {
-                    // V_nl of each stage input needs the whole line: two passes over m
-                    V w[E];
+            for (int h = 0; h < 2; ++h) {
+                if (h == 1) {
+                    // k2, k3 in real space; x[0] <- a_I + k3, x[1] <- a_I + k1/6 + k2/3 + k3/3
+                    if constexpr (NL) {
+                        // V_nl of each stage input needs the whole line: two passes over m
+                        V w[E];
 #pragma unroll
-                    for (int m = 0; m < E; ++m) w[m] = caxpy(x[0][m], half, x[1][m]);
-                    nonlocal(w, vn);
+                        for (int m = 0; m < E; ++m) w[m] = caxpy(x[0][m], half, x[1][m]);
+                        nonlocal(w, vn);
 #pragma unroll
-                    for (int m = 0; m < E; ++m) {
-                        const V k2 = apply_N(w[m], with_vnl(pt[m], p.lt.dt, vn[m]), gdt);
-                        x[1][m] = caxpy(caxpy(x[0][m], sixth, x[1][m]), third, k2);
-                        w[m] = caxpy(x[0][m], half, k2);
-                    }
-                    nonlocal(w, vn);
+                        for (int m = 0; m < E; ++m) {
+                            const V k2 = apply_N(w[m], with_vnl(pt[m], p.lt.dt, vn[m]), gdt);
+                            x[1][m] = caxpy(caxpy(x[0][m], sixth, x[1][m]), third, k2);
+                            w[m] = caxpy(x[0][m], half, k2);
+                        }
+                        nonlocal(w, vn);
 #pragma unroll
-                    for (int m = 0; m < E; ++m) {
-                        const V k3 = apply_N(w[m], with_vnl(pt[m], p.lt.dt, vn[m]), gdt);
-                        x[1][m] = caxpy(x[1][m], third, k3);
-                        x[0][m] = cadd(x[0][m], k3);
-                    }
-                } else {
+                        for (int m = 0; m < E; ++m) {
+                            const V k3 = apply_N(w[m], with_vnl(pt[m], p.lt.dt, vn[m]), gdt);
+                            x[1][m] = caxpy(x[1][m], third, k3);
+                            x[0][m] = cadd(x[0][m], k3);
+                        }
+                    } else {
 #pragma unroll
-                    for (int m = 0; m < E; ++m) {
-                        const V aI = x[0][m], k1 = x[1][m];
-                        const V k2 = apply_N(caxpy(aI, half, k1), pt[m], gdt);
-                        const V k3 = apply_N(caxpy(aI, half, k2), pt[m], gdt);
-                        x[0][m] = cadd(aI, k3);
-                        x[1][m] = caxpy(caxpy(caxpy(aI, sixth, k1), third, k2), third, k3);
+                        for (int m = 0; m < E; ++m) {
+                            const V aI = x[0][m], k1 = x[1][m];
+                            const V k2 = apply_N(caxpy(aI, half, k1), pt[m], gdt);
+                            const V k3 = apply_N(caxpy(aI, half, k2), pt[m], gdt);
+                            x[0][m] = cadd(aI, k3);
+                            x[1][m] = caxpy(caxpy(caxpy(aI, sixth, k1), third, k2), third, k3);
+                        }
                     }
                 }
+                fft<N, E, -1, 2>(x, t, sm2, L, sync, tw);
+                kmul(x);
+                fft<N, E, +1, 2>(x, t, sm2, L, sync, tw);
             }
-            fft<N, E, -1, 2>(x, t, sm2, L, sync, tw);
-            kmul(x);
-            fft<N, E, +1, 2>(x, t, sm2, L, sync, tw);
-        }
-        // k4 = N(D(a_I + k3)); a <- D(acc) + k4/6
-        if constexpr (NL) nonlocal(x[0], vn);
+            // k4 = N(D(a_I + k3)); a <- D(acc) + k4/6
+            if constexpr (NL) nonlocal(x[0], vn);
 #pragma unroll
-        for (int m = 0; m < E; ++m)
-            x[0][m] = caxpy(x[1][m], sixth, apply_N(x[0][m], NL ? with_vnl(pt[m], p.lt.dt, vn[m]) : pt[m], gdt));
+            for (int m = 0; m < E; ++m)
+                x[0][m] = caxpy(x[1][m], sixth, apply_N(x[0][m], NL ? with_vnl(pt[m], p.lt.dt, vn[m]) : pt[m], gdt));
+        }
     }
 
     if (active) {
@@ -398,32 +398,74 @@ template <typename R> cudaError_t launch_rk4ip_1d(int n, int variant, const Para
     }
 }
 
-// Parallel builds: XSDE_REAL_BITS selects one precision and XSDE_PART one half
-// of the lengths per translation unit (part 0 also holds the dispatch).
-#define XSDE_1D_LOW(R)                                                                   \
-    template cudaError_t launch_1d_n<R, 16>(int, const Params1D<R> &, cudaStream_t);     \
-    template cudaError_t launch_1d_n<R, 32>(int, const Params1D<R> &, cudaStream_t);     \
-    template cudaError_t launch_1d_n<R, 64>(int, const Params1D<R> &, cudaStream_t);     \
-    template cudaError_t launch_1d_n<R, 128>(int, const Params1D<R> &, cudaStream_t);    \
-    template cudaError_t launch_1d_n<R, 256>(int, const Params1D<R> &, cudaStream_t);
-#define XSDE_1D_HIGH(X, R)                                                               \
-    X template cudaError_t launch_1d_n<R, 512>(int, const Params1D<R> &, cudaStream_t);  \
-    X template cudaError_t launch_1d_n<R, 1024>(int, const Params1D<R> &, cudaStream_t); \
-    X template cudaError_t launch_1d_n<R, 2048>(int, const Params1D<R> &, cudaStream_t);
-#define XSDE_1D_UNIT(R)                                                                  \
-    XSDE_1D_PART0(R)                                                                     \
-    XSDE_1D_PART1(R)
-
-#if !defined(XSDE_PART)
-#define XSDE_1D_PART0(R) XSDE_1D_LOW(R) template cudaError_t launch_rk4ip_1d<R>(int, int, const Params1D<R> &, cudaStream_t);
-#define XSDE_1D_PART1(R) XSDE_1D_HIGH(, R)
+// Parallel builds: XSDE_REAL_BITS selects one precision and XSDE_PART (0..7)
+// one length, 16 << XSDE_PART, per translation unit; part 0 also holds the
+// dispatch, which sees the other lengths as extern instantiations.
+#define XSDE_1D_N(X, R, N) X template cudaError_t launch_1d_n<R, N>(int, const Params1D<R> &, cudaStream_t);
+#if !defined(XSDE_PART) || XSDE_PART == 0
+#define XSDE_1D_P0(R) XSDE_1D_N(, R, 16)
 #elif XSDE_PART == 0
-#define XSDE_1D_PART0(R) XSDE_1D_HIGH(extern, R) XSDE_1D_LOW(R) template cudaError_t launch_rk4ip_1d<R>(int, int, const Params1D<R> &, cudaStream_t);
-#define XSDE_1D_PART1(R)
+#define XSDE_1D_P0(R) XSDE_1D_N(extern, R, 16)
 #else
-#define XSDE_1D_PART0(R)
-#define XSDE_1D_PART1(R) XSDE_1D_HIGH(, R)
+#define XSDE_1D_P0(R)
 #endif
+#if !defined(XSDE_PART) || XSDE_PART == 1
+#define XSDE_1D_P1(R) XSDE_1D_N(, R, 32)
+#elif XSDE_PART == 0
+#define XSDE_1D_P1(R) XSDE_1D_N(extern, R, 32)
+#else
+#define XSDE_1D_P1(R)
+#endif
+#if !defined(XSDE_PART) || XSDE_PART == 2
+#define XSDE_1D_P2(R) XSDE_1D_N(, R, 64)
+#elif XSDE_PART == 0
+#define XSDE_1D_P2(R) XSDE_1D_N(extern, R, 64)
+#else
+#define XSDE_1D_P2(R)
+#endif
+#if !defined(XSDE_PART) || XSDE_PART == 3
+#define XSDE_1D_P3(R) XSDE_1D_N(, R, 128)
+#elif XSDE_PART == 0
+#define XSDE_1D_P3(R) XSDE_1D_N(extern, R, 128)
+#else
+#define XSDE_1D_P3(R)
+#endif
+#if !defined(XSDE_PART) || XSDE_PART == 4
+#define XSDE_1D_P4(R) XSDE_1D_N(, R, 256)
+#elif XSDE_PART == 0
+#define XSDE_1D_P4(R) XSDE_1D_N(extern, R, 256)
+#else
+#define XSDE_1D_P4(R)
+#endif
+#if !defined(XSDE_PART) || XSDE_PART == 5
+#define XSDE_1D_P5(R) XSDE_1D_N(, R, 512)
+#elif XSDE_PART == 0
+#define XSDE_1D_P5(R) XSDE_1D_N(extern, R, 512)
+#else
+#define XSDE_1D_P5(R)
+#endif
+#if !defined(XSDE_PART) || XSDE_PART == 6
+#define XSDE_1D_P6(R) XSDE_1D_N(, R, 1024)
+#elif XSDE_PART == 0
+#define XSDE_1D_P6(R) XSDE_1D_N(extern, R, 1024)
+#else
+#define XSDE_1D_P6(R)
+#endif
+#if !defined(XSDE_PART) || XSDE_PART == 7
+#define XSDE_1D_P7(R) XSDE_1D_N(, R, 2048)
+#elif XSDE_PART == 0
+#define XSDE_1D_P7(R) XSDE_1D_N(extern, R, 2048)
+#else
+#define XSDE_1D_P7(R)
+#endif
+#if !defined(XSDE_PART) || XSDE_PART == 0
+#define XSDE_1D_DISPATCH(R) template cudaError_t launch_rk4ip_1d<R>(int, int, const Params1D<R> &, cudaStream_t);
+#else
+#define XSDE_1D_DISPATCH(R)
+#endif
+#define XSDE_1D_UNIT(R)                                                                       \
+    XSDE_1D_P0(R) XSDE_1D_P1(R) XSDE_1D_P2(R) XSDE_1D_P3(R) XSDE_1D_P4(R) XSDE_1D_P5(R) XSDE_1D_P6(R) \
+    XSDE_1D_P7(R) XSDE_1D_DISPATCH(R)
 
 #if !defined(XSDE_REAL_BITS) || XSDE_REAL_BITS == 32
 #if !defined(XSDE_PART) || XSDE_PART == 0

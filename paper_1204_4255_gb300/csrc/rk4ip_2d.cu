@@ -434,14 +434,25 @@ template <typename R> cudaError_t launch_col_pass(int mode, const Params2D<R> &p
     }
 }
 
-// XSDE_REAL_BITS selects one precision per translation unit (parallel builds)
+// XSDE_REAL_BITS selects one precision and XSDE_PART the row (0) or column (1)
+// passes per translation unit (parallel builds)
+#if !defined(XSDE_PART) || XSDE_PART == 0
+#define XSDE_2D_ROW(R) template cudaError_t launch_row_pass<R>(int, const Params2D<R> &, cudaStream_t);
+#else
+#define XSDE_2D_ROW(R)
+#endif
+#if !defined(XSDE_PART) || XSDE_PART == 1
+#define XSDE_2D_COL(R) template cudaError_t launch_col_pass<R>(int, const Params2D<R> &, cudaStream_t);
+#else
+#define XSDE_2D_COL(R)
+#endif
 #if !defined(XSDE_REAL_BITS) || XSDE_REAL_BITS == 32
-template cudaError_t launch_row_pass<float>(int, const Params2D<float> &, cudaStream_t);
-template cudaError_t launch_col_pass<float>(int, const Params2D<float> &, cudaStream_t);
+XSDE_2D_ROW(float)
+XSDE_2D_COL(float)
 #endif
 #if !defined(XSDE_REAL_BITS) || XSDE_REAL_BITS == 64
-template cudaError_t launch_row_pass<double>(int, const Params2D<double> &, cudaStream_t);
-template cudaError_t launch_col_pass<double>(int, const Params2D<double> &, cudaStream_t);
+XSDE_2D_ROW(double)
+XSDE_2D_COL(double)
 #endif
 
 }  // namespace xsde

@@ -296,7 +296,12 @@ template <typename R> cudaError_t launch_adjoint_1d(int n, int elems, const AdjP
     }
 }
 
+// XSDE_REAL_BITS selects one precision per translation unit (parallel builds)
+#if !defined(XSDE_REAL_BITS) || XSDE_REAL_BITS == 32
 template cudaError_t launch_adjoint_1d<float>(int, int, const AdjParams<float> &, cudaStream_t);
+#endif
+#if !defined(XSDE_REAL_BITS) || XSDE_REAL_BITS == 64
 template cudaError_t launch_adjoint_1d<double>(int, int, const AdjParams<double> &, cudaStream_t);
+#endif
 
 }  // namespace xsde
