@@ -602,13 +602,12 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
     q.B0 = static_cast<const V *>(p->d_B);
     const int S = sm.every;
     // complex64 lattices the persistent TMA passes cover take the hot modes there
-    // (a cosine / sine dimension 0 keeps the generic column pass)
     bool tma_row = false, tma_col = false;
     CUtensorMap mapA, mapB;
     if constexpr (std::is_same<R, float>::value) {
         if (p->kernel_variant != 1 && (uintptr_t)psi % 16 == 0 && (uintptr_t)p->d_scratch % 16 == 0) {
             tma_row = tma_rows_ok(g.n[1], npaths * g.n[0]);
-            tma_col = p->kernel_variant == 0 && !q.basis0 && tma_col_supported(g.n[0]) && g.n[1] % COL_TMA_C == 0 &&
+            tma_col = p->kernel_variant == 0 && tma_col_supported(g.n[0]) && g.n[1] % COL_TMA_C == 0 &&
                       encode_field_map(&mapA, psi, npaths * g.n[0], g.n[1], g.n[0]) &&
                       encode_field_map(&mapB, p->d_scratch, npaths * g.n[0], g.n[1], g.n[0]);
         }

@@ -289,7 +289,12 @@ template <int N0> struct ColTma {
                                    (THREADS / 32 + 1) * sizeof(double) + NST * sizeof(uint64_t);
 };
 
-template <int N0>
+// TRIG: dimension 0 is a cosine / sine dimension (XMDS2 Sec. 2.1): rows are
+// taken from the tile in the even-odd order of the DCT-II's evaluation by an
+// N0-point FFT (slot s <- row 2s below N0/2, row 2 N0-1-2s above; odd rows
+// negated for the sine basis) and one exchange pairs k with N0-k for
+// U_k = A_k V_k + B_k V_{N0-k} (A in E0, B in p.B0, read through L1)
+template <int N0, bool TRIG = false>
 __global__ void __launch_bounds__(ColTma<N0>::THREADS, ColTma<N0>::CTAS_PER_SM)
     col_pass_tma_kernel(const Params2D<float> p, const __grid_constant__ CUtensorMap mapA,
                         const __grid_constant__ CUtensorMap mapB) {
@@ -366,11 +371,26 @@ __global__ void __launch_bounds__(ColTma<N0>::THREADS, ColTma<N0>::CTAS_PER_SM)
         V *tileb = bufs + (size_t)s * N0 * C;
         V *const sm1[1] = {tileb};
 
+        const bool odd_neg = TRIG && p.basis0 == 2;
+        auto row_of = [&](int j) -> int { return !TRIG ? j : (j < N0 / 2 ? 2 * j : 2 * N0 - 1 - 2 * j); };
         V x[1][E];
 #pragma unroll
-        for (int m = 0; m < E; ++m) x[0][m] = tileb[(t + m * T) * C + c];
+        for (int m = 0; m < E; ++m) {
+            const int j = t + m * T;
+            x[0][m] = tileb[row_of(j) * C + c];
+            if (odd_neg && j >= N0 / 2) x[0][m] = mk<V>(-x[0][m].x, -x[0][m].y);
+        }
         __syncthreads();
         fft<N0, E, -1, 1>(x, t, sm1, L, sync, tw);
+        V xq[E];   // partners V_{N0-k} (TRIG)
+        if constexpr (TRIG) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) tileb[L(t + m * T)] = x[0][m];
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < E; ++m) xq[m] = tileb[L((N0 - t - m * T) & (N0 - 1))];
+            __syncthreads();
+        }
         if (sample && vec == 0) {
             // kinetic energy of a_n: sum_k Re(i L(k)) |F psi|^2 dV/(n0 n1); the
             // dimension-1 factor of exp(L dt/2) already applied is divided out
@@ -382,8 +402,21 @@ __global__ void __launch_bounds__(ColTma<N0>::THREADS, ColTma<N0>::CTAS_PER_SM)
 #pragma unroll
             for (int m = 0; m < E; ++m) {
                 const int kj = t + m * T;
-                const double k0 = p.sm.kscale[0] * (kj < N0 / 2 ? kj : kj - N0);
-                sacc += (p.sm.h0 + p.sm.h2 * (k0 * k0 + k1 * k1)) * (double)cabs2(x[0][m]);
+                if constexpr (TRIG) {
+                    // cosine spectrum from the pair, Parseval weight 2 but at k = 0;
+                    // sine mode N0-1-k sits at k
+                    // (in the field's precision: the sum is accumulated in FP64)
+                    float sn, cs;
+                    sincospif(-(float)kj / (2.0f * N0), &sn, &cs);
+                    const float xr = 0.5f * (cs * (x[0][m].x + xq[m].x) - sn * (x[0][m].y - xq[m].y));
+                    const float xi = 0.5f * (cs * (x[0][m].y + xq[m].y) + sn * (x[0][m].x - xq[m].x));
+                    const double k0 = p.sm.kscale[0] * (p.basis0 == 1 ? kj : N0 - kj);
+                    sacc += (kj == 0 ? 1.0 : 2.0) * (p.sm.h0 + p.sm.h2 * (k0 * k0 + k1 * k1)) *
+                            (double)(xr * xr + xi * xi);
+                } else {
+                    const double k0 = p.sm.kscale[0] * (kj < N0 / 2 ? kj : kj - N0);
+                    sacc += (p.sm.h0 + p.sm.h2 * (k0 * k0 + k1 * k1)) * (double)cabs2(x[0][m]);
+                }
             }
             sacc = warp_sum(sacc * w);
             if ((tid & 31) == 0) scratch[tid >> 5] = sacc;
@@ -400,11 +433,18 @@ __global__ void __launch_bounds__(ColTma<N0>::THREADS, ColTma<N0>::CTAS_PER_SM)
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int j = t + m * T;
-            x[0][m] = cmul_hilo(x[0][m], e0_s[j], e0_s[N0 + j]);
+            if constexpr (TRIG)
+                x[0][m] = cadd(cmul_hilo(x[0][m], e0_s[j], e0_s[N0 + j]),
+                               cmul_hilo(xq[m], __ldg(p.B0 + j), __ldg(p.B0 + N0 + j)));
+            else
+                x[0][m] = cmul_hilo(x[0][m], e0_s[j], e0_s[N0 + j]);
         }
         fft<N0, E, +1, 1>(x, t, sm1, L, sync, tw);
 #pragma unroll
-        for (int m = 0; m < E; ++m) tileb[(t + m * T) * C + c] = x[0][m];
+        for (int m = 0; m < E; ++m) {
+            const int j = t + m * T;
+            tileb[row_of(j) * C + c] = (odd_neg && j >= N0 / 2) ? mk<V>(-x[0][m].x, -x[0][m].y) : x[0][m];
+        }
         fence_proxy_async();
         __syncthreads();
         if (tid == 0) {
@@ -455,7 +495,7 @@ template <int N0>
 cudaError_t col_tma_launch(const Params2D<float> &p, const CUtensorMap &a, const CUtensorMap &b, int grid,
                            cudaStream_t s) {
     using Cfg = ColTma<N0>;
-    auto kern = col_pass_tma_kernel<N0>;
+    auto kern = p.basis0 ? col_pass_tma_kernel<N0, true> : col_pass_tma_kernel<N0, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
     if (e != cudaSuccess) return e;
     const int64_t items = p.npaths * (int64_t)(p.n1 / Cfg::C) * 2;

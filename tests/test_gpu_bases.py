@@ -84,6 +84,22 @@ def test_example3_lattice_matches_the_oracle(shape, dtype, odd):
     _check(got, ref, pp, opp, pq, opq, TOL[dtype])
 
 
+@pytest.mark.parametrize("odd", [False, True])
+@pytest.mark.parametrize("n0", [128, 256, 512])
+def test_example3_tma_column_pass_lengths(n0, odd):
+    """complex64 columns of 128..512 cosine / sine points take the TMA column
+    pass (its pairing step, 8 or 16 points per thread)."""
+    w = W.symmetric_gpe_2d(npaths=2, n0=n0, n1=64, L=6.0, dt=1e-3, nsteps=6)
+    if odd:
+        w.basis = (W.BASIS_SIN, W.BASIS_FOURIER)
+        w.psi0 = w.psi0 * w.coords_of(0)[None, :, None]
+    got, pp, pq = gpu_run(w, "c64", sample_every=3)
+    ref, opp, opq = O.run_workload(w, sample_every=3)
+    _check(got, ref, pp, opp, pq, opq, 1e-4)
+    gen, _, _ = gpu_run(w, "c64", variant=1)                 # generic column pass
+    assert rel_l2(got.reshape(2, -1), gen.reshape(2, -1)) < 1e-5
+
+
 def test_example3_noise_on_the_2d_half_domain():
     w = W.symmetric_gpe_2d(npaths=2, n0=32, n1=64, L=6.0, dt=1e-3, nsteps=16)
     w.basis = (W.BASIS_SIN, W.BASIS_FOURIER)
