@@ -125,17 +125,6 @@ __global__ void __launch_bounds__(PPC *(N / E), MINB) rk4ip_1d_kernel(const Para
         Vs[m] = vtime ? R(0) : potential(p.lt, 1, idx, pj, 0);
     }
 
-    // Long complex64 lines run both transform directions through one copy of
-    // the forward code (the step's code then fits the instruction cache;
-    // measured 4 % faster at 1024 points, slower for short lines and FP64)
-    constexpr bool ONE_FFT = sizeof(R) == 4 && N >= 1024;
-    auto conj_all = [&](V (&v)[2][E]) {
-#pragma unroll
-        for (int iv = 0; iv < 2; ++iv)
-#pragma unroll
-            for (int m = 0; m < E; ++m) v[iv][m].y = -v[iv][m].y;
-    };
-
     // exp(L dt/2) in the lattice's spectral basis, on NV transformed vectors
     auto kmul = [&](auto &v) {
         constexpr int NV = sizeof(v) / sizeof(v[0]);
@@ -324,21 +313,9 @@ __global__ void __launch_bounds__(PPC *(N / E), MINB) rk4ip_1d_kernel(const Para
                         }
                     }
                 }
-                if constexpr (ONE_FFT) {
-                    // D = F^-1 diag F with the inverse taken as conj(F conj(.)): one
-                    // copy of the forward transform serves both directions
-#pragma unroll 1
-                    for (int dir = 0; dir < 2; ++dir) {
-                        if (dir == 1) conj_all(x);
-                        fft<N, E, -1, 2>(x, t, sm2, L, sync, tw);
-                        if (dir == 0) kmul(x);
-                        else conj_all(x);
-                    }
-                } else {
-                    fft<N, E, -1, 2>(x, t, sm2, L, sync, tw);
-                    kmul(x);
-                    fft<N, E, +1, 2>(x, t, sm2, L, sync, tw);
-                }
+                fft<N, E, -1, 2>(x, t, sm2, L, sync, tw);
+                kmul(x);
+                fft<N, E, +1, 2>(x, t, sm2, L, sync, tw);
             }
             // k4 = N(D(a_I + k3)); a <- D(acc) + k4/6
             if constexpr (NL) nonlocal(x[0], vn);
