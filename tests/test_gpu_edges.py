@@ -88,3 +88,13 @@ def test_free_gaussian_matches_the_closed_form(n):
     t = dt * nsteps
     exact = (1 + 1j * t) ** -0.5 * np.exp(-x ** 2 / (2 * (1 + 1j * t)))
     assert rel_l2(got[0], exact) < 1e-12
+
+
+def test_fma_peaks_are_plausible():
+    """The FMA throughput diagnostic: FP32 and FP64 rates of a GB300-class part
+    (dense FMA: tens of TFLOP/s FP32, about one FP64)."""
+    from paper_1204_4255_gb300 import xsde
+    f32, f64 = xsde.xsde_measure_fma_peaks()
+    assert 20.0 < f32 < 200.0, f32
+    assert 0.2 < f64 < 20.0, f64
+    assert xsde.load().xsde_measure_fma_peaks(None, None) == xsde.XSDE_EINVAL

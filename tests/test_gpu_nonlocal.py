@@ -124,3 +124,32 @@ def test_calls_that_reject_the_term():
         P2.set_nonlocal(np.ones(w2.npts, dtype=np.complex128))
     assert e.value.status == xsde.XSDE_EUNSUPPORTED
     P2.close()
+
+
+def test_batch_member_with_the_pair_potential():
+    """A non-local problem inside a graph-captured batch, next to a local one,
+    and the batch re-captured after the kernel is removed."""
+    import torch
+    from paper_1204_4255_gb300 import xsde
+    wa = W.charged_bec(npaths=4, n=256, dt=1e-3, nsteps=20)
+    wb = W.nls_soliton(n=512, nsteps=20)
+    Pa, Pb = make_problem(wa, "c128"), make_problem(wb, "c128")
+    pa = torch.from_numpy(np.ascontiguousarray(wa.psi0)).cuda()
+    pb = torch.from_numpy(np.ascontiguousarray(wb.psi0)).cuda()
+    B = xsde.Batch([(Pa, pa, 0), (Pb, pb, 0)])
+    B.integrate(1e-3, 20)
+    B.synchronize()
+    ref, _, _ = O.run_workload(wa)
+    assert rel_l2(pa.cpu().numpy(), ref) < 1e-10
+    ref, _, _ = O.run_workload(wb)
+    assert rel_l2(pb.cpu().numpy(), ref) < 1e-10
+    Pa.set_nonlocal(None)
+    pa.copy_(torch.from_numpy(np.ascontiguousarray(wa.psi0)))
+    B.integrate(1e-3, 20)
+    B.synchronize()
+    wa.knl = None
+    ref, _, _ = O.run_workload(wa)
+    assert rel_l2(pa.cpu().numpy(), ref) < 1e-10
+    B.close()
+    Pa.close()
+    Pb.close()
