@@ -247,6 +247,15 @@ int xsde_set_nonlocal(xsde_problem *prob, const double *khat);
  * both: XSDE_EINVAL); XSDE_ECUDA on a launch failure. */
 int xsde_measure_fma_peaks(double *fp32_tflops, double *fp64_tflops);
 
+/* Diagnostics: exercise the failure path of the bounded device-side waits
+ * without a fault.  Launches on `stream` one CTA that waits, with the same
+ * bounded mbarrier wait as the TMA pipelines, on a barrier that expects one
+ * arrival nothing makes; after wait_ns nanoseconds (1e3..1e9, else
+ * XSDE_EINVAL) it records the timeout in the problem's error word, so the next
+ * xsde_synchronize reports XSDE_ETIMEOUT (and clears the word; the context
+ * stays usable). */
+int xsde_probe_wait_timeout(xsde_problem *prob, uint64_t wait_ns, void *stream);
+
 /* Register a sampling group for the following xsde_integrate calls.
  * per_path  (device, FP64): [nsamp][npaths][2] = (norm, energy)  if NORM|ENERGY
  * per_point (device, FP64): [nsamp][npts][2]  = (mean |psi|^2, mean |psi|^4)

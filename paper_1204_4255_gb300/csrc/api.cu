@@ -976,6 +976,14 @@ int xsde_set_nonlocal(xsde_problem *p, const double *khat) {
     return XSDE_OK;
 }
 
+int xsde_probe_wait_timeout(xsde_problem *p, uint64_t wait_ns, void *stream) {
+    if (!p) return fail(XSDE_EINVAL, "xsde_probe_wait_timeout: problem is NULL");
+    if (wait_ns < 1000 || wait_ns > 1000000000ull)
+        return fail(XSDE_EINVAL, "xsde_probe_wait_timeout: wait_ns %llu not in [1e3, 1e9]", (unsigned long long)wait_ns);
+    XSDE_CUDA(launch_wait_timeout(wait_ns, p->d_status, static_cast<cudaStream_t>(stream)), "xsde_probe_wait_timeout");
+    return XSDE_OK;
+}
+
 int xsde_measure_fma_peaks(double *fp32_tflops, double *fp64_tflops) {
     if (!fp32_tflops && !fp64_tflops) return fail(XSDE_EINVAL, "xsde_measure_fma_peaks: no output");
     if (measure_fma_peaks(fp32_tflops, fp64_tflops) != 0)

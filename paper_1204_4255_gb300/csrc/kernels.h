@@ -78,6 +78,8 @@ template <typename R> struct Params1D {
 // the default filling 128 threads, a half, a quarter, twice)
 // FP32 / FP64 FMA throughput of the current device (TFLOP/s); 0 or -1
 int measure_fma_peaks(double *fp32_tflops, double *fp64_tflops);
+// one CTA whose bounded wait on a barrier nobody arrives at runs out (ST_TIMEOUT)
+cudaError_t launch_wait_timeout(uint64_t wait_ns, int *status, cudaStream_t s);
 int rk4ip_1d_variants();
 int rk4ip_1d_elems(int variant);
 template <typename R> cudaError_t launch_rk4ip_1d(int n, int variant, const Params1D<R> &p, cudaStream_t s);

@@ -1,9 +1,11 @@
-// peaks.cu -- dense fused-multiply-add throughput of the FP32 and FP64 pipes,
-// the denominators of the roofline fractions of the kernels that are bound by
-// arithmetic rather than by HBM (the whole-run 1D kernel, complex128 passes).
+// peaks.cu -- diagnostics: dense fused-multiply-add throughput of the FP32 and
+// FP64 pipes (the denominators of the roofline fractions of the kernels that
+// are bound by arithmetic rather than by HBM: the whole-run 1D kernel, the
+// complex128 passes), and the failure path of the bounded device-side waits.
 #include <cuda_runtime.h>
 
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace xsde {
 namespace {
@@ -51,7 +53,26 @@ template <typename R> int time_chains(int blocks, int iters, double *tflops) {
     return 0;
 }
 
+// One CTA waits, with the bounded mbarrier wait of the TMA pipelines, on a
+// barrier that expects one arrival nothing makes; when the limit passes it
+// records the timeout in the error word, as a pipeline whose copy never lands.
+__global__ void wait_timeout_kernel(uint64_t wait_ns, int *status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    const bool landed = mbar_wait(&bar, 0u, wait_ns);
+    if (!__syncthreads_and(landed) && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_timeout(uint64_t wait_ns, int *status, cudaStream_t s) {
+    wait_timeout_kernel<<<1, 32, 0, s>>>(wait_ns, status);
+    return cudaGetLastError();
+}
 
 int measure_fma_peaks(double *fp32_tflops, double *fp64_tflops) {
     int dev = 0, sms = 1;

@@ -33,7 +33,7 @@ EXPORTED = (
     "xsde_integrate_static_scratch", "xsde_adjoint", "xsde_kernel_variants", "xsde_autotune",
     "xsde_batch_create", "xsde_batch_integrate", "xsde_batch_destroy", "xsde_integrate_plain",
     "xsde_integrate_adaptive", "xsde_set_noise_substeps", "xsde_set_scheme",
-    "xsde_set_nonlocal", "xsde_grid_set_basis", "xsde_measure_fma_peaks",
+    "xsde_set_nonlocal", "xsde_grid_set_basis", "xsde_measure_fma_peaks", "xsde_probe_wait_timeout",
 )
 XSDE_BASIS_FOURIER, XSDE_BASIS_COS, XSDE_BASIS_SIN = 0, 1, 2
 XSDE_SCHEME_RK4IP, XSDE_SCHEME_SEMI_IMPLICIT = 0, 1
@@ -123,6 +123,7 @@ def load(path: str = LIB_PATH):
         "xsde_set_nonlocal": (ctypes.c_int, [vp, vp]),
         "xsde_grid_set_basis": (ctypes.c_int, [vp, vp]),
         "xsde_measure_fma_peaks": (ctypes.c_int, [vp, vp]),
+        "xsde_probe_wait_timeout": (ctypes.c_int, [vp, ctypes.c_uint64, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -157,6 +158,10 @@ def xsde_grid_create(npts, xmin, xmax) -> ctypes.c_void_p:
 def xsde_grid_set_basis(grid, basis) -> None:
     """basis: one XSDE_BASIS_* per dimension."""
     _check(load().xsde_grid_set_basis(grid, _arr(ctypes.c_int32, basis)))
+
+
+def xsde_probe_wait_timeout(prob, wait_ns: int, stream=None) -> None:
+    _check(load().xsde_probe_wait_timeout(prob, int(wait_ns), _stream_handle(stream)))
 
 
 def xsde_measure_fma_peaks() -> tuple:

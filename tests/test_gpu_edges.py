@@ -98,3 +98,26 @@ def test_fma_peaks_are_plausible():
     assert 20.0 < f32 < 200.0, f32
     assert 0.2 < f64 < 20.0, f64
     assert xsde.load().xsde_measure_fma_peaks(None, None) == xsde.XSDE_EINVAL
+
+
+def test_bounded_wait_timeout_is_reported_and_the_context_stays_usable():
+    """The failure path of the pipelines' bounded mbarrier waits, without a
+    fault: a wait on a barrier nothing arrives at runs out after 20 ms, the next
+    synchronize reports XSDE_ETIMEOUT and clears it, and the problem integrates
+    normally afterwards."""
+    from paper_1204_4255_gb300 import xsde
+    w = W.nls_soliton(n=256, nsteps=20)
+    P = make_problem(w, "c128")
+    xsde.xsde_probe_wait_timeout(P.prob, 20_000_000)
+    with pytest.raises(xsde.XsdeError) as e:
+        P.synchronize()
+    assert e.value.status == xsde.XSDE_ETIMEOUT
+    P.synchronize()
+    got, _, _ = gpu_run(w, "c128", problem=P)
+    ref, _, _ = O.run_workload(w)
+    assert rel_l2(got, ref) < 1e-10
+    for bad in (10, 2_000_000_000):
+        with pytest.raises(xsde.XsdeError) as e:
+            xsde.xsde_probe_wait_timeout(P.prob, bad)
+        assert e.value.status == xsde.XSDE_EINVAL
+    P.close()
