@@ -446,7 +446,9 @@ void xsde_batch_destroy(xsde_batch *batch);
 #define XSDE_KERNEL_KINDS 9
 
 /* Start (enable != 0) or stop recording a CUDA event pair around every kernel
- * launch of this problem, on the launch stream; resets the totals. */
+ * launch of this problem, on the launch stream; resets the totals.  Separately,
+ * with the environment variable XSDE_NVTX=1 every such launch is also wrapped
+ * in an NVTX range named after its kind (for timeline tools). */
 int xsde_profile(xsde_problem *prob, int enable);
 /* Wait for the recorded events and return, per kernel kind, the summed device
  * time in ms and the number of launches since xsde_profile (host arrays of

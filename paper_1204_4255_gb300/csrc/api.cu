@@ -26,6 +26,7 @@
 #include <vector>
 
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/xsde.h"
 #include "kernels.h"
@@ -142,11 +143,29 @@ cudaEvent_t take_event(xsde_problem *p) {
 }
 
 // Launch through `fn` and, when profiling, bracket it with events on stream s.
+// NVTX ranges named after the kernel kinds around every launch, for timeline
+// tools, when the environment sets XSDE_NVTX=1 (read once)
+bool nvtx_enabled() {
+    static const bool on = [] {
+        const char *v = std::getenv("XSDE_NVTX");
+        return v && v[0] == '1';
+    }();
+    return on;
+}
+
+template <typename F> cudaError_t launch_ranged(int kind, F &&fn) {
+    if (!nvtx_enabled()) return fn();
+    nvtxRangePushA(kind >= 0 && kind < XSDE_KERNEL_KINDS ? kKernelNames[kind] : "xsde");
+    cudaError_t e = fn();
+    nvtxRangePop();
+    return e;
+}
+
 template <typename F> cudaError_t timed(xsde_problem *p, int kind, cudaStream_t s, F &&fn) {
-    if (!p->profiling) return fn();
+    if (!p->profiling) return launch_ranged(kind, fn);
     cudaEvent_t a = take_event(p), b = take_event(p);
     if (a) cudaEventRecord(a, s);
-    cudaError_t e = fn();
+    cudaError_t e = launch_ranged(kind, fn);
     if (b) cudaEventRecord(b, s);
     if (a && b) p->marks.push_back({kind, a, b});
     return e;

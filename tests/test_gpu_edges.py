@@ -121,3 +121,28 @@ def test_bounded_wait_timeout_is_reported_and_the_context_stays_usable():
             xsde.xsde_probe_wait_timeout(P.prob, bad)
         assert e.value.status == xsde.XSDE_EINVAL
     P.close()
+
+
+def test_nvtx_ranges_do_not_change_results():
+    """XSDE_NVTX=1 wraps every launch in an NVTX range (read once per
+    process, so the run happens in a child process); the field is the same."""
+    import subprocess
+    import sys
+    code = (
+        "import numpy as np, torch, workloads as W\n"
+        "from gpu_util import gpu_run\n"
+        "w = W.gpe_2d(n=64, nsteps=4)\n"
+        "got, _, _ = gpu_run(w, 'c64')\n"
+        "np.save('out.npy', got)\n")
+    here = os.path.dirname(os.path.abspath(__file__))
+    root = os.path.dirname(here)
+    env = dict(os.environ, XSDE_NVTX="1", PYTHONPATH=os.pathsep.join([root, here]))
+    import tempfile
+    with tempfile.TemporaryDirectory() as tmp:
+        r = subprocess.run([sys.executable, "-c", code], cwd=tmp, env=env, capture_output=True, text=True,
+                           timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        traced = np.load(os.path.join(tmp, "out.npy"))
+    w = W.gpe_2d(n=64, nsteps=4)
+    plain, _, _ = gpu_run(w, "c64")
+    assert np.array_equal(traced, plain)
