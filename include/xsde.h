@@ -145,8 +145,9 @@ int64_t xsde_grid_points(const xsde_grid *grid);
  * dimension 0 of 2D lattices (dimension 1 Fourier); other lattices,
  * xsde_integrate_plain, xsde_integrate_adaptive, xsde_adjoint,
  * xsde_integrate_static_scratch and xsde_set_nonlocal report XSDE_EUNSUPPORTED
- * for such a problem.  Kernel variants are ignored (one launch shape; 2D keeps
- * the generic column pass).  Energy moments use the basis's Parseval weights.
+ * for such a problem.  A 1D cosine / sine problem has one launch shape
+ * (xsde_kernel_variants reports 1); 2D keeps its three variants.  Energy
+ * moments use the basis's Parseval weights.
  * Errors: XSDE_EINVAL for a NULL grid or basis, or an unknown value. */
 #define XSDE_BASIS_FOURIER 0
 #define XSDE_BASIS_COS 1
@@ -204,7 +205,8 @@ int xsde_set_operators(xsde_problem *prob, const xsde_linear_op *L, const xsde_n
  * interaction picture of Sec. 2.6 -- a_I = D(a); m = a_I; m <- a_I + N(m)/2
  * three times; a <- D(2 m - a_I), with D = F^-1 exp(L dt/2) F and N = dt g with
  * the step's noise: deterministic order 2, strong order 1 (Stratonovich).  The
- * semi-implicit step runs on 0D and 1D lattices (one launch shape);
+ * semi-implicit step runs on 0D and 1D lattices (one launch shape: a 1D
+ * problem reports one kernel variant while it is selected);
  * xsde_integrate on other lattices, xsde_integrate_plain and xsde_adjoint
  * report XSDE_EUNSUPPORTED for it. */
 #define XSDE_SCHEME_RK4IP 0
@@ -232,8 +234,8 @@ int xsde_set_noise_substeps(xsde_problem *prob, int32_t substeps);
  * precision.  NULL removes the term.  The call synchronises the device first,
  * so no integration in flight sees a half-written kernel.  Energy moments add
  * the pair energy 1/2 V_nl |psi|^2 dV.  1D lattices only (XSDE_EUNSUPPORTED
- * elsewhere); runs with RK4IP on the default launch shape (the kernel variant
- * is ignored), and xsde_integrate with the semi-implicit scheme,
+ * elsewhere); runs with RK4IP on one launch shape (xsde_kernel_variants
+ * reports 1 while the term is set), and xsde_integrate with the semi-implicit scheme,
  * xsde_integrate_plain, xsde_integrate_adaptive and xsde_adjoint report
  * XSDE_EUNSUPPORTED while it is set.  Non-finite entries: XSDE_EINVAL. */
 int xsde_set_nonlocal(xsde_problem *prob, const double *khat);

@@ -732,7 +732,12 @@ int integrate_on(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t 
 // Number of kernel variants the lattice offers (xsde_set_kernel_variant).
 int variants_for(const xsde_problem *p) {
     switch (p->grid.ndim) {
-        case 1: return rk4ip_1d_variants();
+        // the semi-implicit step, the non-local term and cosine / sine lattices
+        // have one launch shape
+        case 1:
+            return p->scheme != XSDE_SCHEME_RK4IP || p->nonlocal || p->grid.basis[0] != XSDE_BASIS_FOURIER
+                       ? 1
+                       : rk4ip_1d_variants();
         case 2:
         case 3: return 3;
         default: return 1;

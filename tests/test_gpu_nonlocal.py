@@ -153,3 +153,21 @@ def test_batch_member_with_the_pair_potential():
     B.close()
     Pa.close()
     Pb.close()
+
+
+def test_single_launch_shape_is_reported_and_tuned():
+    """While the term is set the problem offers one launch shape; removing it
+    restores the 1D variants."""
+    import torch
+    from paper_1204_4255_gb300 import xsde
+    w = W.charged_bec(npaths=8, n=256, dt=1e-3, nsteps=4)
+    P = make_problem(w, "c64")
+    assert xsde.xsde_kernel_variants(P.prob) == 1
+    psi = torch.from_numpy(np.ascontiguousarray(w.psi0)).to(torch.complex64).cuda()
+    assert P.autotune(psi, w.dt, 4) == 0
+    with pytest.raises(xsde.XsdeError) as e:
+        xsde.xsde_set_kernel_variant(P.prob, 1)
+    assert e.value.status == xsde.XSDE_EINVAL
+    P.set_nonlocal(None)
+    assert xsde.xsde_kernel_variants(P.prob) == 7
+    P.close()
