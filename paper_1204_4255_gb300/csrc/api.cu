@@ -78,6 +78,7 @@ struct xsde_problem {
     int scheme = XSDE_SCHEME_RK4IP;   // see xsde_set_scheme
     void *d_knl = nullptr;    // non-local kernel khat/npts in the problem's precision [npts]
     void *d_B = nullptr;      // cosine / sine dimension 0: the B table of its pair step
+    void *d_Ef[2] = {nullptr, nullptr};   // 2D full-step factors exp(L dt) per dimension (semi-implicit)
     bool nonlocal = false;    // see xsde_set_nonlocal
     uint64_t generation = 0;  // bumped by every call that changes what integrate launches
     void *d_adj = nullptr;    // adjoint checkpoints and stage inputs
@@ -328,6 +329,20 @@ template <typename V> int ensure_tables(xsde_problem *p, double dt, cudaStream_t
         }
         if ((rc = upload<V>(e0, &p->d_E[0], s)) != XSDE_OK) return rc;
         if ((rc = upload<V>(e1, &p->d_E[1], s)) != XSDE_OK) return rc;
+        if (p->scheme == XSDE_SCHEME_SEMI_IMPLICIT) {
+            // a whole step exp(L dt) between two semi-implicit stages (no pairing: Fourier lattices)
+            std::vector<std::complex<double>> f0(g.n[0]), f1(g.n[1]);
+            for (int i = 0; i < g.n[0]; ++i) {
+                const double k = kval(g, 0, i);
+                f0[i] = std::exp((c0 + c2 * (k * k)) * dt) / ((double)g.n[0] * g.n[1]);
+            }
+            for (int i = 0; i < g.n[1]; ++i) {
+                const double k = kval(g, 1, i);
+                f1[i] = std::exp(c2 * (k * k) * dt);
+            }
+            if ((rc = upload<V>(f0, &p->d_Ef[0], s)) != XSDE_OK) return rc;
+            if ((rc = upload<V>(f1, &p->d_Ef[1], s)) != XSDE_OK) return rc;
+        }
     } else if (g.ndim == 3) {
         // exp(L dt/2) = E0(k0) E1(k1) E2(k2); E0 carries exp(c0 dt/2)/(n0 n1 n2)
         for (int d = 0; d < 3; ++d) {
@@ -544,6 +559,63 @@ int run_3d(xsde_problem *p, void *psi, int64_t nsteps, int64_t npaths, uint64_t 
     return XSDE_OK;
 }
 
+// The semi-implicit step on a 2D lattice (XMDS2 Sec. 2.5's semi-implicit
+// method in the interaction picture of Sec. 2.6).  One field, A, row-transformed
+// between passes (SiOp): a step is one row pass (the three midpoint iterations
+// in real space) and one column pass.  Between two steps the half-step factors
+// of D (end of step n) and D (start of step n+1) are applied together as the
+// whole-step exp(L dt); only where the run samples, or ends, is the state
+// brought to a_n itself (half factors, then a multiply-only row pass on the way
+// into the next step).  Two passes over one field per step instead of RK4IP's
+// four over two.
+template <typename R>
+int run_si_2d(xsde_problem *p, Params2D<R> &q, int64_t nsteps, uint64_t step0, cudaStream_t s) {
+    using V = cx<R>;
+    const V *E0h = static_cast<const V *>(p->d_E[0]), *E1h = static_cast<const V *>(p->d_E[1]);
+    const V *E0f = static_cast<const V *>(p->d_Ef[0]), *E1f = static_cast<const V *>(p->d_Ef[1]);
+    const int S = q.sm.every;
+    auto is_sample = [&](int64_t k) { return S > 0 && k % S == 0; };
+    auto row = [&](int op, const V *e1, uint64_t sg, int slot) -> cudaError_t {
+        q.si_op = op;
+        q.E1 = e1;
+        q.sg = sg;
+        q.sample_slot = slot;
+        return timed(p, 4, s, [&] { return launch_row_pass<R>(ROW_SI, q, s); });
+    };
+    auto col = [&](const V *e0) -> cudaError_t {
+        q.E0 = e0;
+        q.sample_slot = -1;
+        return timed(p, 7, s, [&] { return launch_col_pass<R>(COL_SINGLE, q, s); });
+    };
+    auto kinetic = [&](int slot) -> cudaError_t {   // the spectral energy of the state F1 a / n1
+        Params2D<R> k = q;
+        k.B = q.A;
+        k.sample_slot = slot;
+        k.spec_scale = (double)q.n1 * (double)q.n1;
+        return timed(p, 8, s, [&] { return launch_col_pass<R>(COL_SPECTRAL, k, s); });
+    };
+    XSDE_CUDA(row(SI_ENTER, E1h, step0, -1), "row pass");   // state: F1 a_0 / n1
+    bool at_a = true;                                        // state holds a_k (not D a_k)
+    for (int64_t k = 0; k <= nsteps; ++k) {
+        const int slot = is_sample(k) ? (int)(k / S) : -1;
+        if (k == nsteps) {
+            if (slot >= 0) XSDE_CUDA(kinetic(slot), "col pass");
+            XSDE_CUDA(row(SI_EXIT, E1h, step0 + k, slot), "row pass");
+            break;
+        }
+        if (at_a) {   // into step k: F1 a_k / n1 -> F1 D a_k / n1
+            if (slot >= 0) XSDE_CUDA(kinetic(slot), "col pass");
+            XSDE_CUDA(row(SI_MUL, E1h, step0 + k, slot), "row pass");
+            XSDE_CUDA(col(E0h), "col pass");
+        }
+        // step k; then either stop at a_{k+1} or go straight on into step k+1
+        at_a = k + 1 == nsteps || is_sample(k + 1);
+        XSDE_CUDA(row(SI_STEP, at_a ? E1h : E1f, step0 + k, -1), "row pass");
+        XSDE_CUDA(col(at_a ? E0h : E0f), "col pass");
+    }
+    return XSDE_OK;
+}
+
 template <typename R>
 int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t npaths, int64_t path_offset,
                   uint64_t step0, cudaStream_t s) {
@@ -620,6 +692,10 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
     q.basis0 = g.basis[0];
     q.B0 = static_cast<const V *>(p->d_B);
     const int S = sm.every;
+    if (p->scheme == XSDE_SCHEME_SEMI_IMPLICIT) {
+        if (!p->d_Ef[0] || !p->d_Ef[1]) return fail(XSDE_EINVAL, "semi-implicit 2D step: tables missing");
+        return run_si_2d<R>(p, q, nsteps, step0, s);
+    }
     // complex64 lattices the persistent TMA passes cover take the hot modes there
     bool tma_row = false, tma_col = false;
     CUtensorMap mapA, mapB;
@@ -705,8 +781,8 @@ int check_integrate(const char *who, xsde_problem *p, const xsde_vector *psi, do
         return fail(XSDE_EUNSUPPORTED, "%s: at most 65535 paths per call on a 2D lattice", who);
     if (p->samp.every > 0 && nsteps / p->samp.every + 1 > (int64_t)INT32_MAX)
         return fail(XSDE_EINVAL, "%s: too many samples", who);
-    if (p->scheme != XSDE_SCHEME_RK4IP && p->grid.ndim > 1)
-        return fail(XSDE_EUNSUPPORTED, "%s: the semi-implicit scheme runs on 0D and 1D lattices", who);
+    if (p->scheme != XSDE_SCHEME_RK4IP && p->grid.ndim > 2)
+        return fail(XSDE_EUNSUPPORTED, "%s: the semi-implicit scheme runs on 0D, 1D and 2D lattices", who);
     if (p->nonlocal && p->scheme != XSDE_SCHEME_RK4IP)
         return fail(XSDE_EUNSUPPORTED, "%s: the non-local term runs with RK4IP only", who);
     if (any_basis(p->grid)) {
@@ -715,7 +791,7 @@ int check_integrate(const char *who, xsde_problem *p, const xsde_vector *psi, do
         if (g.ndim == 2 && g.basis[1] != XSDE_BASIS_FOURIER)
             return fail(XSDE_EUNSUPPORTED, "%s: on a 2D lattice only dimension 0 may be cosine / sine", who);
         if (g.ndim == 2 && p->scheme != XSDE_SCHEME_RK4IP)
-            return fail(XSDE_EUNSUPPORTED, "%s: the semi-implicit scheme runs on 0D and 1D lattices", who);
+            return fail(XSDE_EUNSUPPORTED, "%s: the semi-implicit scheme on 2D Fourier lattices only", who);
     }
     int dev = -1;
     cudaGetDevice(&dev);
@@ -738,7 +814,7 @@ int variants_for(const xsde_problem *p) {
             return p->scheme != XSDE_SCHEME_RK4IP || p->nonlocal || p->grid.basis[0] != XSDE_BASIS_FOURIER
                        ? 1
                        : rk4ip_1d_variants();
-        case 2:
+        case 2: return p->scheme != XSDE_SCHEME_RK4IP ? 1 : 3;   // the semi-implicit step: one shape
         case 3: return 3;
         default: return 1;
     }
@@ -883,6 +959,8 @@ void xsde_problem_destroy(xsde_problem *p) {
     cudaFree(p->d_tw1d[1]);
     cudaFree(p->d_knl);
     cudaFree(p->d_B);
+    cudaFree(p->d_Ef[0]);
+    cudaFree(p->d_Ef[1]);
     cudaFree(p->d_scratch);
     cudaFree(p->d_adj);
     cudaFree(p->d_status);
@@ -960,7 +1038,10 @@ int xsde_set_scheme(xsde_problem *p, int32_t scheme) {
     if (!p) return fail(XSDE_EINVAL, "xsde_set_scheme: problem is NULL");
     if (scheme != XSDE_SCHEME_RK4IP && scheme != XSDE_SCHEME_SEMI_IMPLICIT)
         return fail(XSDE_EINVAL, "xsde_set_scheme: unknown scheme %d", scheme);
-    if (p->scheme != scheme) ++p->generation;
+    if (p->scheme != scheme) {
+        ++p->generation;
+        p->table_dt = -1.0;   // the semi-implicit 2D step also needs whole-step tables
+    }
     p->scheme = scheme;
     return XSDE_OK;
 }

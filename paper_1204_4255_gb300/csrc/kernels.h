@@ -93,12 +93,22 @@ enum RowMode {
     ROW_STAGE2 = 1,     // A = a_I, B = k1 -> A = u1 = a_I + k3, B = a_I + k1/6 + k2/3 + k3/3
     ROW_STEADY = 2,     // A = D u1, B = D acc -> a' = D acc + N(D u1)/6; A = F1 a', B = F1 N(a')
     ROW_EPILOGUE = 3,   // as STEADY but writes a' in real space to A only
-    ROW_FFT_ONLY = 4    // A (real) -> B = F1 A (for the spectral part of the energy)
+    ROW_FFT_ONLY = 4,   // A (real) -> B = F1 A (for the spectral part of the energy)
+    ROW_SI = 5          // semi-implicit scheme on A alone; sub-operation p.si_op (SiOp)
+};
+// Semi-implicit steps on 2D lattices keep one field, A, row-transformed between
+// passes as F1 u / n1 (u = a_n, or u = D a_n on the way into a step):
+enum SiOp {
+    SI_ENTER = 0,       // A (real a) -> F1 a / n1
+    SI_MUL = 1,         // A *= E1 (sampling: the local terms of F1^-1 A first)
+    SI_STEP = 2,        // A = F1 a_I / n1 -> a_I; m <- a_I + N(m)/2 three times; A = E1 F1 (2m - a_I) / n1
+    SI_EXIT = 3         // A -> real F1^-1 A (sampling: its local terms)
 };
 enum ColMode {
     COL_PROPAGATE = 0,  // A, B -> F0^-1 E0 F0 (A, B)
     COL_SPECTRAL = 1,   // B: accumulate the kinetic energy only (no write)
-    COL_FFT_FWD = 2     // B <- F0 B (the middle transform of a 3D spectral sample)
+    COL_FFT_FWD = 2,    // B <- F0 B (the middle transform of a 3D spectral sample)
+    COL_SINGLE = 3      // A -> F0^-1 E0 F0 A (the semi-implicit scheme's one field)
 };
 
 template <typename R> struct Params2D {
@@ -125,6 +135,8 @@ template <typename R> struct Params2D {
     int ndim = 2;
     int nmid = 1;
     int kinner = 0;
+    int si_op = 0;            // ROW_SI sub-operation (SiOp)
+    double spec_scale = 1.0;  // COL_SPECTRAL: factor on |F0 B|^2 (B = F1 u / n1 needs n1^2)
     // 2D cosine (1) / sine (2) dimension 0 (generic column kernel): rows are
     // gathered in the even-odd order, E0 holds A and B0 B of
     // U_k = A_k V_k + B_k V_{n0-k} (hi [n0] then lo [n0] each)

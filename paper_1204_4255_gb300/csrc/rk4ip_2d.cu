@@ -131,6 +131,60 @@ __global__ void __launch_bounds__(RowCfg<N1>::THREADS) row_pass_kernel(const Par
         }
     };
 
+    if constexpr (MODE == ROW_SI) {
+        // the semi-implicit midpoint step (XMDS2 Sec. 2.5) in the interaction
+        // picture on one field; see SiOp for the state between passes
+        const int op = p.si_op;
+        V y[1][E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) y[0][m] = Arow[t + m * T];
+        auto store_scaled = [&](const V (&f)[E]) {
+            if (active)
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    const V eh = __ldg(p.E1 + t + m * T), el = __ldg(p.E1 + N1 + t + m * T);
+                    Arow[t + m * T] = cmul_hilo(f[m], eh, el);
+                }
+        };
+        if (op == SI_ENTER) {
+            fft<N1, E, -1, 1>(y, t, sm1, L, sync, tw);
+            const R inv = R(1) / R(N1);
+            if (active)
+#pragma unroll
+                for (int m = 0; m < E; ++m) Arow[t + m * T] = cscale(y[0][m], inv);
+            return;
+        }
+        if (op == SI_MUL) {
+            if (sample) {
+                V z[1][E];
+#pragma unroll
+                for (int m = 0; m < E; ++m) z[0][m] = y[0][m];
+                fft<N1, E, +1, 1>(z, t, sm1, L, sync, tw);
+                sample_local(z[0], p.sg);
+            }
+            store_scaled(y[0]);
+            return;
+        }
+        fft<N1, E, +1, 1>(y, t, sm1, L, sync, tw);
+        if (op == SI_EXIT) {
+            if (sample) sample_local(y[0], p.sg);
+            if (active)
+#pragma unroll
+                for (int m = 0; m < E; ++m) Arow[t + m * T] = y[0][m];
+            return;
+        }
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const PointTerm<R> pt = pterm(m, p.sg);
+            V mid = y[0][m];
+            for (int it = 0; it < 3; ++it) mid = caxpy(y[0][m], half, apply_N(mid, pt, gdt));
+            y[0][m] = mk<V>(R(2) * mid.x - y[0][m].x, R(2) * mid.y - y[0][m].y);
+        }
+        fft<N1, E, -1, 1>(y, t, sm1, L, sync, tw);
+        store_scaled(y[0]);
+        return;
+    }
+
     V x[2][E];
     if constexpr (MODE == ROW_PROLOGUE || MODE == ROW_FFT_ONLY) {
 #pragma unroll
@@ -276,7 +330,7 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
         }
         // fields written by propagating row passes already carry the
         // dimension-1 factor of exp(L dt/2); divide its modulus back out
-        const double w = (MODE == COL_SPECTRAL) ? 1.0 : 1.0 / (double)cabs2(p.E1[col]);
+        const double w = (MODE == COL_SPECTRAL) ? p.spec_scale : 1.0 / (double)cabs2(p.E1[col]);
         double s = 0.0;
 #pragma unroll
         for (int m = 0; m < E; ++m) {
@@ -309,7 +363,21 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
         }
     };
 
-    if constexpr (MODE == COL_SPECTRAL || MODE == COL_FFT_FWD) {
+    if constexpr (MODE == COL_SINGLE) {
+        V y[1][E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) y[0][m] = load(p.A, t + m * T);
+        fft<N0, E, -1, 1>(y, t, sm1, L, sync, tw);
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const V eh = __ldg(p.E0 + t + m * T), el = __ldg(p.E0 + N0 + t + m * T);
+            y[0][m] = cmul_hilo(y[0][m], eh, el);
+        }
+        fft<N0, E, +1, 1>(y, t, sm1, L, sync, tw);
+#pragma unroll
+        for (int m = 0; m < E; ++m) store(p.A, t + m * T, y[0][m]);
+        return;
+    } else if constexpr (MODE == COL_SPECTRAL || MODE == COL_FFT_FWD) {
         V y[1][E];
 #pragma unroll
         for (int m = 0; m < E; ++m) y[0][m] = load(p.B, t + m * T);
@@ -375,6 +443,7 @@ template <typename R, int N1> cudaError_t row_mode(int mode, const Params2D<R> &
         case ROW_STEADY: return row_launch<R, N1, ROW_STEADY>(p, s);
         case ROW_EPILOGUE: return row_launch<R, N1, ROW_EPILOGUE>(p, s);
         case ROW_FFT_ONLY: return row_launch<R, N1, ROW_FFT_ONLY>(p, s);
+        case ROW_SI: return row_launch<R, N1, ROW_SI>(p, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -383,7 +452,7 @@ template <typename R, int N0, int MODE> cudaError_t col_launch(const Params2D<R>
     using Cfg = ColCfg<R, N0>;
     const size_t smem = (size_t)2 * N0 * Cfg::C * sizeof(cx<R>) + (Cfg::THREADS / 32 + 1) * sizeof(double);
     auto kern = col_pass_kernel<R, N0, MODE>;
-    if constexpr (MODE != COL_FFT_FWD)
+    if constexpr (MODE != COL_FFT_FWD && MODE != COL_SINGLE)
         if (p.basis0) kern = col_pass_kernel<R, N0, MODE, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -398,6 +467,7 @@ template <typename R, int N0> cudaError_t col_mode(int mode, const Params2D<R> &
         case COL_PROPAGATE: return col_launch<R, N0, COL_PROPAGATE>(p, s);
         case COL_SPECTRAL: return col_launch<R, N0, COL_SPECTRAL>(p, s);
         case COL_FFT_FWD: return col_launch<R, N0, COL_FFT_FWD>(p, s);
+        case COL_SINGLE: return col_launch<R, N0, COL_SINGLE>(p, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -359,7 +359,7 @@ def test_noise_substeps_match_oracle(case, S, dtype):
 
 
 # --------------------------------------------------------------------------- #
-# Semi-implicit midpoint scheme (0D and 1D)                                    #
+# Semi-implicit midpoint scheme (0D, 1D and 2D)                               #
 # --------------------------------------------------------------------------- #
 
 @pytest.mark.parametrize("case,dtype", [("soliton", "c128"), ("soliton", "c64"), ("tw", "c128"), ("tw", "c64"),
@@ -386,10 +386,73 @@ def test_semi_implicit_matches_oracle(case, dtype):
     assert err < tol, err
 
 
-def test_semi_implicit_rejected_on_2d():
+def _si_2d_case(case):
+    if case == "rect":
+        shape = (64, 128)
+    else:
+        shape = (64, 64)
+    w = W.Workload("si2d", shape, (-6.0, -7.0), (6.0, 7.0), 0j, -0.5j, 20.0, W.POT_HARMONIC, (1.0, 0.8), None,
+                   W.NOISE_NONE, 0.0, 0, 1e-3, 30, np.zeros((3,) + shape, dtype=np.complex128))
+    x = w.coords(0)[:, None]
+    y = w.coords(1)[None, :]
+    rng = np.random.default_rng(7)
+    w.psi0 = np.stack([np.exp(-((x - a) ** 2 + (y - b) ** 2) / 2 + 0.3j * x) for a, b in rng.uniform(-1, 1, (3, 2))])
+    w.psi0 = w.psi0.astype(np.complex128)
+    so = 2
+    if case == "noisy":
+        w.noise_kind, w.noise_amp, w.seed = W.NOISE_ADD_COMPLEX, 0.05, 11
+    elif case == "mult":
+        w.noise_kind, w.noise_amp, w.seed = W.NOISE_MUL_REAL, 0.2, 12
+    elif case == "vtable":
+        t = np.arange(w.nsteps)[:, None, None] * w.dt
+        w.V = (0.5 * (x ** 2 + y ** 2) * (1 + 0.3 * np.sin(7 * t))).reshape(w.nsteps, -1)
+        w.pot_kind, so = W.POT_TABLE, 0
+    return w, so
+
+
+@pytest.mark.parametrize("case", ["gpe", "ragged", "noisy", "mult", "vtable", "rect"])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_semi_implicit_2d_matches_oracle(case, dtype):
+    """The 2D semi-implicit schedule (one field, one row and one column pass a
+    step, half-step factors merged between steps) against the oracle's step:
+    fields, per-path norm/energy and per-point moments at every sample."""
+    w, so = _si_2d_case(case)
+    every = 7 if case == "ragged" else 10
+    got, pp, pq = gpu_run(w, dtype, scheme=1, step_offset=so, sample_every=every)
+    grid, ops = O.from_workload(w)
+    ops.scheme = 1
+    ref, opp, opq = O.rk4ip(w.psi0, grid, ops, w.dt, w.nsteps, step0=so, sample_every=every)
+    tol = 1e-10 if dtype == "c128" else 1e-4
+    assert np.max(rel_l2(got.reshape(w.npaths, -1), ref.reshape(w.npaths, -1), axis=1)) < tol
+    assert np.max(np.abs(pp - opp) / np.abs(opp)) < tol
+    assert np.max(np.abs(pq - opq) / np.maximum(np.abs(opq), 1e-3 * np.abs(opq).max())) < tol
+
+
+@pytest.mark.parametrize("nsteps", [0, 1, 2])
+def test_semi_implicit_2d_short_runs(nsteps):
+    w, so = _si_2d_case("gpe")
+    got, pp, _ = gpu_run(w, "c128", scheme=1, nsteps=nsteps, sample_every=1)
+    grid, ops = O.from_workload(w)
+    ops.scheme = 1
+    ref, opp, _ = O.rk4ip(w.psi0, grid, ops, w.dt, nsteps, sample_every=1)
+    assert np.max(rel_l2(got.reshape(w.npaths, -1), ref.reshape(w.npaths, -1), axis=1)) < 1e-12
+    assert np.allclose(pp, opp, rtol=1e-11, atol=0)
+
+
+def test_semi_implicit_2d_bench_lattice_on_sampled_paths():
+    w = W.gpe_2d(npaths=4, nsteps=20)
+    got, _, _ = gpu_run(w, "c64", scheme=1)
+    grid, ops = O.from_workload(w)
+    ops.scheme = 1
+    for p in (0, 3):
+        ref, _, _ = O.rk4ip(w.psi0[p:p + 1], grid, ops, w.dt, w.nsteps, path0=p)
+        assert rel_l2(got[p], ref[0]) < 1e-4, p
+
+
+def test_semi_implicit_rejected_on_3d():
     import torch
     from paper_1204_4255_gb300 import xsde
-    w = W.gpe_2d(n=64, nsteps=1)
+    w = W.gpe_3d(n=16, nsteps=1)
     P = make_problem(w, "c64")
     xsde.xsde_set_scheme(P.prob, xsde.XSDE_SCHEME_SEMI_IMPLICIT)
     psi = torch.from_numpy(w.psi0).to(torch.complex64).cuda()
