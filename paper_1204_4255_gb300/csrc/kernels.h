@@ -100,7 +100,7 @@ enum RowMode {
 // passes as F1 u / n1 (u = a_n, or u = D a_n on the way into a step):
 enum SiOp {
     SI_ENTER = 0,       // A (real a) -> F1 a / n1
-    SI_MUL = 1,         // A *= E1 (sampling: the local terms of F1^-1 A first)
+    SI_MUL = 1,         // A *= n1 E1 (sampling: the local terms of F1^-1 A first)
     SI_STEP = 2,        // A = F1 a_I / n1 -> a_I; m <- a_I + N(m)/2 three times; A = E1 F1 (2m - a_I) / n1
     SI_EXIT = 3         // A -> real F1^-1 A (sampling: its local terms)
 };

@@ -162,6 +162,9 @@ __global__ void __launch_bounds__(RowCfg<N1>::THREADS) row_pass_kernel(const Par
                 fft<N1, E, +1, 1>(z, t, sm1, L, sync, tw);
                 sample_local(z[0], p.sg);
             }
+            // back to the unnormalised F1 a the column pass expects (a power of two: exact)
+#pragma unroll
+            for (int m = 0; m < E; ++m) y[0][m] = cscale(y[0][m], R(N1));
             store_scaled(y[0]);
             return;
         }
