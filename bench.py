@@ -361,6 +361,37 @@ def half_domain_cost(nsteps: int = 200) -> dict:
     return out
 
 
+def semi_implicit_2d_cost(nsteps: int = 100) -> dict:
+    """The bench lattice (64 instances of the 512^2 GPE) advanced by RK4IP and
+    by the semi-implicit step (one field, one row and one column pass a step),
+    complex64 (nsteps steps) and complex128 (nsteps / 10), after a warm-up call."""
+    import torch
+    from paper_1204_4255_gb300 import xsde
+    w = workload(64)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"workload": "2D GPE 512x512 x 64 instances", "unit": UNIT}
+    for scheme, name in ((xsde.XSDE_SCHEME_RK4IP, "rk4ip"), (xsde.XSDE_SCHEME_SEMI_IMPLICIT, "semi_implicit")):
+        for dtype in ("c64", "c128"):
+            P = xsde.Problem(w.n, w.xmin, w.xmax, dtype)
+            P.set_operators(c0=w.c0, c2=w.c2, g=w.gnl, pot_kind=w.pot_kind, omega=(1.0, 1.0, 0.0))
+            xsde.xsde_set_scheme(P.prob, scheme)
+            psi = torch.from_numpy(w.psi0).to(torch.complex64 if dtype == "c64" else torch.complex128).cuda()
+            n = nsteps if dtype == "c64" else max(1, nsteps // 10)
+            P.integrate(psi, w.dt, 5)
+            torch.cuda.synchronize()
+            e0.record()
+            P.integrate(psi, w.dt, n, step_offset=5)
+            e1.record()
+            torch.cuda.synchronize()
+            P.synchronize()
+            ms = e0.elapsed_time(e1)
+            out[f"{name}_{dtype}"] = {"value": 64 * w.npts * n / (ms / 1e3), "ms_per_step": ms / n}
+            P.close()
+            del psi
+    torch.cuda.empty_cache()
+    return out
+
+
 # algorithmic FLOPs per point-step: 8 transforms of 5 log2(N_tot) each, plus
 # the pointwise stage work (about 100), the FFT count convention of the
 # roofline for arithmetic-bound runs
@@ -670,6 +701,7 @@ def run_gpu(args) -> None:
         nonloc = nonlocal_cost() if not args.no_batch else None
         halfdom = half_domain_cost() if not args.no_batch else None
         arith = arithmetic_rooflines(others, plain) if not args.no_batch else None
+        si2d = semi_implicit_2d_cost() if not args.no_batch else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -683,6 +715,7 @@ def run_gpu(args) -> None:
             "norm_check": ok, "adjoint": adj, "batched": bat, "plain_vs_fused": plain,
             "other_workloads": others, "ip_vs_explicit": ipex, "strong_convergence": strong,
             "nonlocal": nonloc, "half_domain": halfdom, "arithmetic_rooflines": arith,
+            "semi_implicit_2d": si2d,
         }
         print(json.dumps(line), flush=True)
     prob.close()
