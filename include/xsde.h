@@ -269,7 +269,8 @@ int xsde_probe_wait_timeout(xsde_problem *prob, uint64_t wait_ns, void *stream);
  * or spec->every == 0 removes the sampling group. */
 int xsde_moments(xsde_problem *prob, const xsde_sampling *spec, double *per_path, double *per_point);
 
-/* Advance psi (all npaths paths, in place) by nsteps RK4IP steps of size dt on
+/* Advance psi (all npaths paths, in place) by nsteps steps of size dt of the
+ * problem's scheme (RK4IP unless xsde_set_scheme chose otherwise) on
  * `stream`, asynchronously.  Global path p of the noise counter is
  * path_offset + local path; the global step index is step_offset + local step
  * (this also selects the row of a time-dependent potential table).  Resuming
