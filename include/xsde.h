@@ -205,12 +205,12 @@ int xsde_set_operators(xsde_problem *prob, const xsde_linear_op *L, const xsde_n
  * interaction picture of Sec. 2.6 -- a_I = D(a); m = a_I; m <- a_I + N(m)/2
  * three times; a <- D(2 m - a_I), with D = F^-1 exp(L dt/2) F and N = dt g with
  * the step's noise: deterministic order 2, strong order 1 (Stratonovich).  The
- * semi-implicit step runs on 0D, 1D and 2D Fourier lattices with one launch
- * shape (the problem reports one kernel variant while it is selected); on 2D
- * lattices it keeps one field and takes one row and one column pass a step,
- * the half-step factors of consecutive steps merged into exp(L dt).
- * xsde_integrate on 3D or cosine / sine 2D lattices, xsde_integrate_plain and
- * xsde_adjoint report XSDE_EUNSUPPORTED for it. */
+ * semi-implicit step runs on 0D to 3D Fourier lattices with one launch shape
+ * (the problem reports one kernel variant while it is selected); on 2D and 3D
+ * lattices it keeps one field and takes one row pass and one (2D) or two (3D)
+ * column passes a step, the half-step factors of consecutive steps merged
+ * into exp(L dt).  xsde_integrate on cosine / sine 2D lattices,
+ * xsde_integrate_plain and xsde_adjoint report XSDE_EUNSUPPORTED for it. */
 #define XSDE_SCHEME_RK4IP 0
 #define XSDE_SCHEME_SEMI_IMPLICIT 1
 int xsde_set_scheme(xsde_problem *prob, int32_t scheme);

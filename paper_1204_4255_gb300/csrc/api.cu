@@ -78,7 +78,7 @@ struct xsde_problem {
     int scheme = XSDE_SCHEME_RK4IP;   // see xsde_set_scheme
     void *d_knl = nullptr;    // non-local kernel khat/npts in the problem's precision [npts]
     void *d_B = nullptr;      // cosine / sine dimension 0: the B table of its pair step
-    void *d_Ef[2] = {nullptr, nullptr};   // 2D full-step factors exp(L dt) per dimension (semi-implicit)
+    void *d_Ef[3] = {nullptr, nullptr, nullptr};   // whole-step factors exp(L dt) per dimension (2D/3D semi-implicit)
     bool nonlocal = false;    // see xsde_set_nonlocal
     uint64_t generation = 0;  // bumped by every call that changes what integrate launches
     void *d_adj = nullptr;    // adjoint checkpoints and stage inputs
@@ -345,14 +345,19 @@ template <typename V> int ensure_tables(xsde_problem *p, double dt, cudaStream_t
         }
     } else if (g.ndim == 3) {
         // exp(L dt/2) = E0(k0) E1(k1) E2(k2); E0 carries exp(c0 dt/2)/(n0 n1 n2)
-        for (int d = 0; d < 3; ++d) {
-            std::vector<std::complex<double>> e(g.n[d]);
-            for (int i = 0; i < g.n[d]; ++i) {
-                const double k = kval(g, d, i);
-                e[i] = d == 0 ? std::exp((c0 + c2 * (k * k)) * (0.5 * dt)) / ((double)g.n[0] * g.n[1] * g.n[2])
-                              : std::exp(c2 * (k * k) * (0.5 * dt));
+        // (and, for the semi-implicit step, the same for the whole step exp(L dt))
+        const int nh = p->scheme == XSDE_SCHEME_SEMI_IMPLICIT ? 2 : 1;
+        for (int h = 0; h < nh; ++h) {
+            const double tau = h == 0 ? 0.5 * dt : dt;
+            for (int d = 0; d < 3; ++d) {
+                std::vector<std::complex<double>> e(g.n[d]);
+                for (int i = 0; i < g.n[d]; ++i) {
+                    const double k = kval(g, d, i);
+                    e[i] = d == 0 ? std::exp((c0 + c2 * (k * k)) * tau) / ((double)g.n[0] * g.n[1] * g.n[2])
+                                  : std::exp(c2 * (k * k) * tau);
+                }
+                if ((rc = upload<V>(e, h == 0 ? &p->d_E[d] : &p->d_Ef[d], s)) != XSDE_OK) return rc;
             }
-            if ((rc = upload<V>(e, &p->d_E[d], s)) != XSDE_OK) return rc;
         }
     }
     p->table_dt = dt;
@@ -461,6 +466,10 @@ int ensure_scratch(xsde_problem *p, size_t need, cudaStream_t s) {
 }
 
 template <typename R>
+int run_si_3d(xsde_problem *p, Params2D<R> &qr, Params2D<R> &q1, Params2D<R> &q0, int64_t nsteps, int64_t npaths,
+              uint64_t step0, cudaStream_t s);
+
+template <typename R>
 int run_3d(xsde_problem *p, void *psi, int64_t nsteps, int64_t npaths, uint64_t step0, const LocalTerm<R> &lt,
            const Sampling &sm, cudaStream_t s) {
     using V = cx<R>;
@@ -494,6 +503,10 @@ int run_3d(xsde_problem *p, void *psi, int64_t nsteps, int64_t npaths, uint64_t 
     q0.tw0 = static_cast<const tw_t<R> *>(p->d_tw[0]);
     q0.E0 = static_cast<const V *>(p->d_E[0]);
     q0.kinner = g.n[2];
+    if (p->scheme == XSDE_SCHEME_SEMI_IMPLICIT) {
+        if (!p->d_Ef[0] || !p->d_Ef[1] || !p->d_Ef[2]) return fail(XSDE_EINVAL, "semi-implicit 3D step: tables missing");
+        return run_si_3d<R>(p, qr, q1, q0, nsteps, npaths, step0, s);
+    }
     // complex64: the persistent TMA passes for the hot modes where they apply
     bool tma_row = false, tma_col1 = false, tma_col0 = false;
     CUtensorMap map1A, map1B, map0A, map0B;
@@ -612,6 +625,68 @@ int run_si_2d(xsde_problem *p, Params2D<R> &q, int64_t nsteps, uint64_t step0, c
         at_a = k + 1 == nsteps || is_sample(k + 1);
         XSDE_CUDA(row(SI_STEP, at_a ? E1h : E1f, step0 + k, -1), "row pass");
         XSDE_CUDA(col(at_a ? E0h : E0f), "col pass");
+    }
+    return XSDE_OK;
+}
+
+// The same schedule on a 3D lattice: the row pass runs along dimension 2, the
+// column passes along dimensions 1 and 0 (each on the one field); the state
+// between passes is F2 u / n2.  The spectral energy needs F1 of the state, taken
+// on a copy in the scratch field.
+template <typename R>
+int run_si_3d(xsde_problem *p, Params2D<R> &qr, Params2D<R> &q1, Params2D<R> &q0, int64_t nsteps, int64_t npaths,
+              uint64_t step0, cudaStream_t s) {
+    using V = cx<R>;
+    const V *Eh[3], *Ef[3];
+    for (int d = 0; d < 3; ++d) {
+        Eh[d] = static_cast<const V *>(p->d_E[d]);
+        Ef[d] = static_cast<const V *>(p->d_Ef[d]);
+    }
+    const int S = qr.sm.every;
+    auto is_sample = [&](int64_t k) { return S > 0 && k % S == 0; };
+    auto row = [&](int op, bool whole, uint64_t sg, int slot) -> cudaError_t {
+        qr.si_op = op;
+        qr.E1 = whole ? Ef[2] : Eh[2];
+        qr.sg = sg;
+        qr.sample_slot = slot;
+        return timed(p, 4, s, [&] { return launch_row_pass<R>(ROW_SI, qr, s); });
+    };
+    auto cols = [&](bool whole) -> cudaError_t {
+        q1.E0 = whole ? Ef[1] : Eh[1];
+        q0.E0 = whole ? Ef[0] : Eh[0];
+        q1.sample_slot = q0.sample_slot = -1;
+        cudaError_t e = timed(p, 7, s, [&] { return launch_col_pass<R>(COL_SINGLE, q1, s); });
+        if (e != cudaSuccess) return e;
+        return timed(p, 7, s, [&] { return launch_col_pass<R>(COL_SINGLE, q0, s); });
+    };
+    auto kinetic = [&](int slot) -> cudaError_t {
+        const size_t bytes = (size_t)npaths * p->grid.npts * sizeof(V);
+        cudaError_t e = cudaMemcpyAsync(q1.B, q1.A, bytes, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+        e = timed(p, 8, s, [&] { return launch_col_pass<R>(COL_FFT_FWD, q1, s); });
+        if (e != cudaSuccess) return e;
+        Params2D<R> k = q0;
+        k.sample_slot = slot;
+        k.spec_scale = (double)qr.n1 * (double)qr.n1;
+        return timed(p, 8, s, [&] { return launch_col_pass<R>(COL_SPECTRAL, k, s); });
+    };
+    XSDE_CUDA(row(SI_ENTER, false, step0, -1), "row pass");
+    bool at_a = true;
+    for (int64_t k = 0; k <= nsteps; ++k) {
+        const int slot = is_sample(k) ? (int)(k / S) : -1;
+        if (k == nsteps) {
+            if (slot >= 0) XSDE_CUDA(kinetic(slot), "col pass");
+            XSDE_CUDA(row(SI_EXIT, false, step0 + k, slot), "row pass");
+            break;
+        }
+        if (at_a) {
+            if (slot >= 0) XSDE_CUDA(kinetic(slot), "col pass");
+            XSDE_CUDA(row(SI_MUL, false, step0 + k, slot), "row pass");
+            XSDE_CUDA(cols(false), "col pass");
+        }
+        at_a = k + 1 == nsteps || is_sample(k + 1);
+        XSDE_CUDA(row(SI_STEP, !at_a, step0 + k, -1), "row pass");
+        XSDE_CUDA(cols(!at_a), "col pass");
     }
     return XSDE_OK;
 }
@@ -781,8 +856,6 @@ int check_integrate(const char *who, xsde_problem *p, const xsde_vector *psi, do
         return fail(XSDE_EUNSUPPORTED, "%s: at most 65535 paths per call on a 2D lattice", who);
     if (p->samp.every > 0 && nsteps / p->samp.every + 1 > (int64_t)INT32_MAX)
         return fail(XSDE_EINVAL, "%s: too many samples", who);
-    if (p->scheme != XSDE_SCHEME_RK4IP && p->grid.ndim > 2)
-        return fail(XSDE_EUNSUPPORTED, "%s: the semi-implicit scheme runs on 0D, 1D and 2D lattices", who);
     if (p->nonlocal && p->scheme != XSDE_SCHEME_RK4IP)
         return fail(XSDE_EUNSUPPORTED, "%s: the non-local term runs with RK4IP only", who);
     if (any_basis(p->grid)) {
@@ -814,8 +887,8 @@ int variants_for(const xsde_problem *p) {
             return p->scheme != XSDE_SCHEME_RK4IP || p->nonlocal || p->grid.basis[0] != XSDE_BASIS_FOURIER
                        ? 1
                        : rk4ip_1d_variants();
-        case 2: return p->scheme != XSDE_SCHEME_RK4IP ? 1 : 3;   // the semi-implicit step: one shape
-        case 3: return 3;
+        case 2:
+        case 3: return p->scheme != XSDE_SCHEME_RK4IP ? 1 : 3;   // the semi-implicit step: one shape
         default: return 1;
     }
 }
@@ -959,8 +1032,7 @@ void xsde_problem_destroy(xsde_problem *p) {
     cudaFree(p->d_tw1d[1]);
     cudaFree(p->d_knl);
     cudaFree(p->d_B);
-    cudaFree(p->d_Ef[0]);
-    cudaFree(p->d_Ef[1]);
+    for (int d = 0; d < 3; ++d) cudaFree(p->d_Ef[d]);
     cudaFree(p->d_scratch);
     cudaFree(p->d_adj);
     cudaFree(p->d_status);

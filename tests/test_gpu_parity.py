@@ -359,7 +359,7 @@ def test_noise_substeps_match_oracle(case, S, dtype):
 
 
 # --------------------------------------------------------------------------- #
-# Semi-implicit midpoint scheme (0D, 1D and 2D)                               #
+# Semi-implicit midpoint scheme (0D, 1D, 2D and 3D)                           #
 # --------------------------------------------------------------------------- #
 
 @pytest.mark.parametrize("case,dtype", [("soliton", "c128"), ("soliton", "c64"), ("tw", "c128"), ("tw", "c64"),
@@ -449,14 +449,28 @@ def test_semi_implicit_2d_bench_lattice_on_sampled_paths():
         assert rel_l2(got[p], ref[0]) < 1e-4, p
 
 
-def test_semi_implicit_rejected_on_3d():
-    import torch
-    from paper_1204_4255_gb300 import xsde
-    w = W.gpe_3d(n=16, nsteps=1)
-    P = make_problem(w, "c64")
-    xsde.xsde_set_scheme(P.prob, xsde.XSDE_SCHEME_SEMI_IMPLICIT)
-    psi = torch.from_numpy(w.psi0).to(torch.complex64).cuda()
-    with pytest.raises(xsde.XsdeError) as e:
-        P.integrate(psi, w.dt, 1)
-    assert e.value.status == xsde.XSDE_EUNSUPPORTED
-    P.close()
+@pytest.mark.parametrize("case", ["gpe", "noisy", "vtable"])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_semi_implicit_3d_matches_oracle(case, dtype):
+    """The semi-implicit schedule on a 3D lattice (row pass along dimension 2,
+    column passes along 1 and 0, one field) against the oracle, with moments."""
+    shape = (16, 32, 16)
+    w = W.Workload("si3d", shape, (-5.0, -6.0, -5.0), (5.0, 6.0, 5.0), 0j, -0.5j, 10.0, W.POT_HARMONIC,
+                   (1.0, 0.7, 1.2), None, W.NOISE_NONE, 0.0, 0, 1e-3, 12, np.zeros((2,) + shape, dtype=np.complex128))
+    x, y, z = np.meshgrid(w.coords(0), w.coords(1), w.coords(2), indexing="ij")
+    w.psi0 = np.stack([np.exp(-((x - a) ** 2 + y ** 2 + (z + a) ** 2) / 2 + 0.2j * y) for a in (0.3, -0.5)])
+    so = 1
+    if case == "noisy":
+        w.noise_kind, w.noise_amp, w.seed = W.NOISE_ADD_COMPLEX, 0.05, 13
+    elif case == "vtable":
+        t = np.arange(w.nsteps)[:, None, None, None] * w.dt
+        w.V = (0.5 * (x ** 2 + y ** 2 + z ** 2) * (1 + 0.4 * np.cos(9 * t))).reshape(w.nsteps, -1)
+        w.pot_kind, so = W.POT_TABLE, 0
+    got, pp, pq = gpu_run(w, dtype, scheme=1, step_offset=so, sample_every=5)
+    grid, ops = O.from_workload(w)
+    ops.scheme = 1
+    ref, opp, opq = O.rk4ip(w.psi0, grid, ops, w.dt, w.nsteps, step0=so, sample_every=5)
+    tol = 1e-10 if dtype == "c128" else 1e-4
+    assert np.max(rel_l2(got.reshape(w.npaths, -1), ref.reshape(w.npaths, -1), axis=1)) < tol
+    assert np.max(np.abs(pp - opp) / np.abs(opp)) < tol
+    assert np.max(np.abs(pq - opq) / np.maximum(np.abs(opq), 1e-3 * np.abs(opq).max())) < tol
