@@ -438,6 +438,39 @@ def test_semi_implicit_free_evolution_is_exact():
     assert np.linalg.norm(out[0] - exact) / np.linalg.norm(exact) < 1e-12
 
 
+def test_semi_implicit_2d_free_flow_and_uniform_potential_are_exact():
+    """On a 2D lattice: g = 0 with a uniform potential v, the semi-implicit
+    step's midpoint iteration solves m = a_I - i v dt m/2 to third order, so
+    one step multiplies by exp(L dt) times the Pade-like factor of the three
+    iterations; with v = 0 the flow is the exact 2D Gaussian spreading."""
+    n, L, t = 128, 20.0, 2.0       # periodic images below 1e-17 at t
+    x = -L + np.arange(n) * (2 * L / n)
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    psi0 = np.exp(-(X ** 2 + Y ** 2) / 2).astype(np.complex128)[None]
+    exact = (1 + 1j * t) ** -1 * np.exp(-(X ** 2 + Y ** 2) / (2 * (1 + 1j * t)))
+    w = W.Workload("free2", (n, n), (-L, -L), (L, L), 0j, -0.5j, 0.0, W.POT_NONE, (0.0, 0.0), None, W.NOISE_NONE,
+                   0.0, 0, 0.25, 8, psi0)
+    grid, ops = O.from_workload(w)
+    ops.scheme = 1
+    out, _, _ = O.rk4ip(w.psi0, grid, ops, w.dt, w.nsteps)
+    assert np.linalg.norm(out[0] - exact) / np.linalg.norm(exact) < 1e-12
+    # uniform potential v: N(u) = -i v dt u, the midpoint iteration m <- a + N(m)/2
+    # three times from m = a gives m = a (1 + z + z^2 + z^3) with z = -i v dt/2,
+    # and the step factor 2 (1 + z + z^2 + z^3) - 1 on top of the free flow
+    v, dt, steps = 0.7, 0.05, 10
+    V = np.full((1, n * n), v)
+    w2 = W.Workload("uni2", (n, n), (-L, -L), (L, L), 0j, -0.5j, 0.0, W.POT_TABLE, (0.0, 0.0), V, W.NOISE_NONE,
+                    0.0, 0, dt, steps, psi0)
+    grid, ops = O.from_workload(w2)
+    ops.scheme = 1
+    out, _, _ = O.rk4ip(w2.psi0, grid, ops, dt, steps)
+    z = -0.5j * v * dt
+    f = 2 * (1 + z + z * z + z ** 3) - 1
+    tt = dt * steps
+    free = (1 + 1j * tt) ** -1 * np.exp(-(X ** 2 + Y ** 2) / (2 * (1 + 1j * tt)))
+    assert np.linalg.norm(out[0] - free * f ** steps) / np.linalg.norm(free) < 1e-12
+
+
 def test_semi_implicit_strong_convergence_on_one_path():
     """Kubo oscillator along one Brownian path per run (substeps): the
     semi-implicit midpoint's error against the exact pathwise solution falls
