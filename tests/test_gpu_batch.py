@@ -233,3 +233,31 @@ def test_batch_rejects_shared_problem_or_field():
         xsde.xsde_set_kernel_variant(P.prob, xsde.xsde_kernel_variants(P.prob))
     P.close()
     Q.close()
+
+
+def test_batch_with_semi_implicit_members():
+    """Semi-implicit 2D and 3D problems inside one graph-captured batch with an
+    RK4IP member: each member equals its oracle run."""
+    import torch
+    from paper_1204_4255_gb300 import xsde
+    w2 = W.gpe_2d(n=64, nsteps=10, npaths=2)
+    w3 = W.gpe_3d(n=16, nsteps=10)
+    w1 = W.nls_soliton(n=256, nsteps=10)
+    members, refs = [], []
+    for w, scheme in ((w2, 1), (w3, 1), (w1, 0)):
+        P = make_problem(w, "c128")
+        xsde.xsde_set_scheme(P.prob, scheme)
+        psi = torch.from_numpy(np.ascontiguousarray(w.psi0)).cuda()
+        members.append((P, psi, 0))
+        grid, ops = O.from_workload(w)
+        ops.scheme = scheme
+        ref, _, _ = O.rk4ip(w.psi0, grid, ops, 1e-4, 10)
+        refs.append(ref)
+    B = xsde.Batch(members)
+    B.integrate(1e-4, 10)
+    B.synchronize()
+    for (P, psi, _), ref in zip(members, refs):
+        assert rel_l2(psi.cpu().numpy(), ref) < 1e-10
+    B.close()
+    for P, _, _ in members:
+        P.close()
