@@ -595,10 +595,25 @@ int run_si_2d(xsde_problem *p, Params2D<R> &q, int64_t nsteps, uint64_t step0, c
         q.sample_slot = slot;
         return timed(p, 4, s, [&] { return launch_row_pass<R>(ROW_SI, q, s); });
     };
+    // complex64 columns of 128..512 points take the persistent TMA column pass
+    // on the one field
+    bool tma_col = false;
+    CUtensorMap mapA;
+    if constexpr (std::is_same<R, float>::value)
+        tma_col = (uintptr_t)q.A % 16 == 0 && tma_col_supported(q.n0) && q.n1 % COL_TMA_C == 0 &&
+                  encode_field_map(&mapA, q.A, q.npaths * q.n0, q.n1, q.n0);
     auto col = [&](const V *e0) -> cudaError_t {
         q.E0 = e0;
         q.sample_slot = -1;
-        return timed(p, 7, s, [&] { return launch_col_pass<R>(COL_SINGLE, q, s); });
+        return timed(p, 7, s, [&] {
+            if constexpr (std::is_same<R, float>::value)
+                if (tma_col) {
+                    Params2D<float> t = q;
+                    t.single_field = 1;
+                    return launch_col_pass_tma(t, mapA, mapA, p->num_sms, s);
+                }
+            return launch_col_pass<R>(COL_SINGLE, q, s);
+        });
     };
     auto kinetic = [&](int slot) -> cudaError_t {   // the spectral energy of the state F1 a / n1
         Params2D<R> k = q;

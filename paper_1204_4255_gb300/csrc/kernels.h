@@ -136,6 +136,7 @@ template <typename R> struct Params2D {
     int nmid = 1;
     int kinner = 0;
     int si_op = 0;            // ROW_SI sub-operation (SiOp)
+    int single_field = 0;     // TMA column pass: propagate A only (the semi-implicit scheme)
     double spec_scale = 1.0;  // COL_SPECTRAL: factor on |F0 B|^2 (B = F1 u / n1 needs n1^2)
     // 2D cosine (1) / sine (2) dimension 0 (generic column kernel): rows are
     // gathered in the even-odd order, E0 holds A and B0 B of

@@ -310,7 +310,9 @@ __global__ void __launch_bounds__(ColTma<N0>::THREADS, ColTma<N0>::CTAS_PER_SM)
     const int tid = threadIdx.x;
     const int c = tid % C, t = tid / C;
     const int tiles = p.n1 / C;
-    const int64_t nitems = p.npaths * (int64_t)tiles * 2;
+    // two fields (A, B) per tile, or A alone for the semi-implicit scheme
+    const int nvec = p.single_field ? 1 : 2;
+    const int64_t nitems = p.npaths * (int64_t)tiles * nvec;
     const int64_t mine = nitems > blockIdx.x ? (nitems - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
     for (int i = tid; i < N0; i += blockDim.x) {
@@ -330,8 +332,8 @@ __global__ void __launch_bounds__(ColTma<N0>::THREADS, ColTma<N0>::CTAS_PER_SM)
     // item -> (vector, path, column tile)
     auto decode = [&](int64_t k, int &vec, int64_t &path, int &tile) {
         const int64_t it = blockIdx.x + k * gridDim.x;
-        vec = (int)(it & 1);
-        const int64_t rest = it >> 1;
+        vec = nvec == 2 ? (int)(it & 1) : 0;
+        const int64_t rest = nvec == 2 ? it >> 1 : it;
         path = rest / tiles;
         tile = (int)(rest - path * tiles);
     };
@@ -498,7 +500,7 @@ cudaError_t col_tma_launch(const Params2D<float> &p, const CUtensorMap &a, const
     auto kern = p.basis0 ? col_pass_tma_kernel<N0, true> : col_pass_tma_kernel<N0, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
     if (e != cudaSuccess) return e;
-    const int64_t items = p.npaths * (int64_t)(p.n1 / Cfg::C) * 2;
+    const int64_t items = p.npaths * (int64_t)(p.n1 / Cfg::C) * (p.single_field ? 1 : 2);
     const int64_t want = (int64_t)grid * Cfg::CTAS_PER_SM;
     const int g = (int)(items < want ? items : want);
     return launch_dependent(kern, g, Cfg::THREADS, Cfg::SMEM, s, p, a, b);

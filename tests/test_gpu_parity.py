@@ -389,6 +389,8 @@ def test_semi_implicit_matches_oracle(case, dtype):
 def _si_2d_case(case):
     if case == "rect":
         shape = (64, 128)
+    elif case == "tma":
+        shape = (128, 64)        # complex64 columns of 128 points: the TMA column pass
     else:
         shape = (64, 64)
     w = W.Workload("si2d", shape, (-6.0, -7.0), (6.0, 7.0), 0j, -0.5j, 20.0, W.POT_HARMONIC, (1.0, 0.8), None,
@@ -410,7 +412,7 @@ def _si_2d_case(case):
     return w, so
 
 
-@pytest.mark.parametrize("case", ["gpe", "ragged", "noisy", "mult", "vtable", "rect"])
+@pytest.mark.parametrize("case", ["gpe", "ragged", "noisy", "mult", "vtable", "rect", "tma"])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_semi_implicit_2d_matches_oracle(case, dtype):
     """The 2D semi-implicit schedule (one field, one row and one column pass a
