@@ -355,12 +355,14 @@ int xsde_integrate_plain(xsde_problem *prob, xsde_vector *psi, double dt, int64_
  * not exceed 16 MiB, e.g. 8 paths of 512x512 complex64, else XSDE_EINVAL) and
  * 192 KiB of tables, rewritten by every call.  The call resolves the arrays'
  * device addresses the first time it runs on a device, so make that first call
- * before any stream capture.  It uploads the tables and waits for `stream`
- * once before launching.  All calls in the process share the arrays: calls
- * that overlap on the GPU (other streams, other threads) race and must not be
- * issued.  The caller still provides psi and any sampling buffers; the problem
- * was created (and its error word allocated) by xsde_problem_create.  Other
- * lattices report XSDE_EUNSUPPORTED. */
+ * before any stream capture.  Every call copies its tables from a host buffer
+ * with cudaMemcpyAsync and waits for `stream` before it launches.  All calls
+ * in the process share the arrays: calls that overlap on the GPU (other
+ * streams, other threads) race and must not be issued.  The caller still
+ * provides psi and any sampling buffers; the problem was created (and its
+ * error word allocated) by xsde_problem_create.  Arguments are checked as by
+ * xsde_integrate.  Other lattices, cosine / sine lattices, the semi-implicit
+ * scheme and a non-local term report XSDE_EUNSUPPORTED. */
 int xsde_integrate_static_scratch(xsde_problem *prob, xsde_vector *psi, double dt, int64_t nsteps,
                                   int64_t npaths, int64_t path_offset, uint64_t step_offset, void *stream);
 

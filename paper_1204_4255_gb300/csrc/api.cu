@@ -1988,33 +1988,26 @@ int static_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int6
 extern "C" int xsde_integrate_static_scratch(xsde_problem *p, xsde_vector *psi, double dt, int64_t nsteps,
                                              int64_t npaths, int64_t path_offset, uint64_t step_offset,
                                              void *stream) {
-    if (!p || !psi) return fail(XSDE_EINVAL, "xsde_integrate_static_scratch: NULL problem or field");
-    if (!p->have_ops) return fail(XSDE_EINVAL, "xsde_integrate_static_scratch: operators not set");
-    if (p->grid.ndim != 2)
-        return fail(XSDE_EUNSUPPORTED, "xsde_integrate_static_scratch: only 2D lattices use a scratch field");
-    if (any_basis(p->grid)) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_static_scratch: Fourier lattices only");
-    if (psi->dtype != p->dtype) return fail(XSDE_EINVAL, "xsde_integrate_static_scratch: field dtype differs");
-    if (!same_lattice(psi->grid, p->grid)) return fail(XSDE_EINVAL, "xsde_integrate_static_scratch: lattice differs");
-    if (npaths != psi->npaths) return fail(XSDE_EINVAL, "xsde_integrate_static_scratch: npaths differs from the field");
-    if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0)
-        return fail(XSDE_EINVAL, "xsde_integrate_static_scratch: dt must be positive and finite, nsteps >= 0");
-    if (path_offset < 0 || path_offset + npaths > (int64_t)UINT32_MAX + 1 ||
-        step_offset + (uint64_t)nsteps + 1 > (uint64_t)UINT32_MAX)
-        return fail(XSDE_EINVAL, "xsde_integrate_static_scratch: global path or step indices exceed 32 bits");
-    if (npaths > 65535) return fail(XSDE_EUNSUPPORTED, "xsde_integrate_static_scratch: at most 65535 paths");
-    if (p->N.pot_kind == XSDE_POT_TABLE && p->N.V_nt > 1 && step_offset + (uint64_t)nsteps > (uint64_t)p->N.V_nt)
-        return fail(XSDE_EINVAL, "xsde_integrate_static_scratch: potential table too short");
+    const char *who = "xsde_integrate_static_scratch";
+    // the argument checks of xsde_integrate (field, dt, 32-bit path and step
+    // counters including noise substeps, potential table rows, current device)
+    int rc = check_integrate(who, p, psi, dt, nsteps, npaths, path_offset, step_offset);
+    if (rc != XSDE_OK) return rc;
+    if (p->grid.ndim != 2) return fail(XSDE_EUNSUPPORTED, "%s: only 2D lattices use a scratch field", who);
+    if (any_basis(p->grid)) return fail(XSDE_EUNSUPPORTED, "%s: Fourier lattices only", who);
+    // the static path runs the RK4IP pass schedule with local terms only
+    if (p->scheme != XSDE_SCHEME_RK4IP)
+        return fail(XSDE_EUNSUPPORTED, "%s: the RK4IP scheme only (the semi-implicit scheme: xsde_integrate)", who);
+    if (p->nonlocal) return fail(XSDE_EUNSUPPORTED, "%s: no non-local term (use xsde_integrate)", who);
     const size_t need = (size_t)npaths * p->grid.npts * elem_bytes(p->dtype);
     if (need > kStaticScratchBytes)
         return fail(XSDE_EINVAL,
-                    "xsde_integrate_static_scratch: the scratch field needs %zu bytes, more than the %zu-byte "
-                    "static buffer (npaths x points x element size); use xsde_integrate or fewer paths per call",
-                    need, kStaticScratchBytes);
-    int dev = -1;
-    XSDE_CUDA(cudaGetDevice(&dev), "xsde_integrate_static_scratch: cudaGetDevice");
-    if (dev != p->device) return fail(XSDE_EINVAL, "xsde_integrate_static_scratch: current device is not the problem's");
+                    "%s: the scratch field needs %zu bytes, more than the %zu-byte static buffer (npaths x points "
+                    "x element size); use xsde_integrate or fewer paths per call",
+                    who, need, kStaticScratchBytes);
+    const int dev = p->device;
     StaticArrays *sa = nullptr;
-    int rc = static_arrays_for(dev, &sa);
+    rc = static_arrays_for(dev, &sa);
     if (rc != XSDE_OK) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     return p->dtype == XSDE_C64
