@@ -297,7 +297,8 @@ int xsde_integrate(xsde_problem *prob, xsde_vector *psi, double dt, int64_t nste
  * 2 GiB) all segments are recomputed at once before the reverse sweep; else one
  * at a time during it, in a buffer of one segment.  Each path runs on one CTA
  * with 8 points per thread, or 4 when the problem's kernel variant is one of
- * the 1D 4- or 2-point shapes (xsde_set_kernel_variant).  Asynchronous on
+ * the 1D 4- or 2-point shapes (xsde_set_kernel_variant) or, at the default
+ * variant 0, when there are fewer paths than SMs.  Asynchronous on
  * `stream`. */
 int xsde_adjoint(xsde_problem *prob, const xsde_vector *psi0, const xsde_vector *target, double dt, int64_t nsteps,
                  int32_t ckpt_every, double *loss, double *dLdV, void *dLdpsi0, void *stream);

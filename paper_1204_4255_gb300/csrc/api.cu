@@ -1304,8 +1304,12 @@ int xsde_adjoint(xsde_problem *p, const xsde_vector *psi0, const xsde_vector *ta
         q.nsteps = nsteps;
         q.K = K;
         q.Etab = static_cast<const V *>(p->d_E[0]);
-        // the problem's points-per-thread shape (the 2-point shape runs as 4)
-        const int elems = rk4ip_1d_elems(p->kernel_variant) == 8 ? 8 : 4;
+        // the problem's points-per-thread shape (the 2-point shape runs as 4);
+        // at the default variant, fewer paths than SMs (one CTA per path, each
+        // step a chain of dependent transforms) spread a path over 4 points per
+        // thread, twice the threads of the 8-point shape
+        int elems = rk4ip_1d_elems(p->kernel_variant) == 8 ? 8 : 4;
+        if (p->kernel_variant == 0 && npaths < p->num_sms) elems = 4;
         q.tw = static_cast<const tw_t<R> *>(elems == 8 ? p->d_tw[0] : p->d_tw1d[0]);
         q.dx = grid_dx(g, 0);
         q.ckpt = static_cast<V *>(p->d_adj);
