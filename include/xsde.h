@@ -146,7 +146,7 @@ int64_t xsde_grid_points(const xsde_grid *grid);
  * xsde_integrate_plain, xsde_integrate_adaptive, xsde_adjoint,
  * xsde_integrate_static_scratch and xsde_set_nonlocal report XSDE_EUNSUPPORTED
  * for such a problem.  A 1D cosine / sine problem has one launch shape
- * (xsde_kernel_variants reports 1); 2D keeps its three variants.  Energy
+ * (xsde_kernel_variants reports 1); 2D keeps its four variants.  Energy
  * moments use the basis's Parseval weights.
  * Errors: XSDE_EINVAL for a NULL grid or basis, or an unknown value. */
 #define XSDE_BASIS_FOURIER 0
@@ -386,10 +386,12 @@ int xsde_synchronize(xsde_problem *prob, void *stream);
  *     the exchanges' latency) and with all its registers in complex128;
  *     variant 6 is variant 0 with the other choice; where a bound applies a
  *     variant repeats another;
- *   2D and 3D lattices (3 variants): 0 uses the persistent TMA-pipelined
- *     complex64 passes where they apply (lines of 128..1024 points, columns
- *     of 128..512), 1 forces the generic passes, 2 uses the TMA row passes and
- *     the generic column passes;
+ *   2D and 3D lattices (4 variants): 0 uses, in complex64, the persistent
+ *     TMA-pipelined row pass (lines of 128..1024 points) and the column pass
+ *     with warp-synchronous two-stage transforms (columns of 128..512 points,
+ *     a multiple of 8 columns; else the TMA column pass), 1 forces the generic
+ *     passes, 2 uses the TMA row passes and the generic column passes, 3 the
+ *     TMA row and TMA column passes;
  *   0D lattices (1 variant).
  * Out-of-range variants report XSDE_EINVAL.  xsde_autotune picks one by
  * timing. */

@@ -45,6 +45,7 @@ UNITS = [
     ("rk4ip_1d.cu", 64, 2),
     ("rk4ip_1d.cu", 64, 1),
     ("rk4ip_1d.cu", 64, 0),
+    ("rk4ip_2d_warp.cu", None),
     ("rk4ip_2d_tma.cu", None),
     ("ark45_1d.cu", None),
     ("plain.cu", None),

@@ -68,6 +68,7 @@ struct xsde_problem {
     double table_dt = -1.0;
     void *d_tw[3] = {nullptr, nullptr, nullptr};
     void *d_tw1d[2] = {nullptr, nullptr};   // 1D: twiddles of the radix-4 and radix-2 plans
+    void *d_tw2[3] = {nullptr, nullptr, nullptr};   // complex64 2D/3D: two-stage plan twiddles (warp column pass)
     void *d_E[3] = {nullptr, nullptr, nullptr};
     void *d_scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -276,6 +277,16 @@ template <typename R, int E = 8> int upload_twiddles(int n, void **dptr, cudaStr
     return upload_raw(tmp, dptr, s);
 }
 
+// twiddles of the two-stage plan of fft2.cuh (E points per lane): entry
+// (r-1) E + j holds w_n^(r j), r in [1, n/E), j in [0, E)
+int upload_twiddles_2stage(int n, int E, void **dptr, cudaStream_t s) {
+    std::vector<float4> tmp((size_t)(n / E - 1) * E);
+    for (int r = 1; r < n / E; ++r)
+        for (int j = 0; j < E; ++j)
+            make_twiddle(std::polar(1.0, -2.0 * M_PI * (double)((long)r * j) / n), &tmp[(size_t)(r - 1) * E + j]);
+    return upload_raw(tmp, dptr, s);
+}
+
 // factor table as [hi[0..n), lo[0..n)]
 template <typename V> int upload(const std::vector<std::complex<double>> &h, void **dptr, cudaStream_t s) {
     const size_t n = h.size();
@@ -292,6 +303,11 @@ template <typename V> int ensure_tables(xsde_problem *p, double dt, cudaStream_t
     int rc;
     for (int d = 0; d < g.ndim; ++d)
         if ((rc = upload_twiddles<decltype(V::x)>(g.n[d], &p->d_tw[d], s)) != XSDE_OK) return rc;
+    if constexpr (std::is_same<V, float2>::value)
+        for (int d = 0; d < g.ndim && g.ndim >= 2; ++d)
+            if (warp_col_supported(g.n[d], WARP_COL_C) &&
+                (rc = upload_twiddles_2stage(g.n[d], warp_col_elems(g.n[d]), &p->d_tw2[d], s)) != XSDE_OK)
+                return rc;
     if (g.ndim == 1) {
         const int n = g.n[0];
         // the radix-4 and radix-2 plans of the 4- and 2-element launch shapes
@@ -441,9 +457,54 @@ bool encode_field_map(CUtensorMap *m, void *base, int64_t rows, int64_t cols, in
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The same view for the warp column pass: box WARP_COL_C x warp_col_box_rows(n0)
+// (64-byte rows), written to shared memory with the 64-byte swizzle.
+bool encode_field_map_warp(CUtensorMap *m, void *base, int64_t rows, int64_t cols, int n0) {
+    auto fn = tensor_map_encoder();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 8};
+    cuuint32_t box[2] = {(cuuint32_t)WARP_COL_C, (cuuint32_t)warp_col_box_rows(n0)};
+    cuuint32_t estr[2] = {1u, 1u};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // The persistent TMA row pass applies to lines of n1 points when the line
 // count fills whole work items.
 bool tma_rows_ok(int n1, int64_t lines) { return tma_row_supported(n1) && lines % (4096 / n1) == 0; }
+
+// Which complex64 pass runs the hot modes (kernel variant, lattice, alignment):
+// PASS_WARP the warp-synchronous column pass of rk4ip_2d_warp.cu, PASS_TMA the
+// persistent passes of rk4ip_2d_tma.cu, PASS_GENERIC the passes of rk4ip_2d.cu.
+// Variant 0 takes the TMA row pass and the warp column pass where they apply
+// (else the TMA, else the generic column pass); 1 is generic throughout; 2 TMA
+// rows with generic columns; 3 the TMA passes for both.
+enum { PASS_GENERIC = 0, PASS_TMA = 1, PASS_WARP = 2 };
+int row_pass_kind(const xsde_problem *p, int n1, int64_t lines) {
+    const int v = p->kernel_variant;
+    if (v == 1) return PASS_GENERIC;
+    return tma_rows_ok(n1, lines) ? PASS_TMA : PASS_GENERIC;
+}
+int col_pass_kind(const xsde_problem *p, int n0, int64_t n1, int basis0) {
+    const int v = p->kernel_variant;
+    if (v == 0 && !basis0 && warp_col_supported(n0, n1)) return PASS_WARP;
+    if ((v == 0 || v == 3) && tma_col_supported(n0) && n1 % COL_TMA_C == 0) return PASS_TMA;
+    return PASS_GENERIC;
+}
+// tensor maps of fields A and B (rows x cols) for a column pass of that kind;
+// a pass whose maps cannot be encoded falls back to the generic kernel
+int col_maps(int kind, CUtensorMap *ma, CUtensorMap *mb, void *A, void *B, int64_t rows, int64_t cols, int n0) {
+    if (kind == PASS_WARP)
+        return encode_field_map_warp(ma, A, rows, cols, n0) && encode_field_map_warp(mb, B, rows, cols, n0)
+                   ? PASS_WARP
+                   : PASS_GENERIC;
+    if (kind == PASS_TMA)
+        return encode_field_map(ma, A, rows, cols, n0) && encode_field_map(mb, B, rows, cols, n0) ? PASS_TMA
+                                                                                                 : PASS_GENERIC;
+    return PASS_GENERIC;
+}
 
 // 3D: per exp(L dt/2) application a row pass along dimension 2 (with E2) and
 // column passes along dimensions 1 and 0 (E1, E0): the three one-dimensional
@@ -507,28 +568,29 @@ int run_3d(xsde_problem *p, void *psi, int64_t nsteps, int64_t npaths, uint64_t 
         if (!p->d_Ef[0] || !p->d_Ef[1] || !p->d_Ef[2]) return fail(XSDE_EINVAL, "semi-implicit 3D step: tables missing");
         return run_si_3d<R>(p, qr, q1, q0, nsteps, npaths, step0, s);
     }
-    // complex64: the persistent TMA passes for the hot modes where they apply
-    bool tma_row = false, tma_col1 = false, tma_col0 = false;
+    // complex64: the warp / TMA passes for the hot modes where they apply
+    int rk = PASS_GENERIC, ck1 = PASS_GENERIC, ck0 = PASS_GENERIC;
     CUtensorMap map1A, map1B, map0A, map0B;
     if constexpr (std::is_same<R, float>::value) {
-        if (p->kernel_variant != 1 && (uintptr_t)psi % 16 == 0 && (uintptr_t)p->d_scratch % 16 == 0) {
-            tma_row = tma_rows_ok(g.n[2], npaths * g.n[0] * g.n[1]);
+        if ((uintptr_t)psi % 16 == 0 && (uintptr_t)p->d_scratch % 16 == 0) {
+            rk = row_pass_kind(p, g.n[2], npaths * g.n[0] * g.n[1]);
             // dimension 1: [npaths n0 n1][n2]; dimension 0: [npaths n0][n1 n2]
-            tma_col1 = p->kernel_variant == 0 && tma_col_supported(g.n[1]) && g.n[2] % COL_TMA_C == 0 &&
-                       encode_field_map(&map1A, psi, npaths * g.n[0] * g.n[1], g.n[2], g.n[1]) &&
-                       encode_field_map(&map1B, p->d_scratch, npaths * g.n[0] * g.n[1], g.n[2], g.n[1]);
-            tma_col0 = p->kernel_variant == 0 && tma_col_supported(g.n[0]) && encode_field_map(&map0A, psi, npaths * g.n[0],
-                                                                       (int64_t)g.n[1] * g.n[2], g.n[0]) &&
-                       encode_field_map(&map0B, p->d_scratch, npaths * g.n[0], (int64_t)g.n[1] * g.n[2], g.n[0]);
+            ck1 = col_maps(col_pass_kind(p, g.n[1], g.n[2], 0), &map1A, &map1B, psi, p->d_scratch,
+                           npaths * g.n[0] * g.n[1], g.n[2], g.n[1]);
+            ck0 = col_maps(col_pass_kind(p, g.n[0], (int64_t)g.n[1] * g.n[2], 0), &map0A, &map0B, psi, p->d_scratch,
+                           npaths * g.n[0], (int64_t)g.n[1] * g.n[2], g.n[0]);
+            q1.tw0w = static_cast<const tw_t<R> *>(p->d_tw2[1]);
+            q0.tw0w = static_cast<const tw_t<R> *>(p->d_tw2[0]);
         }
     }
     auto row = [&](int mode, uint64_t sg, int slot) -> cudaError_t {
         qr.sg = sg;
         qr.sample_slot = slot;
         return timed(p, 2 + mode, s, [&] {
-            if constexpr (std::is_same<R, float>::value)
-                if (tma_row && (mode == ROW_STAGE2 || mode == ROW_STEADY))
+            if constexpr (std::is_same<R, float>::value) {
+                if (rk == PASS_TMA && (mode == ROW_STAGE2 || mode == ROW_STEADY))
                     return launch_row_pass_tma(mode, qr, p->num_sms, s);
+            }
             return launch_row_pass<R>(mode, qr, s);
         });
     };
@@ -536,10 +598,10 @@ int run_3d(xsde_problem *p, void *psi, int64_t nsteps, int64_t npaths, uint64_t 
         q.sample_slot = slot;
         return timed(p, 7 + (mode == COL_SPECTRAL ? 1 : 0), s, [&] {
             if constexpr (std::is_same<R, float>::value) {
-                if (mode == COL_PROPAGATE && &q == &q1 && tma_col1)
-                    return launch_col_pass_tma(q, map1A, map1B, p->num_sms, s);
-                if (mode == COL_PROPAGATE && &q == &q0 && tma_col0)
-                    return launch_col_pass_tma(q, map0A, map0B, p->num_sms, s);
+                const int kind = &q == &q1 ? ck1 : ck0;
+                const CUtensorMap &ma = &q == &q1 ? map1A : map0A, &mb = &q == &q1 ? map1B : map0B;
+                if (mode == COL_PROPAGATE && kind == PASS_WARP) return launch_col_pass_warp(q, ma, mb, p->num_sms, s);
+                if (mode == COL_PROPAGATE && kind == PASS_TMA) return launch_col_pass_tma(q, ma, mb, p->num_sms, s);
             }
             return launch_col_pass<R>(mode, q, s);
         });
@@ -595,22 +657,29 @@ int run_si_2d(xsde_problem *p, Params2D<R> &q, int64_t nsteps, uint64_t step0, c
         q.sample_slot = slot;
         return timed(p, 4, s, [&] { return launch_row_pass<R>(ROW_SI, q, s); });
     };
-    // complex64 columns of 128..512 points take the persistent TMA column pass
+    // complex64 columns of 128..512 points take the warp (or TMA) column pass
     // on the one field
-    bool tma_col = false;
-    CUtensorMap mapA;
-    if constexpr (std::is_same<R, float>::value)
-        tma_col = (uintptr_t)q.A % 16 == 0 && tma_col_supported(q.n0) && q.n1 % COL_TMA_C == 0 &&
-                  encode_field_map(&mapA, q.A, q.npaths * q.n0, q.n1, q.n0);
+    int ck = PASS_GENERIC;
+    CUtensorMap mapA, mapA2;
+    if constexpr (std::is_same<R, float>::value) {
+        if ((uintptr_t)q.A % 16 == 0) {
+            int kind = warp_col_supported(q.n0, q.n1) && p->d_tw2[0] ? PASS_WARP
+                       : tma_col_supported(q.n0) && q.n1 % COL_TMA_C == 0 ? PASS_TMA
+                                                                         : PASS_GENERIC;
+            ck = col_maps(kind, &mapA, &mapA2, q.A, q.A, q.npaths * q.n0, q.n1, q.n0);
+        }
+        q.tw0w = static_cast<const tw_t<R> *>(p->d_tw2[0]);
+    }
     auto col = [&](const V *e0) -> cudaError_t {
         q.E0 = e0;
         q.sample_slot = -1;
         return timed(p, 7, s, [&] {
             if constexpr (std::is_same<R, float>::value)
-                if (tma_col) {
+                if (ck != PASS_GENERIC) {
                     Params2D<float> t = q;
                     t.single_field = 1;
-                    return launch_col_pass_tma(t, mapA, mapA, p->num_sms, s);
+                    return ck == PASS_WARP ? launch_col_pass_warp(t, mapA, mapA, p->num_sms, s)
+                                           : launch_col_pass_tma(t, mapA, mapA, p->num_sms, s);
                 }
             return launch_col_pass<R>(COL_SINGLE, q, s);
         });
@@ -786,32 +855,35 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
         if (!p->d_Ef[0] || !p->d_Ef[1]) return fail(XSDE_EINVAL, "semi-implicit 2D step: tables missing");
         return run_si_2d<R>(p, q, nsteps, step0, s);
     }
-    // complex64 lattices the persistent TMA passes cover take the hot modes there
-    bool tma_row = false, tma_col = false;
+    // complex64 lattices the warp / TMA passes cover take the hot modes there
+    int rk = PASS_GENERIC, ck = PASS_GENERIC;
     CUtensorMap mapA, mapB;
     if constexpr (std::is_same<R, float>::value) {
-        if (p->kernel_variant != 1 && (uintptr_t)psi % 16 == 0 && (uintptr_t)p->d_scratch % 16 == 0) {
-            tma_row = tma_rows_ok(g.n[1], npaths * g.n[0]);
-            tma_col = p->kernel_variant == 0 && tma_col_supported(g.n[0]) && g.n[1] % COL_TMA_C == 0 &&
-                      encode_field_map(&mapA, psi, npaths * g.n[0], g.n[1], g.n[0]) &&
-                      encode_field_map(&mapB, p->d_scratch, npaths * g.n[0], g.n[1], g.n[0]);
+        if ((uintptr_t)psi % 16 == 0 && (uintptr_t)p->d_scratch % 16 == 0) {
+            rk = row_pass_kind(p, g.n[1], npaths * g.n[0]);
+            ck = col_maps(col_pass_kind(p, g.n[0], g.n[1], g.basis[0]), &mapA, &mapB, psi, p->d_scratch,
+                          npaths * g.n[0], g.n[1], g.n[0]);
         }
+        q.tw0w = static_cast<const tw_t<R> *>(p->d_tw2[0]);
     }
     auto row = [&](int mode, uint64_t sg, int slot) -> cudaError_t {
         q.sg = sg;
         q.sample_slot = slot;
         return timed(p, 2 + mode, s, [&] {
-            if constexpr (std::is_same<R, float>::value)
-                if (tma_row && (mode == ROW_STAGE2 || mode == ROW_STEADY))
+            if constexpr (std::is_same<R, float>::value) {
+                if (rk == PASS_TMA && (mode == ROW_STAGE2 || mode == ROW_STEADY))
                     return launch_row_pass_tma(mode, q, p->num_sms, s);
+            }
             return launch_row_pass<R>(mode, q, s);
         });
     };
     auto col = [&](int mode, int slot) -> cudaError_t {
         q.sample_slot = slot;
         return timed(p, 7 + mode, s, [&] {
-            if constexpr (std::is_same<R, float>::value)
-                if (tma_col && mode == COL_PROPAGATE) return launch_col_pass_tma(q, mapA, mapB, p->num_sms, s);
+            if constexpr (std::is_same<R, float>::value) {
+                if (ck == PASS_WARP && mode == COL_PROPAGATE) return launch_col_pass_warp(q, mapA, mapB, p->num_sms, s);
+                if (ck == PASS_TMA && mode == COL_PROPAGATE) return launch_col_pass_tma(q, mapA, mapB, p->num_sms, s);
+            }
             return launch_col_pass<R>(mode, q, s);
         });
     };
@@ -903,7 +975,7 @@ int variants_for(const xsde_problem *p) {
                        ? 1
                        : rk4ip_1d_variants();
         case 2:
-        case 3: return p->scheme != XSDE_SCHEME_RK4IP ? 1 : 3;   // the semi-implicit step: one shape
+        case 3: return p->scheme != XSDE_SCHEME_RK4IP ? 1 : 4;   // the semi-implicit step: one shape
         default: return 1;
     }
 }
@@ -1045,6 +1117,7 @@ void xsde_problem_destroy(xsde_problem *p) {
     }
     cudaFree(p->d_tw1d[0]);
     cudaFree(p->d_tw1d[1]);
+    for (int d = 0; d < 3; ++d) cudaFree(p->d_tw2[d]);
     cudaFree(p->d_knl);
     cudaFree(p->d_B);
     for (int d = 0; d < 3; ++d) cudaFree(p->d_Ef[d]);

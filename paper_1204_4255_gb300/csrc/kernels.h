@@ -143,6 +143,9 @@ template <typename R> struct Params2D {
     // U_k = A_k V_k + B_k V_{n0-k} (hi [n0] then lo [n0] each)
     int basis0 = 0;
     const cx<R> *B0 = nullptr;
+    // twiddles of the two-stage plan of dimension 0 (fft2.cuh), for the warp
+    // column pass: entry (r-1) E + j holds w_n0^(r j), r < n0/E, j < E
+    const tw_t<R> *tw0w = nullptr;
 };
 template <typename R> cudaError_t launch_row_pass(int mode, const Params2D<R> &p, cudaStream_t s);
 template <typename R> cudaError_t launch_col_pass(int mode, const Params2D<R> &p, cudaStream_t s);
@@ -159,6 +162,18 @@ size_t col_tma_box_rows(int n0);
 cudaError_t launch_row_pass_tma(int mode, const Params2D<float> &p, int grid, cudaStream_t s);
 cudaError_t launch_col_pass_tma(const Params2D<float> &p, const CUtensorMap &mapA, const CUtensorMap &mapB, int grid,
                                 cudaStream_t s);
+
+// complex64 column pass with warp-synchronous transforms (rk4ip_2d_warp.cu):
+// COL_PROPAGATE on one or two fields over WARP_COL_C-column tiles with the
+// two-stage plan of fft2.cuh (mapA/mapB: [npaths*n0][n1] 8-byte elements, box
+// WARP_COL_C x warp_col_box_rows(n0), 64-byte swizzle).  `num_sms` sizes the
+// persistent grid.
+constexpr int WARP_COL_C = 8;
+bool warp_col_supported(int n0, int64_t n1);      // column length and columns per slab
+int warp_col_elems(int n0);                       // points per lane (E of the two-stage plan)
+size_t warp_col_box_rows(int n0);
+cudaError_t launch_col_pass_warp(const Params2D<float> &p, const CUtensorMap &mapA, const CUtensorMap &mapB,
+                                 int num_sms, cudaStream_t s);
 
 // --------------------------------------------------------------------------
 // 1D adjoint: loss sum_p 1 - |<target|psi_N>|^2 and dL/dV (rk4ip_adjoint.cu)
