@@ -39,9 +39,9 @@ METRIC = "RK4IP grid-point-steps/s"
 UNIT = "pt-steps/s"
 BYTES_PER_PT_PASS = {"c64": 32, "c128": 64}   # 2 fields in + 2 out per pass
 # DRAM read + write per launch measured by ncu for the default configuration
-# (profiles/tma_passes_512x512x64_c64_full.md); reported only for that
+# (profiles/ summaries of the same kernels); reported only for that
 # configuration and only while the kernels are unchanged since the capture.
-MEASURED_TRAFFIC = {("c64", 64, "col_propagate"): 481.4e6}
+MEASURED_TRAFFIC = {}
 
 
 def _dist():
@@ -218,6 +218,39 @@ def plain_vs_fused(P: int = 64, nsteps: int = 20) -> dict:
         del psi
     torch.cuda.empty_cache()
     return out
+
+
+def c128_figure(P: int = 64, nsteps: int = 10) -> dict:
+    """The bench workload (P instances of 512^2) in complex128 through the fused
+    passes: pt-steps/s over nsteps steps after a warm-up call, as a fraction of
+    the FP64 FMA throughput measured on this GPU (flops model of
+    fft_flops_per_pt_step) and of HBM at 256 B per point-step."""
+    import torch
+    from paper_1204_4255_gb300 import xsde
+    w = workload(P)
+    prob = xsde.Problem(w.n, w.xmin, w.xmax, "c128")
+    prob.set_operators(c0=w.c0, c2=w.c2, g=w.gnl, pot_kind=w.pot_kind, omega=(1.0, 1.0, 0.0))
+    psi = torch.from_numpy(w.psi0).to(torch.complex128).cuda()
+    prob.integrate(psi, w.dt, 2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    prob.integrate(psi, w.dt, nsteps, step_offset=2)
+    e1.record()
+    torch.cuda.synchronize()
+    prob.synchronize()
+    prob.close()
+    del psi
+    torch.cuda.empty_cache()
+    ms = e0.elapsed_time(e1)
+    value = P * w.npts * nsteps / (ms / 1e3)
+    f32, f64 = xsde.xsde_measure_fma_peaks()
+    peak, kind = _peaks()
+    tflops = value * fft_flops_per_pt_step(w.npts) / 1e12
+    return {"value": value, "unit": UNIT, "dtype": "c128", "workload": f"2D GPE 512x512 x {P}, {nsteps} RK4IP steps",
+            "ms_per_rk4ip_step": ms / nsteps, "bound": "alu", "fp64_tflops": tflops, "fp64_fma_peak_tflops": f64,
+            "fp64_frac": tflops / f64, "hbm_frac_at_256B": value * 256 / 1e9 / peak,
+            "flops_model": "8 * 5 log2(N_tot) + 100 per pt-step"}
 
 
 def config_figures() -> dict:
@@ -669,6 +702,18 @@ def run_gpu(args) -> None:
                 "traffic": traffic, "kernel": dom, "peak_source": f"hbm_gbs of {peak_kind}",
                 "launch_ms": dom_ms / dom_n, "algorithmic_bytes_per_launch": alg_bytes,
                 "kernel_share": dom_ms / sum(v[0] for v in prof.values())}
+    # every pass of the steady step against the same bytes model, and the whole
+    # step (4 passes: 128 B / 256 B per point-step) from the bench's own value
+    passes = {}
+    for k in ("col_propagate", "row_stage2", "row_steady"):
+        if k in prof and prof[k][1]:
+            per = prof[k][0] / prof[k][1]
+            ach = BYTES_PER_PT_PASS[dtype] * P * w.npts / (per / 1e3) / 1e9
+            passes[k] = {"launch_ms": per, "achieved": ach, "frac": ach / peak, "launches": prof[k][1]}
+    step_bytes = 4 * BYTES_PER_PT_PASS[dtype]
+    whole_step = {"bytes_per_pt_step": step_bytes, "achieved": value / world * step_bytes / 1e9, "unit": "GB/s",
+                  "peak": peak, "frac": value / world * step_bytes / 1e9 / peak,
+                  "note": "per GPU, from value (every launch of the step, sampling included)"}
 
     # ---- end to end through the public API with host buffers ----------------
     e2e = None
@@ -676,21 +721,22 @@ def run_gpu(args) -> None:
         host_out = torch.empty_like(host_psi).pin_memory()
         host_mom = torch.empty_like(per_path, device="cpu").pin_memory()
         k_e2e = max(2, min(args.steps, 5))
+        prob.integrate_host(host_psi, host_out, w.dt, STEPS_PER_CALL, path_offset=path_offset)   # its device field
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(k_e2e):
-            psi.copy_(host_psi, non_blocking=True)
-            prob.integrate(psi, w.dt, STEPS_PER_CALL, path_offset=path_offset)
-            host_out.copy_(psi, non_blocking=True)
+            # one C-ABI call: host field in, every pass, host field out
+            prob.integrate_host(host_psi, host_out, w.dt, STEPS_PER_CALL, path_offset=path_offset)
             host_mom.copy_(per_path, non_blocking=True)
             torch.cuda.synchronize()
         el = time.perf_counter() - t0
         h2d = host_psi.numel() * host_psi.element_size()
         d2h = h2d + per_path.numel() * 8
         e2e = {"value": pts_per_step * k_e2e * world / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "steps": k_e2e}
+               "d2h_bytes_per_step": d2h, "steps": k_e2e, "call": "xsde_integrate_host (page-locked host field)"}
 
     if rank == 0:
+        c128 = c128_figure(P) if dtype == "c64" and not args.no_batch else None
         cpu = cpu_baseline() if world == 1 and not args.no_cpu_baseline else None
         adj = adjoint_cost("c64") if not args.no_e2e else None
         bat = batched_cost() if not args.no_batch else None
@@ -710,7 +756,8 @@ def run_gpu(args) -> None:
                        "instances_per_gpu": P, "rk4ip_steps_per_bench_step": STEPS_PER_CALL,
                        "sampling": "norm+energy per instance, FP64", "l2": "inputs larger than L2",
                        "parallelism": f"paths sharded over {world} GPU(s), no collective"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roofline, "passes": passes, "whole_step": whole_step, "c128": c128,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "kernels_profiled_step": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]},
             "norm_check": ok, "adjoint": adj, "batched": bat, "plain_vs_fused": plain,
             "other_workloads": others, "ip_vs_explicit": ipex, "strong_convergence": strong,

@@ -280,6 +280,20 @@ int xsde_moments(xsde_problem *prob, const xsde_sampling *spec, double *per_path
 int xsde_integrate(xsde_problem *prob, xsde_vector *psi, double dt, int64_t nsteps, int64_t npaths,
                    int64_t path_offset, uint64_t step_offset, void *stream);
 
+/* As xsde_integrate for a field held in host memory: psi_in (host, npaths x
+ * npts complex values of the problem's dtype, paths outermost) is copied to a
+ * device field the problem owns (allocated on first use, grown when a larger
+ * ensemble comes, freed with the problem), integrated, and copied back to
+ * psi_out (host; may be psi_in) -- the host-to-device copy, every kernel and
+ * the device-to-host copy in stream order on `stream`.  Returns once they are
+ * issued; psi_out holds the result after the stream is synchronised
+ * (xsde_synchronize).  Page-locked host buffers let the copies run
+ * asynchronously; pageable ones make the copies synchronous with the host.
+ * Arguments are checked as by xsde_integrate; a registered sampling group
+ * fills its device buffers as there. */
+int xsde_integrate_host(xsde_problem *prob, const void *psi_in, void *psi_out, int64_t npaths, double dt,
+                        int64_t nsteps, int64_t path_offset, uint64_t step_offset, void *stream);
+
 /* Gradient of a final-state fidelity through the discrete RK4IP scheme
  * (reverse mode through the step of Secs. 2.5-2.6; the workload of
  * Eq. InitialCondition driven by a space-time potential).  For the problem's
@@ -416,8 +430,10 @@ int xsde_autotune(xsde_problem *prob, const xsde_vector *psi, double dt, int64_t
 
 /* A batch advances several independent problems together (the paper's paths
  * and separate simulations, Secs. 2.5 and 3): uneven lattices (0D..3D, any
- * sizes, either precision) in one replay of a CUDA graph whose branches are the
- * members' pass schedules, so their kernels overlap on the GPU.  Each member
+ * sizes, either precision) in one replay of a CUDA graph of the members' pass
+ * schedules.  The 0D / 1D members (one whole-run kernel each) are concurrent
+ * branches; the 2D / 3D members, whose passes each occupy every SM, follow
+ * them one after another.  Each member
  * names its own problem (its operators, sampling group, kernel variant and
  * scratch) and its field; the results equal those of one xsde_integrate per
  * member.  The paper has no batching call: its simulations run one at a time. */

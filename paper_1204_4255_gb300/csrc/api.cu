@@ -89,6 +89,8 @@ struct xsde_problem {
     void *d_plain = nullptr;  // four work fields
     size_t plain_bytes = 0;
     void *d_plain_E = nullptr;  // exp(L dt/2)/npts at every k
+    void *d_hostfield = nullptr;  // device copy of a host field (xsde_integrate_host)
+    size_t hostfield_bytes = 0;
     double plain_dt = -1.0;
     uint64_t plain_gen = ~0ull;
     // launch profiling: CUDA events around every kernel launch of this problem
@@ -1126,6 +1128,7 @@ void xsde_problem_destroy(xsde_problem *p) {
     cudaFree(p->d_status);
     cudaFree(p->d_plain);
     cudaFree(p->d_plain_E);
+    cudaFree(p->d_hostfield);
     plain_plan_destroy(p->plain);
     delete p;
 }
@@ -1181,6 +1184,33 @@ int xsde_integrate(xsde_problem *p, xsde_vector *psi, double dt, int64_t nsteps,
     const int rc = check_integrate("xsde_integrate", p, psi, dt, nsteps, npaths, path_offset, step_offset);
     if (rc != XSDE_OK) return rc;
     return integrate_on(p, psi->data, dt, nsteps, npaths, path_offset, step_offset, static_cast<cudaStream_t>(stream));
+}
+
+int xsde_integrate_host(xsde_problem *p, const void *psi_in, void *psi_out, int64_t npaths, double dt,
+                        int64_t nsteps, int64_t path_offset, uint64_t step_offset, void *stream) {
+    const char *who = "xsde_integrate_host";
+    if (!p || !psi_in || !psi_out) return fail(XSDE_EINVAL, "%s: NULL problem or host field", who);
+    if (npaths < 1) return fail(XSDE_EINVAL, "%s: npaths must be >= 1", who);
+    const size_t bytes = (size_t)npaths * p->grid.npts * elem_bytes(p->dtype);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (p->hostfield_bytes < bytes) {
+        if (p->d_hostfield) {
+            XSDE_CUDA(cudaStreamSynchronize(s), "xsde_integrate_host: field");
+            cudaFree(p->d_hostfield);
+            p->d_hostfield = nullptr;
+            p->hostfield_bytes = 0;
+        }
+        XSDE_CUDA(cudaMalloc(&p->d_hostfield, bytes), "xsde_integrate_host: field");
+        p->hostfield_bytes = bytes;
+    }
+    xsde_vector dev{p->grid, p->dtype, 1, npaths, p->d_hostfield, false};
+    int rc = check_integrate(who, p, &dev, dt, nsteps, npaths, path_offset, step_offset);
+    if (rc != XSDE_OK) return rc;
+    XSDE_CUDA(cudaMemcpyAsync(p->d_hostfield, psi_in, bytes, cudaMemcpyHostToDevice, s), "xsde_integrate_host: copy in");
+    rc = integrate_on(p, p->d_hostfield, dt, nsteps, npaths, path_offset, step_offset, s);
+    if (rc != XSDE_OK) return rc;
+    XSDE_CUDA(cudaMemcpyAsync(psi_out, p->d_hostfield, bytes, cudaMemcpyDeviceToHost, s), "xsde_integrate_host: copy out");
+    return XSDE_OK;
 }
 
 int xsde_set_kernel_variant(xsde_problem *p, int variant) {
@@ -1575,9 +1605,9 @@ int xsde_synchronize(xsde_problem *p, void *stream) {
 // complex64, the persistent TMA-pipelined passes or the generic tiles.
 // xsde_autotune times each on a copy of the caller's field and keeps the
 // fastest.  A batch binds several problems to their fields and records all
-// their pass schedules as parallel branches of one CUDA graph: one host launch
-// replays the whole batch, and the many small 1D and 2D kernels of the
-// members run concurrently instead of one after the other.
+// their pass schedules as one CUDA graph: one host launch replays the whole
+// batch; the single-kernel 0D / 1D members are concurrent branches, the 2D / 3D
+// members (each thousands of passes over every SM) follow one another.
 // ===========================================================================
 struct xsde_batch {
     int device = -1;
@@ -1776,17 +1806,29 @@ int batch_capture(xsde_batch *b, double dt, int64_t nsteps, uint64_t step0) {
     }
     cudaGraph_t graph = nullptr;
     int rc = XSDE_OK;
+    // 0D / 1D members are one whole-run kernel each: they run as concurrent
+    // branches, so their CTAs share the waves of the GPU.  2D / 3D members are
+    // thousands of persistent passes that size their grids to every SM and
+    // hand out work statically; a pass that has to share SMs with long-running
+    // CTAs of another member finishes with its slowest CTA, so these members
+    // follow one another on the capture stream after the concurrent branches.
     cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         e = cudaEventRecord(b->fork, b->cap);
         for (size_t i = 0; i < n && e == cudaSuccess && rc == XSDE_OK; ++i) {
             const xsde_batch_member &m = b->m[i];
+            if (m.prob->grid.ndim >= 2) continue;
             e = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
             if (e != cudaSuccess) break;
             rc = integrate_on(m.prob, m.psi->data, dt, nsteps, m.psi->npaths, m.path_offset, step0, b->streams[i]);
             if (rc != XSDE_OK) break;
             e = cudaEventRecord(b->join[i], b->streams[i]);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->join[i], 0);
+        }
+        for (size_t i = 0; i < n && e == cudaSuccess && rc == XSDE_OK; ++i) {
+            const xsde_batch_member &m = b->m[i];
+            if (m.prob->grid.ndim < 2) continue;
+            rc = integrate_on(m.prob, m.psi->data, dt, nsteps, m.psi->npaths, m.path_offset, step0, b->cap);
         }
         const cudaError_t e_end = cudaStreamEndCapture(b->cap, &graph);
         if (e == cudaSuccess) e = e_end;

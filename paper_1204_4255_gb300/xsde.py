@@ -28,7 +28,7 @@ EXPORTED = (
     "xsde_vector_alloc", "xsde_vector_wrap", "xsde_vector_data", "xsde_vector_free",
     "xsde_noise_alloc", "xsde_noise_free", "xsde_noise_philox", "xsde_noise_normals",
     "xsde_problem_create", "xsde_problem_destroy", "xsde_set_operators", "xsde_moments",
-    "xsde_integrate", "xsde_synchronize", "xsde_last_error", "xsde_version",
+    "xsde_integrate", "xsde_integrate_host", "xsde_synchronize", "xsde_last_error", "xsde_version",
     "xsde_profile", "xsde_profile_report", "xsde_kernel_name", "xsde_set_kernel_variant",
     "xsde_integrate_static_scratch", "xsde_adjoint", "xsde_kernel_variants", "xsde_autotune",
     "xsde_batch_create", "xsde_batch_integrate", "xsde_batch_destroy", "xsde_integrate_plain",
@@ -102,6 +102,7 @@ def load(path: str = LIB_PATH):
         "xsde_set_operators": (ctypes.c_int, [vp, ctypes.POINTER(xsde_linear_op), ctypes.POINTER(xsde_nonlinear_op)]),
         "xsde_moments": (ctypes.c_int, [vp, ctypes.POINTER(xsde_sampling), vp, vp]),
         "xsde_integrate": (ctypes.c_int, [vp, vp, dp, i64, i64, i64, u64, vp]),
+        "xsde_integrate_host": (ctypes.c_int, [vp, vp, vp, i64, dp, i64, i64, u64, vp]),
         "xsde_synchronize": (ctypes.c_int, [vp, vp]),
         "xsde_last_error": (ctypes.c_char_p, []),
         "xsde_version": (ctypes.c_char_p, []),
@@ -243,6 +244,12 @@ def xsde_integrate(prob, vec, dt: float, nsteps: int, npaths: int, path_offset: 
                    stream: int = 0) -> None:
     _check(load().xsde_integrate(prob, vec, dt, nsteps, npaths, path_offset, step_offset,
                                  ctypes.c_void_p(stream or None)))
+
+
+def xsde_integrate_host(prob, in_ptr: int, out_ptr: int, npaths: int, dt: float, nsteps: int,
+                        path_offset: int = 0, step_offset: int = 0, stream: int = 0) -> None:
+    _check(load().xsde_integrate_host(prob, ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), npaths, dt, nsteps,
+                                      path_offset, step_offset, ctypes.c_void_p(stream or None)))
 
 
 def xsde_integrate_plain(prob, vec, dt: float, nsteps: int, npaths: int, path_offset: int = 0,
@@ -439,6 +446,13 @@ class Problem:
             xsde_integrate(self.prob, vec, dt, nsteps, npaths, path_offset, step_offset, _stream_handle(stream))
         finally:
             xsde_vector_free(vec)
+
+    def integrate_host(self, psi_in, psi_out, dt: float, nsteps: int, path_offset: int = 0, step_offset: int = 0,
+                       stream=None):
+        """psi_in / psi_out: CPU complex tensors [npaths, *shape] (page-locked for
+        asynchronous copies); psi_out holds the result once the stream is synchronised."""
+        xsde_integrate_host(self.prob, psi_in.data_ptr(), psi_out.data_ptr(), psi_in.shape[0], dt, nsteps,
+                            path_offset, step_offset, _stream_handle(stream))
 
     def integrate_plain(self, psi, dt: float, nsteps: int, path_offset: int = 0, step_offset: int = 0,
                         stream=None):

@@ -146,3 +146,41 @@ def test_nvtx_ranges_do_not_change_results():
     w = W.gpe_2d(n=64, nsteps=4)
     plain, _, _ = gpu_run(w, "c64")
     assert np.array_equal(traced, plain)
+
+
+@pytest.mark.parametrize("shape,dtype", [((256,), "c128"), ((128, 256), "c64"), ((16, 16, 32), "c64")])
+def test_integrate_host_equals_integrate(shape, dtype):
+    """xsde_integrate_host (host field in, host field out, copies on the stream)
+    gives exactly the field xsde_integrate gives on a device copy, with the
+    sampling group filled the same way; psi_out may be psi_in."""
+    import torch
+    w = _gpe(shape, npaths=3, nsteps=7)
+    tdt = torch.complex64 if dtype == "c64" else torch.complex128
+    host = torch.from_numpy(np.ascontiguousarray(w.psi0)).to(tdt).pin_memory()
+    out = torch.empty_like(host).pin_memory()
+
+    def run(host_call):
+        P = make_problem(w, dtype)
+        pp = torch.zeros((3, 3, 2), dtype=torch.float64, device="cuda")
+        P.moments(3, 3, pp, None)
+        if host_call:
+            P.integrate_host(host, out, w.dt, 7, step_offset=2)
+            P.synchronize()
+            res = out.clone()
+            inplace = host.clone().pin_memory()
+            P.integrate_host(inplace, inplace, w.dt, 7, step_offset=2)
+            P.synchronize()
+            assert torch.equal(inplace, res)
+        else:
+            psi = host.cuda()
+            P.integrate(psi, w.dt, 7, step_offset=2)
+            P.synchronize()
+            res = psi.cpu()
+        P.close()
+        return res.numpy(), pp.cpu().numpy()
+
+    a, pa = run(True)
+    b, pb = run(False)
+    assert np.array_equal(a, b)
+    # 2D / 3D samples are FP64 atomic sums over CTAs: equal up to summation order
+    np.testing.assert_allclose(pa, pb, rtol=1e-12, atol=0)
