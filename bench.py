@@ -39,9 +39,9 @@ METRIC = "RK4IP grid-point-steps/s"
 UNIT = "pt-steps/s"
 BYTES_PER_PT_PASS = {"c64": 32, "c128": 64}   # 2 fields in + 2 out per pass
 # DRAM read + write per launch measured by ncu for the default configuration
-# (profiles/ summaries of the same kernels); reported only for that
+# (profiles/col_pass_warp_512x512x64_c64_full.md); reported only for that
 # configuration and only while the kernels are unchanged since the capture.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {("c64", 64, "col_propagate"): 481.5e6}
 
 
 def _dist():
@@ -772,7 +772,8 @@ def run_gpu(args) -> None:
 
 def run_case(name: str) -> None:
     """One workload, one warm-up call and one timed call of `nsteps` RK4IP
-    steps, for kernel profiles (ncu captures of a single kernel): tw1d (the
+    steps, for kernel profiles (ncu captures of a single kernel): gpe2d (the
+    bench lattice, 64 x 512^2 GPE, complex64, 4 steps), tw1d (the
     truncated-Wigner 1D ensemble, 4096 x 1024, complex64, 100 steps), gpe3d
     (the 128^3 GPE, one instance, complex64, 10 steps, autotuned), charged
     (Example 5's non-local condensate, 4096 x 1024, complex64, 100 steps) and
@@ -781,6 +782,7 @@ def run_case(name: str) -> None:
     import workloads as W
     from paper_1204_4255_gb300 import xsde
     cases = {
+        "gpe2d": (lambda: W.gpe_2d(npaths=64, nsteps=4), 4),
         "tw1d": (lambda: W.truncated_wigner(nsteps=100), 100),
         "gpe3d": (lambda: W.gpe_3d(nsteps=10), 10),
         "charged": (lambda: W.charged_bec(npaths=4096, n=1024, nsteps=100), 100),
@@ -823,7 +825,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched and plain-vs-fused figures")
-    ap.add_argument("--case", choices=["tw1d", "gpe3d", "charged", "example3"],
+    ap.add_argument("--case", choices=["gpe2d", "tw1d", "gpe3d", "charged", "example3"],
                     help="run one workload once (for kernel profiles) instead of the bench")
     args = ap.parse_args()
     if args.case:
