@@ -253,6 +253,48 @@ def c128_figure(P: int = 64, nsteps: int = 10) -> dict:
             "flops_model": "8 * 5 log2(N_tot) + 100 per pt-step"}
 
 
+def gpe3d_figure(P: int = 8, nsteps: int = 20) -> dict:
+    """P instances of the 128^3 GPE in complex64 (fields of P x 16 MiB, larger
+    than L2 for P = 8): pt-steps/s over nsteps steps after a warm-up call, the
+    per-launch HBM fraction of each pass kind (32 B per point and pass) and of
+    the whole step at the 6 passes (192 B) it makes and at the 4-pass model
+    (128 B)."""
+    import torch
+    import workloads as W
+    from paper_1204_4255_gb300 import xsde
+    w = W.gpe_3d(npaths=P, nsteps=nsteps)
+    prob = xsde.Problem(w.n, w.xmin, w.xmax, "c64")
+    prob.set_operators(c0=w.c0, c2=w.c2, g=w.gnl, pot_kind=w.pot_kind, omega=(1.0, 1.0, 1.0))
+    psi = torch.from_numpy(w.psi0).to(torch.complex64).cuda()
+    prob.integrate(psi, w.dt, 2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    prob.integrate(psi, w.dt, nsteps, step_offset=2)
+    e1.record()
+    torch.cuda.synchronize()
+    xsde.xsde_profile(prob.prob, True)
+    prob.integrate(psi, w.dt, nsteps, step_offset=2 + nsteps)
+    prob.synchronize()
+    prof = xsde.xsde_profile_report(prob.prob)
+    xsde.xsde_profile(prob.prob, False)
+    prob.close()
+    del psi
+    torch.cuda.empty_cache()
+    ms = e0.elapsed_time(e1)
+    value = P * w.npts * nsteps / (ms / 1e3)
+    peak, kind = _peaks()
+    per_pass = {}
+    for k, (tot, n) in prof.items():
+        if n and k in ("col_propagate", "row_stage2", "row_steady"):
+            ach = 32 * P * w.npts / (tot / n / 1e3) / 1e9
+            per_pass[k] = {"launch_ms": tot / n, "launches": n, "achieved": ach, "frac": ach / peak}
+    return {"workload": f"3D GPE 128^3 x {P} instances, complex64, {nsteps} RK4IP steps", "value": value,
+            "unit": UNIT, "ms_per_rk4ip_step": ms / nsteps, "passes_per_step": 6,
+            "hbm_frac_at_192B": value * 192 / 1e9 / peak, "hbm_frac_at_128B": value * 128 / 1e9 / peak,
+            "per_pass": per_pass, "peak": peak}
+
+
 def config_figures() -> dict:
     """The other workloads at their full sizes, device time of one whole run each
     (after a warm-up run): the NLS soliton (256 points, 1000 steps, one path),
@@ -748,6 +790,7 @@ def run_gpu(args) -> None:
         halfdom = half_domain_cost() if not args.no_batch else None
         arith = arithmetic_rooflines(others, plain) if not args.no_batch else None
         si2d = semi_implicit_2d_cost() if not args.no_batch else None
+        g3d = gpe3d_figure() if not args.no_batch else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -762,7 +805,7 @@ def run_gpu(args) -> None:
             "norm_check": ok, "adjoint": adj, "batched": bat, "plain_vs_fused": plain,
             "other_workloads": others, "ip_vs_explicit": ipex, "strong_convergence": strong,
             "nonlocal": nonloc, "half_domain": halfdom, "arithmetic_rooflines": arith,
-            "semi_implicit_2d": si2d,
+            "semi_implicit_2d": si2d, "gpe_3d_8x128": g3d,
         }
         print(json.dumps(line), flush=True)
     prob.close()

@@ -138,13 +138,14 @@ def gpe_2d(n: int = 512, dt: float = 1e-4, nsteps: int = 2000, g: float = 500.0,
 
 
 def gpe_3d(n: int = 128, dt: float = 1e-4, nsteps: int = 500, g: float = 200.0, box: float = 10.0,
-           seed: int = 4) -> Workload:
+           seed: int = 4, npaths: int = 1) -> Workload:
     """3D GPE on [-box, box)^3, V = r^2/2, Thomas-Fermi state (norm 1) with
-    exp(i 0.01 N(0,1)) phase noise."""
+    exp(i 0.01 N(0,1)) phase noise; npaths > 1 stacks independent instances,
+    each with its own phase noise (the first one is the npaths = 1 instance)."""
     shape = (n, n, n)
     tf = thomas_fermi(shape, (-box,) * 3, (box,) * 3, (1.0, 1.0, 1.0), g)
     rng = np.random.default_rng(seed)
-    psi0 = tf[None] * np.exp(1j * 0.01 * rng.standard_normal((1,) + shape))
+    psi0 = tf[None] * np.exp(1j * 0.01 * rng.standard_normal((npaths,) + shape))
     return Workload("gpe_3d", shape, (-box,) * 3, (box,) * 3, 0j, -0.5j, g, POT_HARMONIC,
                     (1.0, 1.0, 1.0), None, NOISE_NONE, 0.0, 0, dt, nsteps, psi0.astype(np.complex128))
 
