@@ -387,6 +387,32 @@ def nonlocal_cost(npaths: int = 4096, n: int = 1024, nsteps: int = 200) -> dict:
         res["cost_ratio"] = res["local_only"]["value"] / res["nonlocal"]["value"]
         out[dtype] = res
         P.close()
+    # 2D: the charged condensate on the 2D trap, 16 paths x 256^2, 20 steps; the
+    # term takes a density convolution (row, column, row pass) before each of
+    # the four N evaluations, on the generic passes
+    w2 = W.charged_bec_2d(npaths=16, n=(256, 256), nsteps=20)
+    out["2d"] = {"workload": "2D charged condensate 16 paths x 256^2, 20 RK4IP steps"}
+    for dtype in ("c64", "c128"):
+        P = xsde.Problem(w2.n, w2.xmin, w2.xmax, dtype)
+        P.set_operators(c0=w2.c0, c2=w2.c2, g=w2.gnl, pot_kind=w2.pot_kind, omega=(1.0, 1.0, 0.0))
+        src = torch.from_numpy(w2.psi0).to(torch.complex64 if dtype == "c64" else torch.complex128).cuda()
+        res = {}
+        for label, khat in (("nonlocal", w2.knl), ("local_only", None)):
+            P.set_nonlocal(khat)
+            psi = src.clone()
+            P.integrate(psi, w2.dt, 2)
+            torch.cuda.synchronize()
+            e0.record()
+            P.integrate(psi, w2.dt, w2.nsteps, step_offset=2)
+            e1.record()
+            torch.cuda.synchronize()
+            P.synchronize()
+            ms = e0.elapsed_time(e1)
+            res[label] = {"value": w2.npaths * w2.npts * w2.nsteps / (ms / 1e3), "ms": ms}
+        res["cost_ratio"] = res["local_only"]["value"] / res["nonlocal"]["value"]
+        out["2d"][dtype] = res
+        P.close()
+        del psi, src
     torch.cuda.empty_cache()
     return out
 

@@ -235,8 +235,12 @@ int xsde_set_noise_substeps(xsde_problem *prob, int32_t substeps);
  * k - npts); read during the call and copied to the device in the problem's
  * precision.  NULL removes the term.  The call synchronises the device first,
  * so no integration in flight sees a half-written kernel.  Energy moments add
- * the pair energy 1/2 V_nl |psi|^2 dV.  1D lattices only (XSDE_EUNSUPPORTED
- * elsewhere); runs with RK4IP on one launch shape (xsde_kernel_variants
+ * the pair energy 1/2 V_nl |psi|^2 dV.  1D and 2D Fourier lattices
+ * (XSDE_EUNSUPPORTED elsewhere); on 2D lattices khat is [n0][n1] and each N
+ * evaluation takes a density convolution of its own (a row pass forming the
+ * density's row transform, a column pass multiplying by khat, the evaluating
+ * row pass finishing the inverse), three work fields of the field's size and
+ * twelve passes a step.  Runs with RK4IP on one launch shape (xsde_kernel_variants
  * reports 1 while the term is set), and xsde_integrate with the semi-implicit scheme,
  * xsde_integrate_plain, xsde_integrate_adaptive and xsde_adjoint report
  * XSDE_EUNSUPPORTED while it is set.  Non-finite entries: XSDE_EINVAL. */
@@ -468,8 +472,9 @@ void xsde_batch_destroy(xsde_batch *batch);
 
 /* Kernel kinds reported by xsde_profile_report, in this order:
  * rk4ip_0d, rk4ip_1d, row_prologue, row_stage2, row_steady, row_epilogue,
- * row_fft_only, col_propagate, col_spectral (see xsde_kernel_name). */
-#define XSDE_KERNEL_KINDS 9
+ * row_fft_only, col_propagate, col_spectral, row_nonlocal, col_convolve (see
+ * xsde_kernel_name). */
+#define XSDE_KERNEL_KINDS 11
 
 /* Start (enable != 0) or stop recording a CUDA event pair around every kernel
  * launch of this problem, on the launch stream; resets the totals.  Separately,

@@ -133,7 +133,8 @@ bool pow2_in_range(int n) { return n >= 16 && n <= 2048 && (n & (n - 1)) == 0; }
 
 const char *const kKernelNames[XSDE_KERNEL_KINDS] = {
     "rk4ip_0d",      "rk4ip_1d",      "row_prologue", "row_stage2", "row_steady",
-    "row_epilogue",  "row_fft_only",  "col_propagate", "col_spectral"};
+    "row_epilogue",  "row_fft_only",  "col_propagate", "col_spectral", "row_nonlocal",
+    "col_convolve"};
 
 cudaEvent_t take_event(xsde_problem *p) {
     if (!p->event_pool.empty()) {
@@ -515,6 +516,9 @@ int col_maps(int kind, CUtensorMap *ma, CUtensorMap *mb, void *A, void *B, int64
 // (dimension 2 rows, dimension 1 columns) and the kinetic reduction along
 // dimension 0.
 // the scratch field B of the 2D/3D pass schedule (grown, never shrunk)
+// scratch fields of one 2D / 3D call: B, and C and D with the 2D non-local term
+int scratch_fields(const xsde_problem *p) { return p->nonlocal && p->grid.ndim == 2 ? 3 : 1; }
+
 int ensure_scratch(xsde_problem *p, size_t need, cudaStream_t s) {
     if (p->scratch_bytes >= need) return XSDE_OK;
     if (p->d_scratch) {
@@ -777,6 +781,62 @@ int run_si_3d(xsde_problem *p, Params2D<R> &qr, Params2D<R> &q1, Params2D<R> &q0
     return XSDE_OK;
 }
 
+// RK4IP with the non-local pair potential (Example 5) on a 2D lattice, generic
+// passes.  Every evaluation of N reads the V_nl of its own argument, so each is
+// preceded by a density convolution (NlOp): a row pass forms C = F1 |u|^2, a
+// column pass COL_CONV takes it to F1 V_nl, the next row pass uses it.  A step:
+//   col(propagate) S2A conv S2B conv S2C col(propagate) SDA conv SDB [conv PROLOGUE]
+// i.e. 6 row passes, 2 propagating and 4 convolving column passes (the
+// prologue of the next step is the tail of this one).
+template <typename R>
+int run_nl_2d(xsde_problem *p, Params2D<R> &q, int64_t nsteps, uint64_t step0, cudaStream_t s) {
+    const int S = q.sm.every;
+    const bool sampling = S > 0;
+    auto row = [&](int op, uint64_t sg, int slot, int last = 0) -> cudaError_t {
+        q.nl_op = op;
+        q.nl_last = last;
+        q.sg = sg;
+        q.sample_slot = slot;
+        return timed(p, 9, s, [&] { return launch_row_pass<R>(ROW_NL, q, s); });
+    };
+    auto col = [&](int mode, int slot) -> cudaError_t {
+        q.sample_slot = slot;
+        return timed(p, mode == COL_CONV ? 10 : 7, s, [&] { return launch_col_pass<R>(mode, q, s); });
+    };
+    if (nsteps > 0) {
+        XSDE_CUDA(row(NL_DENSITY, step0, -1), "row pass");
+        XSDE_CUDA(col(COL_CONV, -1), "col pass");
+        XSDE_CUDA(row(NL_PROLOGUE, step0, sampling ? 0 : -1), "row pass");
+        for (int64_t n = 0; n < nsteps; ++n) {
+            const uint64_t sg = step0 + n;
+            XSDE_CUDA(col(COL_PROPAGATE, (sampling && n % S == 0) ? (int)(n / S) : -1), "col pass");
+            XSDE_CUDA(row(NL_S2A, sg, -1), "row pass");
+            XSDE_CUDA(col(COL_CONV, -1), "col pass");
+            XSDE_CUDA(row(NL_S2B, sg, -1), "row pass");
+            XSDE_CUDA(col(COL_CONV, -1), "col pass");
+            XSDE_CUDA(row(NL_S2C, sg, -1), "row pass");
+            XSDE_CUDA(col(COL_PROPAGATE, -1), "col pass");
+            XSDE_CUDA(row(NL_SDA, sg, -1), "row pass");
+            XSDE_CUDA(col(COL_CONV, -1), "col pass");
+            const bool last = n + 1 == nsteps;
+            XSDE_CUDA(row(NL_SDB, sg, -1, last ? 1 : 0), "row pass");
+            if (!last) {
+                XSDE_CUDA(col(COL_CONV, -1), "col pass");
+                const int slot = (sampling && (n + 1) % S == 0) ? (int)((n + 1) / S) : -1;
+                XSDE_CUDA(row(NL_PROLOGUE, sg + 1, slot), "row pass");
+            }
+        }
+    }
+    if (sampling && nsteps % S == 0) {
+        const int slot = (int)(nsteps / S);
+        XSDE_CUDA(row(NL_DENSITY, step0 + nsteps, -1), "row pass");
+        XSDE_CUDA(col(COL_CONV, -1), "col pass");
+        XSDE_CUDA(row(NL_FFT, step0 + nsteps, slot), "row pass");
+        XSDE_CUDA(col(COL_SPECTRAL, slot), "col pass");
+    }
+    return XSDE_OK;
+}
+
 template <typename R>
 int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t npaths, int64_t path_offset,
                   uint64_t step0, cudaStream_t s) {
@@ -834,8 +894,8 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
         return XSDE_OK;
     }
     if (g.ndim == 3) return run_3d<R>(p, psi, nsteps, npaths, step0, lt, sm, s);
-    // 2D: scratch field B (same shape as psi)
-    int rc_s = ensure_scratch(p, (size_t)npaths * g.npts * sizeof(V), s);
+    // 2D: scratch field B (same shape as psi); C and D with the non-local term
+    int rc_s = ensure_scratch(p, (size_t)scratch_fields(p) * npaths * g.npts * sizeof(V), s);
     if (rc_s != XSDE_OK) return rc_s;
     Params2D<R> q;
     q.A = static_cast<V *>(psi);
@@ -856,6 +916,12 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
     if (p->scheme == XSDE_SCHEME_SEMI_IMPLICIT) {
         if (!p->d_Ef[0] || !p->d_Ef[1]) return fail(XSDE_EINVAL, "semi-implicit 2D step: tables missing");
         return run_si_2d<R>(p, q, nsteps, step0, s);
+    }
+    if (p->nonlocal) {
+        q.C = q.B + (size_t)npaths * g.npts;
+        q.D = q.C + (size_t)npaths * g.npts;
+        q.K2 = static_cast<const V *>(p->d_knl);
+        return run_nl_2d<R>(p, q, nsteps, step0, s);
     }
     // complex64 lattices the warp / TMA passes cover take the hot modes there
     int rk = PASS_GENERIC, ck = PASS_GENERIC;
@@ -977,7 +1043,8 @@ int variants_for(const xsde_problem *p) {
                        ? 1
                        : rk4ip_1d_variants();
         case 2:
-        case 3: return p->scheme != XSDE_SCHEME_RK4IP ? 1 : 4;   // the semi-implicit step: one shape
+        case 3:   // the semi-implicit step and the 2D non-local term: one shape
+            return p->scheme != XSDE_SCHEME_RK4IP || p->nonlocal ? 1 : 4;
         default: return 1;
     }
 }
@@ -1243,8 +1310,9 @@ int xsde_set_nonlocal(xsde_problem *p, const double *khat) {
         p->nonlocal = false;
         return XSDE_OK;
     }
-    if (p->grid.ndim != 1 || any_basis(p->grid))
-        return fail(XSDE_EUNSUPPORTED, "xsde_set_nonlocal: 1D Fourier lattices only (a circular convolution)");
+    if (p->grid.ndim < 1 || p->grid.ndim > 2 || any_basis(p->grid))
+        return fail(XSDE_EUNSUPPORTED,
+                    "xsde_set_nonlocal: 1D and 2D Fourier lattices only (a circular convolution)");
     int dev = -1;
     cudaGetDevice(&dev);
     if (dev != p->device)
@@ -1766,7 +1834,7 @@ int tune_problem(xsde_problem *p, const xsde_vector *psi, double dt, int64_t nst
 int prepare_member(xsde_problem *p, double dt, int64_t npaths, cudaStream_t s) {
     int rc = p->dtype == XSDE_C64 ? ensure_tables<cx<float>>(p, dt, s) : ensure_tables<cx<double>>(p, dt, s);
     if (rc == XSDE_OK && p->grid.ndim >= 2)
-        rc = ensure_scratch(p, (size_t)npaths * p->grid.npts * elem_bytes(p->dtype), s);
+        rc = ensure_scratch(p, (size_t)scratch_fields(p) * npaths * p->grid.npts * elem_bytes(p->dtype), s);
     return rc;
 }
 

@@ -94,7 +94,23 @@ enum RowMode {
     ROW_STEADY = 2,     // A = D u1, B = D acc -> a' = D acc + N(D u1)/6; A = F1 a', B = F1 N(a')
     ROW_EPILOGUE = 3,   // as STEADY but writes a' in real space to A only
     ROW_FFT_ONLY = 4,   // A (real) -> B = F1 A (for the spectral part of the energy)
-    ROW_SI = 5          // semi-implicit scheme on A alone; sub-operation p.si_op (SiOp)
+    ROW_SI = 5,         // semi-implicit scheme on A alone; sub-operation p.si_op (SiOp)
+    ROW_NL = 6          // RK4IP with a non-local pair potential; sub-operation p.nl_op (NlOp)
+};
+// RK4IP steps with a non-local potential V_nl[u] = Re F^-1[khat F |u|^2] on 2D
+// lattices evaluate every N(u) with the V_nl of its own argument, so each
+// evaluation waits for a density convolution: a row pass forms C = F1 |u|^2, a
+// column pass (COL_CONV) takes C to F1 V_nl, and the next row pass reads V_nl
+// as Re F1^-1 C.  Fields between passes (A, B as in RowMode; D real space):
+enum NlOp {
+    NL_DENSITY = 0,     // A (real u) -> C = F1 |u|^2
+    NL_PROLOGUE = 1,    // A (real a), C -> A = E1 F1 a, B = E1 F1 N(a) (at step sg; sample of a)
+    NL_FFT = 2,         // A (real a), C -> sample of a (local terms with V_nl), B = F1 a
+    NL_S2A = 3,         // A = F1 a_I, B = F1 k1 -> C = F1 |a_I + k1/2|^2
+    NL_S2B = 4,         // A, B, C -> D = k2 = N(a_I + k1/2), C = F1 |a_I + k2/2|^2
+    NL_S2C = 5,         // A, B, C, D -> k3; A = E1 F1 (a_I + k3), B = E1 F1 (a_I + k1/6 + k2/3 + k3/3)
+    NL_SDA = 6,         // A = F1 D(a_I + k3) -> C = F1 |D(a_I + k3)|^2
+    NL_SDB = 7,         // A, B = F1 D(acc), C -> A = a' = D(acc) + k4/6 (real), C = F1 |a'|^2 unless nl_last
 };
 // Semi-implicit steps on 2D lattices keep one field, A, row-transformed between
 // passes as F1 u / n1 (u = a_n, or u = D a_n on the way into a step):
@@ -108,7 +124,8 @@ enum ColMode {
     COL_PROPAGATE = 0,  // A, B -> F0^-1 E0 F0 (A, B)
     COL_SPECTRAL = 1,   // B: accumulate the kinetic energy only (no write)
     COL_FFT_FWD = 2,    // B <- F0 B (the middle transform of a 3D spectral sample)
-    COL_SINGLE = 3      // A -> F0^-1 E0 F0 A (the semi-implicit scheme's one field)
+    COL_SINGLE = 3,     // A -> F0^-1 E0 F0 A (the semi-implicit scheme's one field)
+    COL_CONV = 4        // C -> F0^-1 K2(k0, k1) F0 C (the non-local kernel, not separable)
 };
 
 template <typename R> struct Params2D {
@@ -146,6 +163,14 @@ template <typename R> struct Params2D {
     // twiddles of the two-stage plan of dimension 0 (fft2.cuh), for the warp
     // column pass: entry (r-1) E + j holds w_n0^(r j), r < n0/E, j < E
     const tw_t<R> *tw0w = nullptr;
+    // non-local term (2D, ROW_NL / COL_CONV): density / potential field C and the
+    // real-space stage field D (same shape as A), the kernel K2 = khat / (n0 n1)
+    // [n0][n1] in FFT order, the sub-operation and whether NL_SDB ends the run
+    cx<R> *C = nullptr;
+    cx<R> *D = nullptr;
+    const cx<R> *K2 = nullptr;
+    int nl_op = 0;
+    int nl_last = 0;
 };
 template <typename R> cudaError_t launch_row_pass(int mode, const Params2D<R> &p, cudaStream_t s);
 template <typename R> cudaError_t launch_col_pass(int mode, const Params2D<R> &p, cudaStream_t s);

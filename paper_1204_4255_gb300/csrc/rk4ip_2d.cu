@@ -107,13 +107,16 @@ __global__ void __launch_bounds__(RowCfg<N1>::THREADS) row_pass_kernel(const Par
         return point_term(p.lt, potv(m, gs), (uint32_t)(i0 * N1 + i1), gp, (uint32_t)gs);
     };
     // local part of the sampling group for the real-space field f at global step gs
-    auto sample_local = [&](const V (&f)[E], uint64_t gs) {
+    // (vnl: the non-local potential of f, whose pair energy 1/2 V_nl |f|^2 the
+    // energy adds; nullptr without the term)
+    auto sample_local = [&](const V (&f)[E], uint64_t gs, const R *vnl = nullptr) {
         double acc[2] = {0.0, 0.0};
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const double m2 = (double)cabs2(f[m]);
             acc[0] += m2;
             acc[1] += (double)potv(m, gs) * m2 + 0.5 * p.sm.g * m2 * m2;
+            if (vnl) acc[1] += 0.5 * (double)vnl[m] * m2;
             if (active && (p.sm.which & (MOM_MOD2 | MOM_MOD4)) && p.sm.per_point) {
                 double *pp = p.sm.per_point + 2 * ((int64_t)p.sample_slot * p.lt.npts + (int64_t)i0 * N1 + t + m * T);
                 atomicAdd(pp, m2 * p.sm.inv_paths);
@@ -189,7 +192,112 @@ __global__ void __launch_bounds__(RowCfg<N1>::THREADS) row_pass_kernel(const Par
     }
 
     V x[2][E];
-    if constexpr (MODE == ROW_PROLOGUE || MODE == ROW_FFT_ONLY) {
+    if constexpr (MODE == ROW_NL) {
+        // RK4IP with the non-local potential (Example 5) on a 2D lattice: see NlOp
+        const int op = p.nl_op;
+        V *Crow = p.C + rrow * N1;
+        V *Drow = p.D + rrow * N1;
+        // C = F1 |u|^2 of this line (the density the column pass convolves)
+        auto density_out = [&](const V (&u)[E]) {
+            V y[1][E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) y[0][m] = mk<V>(cabs2(u[m]), R(0));
+            fft<N1, E, -1, 1>(y, t, sm1, L, sync, tw);
+            if (active)
+#pragma unroll
+                for (int m = 0; m < E; ++m) Crow[t + m * T] = y[0][m];
+        };
+        // V_nl = Re F1^-1 C (C = F1 V_nl after the convolving column pass)
+        auto vnl_in = [&](R (&v)[E]) {
+            V y[1][E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) y[0][m] = Crow[t + m * T];
+            fft<N1, E, +1, 1>(y, t, sm1, L, sync, tw);
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = y[0][m].x;
+        };
+        // the point term of step gs with V_nl added to the potential
+        auto ptv = [&](int m, uint64_t gs, R vnl) -> PointTerm<R> {
+            PointTerm<R> pt = pterm(m, gs);
+            pt.dtV += p.lt.dt * vnl;
+            return pt;
+        };
+        R v[E];
+        if (op == NL_DENSITY || op == NL_PROLOGUE || op == NL_FFT) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) x[0][m] = Arow[t + m * T];
+            if (op == NL_DENSITY) {
+                density_out(x[0]);
+                return;
+            }
+            vnl_in(v);
+            if (sample) sample_local(x[0], p.sg, v);
+            if (op == NL_FFT) {
+                V y[1][E];
+#pragma unroll
+                for (int m = 0; m < E; ++m) y[0][m] = x[0][m];
+                fft<N1, E, -1, 1>(y, t, sm1, L, sync, tw);
+                if (active)
+#pragma unroll
+                    for (int m = 0; m < E; ++m) Brow[t + m * T] = y[0][m];
+                return;
+            }
+#pragma unroll
+            for (int m = 0; m < E; ++m) x[1][m] = apply_N(x[0][m], ptv(m, p.sg, v[m]), gdt);
+        } else if (op == NL_SDA) {
+            V y[1][E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) y[0][m] = Arow[t + m * T];
+            fft<N1, E, +1, 1>(y, t, sm1, L, sync, tw);
+            density_out(y[0]);
+            return;
+        } else {
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                x[0][m] = Arow[t + m * T];
+                x[1][m] = Brow[t + m * T];
+            }
+            fft<N1, E, +1, 2>(x, t, sm2, L, sync, tw);
+            if (op == NL_S2A) {
+                V u[E];
+#pragma unroll
+                for (int m = 0; m < E; ++m) u[m] = caxpy(x[0][m], half, x[1][m]);
+                density_out(u);
+                return;
+            }
+            vnl_in(v);
+            if (op == NL_S2B) {
+                V u[E];
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    const V k2 = apply_N(caxpy(x[0][m], half, x[1][m]), ptv(m, p.sg, v[m]), gdt);
+                    if (active) Drow[t + m * T] = k2;
+                    u[m] = caxpy(x[0][m], half, k2);
+                }
+                density_out(u);
+                return;
+            }
+            if (op == NL_SDB) {
+                // k4 = N(D(a_I + k3)) at step sg; a' = D(acc) + k4/6, real space
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    x[0][m] = caxpy(x[1][m], sixth, apply_N(x[0][m], ptv(m, p.sg, v[m]), gdt));
+                    if (active) Arow[t + m * T] = x[0][m];
+                }
+                if (!p.nl_last) density_out(x[0]);
+                return;
+            }
+            // NL_S2C: k3 = N(a_I + k2/2) with the V_nl of that argument
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const V aI = x[0][m], k1 = x[1][m];
+                const V k2 = active ? Drow[t + m * T] : mk<V>(R(0), R(0));
+                const V k3 = apply_N(caxpy(aI, half, k2), ptv(m, p.sg, v[m]), gdt);
+                x[0][m] = cadd(aI, k3);
+                x[1][m] = caxpy(caxpy(caxpy(aI, sixth, k1), third, k2), third, k3);
+            }
+        }
+    } else if constexpr (MODE == ROW_PROLOGUE || MODE == ROW_FFT_ONLY) {
 #pragma unroll
         for (int m = 0; m < E; ++m) x[0][m] = Arow[t + m * T];
         if (sample) sample_local(x[0], p.sg);
@@ -366,7 +474,20 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
         }
     };
 
-    if constexpr (MODE == COL_SINGLE) {
+    if constexpr (MODE == COL_CONV) {
+        // C <- F0^-1 K2(k0, col) F0 C: the density convolution of the non-local
+        // term (the kernel of a pair function is not separable per dimension)
+        V y[1][E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) y[0][m] = p.C[base + (int64_t)(t + m * T) * n1];
+        fft<N0, E, -1, 1>(y, t, sm1, L, sync, tw);
+#pragma unroll
+        for (int m = 0; m < E; ++m) y[0][m] = cmul(y[0][m], __ldg(p.K2 + (int64_t)(t + m * T) * n1 + col));
+        fft<N0, E, +1, 1>(y, t, sm1, L, sync, tw);
+#pragma unroll
+        for (int m = 0; m < E; ++m) p.C[base + (int64_t)(t + m * T) * n1] = y[0][m];
+        return;
+    } else if constexpr (MODE == COL_SINGLE) {
         V y[1][E];
 #pragma unroll
         for (int m = 0; m < E; ++m) y[0][m] = load(p.A, t + m * T);
@@ -447,6 +568,7 @@ template <typename R, int N1> cudaError_t row_mode(int mode, const Params2D<R> &
         case ROW_EPILOGUE: return row_launch<R, N1, ROW_EPILOGUE>(p, s);
         case ROW_FFT_ONLY: return row_launch<R, N1, ROW_FFT_ONLY>(p, s);
         case ROW_SI: return row_launch<R, N1, ROW_SI>(p, s);
+        case ROW_NL: return row_launch<R, N1, ROW_NL>(p, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -455,7 +577,7 @@ template <typename R, int N0, int MODE> cudaError_t col_launch(const Params2D<R>
     using Cfg = ColCfg<R, N0>;
     const size_t smem = (size_t)2 * N0 * Cfg::C * sizeof(cx<R>) + (Cfg::THREADS / 32 + 1) * sizeof(double);
     auto kern = col_pass_kernel<R, N0, MODE>;
-    if constexpr (MODE != COL_FFT_FWD && MODE != COL_SINGLE)
+    if constexpr (MODE != COL_FFT_FWD && MODE != COL_SINGLE && MODE != COL_CONV)
         if (p.basis0) kern = col_pass_kernel<R, N0, MODE, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -471,6 +593,7 @@ template <typename R, int N0> cudaError_t col_mode(int mode, const Params2D<R> &
         case COL_SPECTRAL: return col_launch<R, N0, COL_SPECTRAL>(p, s);
         case COL_FFT_FWD: return col_launch<R, N0, COL_FFT_FWD>(p, s);
         case COL_SINGLE: return col_launch<R, N0, COL_SINGLE>(p, s);
+        case COL_CONV: return col_launch<R, N0, COL_CONV>(p, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -38,7 +38,7 @@ EXPORTED = (
 XSDE_BASIS_FOURIER, XSDE_BASIS_COS, XSDE_BASIS_SIN = 0, 1, 2
 XSDE_SCHEME_RK4IP, XSDE_SCHEME_SEMI_IMPLICIT = 0, 1
 XSDE_BATCH_AUTOTUNE = 1
-XSDE_KERNEL_KINDS = 9
+XSDE_KERNEL_KINDS = 11
 
 
 class XsdeError(RuntimeError):

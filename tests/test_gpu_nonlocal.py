@@ -1,9 +1,10 @@
 """GPU parity of the non-local term (Example 5, Sec. 3.5: a pair potential
 applied as an FFT convolution of |psi|^2) through the C-ABI against the FP64
-oracle: every 1D length, both precisions, ragged path counts, noise, a
-time-dependent potential table, the energy moment with the pair term, the
-contact-interaction limit, the full-size ensemble on sampled paths, and the
-calls that reject the term.
+oracle: every 1D length and 2D lattices from 16x16 to 128x128 (square and
+not), both precisions, ragged path counts, noise, a time-dependent potential
+table, the energy moment with the pair term, the contact-interaction limit,
+the full-size 1D ensemble on sampled paths, batches, and the calls that
+reject the term.
 
 Tolerances: complex128 within 1e-10 relative L2 of the oracle, complex64
 within 1e-4 (the fixed-step bar of the other parity tests)."""
@@ -118,12 +119,12 @@ def test_calls_that_reject_the_term():
     P.integrate(psi, w.dt, 4)      # the old kernel is still in place
     P.synchronize()
     P.close()
-    w2 = W.gpe_2d(n=64, nsteps=2, npaths=1)
-    P2 = make_problem(w2, "c64")
+    w3 = W.gpe_3d(n=16, nsteps=2)
+    P3 = make_problem(w3, "c64")
     with pytest.raises(xsde.XsdeError) as e:
-        P2.set_nonlocal(np.ones(w2.npts, dtype=np.complex128))
+        P3.set_nonlocal(np.ones(w3.npts, dtype=np.complex128))
     assert e.value.status == xsde.XSDE_EUNSUPPORTED
-    P2.close()
+    P3.close()
 
 
 def test_batch_member_with_the_pair_potential():
@@ -171,3 +172,82 @@ def test_single_launch_shape_is_reported_and_tuned():
     P.set_nonlocal(None)
     assert xsde.xsde_kernel_variants(P.prob) == 7
     P.close()
+
+
+# ---------------------------------------------------------------------------
+# 2D lattices: a density convolution before every N evaluation
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(16, 16), (32, 64), (64, 32), (128, 128)])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_2d_charged_condensate_matches_the_oracle(shape, dtype):
+    """State, norm, energy with the pair term and per-point moments, sampled
+    every 20 steps (the last sample at the end of the run) and every 15 (none
+    at the end)."""
+    for every in (20, 15):
+        w = W.charged_bec_2d(npaths=3, n=shape, dt=1e-3, nsteps=40, box=8.0)
+        got, pp, pq = gpu_run(w, dtype, sample_every=every)
+        ref, opp, opq = O.run_workload(w, sample_every=every)
+        tol = TOL[dtype]
+        assert np.max(rel_l2(got.reshape(3, -1), ref.reshape(3, -1), axis=1)) < tol
+        assert np.max(np.abs(pp - opp) / np.abs(opp)) < tol
+        assert np.linalg.norm(pq - opq) / np.linalg.norm(opq) < tol
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_2d_noisy_path_subset_with_the_pair_potential(dtype):
+    w = W.charged_bec_2d(npaths=6, n=(32, 32), dt=1e-3, nsteps=30, box=8.0, noise_amp=0.02)
+    got, pp, _ = gpu_run(w, dtype, sample_every=10, path0=2, npaths=3)
+    ref, opp, _ = O.run_workload(w, sample_every=10, path0=2, npaths=3)
+    assert np.max(rel_l2(got.reshape(3, -1), ref.reshape(3, -1), axis=1)) < TOL[dtype]
+    assert np.max(np.abs(pp - opp) / np.abs(opp)) < TOL[dtype]
+
+
+def test_2d_time_dependent_table_with_the_pair_potential():
+    w = W.charged_bec_2d(npaths=2, n=(32, 16), dt=1e-3, nsteps=12, box=6.0)
+    rng = np.random.default_rng(5)
+    X, Y = np.meshgrid(w.coords_of(0), w.coords_of(1), indexing="ij")
+    w.V = np.stack([0.5 * (X ** 2 + Y ** 2) * (1 + 0.1 * np.sin(k)) + 0.05 * rng.standard_normal(X.shape)
+                    for k in range(12)]).reshape(12, -1)
+    w.pot_kind = W.POT_TABLE
+    got, _, _ = gpu_run(w, "c128")
+    ref, _, _ = O.run_workload(w)
+    assert rel_l2(got.reshape(2, -1), ref.reshape(2, -1)) < 1e-10
+
+
+def test_2d_constant_kernel_equals_the_contact_interaction():
+    """khat = c at every mode gives V_nl = c |psi|^2: the run equals the local
+    run with g + c (1e-12, complex128)."""
+    w = W.charged_bec_2d(npaths=2, n=(32, 32), dt=1e-3, nsteps=20, box=8.0)
+    c = 0.7
+    w.knl = np.full(w.n, c, dtype=np.complex128)
+    got, _, _ = gpu_run(w, "c128")
+    w.knl, w.gnl = None, w.gnl + c
+    ref, _, _ = gpu_run(w, "c128")
+    assert rel_l2(got, ref) < 1e-12
+
+
+def test_2d_batch_member_with_the_pair_potential():
+    """A 2D non-local problem recorded in a batch next to a local one gives what
+    xsde_integrate gives, bit for bit."""
+    import torch
+    from paper_1204_4255_gb300 import xsde
+    ws = [W.charged_bec_2d(npaths=2, n=(32, 64), dt=1e-3, nsteps=6, box=8.0), W.gpe_2d(n=64, npaths=2, nsteps=6)]
+    def run(batch):
+        probs = [make_problem(w, "c64") for w in ws]
+        psis = [torch.from_numpy(np.ascontiguousarray(w.psi0)).to(torch.complex64).cuda() for w in ws]
+        if batch:
+            B = xsde.Batch([(P, x, 0) for P, x in zip(probs, psis)])
+            B.integrate(1e-3, 6)
+            B.synchronize()
+            B.close()
+        else:
+            for P, x in zip(probs, psis):
+                P.integrate(x, 1e-3, 6)
+                P.synchronize()
+        out = [x.cpu().numpy() for x in psis]
+        for P in probs:
+            P.close()
+        return out
+    for a, b in zip(run(True), run(False)):
+        assert np.array_equal(a, b)
