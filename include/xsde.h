@@ -57,7 +57,9 @@ typedef enum {
     XSDE_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
     XSDE_ENONFINITE = 5,    /* the field became NaN/Inf */
     XSDE_EUNSUPPORTED = 6,  /* valid but not implemented (size, dtype, combination) */
-    XSDE_ELIMIT = 7         /* an adaptive integration used up its step attempts */
+    XSDE_ELIMIT = 7,        /* an adaptive integration used up its step attempts */
+    XSDE_EBOUNDS = 8        /* an index left its buffer (only the bounds-checking build,
+                               libxsde_bounds.so, checks; the access was skipped) */
 } xsde_status;
 
 typedef enum { XSDE_C64 = 1, XSDE_C128 = 2 } xsde_dtype;
@@ -387,8 +389,10 @@ int xsde_integrate_static_scratch(xsde_problem *prob, xsde_vector *psi, double d
 
 /* Wait for `stream`, then report device-side errors of this problem's calls:
  * XSDE_ENONFINITE if a sampled field held NaN/Inf, XSDE_ETIMEOUT if a bounded
- * wait gave up, XSDE_ELIMIT if an adaptive path used up its step attempts.
- * Clears the device error word. */
+ * wait gave up, XSDE_ELIMIT if an adaptive path used up its step attempts,
+ * XSDE_EBOUNDS if (in the bounds-checking build) a kernel computed an index
+ * outside a field, table, sampling buffer or copy range.  Clears the device
+ * error word. */
 int xsde_synchronize(xsde_problem *prob, void *stream);
 
 /* Kernel implementation for this problem, in [0, xsde_kernel_variants(prob)).

@@ -17,6 +17,10 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libxsde.so")
+# the bounds-checking build (-DXSDE_BOUNDS=1): every kernel checks its global
+# indices and copy ranges (csrc/bounds.cuh); a debugging aid, not the product path
+BUILD_BOUNDS = os.path.join(HERE, "_build_bounds")
+LIB_BOUNDS = os.path.join(HERE, "libxsde_bounds.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
@@ -72,19 +76,19 @@ def _deps() -> list:
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def _compile(unit, verbose: bool) -> str:
+def _compile(unit, verbose: bool, bounds: bool = False) -> str:
     src, bits = unit[0], unit[1]
     part = unit[2] if len(unit) > 2 else None
     stem = os.path.splitext(src)[0] + (f"_f{bits}" if bits else "") + (f"_p{part}" if part is not None else "")
-    obj = os.path.join(BUILD, stem + ".o")
-    cmd = [nvcc(), *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+    obj = os.path.join(BUILD_BOUNDS if bounds else BUILD, stem + ".o")
+    cmd = [nvcc(), *ARCH, *FLAGS, *(["-DXSDE_BOUNDS=1"] if bounds else []), "-c", os.path.join(CSRC, src), "-o", obj]
     if bits:
         cmd.insert(-4, f"-DXSDE_REAL_BITS={bits}")
     if part is not None:
@@ -97,24 +101,26 @@ def _compile(unit, verbose: bool) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link libxsde.so unless it is newer than every source."""
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, bounds: bool = False) -> str:
+    """Compile and link libxsde.so (or, with bounds, libxsde_bounds.so) unless
+    it is newer than every source."""
+    lib = LIB_BOUNDS if bounds else LIB
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(BUILD_BOUNDS if bounds else BUILD, exist_ok=True)
     workers = max(1, min(len(UNITS), os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(workers) as ex:
-        objs = list(ex.map(lambda u: _compile(u, verbose), UNITS))
-    tmp = LIB + f".{os.getpid()}.tmp"
+        objs = list(ex.map(lambda u: _compile(u, verbose, bounds), UNITS))
+    tmp = lib + f".{os.getpid()}.tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-lcufft"]
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, bounds="--bounds" in sys.argv))

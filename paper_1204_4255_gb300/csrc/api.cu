@@ -418,6 +418,7 @@ void fill_terms(const xsde_problem *p, double dt, int64_t npaths, int64_t path_o
     lt.key = make_uint2((uint32_t)(p->noise.seed & 0xffffffffu), (uint32_t)(p->noise.seed >> 32));
     lt.path_offset = path_offset;
     lt.substeps = p->noise_substeps;
+    lt.status = p->d_status;
 
     sm.every = p->samp.every;
     sm.which = p->samp.which;
@@ -848,6 +849,7 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
     fill_terms<R>(p, dt, npaths, path_offset, lt, sm);
     const xsde_grid &g = p->grid;
     const bool sampling = sm.every > 0;
+    sm.nsamp = sampling ? nsteps / sm.every + 1 : 0;
     if (sampling) {
         const int64_t nsamp = nsteps / sm.every + 1;
         if (sm.per_path && (sm.which & (MOM_NORM | MOM_ENERGY)))
@@ -1489,6 +1491,8 @@ int xsde_adjoint(xsde_problem *p, const xsde_vector *psi0, const xsde_vector *ta
         q.loss = loss;
         q.dLdV = dLdV;
         q.dLdpsi0 = static_cast<V *>(dLdpsi0);
+        q.status = p->d_status;
+        q.interm_steps = full ? nsteps : K;
         const int phases[3] = {ADJ_FORWARD, ADJ_RECOMPUTE, ADJ_REVERSE};
         for (int i = 0; i < (full ? 3 : 1); ++i) {
             q.phase = full ? phases[i] : ADJ_SEQUENTIAL;
@@ -1659,6 +1663,7 @@ int xsde_synchronize(xsde_problem *p, void *stream) {
     if (st & ST_TIMEOUT) return fail(XSDE_ETIMEOUT, "a bounded device-side wait gave up");
     if (st & ST_NONFINITE) return fail(XSDE_ENONFINITE, "the field became non-finite");
     if (st & ST_STEP_LIMIT) return fail(XSDE_ELIMIT, "an adaptive path used up its step attempts");
+    if (st & ST_BOUNDS) return fail(XSDE_EBOUNDS, "an index left its buffer (bounds-checking build)");
     return XSDE_OK;
 }
 
@@ -2117,6 +2122,7 @@ int static_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int6
     Sampling sm;
     fill_terms<R>(p, dt, npaths, path_offset, lt, sm);
     const bool sampling = sm.every > 0;
+    sm.nsamp = sampling ? nsteps / sm.every + 1 : 0;
     if (sampling) {
         const int64_t nsamp = nsteps / sm.every + 1;
         if (sm.per_path && (sm.which & (MOM_NORM | MOM_ENERGY)))

@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(N / E) ark45_1d_kernel(const AdaptiveParams<R>
     const LineLayout<V> L{};
     const int t = threadIdx.x;
     const int64_t path = blockIdx.x;
+    if (!XSDE_IN(path, p.npaths, p.status)) return;   // whole CTA: one path each
 
     for (int i = t; i < N; i += T) tws[i] = p.tw[i];
     __syncthreads();

@@ -9,6 +9,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "bounds.cuh"
 #include "device_common.cuh"
 #include "fft.cuh"
 
@@ -35,6 +36,7 @@ template <typename R> struct LocalTerm {
     uint2 key;            // Philox key (seed_lo, seed_hi)
     int64_t path_offset;  // global index of local path 0
     int substeps = 1;     // a step's noise is the mean of this many finer steps' (see point_term)
+    int *status = nullptr;  // device error word (index checks of the bounds-checking build)
 };
 
 // Sampling group: FP64 per-path (norm, energy) and per-point (mean |psi|^2, |psi|^4).
@@ -48,6 +50,7 @@ struct Sampling {
     double h0, h2;         // Re(i L(k)) = h0 + h2 |k|^2 (kinetic energy density)
     double kscale[3];      // 2 pi / (xmax - xmin) per dimension
     double g;              // g_nl (interaction energy g/2 |psi|^4)
+    int64_t nsamp = 0;     // samples of the call (extent of per_path / per_point)
 };
 
 enum { MOM_NORM = 1, MOM_ENERGY = 2, MOM_MOD2 = 4, MOM_MOD4 = 8 };
@@ -221,6 +224,8 @@ template <typename R> struct AdjParams {
     double *loss;          // accumulated (zeroed by the caller)
     double *dLdV;          // [nsteps][N], accumulated (zeroed by the caller)
     cx<R> *dLdpsi0;        // [npaths][N] or nullptr
+    int *status = nullptr; // device error word (bounds-checking build)
+    int64_t interm_steps = 0;  // steps held by interm (nsteps, or K)
 };
 template <typename R> cudaError_t launch_adjoint_1d(int n, int elems, const AdjParams<R> &p, cudaStream_t s);
 
@@ -350,7 +355,7 @@ __device__ __forceinline__ R potential(const LocalTerm<R> &lt, int ndim, const i
     if (lt.pot == PM_TABLE) {
         int64_t row = lt.V_nt > 1 ? (int64_t)gstep : 0;
         if (row >= lt.V_nt) row = lt.V_nt - 1;
-        return lt.V[row * lt.npts + j];
+        return XSDE_IN(row * lt.npts + j, lt.V_nt * lt.npts, lt.status) ? lt.V[row * lt.npts + j] : R(0);
     }
     return R(0);
 }

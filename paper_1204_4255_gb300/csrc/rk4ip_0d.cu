@@ -17,7 +17,7 @@ template <typename R> __global__ void __launch_bounds__(kThreads0D) rk4ip_0d_ker
     const int64_t lp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = lp < p.npaths;
     const uint32_t gp = (uint32_t)(p.lt.path_offset + lp);
-    V z = active ? p.psi[lp] : mk<V>(R(0), R(0));
+    V z = (active && XSDE_IN(lp, p.npaths, p.status)) ? p.psi[lp] : mk<V>(R(0), R(0));
     const V E = p.Ehalf;
     const R gdt = p.lt.gdt;
     const R sixth = R(1) / R(6), third = R(1) / R(3), half = R(0.5);
@@ -31,14 +31,15 @@ template <typename R> __global__ void __launch_bounds__(kThreads0D) rk4ip_0d_ker
             const double m2 = active ? (double)cabs2(z) : 0.0;
             if (active) {
                 const double v = (double)potential(p.lt, 0, idx0, 0, p.step0 + n);
-                if ((p.sm.which & (MOM_NORM | MOM_ENERGY)) && p.sm.per_path) {
+                if ((p.sm.which & (MOM_NORM | MOM_ENERGY)) && p.sm.per_path &&
+                    XSDE_IN(s * p.npaths + lp, p.sm.nsamp * p.npaths, p.status)) {
                     double *pq = p.sm.per_path + 2 * (s * p.npaths + lp);
                     pq[0] = m2;
                     pq[1] = (p.sm.h0 + v) * m2 + 0.5 * p.sm.g * m2 * m2;
                 }
                 if (!isfinite(m2)) atomicOr(p.status, ST_NONFINITE);
             }
-            if ((p.sm.which & (MOM_MOD2 | MOM_MOD4)) && p.sm.per_point) {
+            if ((p.sm.which & (MOM_MOD2 | MOM_MOD4)) && p.sm.per_point && XSDE_IN(s, p.sm.nsamp, p.status)) {
                 double a = warp_sum(m2), b = warp_sum(m2 * m2);
                 if ((threadIdx.x & 31) == 0) {
                     red[0][threadIdx.x >> 5] = a;
@@ -59,7 +60,7 @@ template <typename R> __global__ void __launch_bounds__(kThreads0D) rk4ip_0d_ker
         }
         if (n == p.nsteps) break;
         const uint64_t sg = p.step0 + n;
-        const R v = vtime ? p.lt.V[sg] : Vstatic;
+        const R v = vtime ? (XSDE_IN(sg, p.lt.V_nt, p.status) ? p.lt.V[sg] : R(0)) : Vstatic;
         const PointTerm<R> pt = point_term(p.lt, v, 0u, gp, (uint32_t)sg);
         if (p.scheme == 1) {
             // semi-implicit midpoint: a_I = D a; m <- a_I + N(m)/2 (three times); a <- D(2m - a_I)
@@ -78,7 +79,7 @@ template <typename R> __global__ void __launch_bounds__(kThreads0D) rk4ip_0d_ker
         const V acc = caxpy(caxpy(caxpy(aI, sixth, k1), third, k2), third, k3);
         z = caxpy(cmul(E, acc), sixth, k4);
     }
-    if (active) p.psi[lp] = z;
+    if (active && XSDE_IN(lp, p.npaths, p.status)) p.psi[lp] = z;
 }
 
 }  // namespace

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(PPC *(N / E), MINB) rk4ip_1d_kernel(const Para
     for (int m = 0; m < E; ++m) {
         const int j = t + m * T;
         const int pj = point_of(j);
-        x[0][m] = active ? psi[pj] : mk<V>(R(0), R(0));
+        x[0][m] = (active && XSDE_IN(lp * N + pj, p.npaths * N, p.status)) ? psi[pj] : mk<V>(R(0), R(0));
         if (negated(j)) x[0][m] = mk<V>(-x[0][m].x, -x[0][m].y);
         Ek[m] = p.Etab[j];
         El[m] = p.Etab[N + j];
@@ -188,7 +188,8 @@ __global__ void __launch_bounds__(PPC *(N / E), MINB) rk4ip_1d_kernel(const Para
                 acc[0] += m2;
                 acc[1] += vv * m2 + 0.5 * p.sm.g * m2 * m2;
                 if constexpr (NL) acc[1] += 0.5 * (double)vn[m] * m2;   // pair energy, counted once
-                if (active && (p.sm.which & (MOM_MOD2 | MOM_MOD4)) && p.sm.per_point) {
+                if (active && (p.sm.which & (MOM_MOD2 | MOM_MOD4)) && p.sm.per_point &&
+                    XSDE_IN(s * N + j, p.sm.nsamp * N, p.status)) {
                     double *pp = p.sm.per_point + 2 * (s * N + j);
                     atomicAdd(pp, m2 * p.sm.inv_paths);
                     atomicAdd(pp + 1, m2 * m2 * p.sm.inv_paths);
@@ -227,7 +228,8 @@ __global__ void __launch_bounds__(PPC *(N / E), MINB) rk4ip_1d_kernel(const Para
             slot_sum3<T>(acc, t, reinterpret_cast<double *>(bufB), sync);
             if (t == 0 && active) {
                 const double norm = acc[0] * p.sm.dV;
-                if ((p.sm.which & (MOM_NORM | MOM_ENERGY)) && p.sm.per_path) {
+                if ((p.sm.which & (MOM_NORM | MOM_ENERGY)) && p.sm.per_path &&
+                    XSDE_IN(s * p.npaths + lp, p.sm.nsamp * p.npaths, p.status)) {
                     double *pq = p.sm.per_path + 2 * (s * p.npaths + lp);
                     pq[0] = norm;
                     pq[1] = (acc[1] + acc[2] / N) * p.sm.dV;
@@ -246,7 +248,7 @@ __global__ void __launch_bounds__(PPC *(N / E), MINB) rk4ip_1d_kernel(const Para
             const int j = t + m * T;
             const int pj = point_of(j);
             R v = Vs[m];
-            if (vtime) v = p.lt.V[(int64_t)sg * N + pj];
+            if (vtime) v = XSDE_IN((int64_t)sg * N + pj, p.lt.V_nt * N, p.status) ? p.lt.V[(int64_t)sg * N + pj] : R(0);
             if constexpr (NOISE) {
                 pt[m] = point_term(p.lt, v, (uint32_t)pj, gp, (uint32_t)sg);
                 if (negated(j)) pt[m].na = mk<V>(-pt[m].na.x, -pt[m].na.y);
@@ -329,7 +331,8 @@ __global__ void __launch_bounds__(PPC *(N / E), MINB) rk4ip_1d_kernel(const Para
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int j = t + m * T;
-            psi[point_of(j)] = negated(j) ? mk<V>(-x[0][m].x, -x[0][m].y) : x[0][m];
+            if (XSDE_IN(lp * N + point_of(j), p.npaths * N, p.status))
+                psi[point_of(j)] = negated(j) ? mk<V>(-x[0][m].x, -x[0][m].y) : x[0][m];
         }
     }
 }

@@ -74,7 +74,8 @@ __global__ void __launch_bounds__(RowCfg<N1>::THREADS) row_pass_kernel(const Par
 
     const int64_t nrows = p.npaths * (int64_t)p.n0;
     const int64_t row = (int64_t)blockIdx.x * LINES + line;
-    const bool active = row < nrows;
+    // (bounds-checking build: the line's last element inside the field)
+    const bool active = row < nrows && XSDE_IN(row * N1 + N1 - 1, nrows * N1, p.status);
     const int64_t rrow = active ? row : 0;
     const int64_t path = rrow / p.n0;
     // line within the path; its lattice indices are (i0) in 2D, (i0, i1) in 3D
@@ -118,7 +119,9 @@ __global__ void __launch_bounds__(RowCfg<N1>::THREADS) row_pass_kernel(const Par
             acc[1] += (double)potv(m, gs) * m2 + 0.5 * p.sm.g * m2 * m2;
             if (vnl) acc[1] += 0.5 * (double)vnl[m] * m2;
             if (active && (p.sm.which & (MOM_MOD2 | MOM_MOD4)) && p.sm.per_point) {
-                double *pp = p.sm.per_point + 2 * ((int64_t)p.sample_slot * p.lt.npts + (int64_t)i0 * N1 + t + m * T);
+                const int64_t ip = (int64_t)p.sample_slot * p.lt.npts + (int64_t)i0 * N1 + t + m * T;
+                if (!XSDE_IN(ip, p.sm.nsamp * p.lt.npts, p.status)) continue;
+                double *pp = p.sm.per_point + 2 * ip;
                 atomicAdd(pp, m2 * p.sm.inv_paths);
                 atomicAdd(pp + 1, m2 * m2 * p.sm.inv_paths);
             }
@@ -126,7 +129,9 @@ __global__ void __launch_bounds__(RowCfg<N1>::THREADS) row_pass_kernel(const Par
         group_sum2<T>(acc, t, scratch);
         if (t == 0 && active) {
             if ((p.sm.which & (MOM_NORM | MOM_ENERGY)) && p.sm.per_path) {
-                double *pq = p.sm.per_path + 2 * ((int64_t)p.sample_slot * p.npaths + path);
+                const int64_t iq = (int64_t)p.sample_slot * p.npaths + path;
+                if (!XSDE_IN(iq, p.sm.nsamp * p.npaths, p.status)) return;
+                double *pq = p.sm.per_path + 2 * iq;
                 atomicAdd(pq, acc[0] * p.sm.dV);
                 atomicAdd(pq + 1, acc[1] * p.sm.dV);
             }
@@ -398,6 +403,12 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
     const int n1 = p.n1;
     const int64_t base = path * (int64_t)N0 * n1 + col;
     const bool sample = p.sample_slot >= 0;
+#if XSDE_BOUNDS
+    // the column's last element inside the field (one decision for the CTA)
+    if (!__syncthreads_and(XSDE_IN(base + (int64_t)(N0 - 1) * n1, p.npaths * (int64_t)N0 * n1, p.status) &&
+                           XSDE_IN(col, n1, p.status)))
+        return;
+#endif
     // A cosine / sine dimension 0 (TRIG; XMDS2 Sec. 2.1) gathers its rows in the
     // even-odd order of the DCT-II's evaluation by an N0-point FFT (slot s holds
     // row 2s below N0/2, row 2 N0-1-2s above; odd rows negated for the sine
@@ -469,6 +480,7 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
             double tot = 0.0;
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += scratch[w];
             if ((p.sm.which & (MOM_NORM | MOM_ENERGY)) && p.sm.per_path)
+                if (XSDE_IN((int64_t)p.sample_slot * p.npaths + path, p.sm.nsamp * p.npaths, p.status))
                 atomicAdd(p.sm.per_path + 2 * ((int64_t)p.sample_slot * p.npaths + path) + 1,
                           tot * p.sm.dV / ((double)N0 * n1));
         }

@@ -121,6 +121,12 @@ __global__ void __launch_bounds__(RowTma<N1>::THREADS, 1) row_pass_tma_kernel(co
         const int s = (int)(k % NST);
         const int64_t row0 = (blockIdx.x + k * gridDim.x) * ROWS;
         V *dst = bufs + (size_t)s * 2 * ROWS * N1;
+        // (bounds-checking build: a copy past the fields is skipped, the stage
+        // completes without bytes)
+        if (!XSDE_IN(row0 + ROWS - 1, p.npaths * (int64_t)p.n0, p.status)) {
+            mbar_arrive(bars + s);
+            return;
+        }
         mbar_arrive_expect_tx(bars + s, (uint32_t)(2 * vec_bytes));
         bulk_load(dst, p.A + row0 * N1, (uint32_t)vec_bytes, bars + s);
         bulk_load(dst + ROWS * N1, p.B + row0 * N1, (uint32_t)vec_bytes, bars + s);
@@ -229,7 +235,9 @@ __global__ void __launch_bounds__(RowTma<N1>::THREADS, 1) row_pass_tma_kernel(co
                     const double m2 = (double)cabs2(x[0][m]);
                     acc[0] += m2;
                     acc[1] += (double)potv(m, p.sg + 1) * m2 + 0.5 * p.sm.g * m2 * m2;
-                    if ((p.sm.which & (MOM_MOD2 | MOM_MOD4)) && p.sm.per_point) {
+                    if ((p.sm.which & (MOM_MOD2 | MOM_MOD4)) && p.sm.per_point &&
+                        XSDE_IN((int64_t)p.sample_slot * p.lt.npts + (int64_t)i0 * N1 + t + m * T,
+                                p.sm.nsamp * p.lt.npts, p.status)) {
                         double *pp = p.sm.per_point + 2 * ((int64_t)p.sample_slot * p.lt.npts + (int64_t)i0 * N1 + t + m * T);
                         atomicAdd(pp, m2 * p.sm.inv_paths);
                         atomicAdd(pp + 1, m2 * m2 * p.sm.inv_paths);
@@ -237,7 +245,8 @@ __global__ void __launch_bounds__(RowTma<N1>::THREADS, 1) row_pass_tma_kernel(co
                 }
                 line_sum2<T>(acc, t, line, scratch);
                 if (t == 0) {
-                    if ((p.sm.which & (MOM_NORM | MOM_ENERGY)) && p.sm.per_path) {
+                    if ((p.sm.which & (MOM_NORM | MOM_ENERGY)) && p.sm.per_path &&
+                        XSDE_IN((int64_t)p.sample_slot * p.npaths + path, p.sm.nsamp * p.npaths, p.status)) {
                         double *pq = p.sm.per_path + 2 * ((int64_t)p.sample_slot * p.npaths + path);
                         atomicAdd(pq, acc[0] * p.sm.dV);
                         atomicAdd(pq + 1, acc[1] * p.sm.dV);
@@ -261,8 +270,10 @@ __global__ void __launch_bounds__(RowTma<N1>::THREADS, 1) row_pass_tma_kernel(co
         __syncthreads();
         if (tid == 0) {
             V *src = bufs + (size_t)s * 2 * ROWS * N1;
-            bulk_store(p.A + row0 * N1, src, (uint32_t)vec_bytes);
-            bulk_store(p.B + row0 * N1, src + ROWS * N1, (uint32_t)vec_bytes);
+            if (XSDE_IN(row0 + ROWS - 1, p.npaths * (int64_t)p.n0, p.status)) {
+                bulk_store(p.A + row0 * N1, src, (uint32_t)vec_bytes);
+                bulk_store(p.B + row0 * N1, src + ROWS * N1, (uint32_t)vec_bytes);
+            }
             bulk_commit();
             if (k + NST - 1 < mine) {
                 bulk_wait_read<1>();     // the stage of item k-1 has been read out
@@ -344,6 +355,12 @@ __global__ void __launch_bounds__(ColTma<N0>::THREADS, ColTma<N0>::CTAS_PER_SM)
         const int s = (int)(k % NST);
         V *dst = bufs + (size_t)s * N0 * C;
         const CUtensorMap *map = vec ? &mapB : &mapA;
+        // (bounds-checking build: a tile past the field is skipped, the stage
+        // completes without bytes)
+        if (!XSDE_IN(tile * C + C - 1, p.n1, p.status) || !XSDE_IN(path, p.npaths, p.status)) {
+            mbar_arrive(bars + s);
+            return;
+        }
         mbar_arrive_expect_tx(bars + s, (uint32_t)Cfg::ITEM);
 #pragma unroll
         for (int b = 0; b < N0 / BOXR; ++b)
@@ -426,7 +443,8 @@ __global__ void __launch_bounds__(ColTma<N0>::THREADS, ColTma<N0>::CTAS_PER_SM)
             if (tid == 0) {
                 double tot = 0.0;
                 for (int q = 0; q < Cfg::THREADS / 32; ++q) tot += scratch[q];
-                if ((p.sm.which & (MOM_NORM | MOM_ENERGY)) && p.sm.per_path)
+                if ((p.sm.which & (MOM_NORM | MOM_ENERGY)) && p.sm.per_path &&
+                    XSDE_IN((int64_t)p.sample_slot * p.npaths + path, p.sm.nsamp * p.npaths, p.status))
                     atomicAdd(p.sm.per_path + 2 * ((int64_t)p.sample_slot * p.npaths + path) + 1,
                               tot * p.sm.dV / ((double)N0 * p.n1));
             }
@@ -451,9 +469,10 @@ __global__ void __launch_bounds__(ColTma<N0>::THREADS, ColTma<N0>::CTAS_PER_SM)
         __syncthreads();
         if (tid == 0) {
             const CUtensorMap *map = vec ? &mapB : &mapA;
+            if (XSDE_IN(tile * C + C - 1, p.n1, p.status) && XSDE_IN(path, p.npaths, p.status))
 #pragma unroll
-            for (int b = 0; b < N0 / BOXR; ++b)
-                tma_store_2d(map, tile * C, (int)(path * N0 + b * BOXR), tileb + (size_t)b * BOXR * C);
+                for (int b = 0; b < N0 / BOXR; ++b)
+                    tma_store_2d(map, tile * C, (int)(path * N0 + b * BOXR), tileb + (size_t)b * BOXR * C);
             bulk_commit();
             if (k + NST - 1 < mine) {
                 bulk_wait_read<1>();

@@ -122,6 +122,12 @@ __global__ void __launch_bounds__(ColW<N0>::THREADS, ColW<N0>::CTAS_PER_SM)
         const int s = (int)(k % NST);
         unsigned char *dst = tiles + (size_t)s * Cfg::TILE;
         issued[s] = k;
+        // (bounds-checking build: a tile past the field is skipped, the stage
+        // completes without bytes)
+        if (!XSDE_IN(tile * C + C - 1, p.n1, p.status) || !XSDE_IN(path, p.npaths, p.status)) {
+            mbar_arrive(full + s);
+            return;
+        }
         mbar_arrive_expect_tx(full + s, (uint32_t)Cfg::TILE);
 #pragma unroll
         for (int b = 0; b < N0 / BOXR; ++b)
@@ -133,9 +139,11 @@ __global__ void __launch_bounds__(ColW<N0>::THREADS, ColW<N0>::CTAS_PER_SM)
         int64_t path;
         decode(k, vec, path, tile);
         const unsigned char *src = tiles + (size_t)(k % NST) * Cfg::TILE;
+        if (XSDE_IN(tile * C + C - 1, p.n1, p.status) && XSDE_IN(path, p.npaths, p.status))
 #pragma unroll
-        for (int b = 0; b < N0 / BOXR; ++b)
-            tma_store_2d(vec ? &mapB : &mapA, tile * C, (int)(path * N0 + b * BOXR), src + (size_t)b * BOXR * (C * 8));
+            for (int b = 0; b < N0 / BOXR; ++b)
+                tma_store_2d(vec ? &mapB : &mapA, tile * C, (int)(path * N0 + b * BOXR),
+                             src + (size_t)b * BOXR * (C * 8));
         bulk_commit();
     };
     // leave on a copy that never lands: record it, stop the CTA's other warps
@@ -199,7 +207,8 @@ __global__ void __launch_bounds__(ColW<N0>::THREADS, ColW<N0>::CTAS_PER_SM)
                 sacc += (p.sm.h0 + p.sm.h2 * (k0 * k0 + k1 * k1)) * (double)cabs2(x[m]);
             }
             sacc = warp_sum(sacc * w);
-            if (lane == 0 && (p.sm.which & (MOM_NORM | MOM_ENERGY)) && p.sm.per_path)
+            if (lane == 0 && (p.sm.which & (MOM_NORM | MOM_ENERGY)) && p.sm.per_path &&
+                XSDE_IN((int64_t)p.sample_slot * p.npaths + path, p.sm.nsamp * p.npaths, p.status))
                 atomicAdd(p.sm.per_path + 2 * ((int64_t)p.sample_slot * p.npaths + path) + 1,
                           sacc * p.sm.dV / ((double)N0 * p.n1));
         }

@@ -58,6 +58,8 @@ __global__ void __launch_bounds__(N / E) rk4ip_adjoint_kernel(const AdjParams<R>
     const LineLayout<V> L{};
     const int t = threadIdx.x;
     const int64_t path = blockIdx.x;
+    if (!XSDE_IN(path, p.npaths, p.status)) return;   // whole CTA: one path each
+    const int64_t nck = (p.nsteps + p.K - 1) / p.K;    // checkpoints held by p.ckpt
 
     for (int i = t; i < N; i += blockDim.x) tws[i] = p.tw[i];
     __syncthreads();
@@ -100,7 +102,8 @@ __global__ void __launch_bounds__(N / E) rk4ip_adjoint_kernel(const AdjParams<R>
     // stage inputs of this path: [nsteps][4][N] (full) or [K][4][N]
     V *interm = p.interm + (size_t)path * (full ? p.nsteps : p.K) * 4 * N;
     // one forward step from x[0]; with `store`, keeps the stage inputs of step n
-    auto forward = [&](V (&x)[2][E], int64_t n, bool store, int64_t slot) {
+    auto forward = [&](V (&x)[2][E], int64_t n, bool store_in, int64_t slot) {
+        const bool store = store_in && XSDE_IN(slot, p.interm_steps, p.status);
         R dtv[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) {
@@ -138,6 +141,7 @@ __global__ void __launch_bounds__(N / E) rk4ip_adjoint_kernel(const AdjParams<R>
     // ---- recomputation of segment blockIdx.y from its checkpoint ------------
     if (p.phase == ADJ_RECOMPUTE) {
         const int64_t n0 = (int64_t)blockIdx.y * p.K, n1 = n0 + p.K;   // never the last segment
+        if (!XSDE_IN(blockIdx.y, nck, p.status)) return;
 #pragma unroll
         for (int m = 0; m < E; ++m) x[0][m] = p.ckpt[blockIdx.y * stride + path * N + t + m * T];
         for (int64_t n = n0; n < n1; ++n) forward(x, n, true, n);
@@ -154,7 +158,7 @@ __global__ void __launch_bounds__(N / E) rk4ip_adjoint_kernel(const AdjParams<R>
         // the last segment keeps its stage inputs right away: the reverse
         // sweep starts there and needs no recomputation of it
         for (int64_t n = 0; n < p.nsteps; ++n) {
-            if (n % p.K == 0) {
+            if (n % p.K == 0 && XSDE_IN(n / p.K, nck, p.status)) {
 #pragma unroll
                 for (int m = 0; m < E; ++m) p.ckpt[(n / p.K) * stride + path * N + t + m * T] = x[0][m];
             }
@@ -208,13 +212,14 @@ __global__ void __launch_bounds__(N / E) rk4ip_adjoint_kernel(const AdjParams<R>
     for (int64_t sgi = nseg - 1; sgi >= 0; --sgi) {
         const int64_t n0 = sgi * p.K;
         const int64_t n1 = (n0 + p.K < p.nsteps) ? n0 + p.K : p.nsteps;
-        if (!full && sgi != nseg - 1) {
+        if (!full && sgi != nseg - 1 && XSDE_IN(sgi, nck, p.status)) {
 #pragma unroll
             for (int m = 0; m < E; ++m) x[0][m] = p.ckpt[sgi * stride + path * N + t + m * T];
             for (int64_t n = n0; n < n1; ++n) forward(x, n, true, n - n0);
         }
         for (int64_t n = n1 - 1; n >= n0; --n) {
             const int64_t slot = full ? n : n - n0;
+            if (!XSDE_IN(slot, p.interm_steps, p.status) || !XSDE_IN(n, p.nsteps, p.status)) break;
             R dtv[E], gv[E];
             V y[2][E], w2s[E], w3s[E];
 #pragma unroll

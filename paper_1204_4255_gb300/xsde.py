@@ -14,9 +14,12 @@ import ctypes
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libxsde.so")
+# XSDE_LIBRARY selects another build of the same C-ABI (the bounds-checking
+# libxsde_bounds.so) for the whole process
+LIB_PATH = os.environ.get("XSDE_LIBRARY") or os.path.join(_HERE, "libxsde.so")
 
-XSDE_OK, XSDE_EINVAL, XSDE_ENOMEM, XSDE_ECUDA, XSDE_ETIMEOUT, XSDE_ENONFINITE, XSDE_EUNSUPPORTED, XSDE_ELIMIT = range(8)
+(XSDE_OK, XSDE_EINVAL, XSDE_ENOMEM, XSDE_ECUDA, XSDE_ETIMEOUT, XSDE_ENONFINITE, XSDE_EUNSUPPORTED, XSDE_ELIMIT,
+ XSDE_EBOUNDS) = range(9)
 XSDE_C64, XSDE_C128 = 1, 2
 XSDE_POT_NONE, XSDE_POT_HARMONIC, XSDE_POT_TABLE = 0, 1, 2
 XSDE_NOISE_NONE, XSDE_NOISE_WIENER_REAL, XSDE_NOISE_WIENER_COMPLEX = 0, 1, 2
