@@ -647,6 +647,50 @@ def batched_cost(reps: int = 3) -> dict:
             "sum_of_alone_ms": sum(c["ms_alone"] for c in classes.values()), "classes": classes}
 
 
+def oracle_table(budget_s: float = 6.0) -> dict:
+    """The FP64 oracle on the host cores for each configuration of the
+    comparison table, one thread and all threads: pt-steps/s (0D: path-steps/s)
+    over as many whole steps as fit in about budget_s (at least one), on the
+    configuration itself or on a stated subset of its paths.  Not part of the
+    default bench run (python bench.py --oracle-table)."""
+    import workloads as W
+    from oracle import oracle as O
+    cases = [
+        ("1 NLS soliton 256, c128", W.nls_soliton(), None),
+        ("2 GPE 512x512, 1 instance", W.gpe_2d(), None),
+        ("3 truncated Wigner 4096x1024 (64-path subset)", W.truncated_wigner(sample_every=0), 64),
+        ("3 OU 65536 paths", W.ornstein_uhlenbeck(sample_every=0), None),
+        ("4 batched: 3D GPE 128^3", W.gpe_3d(), None),
+        ("4 batched: 1D NLS 2048 x 256 (16-path subset)", W.batched_instances(n3=0, sizes2=(), count1=16,
+                                                                          sizes1=(2048,))[0], None),
+        ("5 adjoint control 1024 (forward)", W.adjoint_control(), None),
+    ]
+    out = {"cores": os.cpu_count(), "budget_s": budget_s}
+    for name, w, sub in cases:
+        grid, ops = O.from_workload(w)
+        psi = w.psi0[:sub] if sub else w.psi0
+        row = {}
+        for label, threads in (("1_core", 1), ("all_cores", os.cpu_count() or 1)):
+            O.set_threads(threads)
+            steps, el = 0, 0.0
+            t0 = time.perf_counter()
+            x = psi
+            while el < budget_s and steps < max(1, w.nsteps):
+                x, _, _ = O.rk4ip(x, grid, ops, w.dt, 1, step0=steps)
+                steps += 1
+                el = time.perf_counter() - t0
+            row[label] = {"value": x.shape[0] * w.npts * steps / el, "steps": steps, "s": el}
+        row["paths"] = int(psi.shape[0])
+        out[name] = row
+    w = W.adjoint_control()
+    grid, ops = O.from_workload(w)
+    O.set_threads(os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    O.adjoint(w.psi0, grid, ops, w.extra["target"], w.dt, w.nsteps)
+    out["5 adjoint control 1024 (loss + gradient, all cores)"] = {"s": time.perf_counter() - t0}
+    return out
+
+
 def run_reference(args) -> None:
     rank, world, _ = _dist()
     if rank != 0:
@@ -896,7 +940,12 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched and plain-vs-fused figures")
     ap.add_argument("--case", choices=["gpe2d", "tw1d", "gpe3d", "charged", "example3"],
                     help="run one workload once (for kernel profiles) instead of the bench")
+    ap.add_argument("--oracle-table", action="store_true",
+                    help="time the FP64 oracle on every configuration (host cores) and exit")
     args = ap.parse_args()
+    if args.oracle_table:
+        print(json.dumps(oracle_table()), flush=True)
+        return
     if args.case:
         run_case(args.case)
     elif args.impl == "reference":

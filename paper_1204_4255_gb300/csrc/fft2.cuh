@@ -121,31 +121,32 @@ template <int R, int S> __device__ __forceinline__ void dft_reg(float2 *u) {
     else dft_4x<R, S>(u);
 }
 
-// Physical slot of logical index i during the exchange: the low three bits are
-// XOR-ed with the three bits above log2(E).  With 128-byte swizzled tile rows
-// (two or four columns per warp) both the stage-1 writes and the stage-2 reads
-// then spread a column's lanes evenly over the eight 16-byte bank groups.
+// Physical row of logical index i during a column exchange: the low three bits
+// are XOR-ed with the three bits above log2(E).  With swizzled tile rows (two
+// or four columns per warp) both the stage-1 writes and the stage-2 reads then
+// spread a column's lanes evenly over the eight 16-byte bank groups.
 template <int E> __device__ __forceinline__ int xslot(int i) { return i ^ ((i >> ilog2c(E)) & 7); }
 
 // Twiddle table of the two-stage plan: entry (r - 1) E + j holds w_N^(r j)
 // for r in [1, P), j in [0, E) as (cos_hi, sin_hi, cos_lo, sin_lo).
 template <int N, int E> __host__ __device__ constexpr int warp_fft_table_size() { return (N / E - 1) * E; }
 
-// One transform of the column held by this lane.  `at(row)` is the address of
-// the column's element in physical row `row`; the caller has synchronised the
-// warp since the slots were last read.  Ends with a __syncwarp() before the
+// One transform of the line held by this lane's group of P lanes.  `xat(i)` is
+// the address of the exchange slot of logical index i (the caller's layout
+// spreads both exchange patterns over the banks); the caller has synchronised
+// the warp since the slots were last read.  Ends with a __syncwarp() before the
 // result is in registers, so the slots may be rewritten by the caller.
-template <int N, int E, int S, typename At, typename Tw>
-__device__ __forceinline__ void warp_fft(float2 (&x)[E], int t, const At &at, const Tw &tw) {
+template <int N, int E, int S, typename XAt, typename Tw>
+__device__ __forceinline__ void warp_fft(float2 (&x)[E], int t, const XAt &xat, const Tw &tw) {
     constexpr int P = N / E;
-    static_assert(P == 8 || P == 16, "two-stage plan: 8 or 16 lanes per column");
+    static_assert(P == 8 || P == 16, "two-stage plan: 8 or 16 lanes per line");
     static_assert(E >= P && E % P == 0, "two-stage plan: E >= P");
     dft_reg<E, S>(x);
 #pragma unroll
-    for (int r = 0; r < E; ++r) *at(xslot<E>(E * t + r)) = x[r];
+    for (int r = 0; r < E; ++r) *xat(E * t + r) = x[r];
     __syncwarp();
 #pragma unroll
-    for (int m = 0; m < E; ++m) x[m] = *at(xslot<E>(t + P * m));
+    for (int m = 0; m < E; ++m) x[m] = *xat(t + P * m);
     __syncwarp();
 #pragma unroll
     for (int q = 0; q < E / P; ++q) {
@@ -168,10 +169,10 @@ __device__ __forceinline__ void warp_fft(float2 (&x)[E], int t, const At &at, co
 // twiddles' rounding, where the same-order inverse warp_fft<N, E, +1> is not
 // (on the 512^2 GPE over 2000 steps the norm drifts half as much).  Same
 // synchronisation contract as warp_fft.
-template <int N, int E, typename At, typename Tw>
-__device__ __forceinline__ void warp_ifft_t(float2 (&x)[E], int t, const At &at, const Tw &tw) {
+template <int N, int E, typename XAt, typename Tw>
+__device__ __forceinline__ void warp_ifft_t(float2 (&x)[E], int t, const XAt &xat, const Tw &tw) {
     constexpr int P = N / E;
-    static_assert(P == 8 || P == 16, "two-stage plan: 8 or 16 lanes per column");
+    static_assert(P == 8 || P == 16, "two-stage plan: 8 or 16 lanes per line");
 #pragma unroll
     for (int q = 0; q < E / P; ++q) {
         const int j = t + P * q;
@@ -184,10 +185,10 @@ __device__ __forceinline__ void warp_ifft_t(float2 (&x)[E], int t, const At &at,
         for (int r = 1; r < P; ++r) x[q + (E / P) * r] = twiddle_mul<+1>(u[r], tw((r - 1) * E + j));
     }
 #pragma unroll
-    for (int m = 0; m < E; ++m) *at(xslot<E>(t + P * m)) = x[m];
+    for (int m = 0; m < E; ++m) *xat(t + P * m) = x[m];
     __syncwarp();
 #pragma unroll
-    for (int r = 0; r < E; ++r) x[r] = *at(xslot<E>(E * t + r));
+    for (int r = 0; r < E; ++r) x[r] = *xat(E * t + r);
     __syncwarp();
     dft_reg<E, +1>(x);
 }
