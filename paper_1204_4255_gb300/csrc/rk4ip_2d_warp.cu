@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(ColW<N0>::THREADS, ColW<N0>::CTAS_PER_SM)
     const int64_t mine = nitems > blockIdx.x ? (nitems - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
     for (int i = tid; i < Cfg::NTW; i += blockDim.x) tw_s[i] = p.tw0w[i];
-    for (int i = tid; i < 2 * N0; i += blockDim.x) e0_s[i] = p.E0[i];
+    for (int i = tid; i < N0; i += blockDim.x) e0_s[i] = p.E0[i];
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) {
             mbar_init(full + s, 1);
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(ColW<N0>::THREADS, ColW<N0>::CTAS_PER_SM)
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int j = t + P * m;
-            x[m] = cmul_hilo(x[m], e0_s[j], e0_s[N0 + j]);
+            x[m] = cmul(x[m], e0_s[j]);   // the factor's FP32 rounding, as in the row pass
         }
         warp_ifft_t<N0, E>(x, t, xat, tw);
 #pragma unroll

@@ -186,7 +186,9 @@ def test_2d_c64_pipelined_passes_match_generic_and_oracle(shape):
     assert np.max(rel_l2(fast.reshape(3, -1), ref.reshape(3, -1), axis=1)) < 1e-4
     assert np.max(rel_l2(fast.reshape(3, -1), gen.reshape(3, -1), axis=1)) < 1e-5
     assert np.max(np.abs(pp_f - opp) / np.abs(opp)) < 1e-4
-    assert np.max(np.abs(pq_f - opq) / np.abs(opq)) < 1e-4
+    # per-point moments against max(|oracle|, 1e-3 of the peak): the Gaussian tails
+    # (|psi|^2 ~ 1e-21 of the peak) lie below complex64 resolution of the field
+    assert np.max(np.abs(pq_f - opq) / np.maximum(np.abs(opq), 1e-3 * np.abs(opq).max())) < 1e-4
 
 
 def test_2d_gpe_512_c128_first_steps():
@@ -306,7 +308,9 @@ def test_c64_pipelined_passes_3d_and_short_lines(shape):
     assert np.max(rel_l2(fast.reshape(npaths, -1), gen.reshape(npaths, -1), axis=1)) < 1e-5
     assert np.max(rel_l2(mixed.reshape(npaths, -1), gen.reshape(npaths, -1), axis=1)) < 1e-5
     assert np.max(np.abs(pp_f - opp) / np.abs(opp)) < 1e-4
-    assert np.max(np.abs(pq_f - opq) / np.abs(opq)) < 1e-4
+    # per-point moments against max(|oracle|, 1e-3 of the peak): the Gaussian tails
+    # (|psi|^2 ~ 1e-21 of the peak) lie below complex64 resolution of the field
+    assert np.max(np.abs(pq_f - opq) / np.maximum(np.abs(opq), 1e-3 * np.abs(opq).max())) < 1e-4
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
