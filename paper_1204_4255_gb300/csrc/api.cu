@@ -285,8 +285,15 @@ template <typename R, int E = 8> int upload_twiddles(int n, void **dptr, cudaStr
 int upload_twiddles_2stage(int n, int E, void **dptr, cudaStream_t s) {
     std::vector<float4> tmp((size_t)(n / E - 1) * E);
     for (int r = 1; r < n / E; ++r)
-        for (int j = 0; j < E; ++j)
-            make_twiddle(std::polar(1.0, -2.0 * M_PI * (double)((long)r * j) / n), &tmp[(size_t)(r - 1) * E + j]);
+        for (int j = 0; j < E; ++j) {
+            // (c, s) the FP32 rounding of w_n^(r j); (c eps, s eps), eps =
+            // 1/(c^2 + s^2) - 1, the part that makes the backward transform the
+            // exact inverse
+            const std::complex<double> w = std::polar(1.0, -2.0 * M_PI * (double)((long)r * j) / n);
+            const float c = (float)w.real(), sn = (float)w.imag();
+            const double eps = 1.0 / ((double)c * c + (double)sn * sn) - 1.0;
+            tmp[(size_t)(r - 1) * E + j] = make_float4(c, sn, (float)(c * eps), (float)(sn * eps));
+        }
     return upload_raw(tmp, dptr, s);
 }
 

@@ -9,11 +9,20 @@
 //   stage 1 (Ns = 1, radix E) : butterfly j = t, inputs x[t + P r], outputs y[E t + r]
 //   stage 2 (Ns = E, radix P) : butterflies j = t + P q (q < E/P), inputs x[j + E r],
 //                               twiddles w^(r j), outputs y[j + E r] -- natural order.
-// Forward transforms (S = -1) are unnormalised, inverse ones (S = +1) take the
-// conjugate roots (XMDS2 Sec. 2.2's spectral transform for the Fourier basis
-// of Sec. 2.1).  The radix-16 and radix-32 DFTs are 4 x 4 and 4 x 8 products
-// whose internal roots are compile-time FP64 values split into an FP32 pair
-// and applied with the compensated products of device_common.cuh.
+// The forward transform (XMDS2 Sec. 2.2's spectral transform for the Fourier
+// basis of Sec. 2.1) is unnormalised.  The backward one is its exact inverse
+// (times N), taken factor by factor in reverse order: every root the forward
+// multiplies by is the FP32 rounding w~ of the FP64 value, and the backward
+// multiplies by 1/w~ = conj(w~) (1 + eps), eps = 1/|w~|^2 - 1, held as the
+// pair conj(w~) + conj(w~) eps and applied with one rounding per component
+// (cmulconj_hilo: a correction of a fraction of an ulp added after the product
+// had been rounded would be lost, and systematically so).  A forward /
+// backward pair is then the identity up to the arithmetic's rounding, whatever
+// the modulus of the rounded roots -- the modulus bias of plain FP32 roots in
+// both directions drains the norm by ~1e-4 over a 2000-step 2D run -- at 4 + 8
+// instructions per root pair instead of 8 + 8 for compensated roots both ways.
+// The radix-16 and radix-32 DFTs are 4 x 4 and 4 x 8 products whose internal
+// roots are compile-time FP64 values rounded the same way.
 #pragma once
 
 #include <type_traits>
@@ -62,53 +71,68 @@ template <int B, int E, typename F> __device__ __forceinline__ void static_for(F
     }
 }
 
-// x * exp(S 2 pi i K / N) for compile-time K, N.  Multiples of pi/2 are exact
-// swaps and sign changes; odd multiples of pi/4 use the split 1/sqrt(2) of
-// dft8; every other root is an FP32 hi + lo pair of the FP64 value.
-template <int K, int N, int S> __device__ __forceinline__ float2 rot_const(float2 x) {
-    constexpr int k = ((K % N) + N) % N;
-    constexpr int e8 = (8 * k) % N == 0 ? (8 * k) / N : -1;   // k = e8 N / 8
-    if constexpr (k == 0) {
-        return x;
-    } else if constexpr (e8 >= 0) {
-        // exp(S i pi e8 / 4): (S < 0) e8 -> 8 - e8 with S > 0
-        constexpr int e = S < 0 ? (8 - e8) % 8 : e8;
-        if constexpr (e == 2) return cmul_i(x);
-        else if constexpr (e == 4) return make_float2(-x.x, -x.y);
-        else if constexpr (e == 6) return cmul_mi(x);
-        else if constexpr (e == 1) return make_float2(mul_rsqrt2(x.x - x.y), mul_rsqrt2(x.x + x.y));
-        else if constexpr (e == 3) return make_float2(-mul_rsqrt2(x.x + x.y), mul_rsqrt2(x.x - x.y));
-        else if constexpr (e == 5) return make_float2(mul_rsqrt2(x.y - x.x), -mul_rsqrt2(x.x + x.y));
-        else return make_float2(mul_rsqrt2(x.x + x.y), mul_rsqrt2(x.y - x.x));   // e == 7
-    } else {
-        constexpr double c = cos_2pi_frac(k, N), s = S * sin_2pi_frac(k, N);
-        constexpr float ch = (float)c, sh = (float)s;
-        constexpr float cl = (float)(c - (double)ch), sl = (float)(s - (double)sh);
-        return cmul_hilo(x, make_float2(ch, sh), make_float2(cl, sl));
-    }
+// The FP32 rounding of exp(-2 pi i K / N) for compile-time K, N, and the eps
+// of its exact inverse.
+template <int K, int N> struct Root {
+    static constexpr int k = ((K % N) + N) % N;
+    static constexpr double c = cos_2pi_frac(k, N), s = -sin_2pi_frac(k, N);
+    static constexpr float ch = (float)c, sh = (float)s;
+    static constexpr double eps = 1.0 / ((double)ch * (double)ch + (double)sh * (double)sh) - 1.0;
+    static constexpr float cl = (float)((double)ch * eps), sl = (float)((double)sh * eps);   // w~ eps
+    // k a multiple of N/8: exp(-i pi e8 / 4)
+    static constexpr int e8 = (8 * k) % N == 0 ? (8 * k) / N : -1;
+};
+
+// x * exp(-i pi e / 4) (FWD) or x * exp(+i pi e / 4) (!FWD): exact swaps and
+// sign changes at multiples of pi/2, the split 1/sqrt(2) of dft8 at odd
+// multiples of pi/4 (accurate to ~1e-15, so either direction is the other's
+// inverse to rounding)
+template <int E8, bool FWD> __device__ __forceinline__ float2 rot_eighth(float2 x) {
+    constexpr int e = FWD ? (8 - E8) % 8 : E8;   // as a positive rotation
+    if constexpr (e == 0) return x;
+    else if constexpr (e == 2) return cmul_i(x);
+    else if constexpr (e == 4) return make_float2(-x.x, -x.y);
+    else if constexpr (e == 6) return cmul_mi(x);
+    else if constexpr (e == 1) return make_float2(mul_rsqrt2(x.x - x.y), mul_rsqrt2(x.x + x.y));
+    else if constexpr (e == 3) return make_float2(-mul_rsqrt2(x.x + x.y), mul_rsqrt2(x.x - x.y));
+    else if constexpr (e == 5) return make_float2(mul_rsqrt2(x.y - x.x), -mul_rsqrt2(x.x + x.y));
+    else return make_float2(mul_rsqrt2(x.x + x.y), mul_rsqrt2(x.y - x.x));   // e == 7
 }
 
-// DFT of R = 16 or 32 points in registers, natural order in and out:
+// forward root: x * w~
+template <int K, int N> __device__ __forceinline__ float2 rot_fwd(float2 x) {
+    using W = Root<K, N>;
+    if constexpr (W::e8 >= 0) return rot_eighth<W::e8, true>(x);
+    else return make_float2(fmaf(x.x, W::ch, -x.y * W::sh), fmaf(x.x, W::sh, x.y * W::ch));
+}
+// its inverse: x * conj(w~ + w~ eps), one rounding per component
+template <int K, int N> __device__ __forceinline__ float2 rot_inv(float2 x) {
+    using W = Root<K, N>;
+    if constexpr (W::e8 >= 0) return rot_eighth<W::e8, false>(x);
+    else return cmulconj_hilo(x, make_float2(W::ch, W::sh), make_float2(W::cl, W::sl));
+}
+
+// Forward DFT of R = 16 or 32 points in registers, natural order in and out:
 // n = n1 + 4 n2, k = k2 + (R/4) k1; inner DFT_{R/4} over n2, roots w_R^(n1 k2),
 // outer DFT_4 over n1.
-template <int R, int S> __device__ __forceinline__ void dft_4x(float2 *u) {
+template <int R> __device__ __forceinline__ void dft_4x_fwd(float2 *u) {
     constexpr int Q = R / 4;
     static_for<0, 4>([&](auto n1c) {
         constexpr int n1 = decltype(n1c)::value;
         float2 v[Q];
 #pragma unroll
         for (int n2 = 0; n2 < Q; ++n2) v[n2] = u[n1 + 4 * n2];
-        dft<Q, S>(v);
+        dft<Q, -1>(v);
         static_for<0, Q>([&](auto k2c) {
             constexpr int k2 = decltype(k2c)::value;
-            u[n1 + 4 * k2] = rot_const<n1 * k2, R, S>(v[k2]);
+            u[n1 + 4 * k2] = rot_fwd<n1 * k2, R>(v[k2]);
         });
     });
     float2 o[R];
 #pragma unroll
     for (int k2 = 0; k2 < Q; ++k2) {
         float2 v[4] = {u[4 * k2], u[4 * k2 + 1], u[4 * k2 + 2], u[4 * k2 + 3]};
-        dft4<S>(v);
+        dft4<-1>(v);
 #pragma unroll
         for (int k1 = 0; k1 < 4; ++k1) o[k2 + Q * k1] = v[k1];
     }
@@ -116,9 +140,50 @@ template <int R, int S> __device__ __forceinline__ void dft_4x(float2 *u) {
     for (int k = 0; k < R; ++k) u[k] = o[k];
 }
 
-template <int R, int S> __device__ __forceinline__ void dft_reg(float2 *u) {
-    if constexpr (R <= 8) dft<R, S>(u);
-    else dft_4x<R, S>(u);
+// R times the inverse of dft_4x_fwd<R>: its factors in reverse order, each
+// inverted (DFT_4 and DFT_{R/4} by their conjugates, the roots by rot_inv).
+template <int R> __device__ __forceinline__ void dft_4x_bwd(float2 *u) {
+    constexpr int Q = R / 4;
+    float2 o[R];
+    static_for<0, Q>([&](auto k2c) {
+        constexpr int k2 = decltype(k2c)::value;
+        float2 v[4] = {u[k2], u[k2 + Q], u[k2 + 2 * Q], u[k2 + 3 * Q]};
+        dft4<+1>(v);
+        static_for<0, 4>([&](auto n1c) {
+            constexpr int n1 = decltype(n1c)::value;
+            o[n1 + 4 * k2] = rot_inv<n1 * k2, R>(v[n1]);
+        });
+    });
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) {
+        float2 v[Q];
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) v[k2] = o[n1 + 4 * k2];
+        dft<Q, +1>(v);
+#pragma unroll
+        for (int n2 = 0; n2 < Q; ++n2) u[n1 + 4 * n2] = v[n2];
+    }
+}
+
+// DFT_R forward, and R times its inverse (radix 8 and below: dft8's roots are
+// the accurate 1/sqrt(2) pair, so the conjugate DFT is the inverse)
+template <int R> __device__ __forceinline__ void dft_fwd(float2 *u) {
+    if constexpr (R <= 8) dft<R, -1>(u);
+    else dft_4x_fwd<R>(u);
+}
+template <int R> __device__ __forceinline__ void dft_bwd(float2 *u) {
+    if constexpr (R <= 8) dft<R, +1>(u);
+    else dft_4x_bwd<R>(u);
+}
+
+// Stage-2 twiddle entry (c, s, c eps, s eps): c + i s the FP32 rounding of
+// w_N^(r j), eps = 1/(c^2 + s^2) - 1.  Forward: x * (c + i s); backward:
+// x * conj((c + i s)(1 + eps)), its exact inverse, rounded once.
+__device__ __forceinline__ float2 tw_fwd(float2 x, float4 w) {
+    return make_float2(fmaf(x.x, w.x, -x.y * w.y), fmaf(x.x, w.y, x.y * w.x));
+}
+__device__ __forceinline__ float2 tw_bwd(float2 x, float4 w) {
+    return cmulconj_hilo(x, make_float2(w.x, w.y), make_float2(w.z, w.w));
 }
 
 // Physical row of logical index i during a column exchange: the low three bits
@@ -128,20 +193,21 @@ template <int R, int S> __device__ __forceinline__ void dft_reg(float2 *u) {
 template <int E> __device__ __forceinline__ int xslot(int i) { return i ^ ((i >> ilog2c(E)) & 7); }
 
 // Twiddle table of the two-stage plan: entry (r - 1) E + j holds w_N^(r j)
-// for r in [1, P), j in [0, E) as (cos_hi, sin_hi, cos_lo, sin_lo).
+// for r in [1, P), j in [0, E) as (c, s, c eps, s eps) (tw_fwd / tw_bwd).
 template <int N, int E> __host__ __device__ constexpr int warp_fft_table_size() { return (N / E - 1) * E; }
 
-// One transform of the line held by this lane's group of P lanes.  `xat(i)` is
-// the address of the exchange slot of logical index i (the caller's layout
-// spreads both exchange patterns over the banks); the caller has synchronised
-// the warp since the slots were last read.  Ends with a __syncwarp() before the
-// result is in registers, so the slots may be rewritten by the caller.
-template <int N, int E, int S, typename XAt, typename Tw>
+// The forward transform of the line held by this lane's group of P lanes.
+// `xat(i)` is the address of the exchange slot of logical index i (the
+// caller's layout spreads both exchange patterns over the banks); the caller
+// has synchronised the warp since the slots were last read.  Ends with a
+// __syncwarp() before the result is in registers, so the slots may be
+// rewritten by the caller.
+template <int N, int E, typename XAt, typename Tw>
 __device__ __forceinline__ void warp_fft(float2 (&x)[E], int t, const XAt &xat, const Tw &tw) {
     constexpr int P = N / E;
     static_assert(P == 8 || P == 16, "two-stage plan: 8 or 16 lanes per line");
     static_assert(E >= P && E % P == 0, "two-stage plan: E >= P");
-    dft_reg<E, S>(x);
+    dft_fwd<E>(x);
 #pragma unroll
     for (int r = 0; r < E; ++r) *xat(E * t + r) = x[r];
     __syncwarp();
@@ -154,23 +220,18 @@ __device__ __forceinline__ void warp_fft(float2 (&x)[E], int t, const XAt &xat, 
         float2 u[P];
         u[0] = x[q];
 #pragma unroll
-        for (int r = 1; r < P; ++r) u[r] = twiddle_mul<S>(x[q + (E / P) * r], tw((r - 1) * E + j));
-        dft_reg<P, S>(u);
+        for (int r = 1; r < P; ++r) u[r] = tw_fwd(x[q + (E / P) * r], tw((r - 1) * E + j));
+        dft_fwd<P>(u);
 #pragma unroll
         for (int r = 0; r < P; ++r) x[q + (E / P) * r] = u[r];
     }
 }
 
-// The conjugate transpose of warp_fft<N, E, -1>: stage 2 transposed (DFT_P with
-// the conjugate roots, then the conjugate twiddles), the exchange transposed,
-// then DFT_E with the conjugate roots.  In exact arithmetic it is N times the
-// inverse of the forward transform computed with the same rounded twiddles, so
-// a forward / inverse pair around a unit-modulus factor is unitary whatever the
-// twiddles' rounding, where the same-order inverse warp_fft<N, E, +1> is not
-// (on the 512^2 GPE over 2000 steps the norm drifts half as much).  Same
+// N times the inverse of warp_fft<N, E>: stage 2 undone (DFT_P inverted, then
+// the twiddles), the exchange undone, then DFT_E inverted.  Same
 // synchronisation contract as warp_fft.
 template <int N, int E, typename XAt, typename Tw>
-__device__ __forceinline__ void warp_ifft_t(float2 (&x)[E], int t, const XAt &xat, const Tw &tw) {
+__device__ __forceinline__ void warp_ifft(float2 (&x)[E], int t, const XAt &xat, const Tw &tw) {
     constexpr int P = N / E;
     static_assert(P == 8 || P == 16, "two-stage plan: 8 or 16 lanes per line");
 #pragma unroll
@@ -179,10 +240,10 @@ __device__ __forceinline__ void warp_ifft_t(float2 (&x)[E], int t, const XAt &xa
         float2 u[P];
 #pragma unroll
         for (int r = 0; r < P; ++r) u[r] = x[q + (E / P) * r];
-        dft_reg<P, +1>(u);
+        dft_bwd<P>(u);
         x[q] = u[0];
 #pragma unroll
-        for (int r = 1; r < P; ++r) x[q + (E / P) * r] = twiddle_mul<+1>(u[r], tw((r - 1) * E + j));
+        for (int r = 1; r < P; ++r) x[q + (E / P) * r] = tw_bwd(u[r], tw((r - 1) * E + j));
     }
 #pragma unroll
     for (int m = 0; m < E; ++m) *xat(t + P * m) = x[m];
@@ -190,7 +251,7 @@ __device__ __forceinline__ void warp_ifft_t(float2 (&x)[E], int t, const XAt &xa
 #pragma unroll
     for (int r = 0; r < E; ++r) x[r] = *xat(E * t + r);
     __syncwarp();
-    dft_reg<E, +1>(x);
+    dft_bwd<E>(x);
 }
 
 }  // namespace xsde

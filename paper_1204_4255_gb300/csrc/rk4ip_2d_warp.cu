@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(ColW<N0>::THREADS, ColW<N0>::CTAS_PER_SM)
 #pragma unroll
         for (int m = 0; m < E; ++m) x[m] = *at(t + P * m);
         __syncwarp();
-        warp_fft<N0, E, -1>(x, t, xat, tw);
+        warp_fft<N0, E>(x, t, xat, tw);
         if (sample && vec == 0) {
             // kinetic energy of a_n: sum_k Re(i L(k)) |F psi|^2 dV/(n0 n1); the
             // dimension-1 factor of exp(L dt/2) already applied is divided out
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(ColW<N0>::THREADS, ColW<N0>::CTAS_PER_SM)
             const int j = t + P * m;
             x[m] = cmul(x[m], e0_s[j]);   // the factor's FP32 rounding, as in the row pass
         }
-        warp_ifft_t<N0, E>(x, t, xat, tw);
+        warp_ifft<N0, E>(x, t, xat, tw);
 #pragma unroll
         for (int m = 0; m < E; ++m) *at(t + P * m) = x[m];
         // the tile goes out through the tensor-memory-access unit (async proxy)
