@@ -69,6 +69,7 @@ struct xsde_problem {
     void *d_tw[3] = {nullptr, nullptr, nullptr};
     void *d_tw1d[2] = {nullptr, nullptr};   // 1D: twiddles of the radix-4 and radix-2 plans
     void *d_tw2[3] = {nullptr, nullptr, nullptr};   // complex64 2D/3D: two-stage plan twiddles (warp column pass)
+    void *d_twp = nullptr;   // complex64 2D/3D: paired twiddles of the row dimension (TMA row pass)
     void *d_E[3] = {nullptr, nullptr, nullptr};
     void *d_scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -259,12 +260,25 @@ void make_twiddle(const std::complex<double> &z, float4 *out) {
     *out = make_float4(hi.x, hi.y, lo.x, lo.y);
 }
 
+// the paired form (c, s, c eps, s eps) of a twiddle for fft.cuh's fftp_* and
+// fft2.cuh: (c, s) its FP32 rounding, eps = 1/(c^2 + s^2) - 1, the part that
+// makes the backward transform the exact inverse of the forward
+void make_twiddle_paired(const std::complex<double> &z, float4 *out) {
+    const float c = (float)z.real(), sn = (float)z.imag();
+    const double eps = 1.0 / ((double)c * c + (double)sn * sn) - 1.0;
+    *out = make_float4(c, sn, (float)(c * eps), (float)(sn * eps));
+}
+
 // per-stage layout of fft.cuh: stage (Ns, R) holds w_n^(r k n/(Ns R)) at
 // [stage_table_offset(n, Ns) + (r-1) Ns + k]; n entries are allocated (the
-// table needs at most n - 1)
-template <typename R, int E = 8> int upload_twiddles(int n, void **dptr, cudaStream_t s) {
+// table needs at most n - 1).  PAIRED (complex64): entries for fftp_*.
+template <typename R, int E = 8, bool PAIRED = false> int upload_twiddles(int n, void **dptr, cudaStream_t s) {
     std::vector<tw_t<R>> tmp(n);
-    make_twiddle(std::complex<double>(0.0, 0.0), &tmp[n - 1]);
+    auto put = [&](const std::complex<double> &z, tw_t<R> *out) {
+        if constexpr (PAIRED) make_twiddle_paired(z, out);
+        else make_twiddle(z, out);
+    };
+    put(std::complex<double>(0.0, 0.0), &tmp[n - 1]);
     for (int ns = 1; ns < n;) {
         const int rad = stage_radix<E>(n / ns);
         if (ns > 1) {
@@ -272,7 +286,7 @@ template <typename R, int E = 8> int upload_twiddles(int n, void **dptr, cudaStr
             for (int r = 1; r < rad; ++r)
                 for (int k = 0; k < ns; ++k) {
                     const long m = (long)r * k * (n / (ns * rad));
-                    make_twiddle(std::polar(1.0, -2.0 * M_PI * (double)m / n), &tmp[off + (r - 1) * ns + k]);
+                    put(std::polar(1.0, -2.0 * M_PI * (double)m / n), &tmp[off + (r - 1) * ns + k]);
                 }
         }
         ns *= rad;
@@ -285,15 +299,8 @@ template <typename R, int E = 8> int upload_twiddles(int n, void **dptr, cudaStr
 int upload_twiddles_2stage(int n, int E, void **dptr, cudaStream_t s) {
     std::vector<float4> tmp((size_t)(n / E - 1) * E);
     for (int r = 1; r < n / E; ++r)
-        for (int j = 0; j < E; ++j) {
-            // (c, s) the FP32 rounding of w_n^(r j); (c eps, s eps), eps =
-            // 1/(c^2 + s^2) - 1, the part that makes the backward transform the
-            // exact inverse
-            const std::complex<double> w = std::polar(1.0, -2.0 * M_PI * (double)((long)r * j) / n);
-            const float c = (float)w.real(), sn = (float)w.imag();
-            const double eps = 1.0 / ((double)c * c + (double)sn * sn) - 1.0;
-            tmp[(size_t)(r - 1) * E + j] = make_float4(c, sn, (float)(c * eps), (float)(sn * eps));
-        }
+        for (int j = 0; j < E; ++j)
+            make_twiddle_paired(std::polar(1.0, -2.0 * M_PI * (double)((long)r * j) / n), &tmp[(size_t)(r - 1) * E + j]);
     return upload_raw(tmp, dptr, s);
 }
 
@@ -313,11 +320,15 @@ template <typename V> int ensure_tables(xsde_problem *p, double dt, cudaStream_t
     int rc;
     for (int d = 0; d < g.ndim; ++d)
         if ((rc = upload_twiddles<decltype(V::x)>(g.n[d], &p->d_tw[d], s)) != XSDE_OK) return rc;
-    if constexpr (std::is_same<V, float2>::value)
+    if constexpr (std::is_same<V, float2>::value) {
         for (int d = 0; d < g.ndim && g.ndim >= 2; ++d)
             if (warp_col_supported(g.n[d], WARP_COL_C) &&
                 (rc = upload_twiddles_2stage(g.n[d], warp_col_elems(g.n[d]), &p->d_tw2[d], s)) != XSDE_OK)
                 return rc;
+        if (g.ndim >= 2 && tma_row_supported(g.n[g.ndim - 1]) &&
+            (rc = upload_twiddles<float, 8, true>(g.n[g.ndim - 1], &p->d_twp, s)) != XSDE_OK)
+            return rc;
+    }
     if (g.ndim == 1) {
         const int n = g.n[0];
         // the radix-4 and radix-2 plans of the 4- and 2-element launch shapes
@@ -595,6 +606,8 @@ int run_3d(xsde_problem *p, void *psi, int64_t nsteps, int64_t npaths, uint64_t 
                            npaths * g.n[0], (int64_t)g.n[1] * g.n[2], g.n[0]);
             q1.tw0w = static_cast<const tw_t<R> *>(p->d_tw2[1]);
             q0.tw0w = static_cast<const tw_t<R> *>(p->d_tw2[0]);
+            qr.tw1p = static_cast<const tw_t<R> *>(p->d_twp);
+            if (!qr.tw1p) rk = PASS_GENERIC;
         }
     }
     auto row = [&](int mode, uint64_t sg, int slot) -> cudaError_t {
@@ -942,6 +955,8 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
                           npaths * g.n[0], g.n[1], g.n[0]);
         }
         q.tw0w = static_cast<const tw_t<R> *>(p->d_tw2[0]);
+        q.tw1p = static_cast<const tw_t<R> *>(p->d_twp);
+        if (!q.tw1p) rk = PASS_GENERIC;
     }
     auto row = [&](int mode, uint64_t sg, int slot) -> cudaError_t {
         q.sg = sg;
@@ -1196,6 +1211,7 @@ void xsde_problem_destroy(xsde_problem *p) {
     cudaFree(p->d_tw1d[0]);
     cudaFree(p->d_tw1d[1]);
     for (int d = 0; d < 3; ++d) cudaFree(p->d_tw2[d]);
+    cudaFree(p->d_twp);
     cudaFree(p->d_knl);
     cudaFree(p->d_B);
     for (int d = 0; d < 3; ++d) cudaFree(p->d_Ef[d]);
@@ -1861,6 +1877,8 @@ std::vector<uintptr_t> member_signature(const xsde_batch_member &m) {
     }
     v.push_back((uintptr_t)p->d_tw1d[0]);
     v.push_back((uintptr_t)p->d_tw1d[1]);
+    for (int d = 0; d < 3; ++d) v.push_back((uintptr_t)p->d_tw2[d]);
+    v.push_back((uintptr_t)p->d_twp);
     return v;
 }
 

@@ -220,6 +220,118 @@ __device__ __forceinline__ void fft(V (&v)[NV][E], int t, V *const (&sm)[NV], co
     fft_from<N, E, S, 1, NV>(v, t, sm, L, sync, tw);
 }
 
+// --- paired complex64 transforms ---------------------------------------------
+// fftp_fwd is fft<N, E, -1> with every twiddle applied as its FP32 rounding
+// w~ alone; fftp_bwd is N times its exact inverse: the stages and exchanges
+// undone in reverse order, each butterfly by the conjugate DFT_R (dft8's
+// 1/sqrt(2) is accurate to ~1e-15) and each twiddle by 1/w~ = conj(w~)(1 + eps),
+// eps = 1/|w~|^2 - 1, applied from the pair (w~, w~ eps) with one rounding per
+// component.  Table entries (c, s, c eps, s eps) in the per-stage layout.  A
+// forward / backward pair is the identity up to rounding whatever the modulus
+// of the rounded twiddles, which is what keeps a long run's norm: plain FP32
+// twiddles in both directions drain ~1e-4 over 2000 2D steps.
+__device__ __forceinline__ float2 twp_fwd(float2 x, float4 w) {
+    return make_float2(fmaf(x.x, w.x, -x.y * w.y), fmaf(x.x, w.y, x.y * w.x));
+}
+__device__ __forceinline__ float2 twp_bwd(float2 x, float4 w) {
+    return cmulconj_hilo(x, make_float2(w.x, w.y), make_float2(w.z, w.w));
+}
+
+template <int N, int E, int R, int Ns, bool FWD, int NV, typename Tw>
+__device__ __forceinline__ void fftp_stage(float2 (&v)[NV][E], int t, const Tw &tw) {
+    constexpr int B = E / R, T = N / E;
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        float4 w[R];
+        if constexpr (Ns > 1) {
+            const int k = (t + q * T) & (Ns - 1);
+            constexpr int off = stage_table_offset<E>(N, Ns);
+#pragma unroll
+            for (int r = 1; r < R; ++r) w[r] = tw(off + (r - 1) * Ns + k);
+        }
+#pragma unroll
+        for (int iv = 0; iv < NV; ++iv) {
+            float2 u[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) u[r] = v[iv][q + r * B];
+            if constexpr (FWD) {
+                if constexpr (Ns > 1) {
+#pragma unroll
+                    for (int r = 1; r < R; ++r) u[r] = twp_fwd(u[r], w[r]);
+                }
+                dft<R, -1>(u);
+            } else {
+                dft<R, +1>(u);
+                if constexpr (Ns > 1) {
+#pragma unroll
+                    for (int r = 1; r < R; ++r) u[r] = twp_bwd(u[r], w[r]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[iv][q + r * B] = u[r];
+        }
+    }
+}
+
+// the inverse permutation of fft_exchange<N, E, R, Ns>
+template <int N, int E, int R, int Ns, int NV, typename V, typename Layout, typename Sync>
+__device__ __forceinline__ void fft_exchange_back(V (&v)[NV][E], int t, V *const (&sm)[NV], const Layout &L,
+                                                  const Sync &sync) {
+    constexpr int B = E / R, T = N / E;
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        const int slot = L(t + m * T);
+#pragma unroll
+        for (int iv = 0; iv < NV; ++iv) sm[iv][slot] = v[iv][m];
+    }
+    sync();
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        const int j = t + q * T;
+        const int k = j & (Ns - 1);
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int slot = L(base + r * Ns);
+#pragma unroll
+            for (int iv = 0; iv < NV; ++iv) v[iv][q + r * B] = sm[iv][slot];
+        }
+    }
+    sync();
+}
+
+template <int N, int E, int Ns, int NV, typename Layout, typename Sync, typename Tw>
+__device__ __forceinline__ void fftp_fwd_from(float2 (&v)[NV][E], int t, float2 *const (&sm)[NV], const Layout &L,
+                                              const Sync &sync, const Tw &tw) {
+    constexpr int R = stage_radix<E>(N / Ns);
+    static_assert(E % R == 0, "radix must divide the elements per thread");
+    fftp_stage<N, E, R, Ns, true, NV>(v, t, tw);
+    if constexpr (Ns * R < N) {
+        fft_exchange<N, E, R, Ns, NV>(v, t, sm, L, sync);
+        fftp_fwd_from<N, E, Ns * R, NV>(v, t, sm, L, sync, tw);
+    }
+}
+template <int N, int E, int Ns, int NV, typename Layout, typename Sync, typename Tw>
+__device__ __forceinline__ void fftp_bwd_from(float2 (&v)[NV][E], int t, float2 *const (&sm)[NV], const Layout &L,
+                                              const Sync &sync, const Tw &tw) {
+    constexpr int R = stage_radix<E>(N / Ns);
+    if constexpr (Ns * R < N) {
+        fftp_bwd_from<N, E, Ns * R, NV>(v, t, sm, L, sync, tw);
+        fft_exchange_back<N, E, R, Ns, NV>(v, t, sm, L, sync);
+    }
+    fftp_stage<N, E, R, Ns, false, NV>(v, t, tw);
+}
+template <int N, int E, int NV, typename Layout, typename Sync, typename Tw>
+__device__ __forceinline__ void fftp_fwd(float2 (&v)[NV][E], int t, float2 *const (&sm)[NV], const Layout &L,
+                                         const Sync &sync, const Tw &tw) {
+    fftp_fwd_from<N, E, 1, NV>(v, t, sm, L, sync, tw);
+}
+template <int N, int E, int NV, typename Layout, typename Sync, typename Tw>
+__device__ __forceinline__ void fftp_bwd(float2 (&v)[NV][E], int t, float2 *const (&sm)[NV], const Layout &L,
+                                         const Sync &sync, const Tw &tw) {
+    fftp_bwd_from<N, E, 1, NV>(v, t, sm, L, sync, tw);
+}
+
 // --- index maps and barriers ------------------------------------------------
 
 // Exchange buffer of one line.  8-byte elements (complex64): rows of 16 slots

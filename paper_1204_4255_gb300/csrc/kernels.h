@@ -166,6 +166,9 @@ template <typename R> struct Params2D {
     // twiddles of the two-stage plan of dimension 0 (fft2.cuh), for the warp
     // column pass: entry (r-1) E + j holds w_n0^(r j), r < n0/E, j < E
     const tw_t<R> *tw0w = nullptr;
+    // complex64 TMA row pass: the paired twiddles of fftp_fwd / fftp_bwd (fft.cuh)
+    // for the row dimension
+    const tw_t<R> *tw1p = nullptr;
     // non-local term (2D, ROW_NL / COL_CONV): density / potential field C and the
     // real-space stage field D (same shape as A), the kernel K2 = khat / (n0 n1)
     // [n0][n1] in FFT order, the sub-operation and whether NL_SDB ends the run

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(RowTma<N1>::THREADS, 1) row_pass_tma_kernel(co
     const size_t vec_bytes = (size_t)ROWS * N1 * sizeof(V);
 
     for (int i = tid; i < N1; i += blockDim.x) {
-        tw_s[i] = p.tw1[i];
+        tw_s[i] = p.tw1p[i];
         e1_s[i] = p.E1[i];
     }
     if (tid == 0) {
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(RowTma<N1>::THREADS, 1) row_pass_tma_kernel(co
             x[1][m] = lineB[t + m * T];
         }
         sync();   // the line's natural-order reads complete before swizzled exchanges
-        fft<N1, E, +1, 2>(x, t, sm2, L, sync, tw);
+        fftp_bwd<N1, E, 2>(x, t, sm2, L, sync, tw);
         if constexpr (MODE == ROW_STAGE2) {
 #pragma unroll
             for (int m = 0; m < E; ++m) {
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(RowTma<N1>::THREADS, 1) row_pass_tma_kernel(co
 #pragma unroll
             for (int m = 0; m < E; ++m) x[1][m] = apply_N(x[0][m], pterm(m, p.sg + 1), gdt);
         }
-        fft<N1, E, -1, 2>(x, t, sm2, L, sync, tw);
+        fftp_fwd<N1, E, 2>(x, t, sm2, L, sync, tw);
         // the dimension-1 factor of exp(L dt/2), its FP32 rounding alone (the
         // propagator tables, unlike the transforms' roots, need no
         // compensation: on the 512^2 GPE over 2000 steps the norm drift stays
