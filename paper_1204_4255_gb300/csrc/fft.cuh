@@ -237,6 +237,28 @@ __device__ __forceinline__ float2 twp_bwd(float2 x, float4 w) {
     return cmulconj_hilo(x, make_float2(w.x, w.y), make_float2(w.z, w.w));
 }
 
+// Paired twiddles staged in shared memory as two float2 arrays, (c, s) and
+// (c eps, s eps): the forward transform reads only the first, 8 bytes a lane
+// at an 8-byte stride (a float4 entry read for its first half would put lanes
+// 8 entries apart on the same banks).  The row pass uses it (its shared-memory
+// pipe is ~60 % busy); the warp column pass keeps float4 entries, where two
+// 8-byte reads per backward twiddle cost more issue than they save.
+struct PairedTwiddles {
+    const float2 *hi, *lo;
+    __device__ __forceinline__ float4 operator()(int m) const {
+        const float2 h = hi[m], l = lo[m];
+        return make_float4(h.x, h.y, l.x, l.y);
+    }
+};
+// stage a paired table of n float4 entries from global memory into hi / lo
+__device__ __forceinline__ void stage_paired(float2 *hi, float2 *lo, const float4 *g, int n, int tid, int nthreads) {
+    for (int i = tid; i < n; i += nthreads) {
+        const float4 w = g[i];
+        hi[i] = make_float2(w.x, w.y);
+        lo[i] = make_float2(w.z, w.w);
+    }
+}
+
 template <int N, int E, int R, int Ns, bool FWD, int NV, typename Tw>
 __device__ __forceinline__ void fftp_stage(float2 (&v)[NV][E], int t, const Tw &tw) {
     constexpr int B = E / R, T = N / E;

@@ -103,10 +103,10 @@ __global__ void __launch_bounds__(RowTma<N1>::THREADS, 1) row_pass_tma_kernel(co
     const int64_t mine = nitems > blockIdx.x ? (nitems - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const size_t vec_bytes = (size_t)ROWS * N1 * sizeof(V);
 
-    for (int i = tid; i < N1; i += blockDim.x) {
-        tw_s[i] = p.tw1p[i];
-        e1_s[i] = p.E1[i];
-    }
+    // the paired twiddles as (c, s) and (c eps, s eps) halves in tw_s's N1 entries
+    float2 *tw_hi = reinterpret_cast<float2 *>(tw_s), *tw_lo = tw_hi + N1;
+    stage_paired(tw_hi, tw_lo, p.tw1p, N1, tid, blockDim.x);
+    for (int i = tid; i < N1; i += blockDim.x) e1_s[i] = p.E1[i];
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) mbar_init(bars + s, 1);
         fence_barrier_init();
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(RowTma<N1>::THREADS, 1) row_pass_tma_kernel(co
     const float gdt = p.lt.gdt;
     const float sixth = 1.0f / 6.0f, third = 1.0f / 3.0f, half = 0.5f;
     const bool vtime = p.lt.pot == PM_TABLE && p.lt.V_nt > 1;
-    const TwiddleTable<TW> tw{tw_s};
+    const PairedTwiddles tw{tw_hi, tw_lo};
     const SwizzledLine L{};
     // a line's exchanges involve only its own T threads: one warp, or a named
     // barrier per line (ids 1..ROWS), so the lines of an item drift apart and
