@@ -888,7 +888,8 @@ def run_case(name: str) -> None:
     steps, for kernel profiles (ncu captures of a single kernel): gpe2d (the
     bench lattice, 64 x 512^2 GPE, complex64, 4 steps), tw1d (the
     truncated-Wigner 1D ensemble, 4096 x 1024, complex64, 100 steps), gpe3d
-    (the 128^3 GPE, one instance, complex64, 10 steps, autotuned), charged
+    (the 128^3 GPE, one instance, complex64, 10 steps, autotuned), gpe3d8 (8
+    instances of the 128^3 GPE, fields larger than L2, 4 steps), charged
     (Example 5's non-local condensate, 4096 x 1024, complex64, 100 steps) and
     example3 (64 x (256 cosine x 512 Fourier), complex64, 20 steps)."""
     import torch
@@ -898,6 +899,7 @@ def run_case(name: str) -> None:
         "gpe2d": (lambda: W.gpe_2d(npaths=64, nsteps=4), 4),
         "tw1d": (lambda: W.truncated_wigner(nsteps=100), 100),
         "gpe3d": (lambda: W.gpe_3d(nsteps=10), 10),
+        "gpe3d8": (lambda: W.gpe_3d(npaths=8, nsteps=4), 4),
         "charged": (lambda: W.charged_bec(npaths=4096, n=1024, nsteps=100), 100),
         "example3": (lambda: W.symmetric_gpe_2d(npaths=64, nsteps=20), 20),
     }
@@ -938,7 +940,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched and plain-vs-fused figures")
-    ap.add_argument("--case", choices=["gpe2d", "tw1d", "gpe3d", "charged", "example3"],
+    ap.add_argument("--case", choices=["gpe2d", "tw1d", "gpe3d", "gpe3d8", "charged", "example3"],
                     help="run one workload once (for kernel profiles) instead of the bench")
     ap.add_argument("--oracle-table", action="store_true",
                     help="time the FP64 oracle on every configuration (host cores) and exit")

@@ -50,11 +50,11 @@ template <int N0> struct ColW {
     static constexpr int CPW = 32 / P;                         // columns per warp
     static constexpr int NW = C / CPW;                         // warps per CTA: 4 / 4 / 2
     static constexpr int THREADS = NW * 32;
-    static constexpr int NST = N0 == 512 ? 2 : 3;              // shared-memory stages
+    static constexpr int NST = N0 == 512 ? 2 : 3;              // shared-memory stages (3 at 512: no faster)
     static constexpr int BOXR = N0 < 256 ? N0 : 256;           // tensor-copy box rows
     static constexpr size_t TILE = (size_t)N0 * C * sizeof(V); // 32 / 16 / 8 KB
     static constexpr int NTW = warp_fft_table_size<N0, E>();
-    static constexpr size_t SMEM = 1024 + NST * TILE + NTW * sizeof(TW) + 2 * N0 * sizeof(V) +
+    static constexpr size_t SMEM = 1024 + NST * TILE + NTW * sizeof(TW) + N0 * sizeof(V) +
                                    NST * (sizeof(uint64_t) + sizeof(long long) + sizeof(int)) + 16;
     static constexpr int CTAS_PER_SM = N0 == 512 ? 2 : N0 == 256 ? 3 : 6;
     static_assert(CTAS_PER_SM * (SMEM + 1024) <= 233472, "shared memory per SM");
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(ColW<N0>::THREADS, ColW<N0>::CTAS_PER_SM)
     unsigned char *tiles = base;
     TW *tw_s = reinterpret_cast<TW *>(base + NST * Cfg::TILE);
     V *e0_s = reinterpret_cast<V *>(tw_s + Cfg::NTW);
-    uint64_t *full = reinterpret_cast<uint64_t *>(e0_s + 2 * N0);
+    uint64_t *full = reinterpret_cast<uint64_t *>(e0_s + N0);   // e0_s: the N0 FP32 factors
     volatile long long *issued = reinterpret_cast<volatile long long *>(full + NST);   // last item loaded per stage
     int *done = reinterpret_cast<int *>(const_cast<long long *>(issued) + NST);         // warps finished per stage
     volatile int *abort_flag = done + NST;
