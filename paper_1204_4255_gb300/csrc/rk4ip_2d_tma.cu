@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(RowTma<N1>::THREADS, 1) row_pass_tma_kernel(co
     // the paired twiddles as (c, s) and (c eps, s eps) halves in tw_s's N1 entries
     float2 *tw_hi = reinterpret_cast<float2 *>(tw_s), *tw_lo = tw_hi + N1;
     stage_paired(tw_hi, tw_lo, p.tw1p, N1, tid, blockDim.x);
-    for (int i = tid; i < N1; i += blockDim.x) e1_s[i] = p.E1[i];
+    for (int i = tid; i < 2 * N1; i += blockDim.x) e1_s[i] = p.E1[i];
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) mbar_init(bars + s, 1);
         fence_barrier_init();
@@ -257,16 +257,15 @@ __global__ void __launch_bounds__(RowTma<N1>::THREADS, 1) row_pass_tma_kernel(co
             for (int m = 0; m < E; ++m) x[1][m] = apply_N(x[0][m], pterm(m, p.sg + 1), gdt);
         }
         fftp_fwd<N1, E, 2>(x, t, sm2, L, sync, tw);
-        // the dimension-1 factor of exp(L dt/2), its FP32 rounding alone (the
-        // propagator tables, unlike the transforms' roots, need no
-        // compensation: on the 512^2 GPE over 2000 steps the norm drift stays
-        // below 1e-6 either way); results back in natural order
+        // the dimension-1 factor of exp(L dt/2) (hi/lo: a factor whose FP32
+        // rounding misses its modulus by ~6e-8 would scale the populated modes
+        // by that at every step); results back in natural order
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int j = t + m * T;
-            const V eh = e1_s[j];
-            lineA[j] = cmul(x[0][m], eh);
-            lineB[j] = cmul(x[1][m], eh);
+            const V eh = e1_s[j], el = e1_s[N1 + j];
+            lineA[j] = cmul_hilo(x[0][m], eh, el);
+            lineB[j] = cmul_hilo(x[1][m], eh, el);
         }
         fence_proxy_async();
         __syncthreads();
@@ -459,7 +458,7 @@ __global__ void __launch_bounds__(ColTma<N0>::THREADS, ColTma<N0>::CTAS_PER_SM)
                 x[0][m] = cadd(cmul_hilo(x[0][m], e0_s[j], e0_s[N0 + j]),
                                cmul_hilo(xq[m], __ldg(p.B0 + j), __ldg(p.B0 + N0 + j)));
             else
-                x[0][m] = cmul(x[0][m], e0_s[j]);   // FP32 rounding of the factor (as the row pass)
+                x[0][m] = cmul_hilo(x[0][m], e0_s[j], e0_s[N0 + j]);
         }
         fft<N0, E, +1, 1>(x, t, sm1, L, sync, tw);
 #pragma unroll

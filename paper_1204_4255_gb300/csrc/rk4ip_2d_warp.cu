@@ -54,7 +54,7 @@ template <int N0> struct ColW {
     static constexpr int BOXR = N0 < 256 ? N0 : 256;           // tensor-copy box rows
     static constexpr size_t TILE = (size_t)N0 * C * sizeof(V); // 32 / 16 / 8 KB
     static constexpr int NTW = warp_fft_table_size<N0, E>();
-    static constexpr size_t SMEM = 1024 + NST * TILE + NTW * sizeof(TW) + N0 * sizeof(V) +
+    static constexpr size_t SMEM = 1024 + NST * TILE + NTW * sizeof(TW) + 2 * N0 * sizeof(V) +
                                    NST * (sizeof(uint64_t) + sizeof(long long) + sizeof(int)) + 16;
     static constexpr int CTAS_PER_SM = N0 == 512 ? 2 : N0 == 256 ? 3 : 6;
     static_assert(CTAS_PER_SM * (SMEM + 1024) <= 233472, "shared memory per SM");
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(ColW<N0>::THREADS, ColW<N0>::CTAS_PER_SM)
     unsigned char *tiles = base;
     TW *tw_s = reinterpret_cast<TW *>(base + NST * Cfg::TILE);
     V *e0_s = reinterpret_cast<V *>(tw_s + Cfg::NTW);
-    uint64_t *full = reinterpret_cast<uint64_t *>(e0_s + N0);   // e0_s: the N0 FP32 factors
+    uint64_t *full = reinterpret_cast<uint64_t *>(e0_s + 2 * N0);   // e0_s: hi[N0] | lo[N0]
     volatile long long *issued = reinterpret_cast<volatile long long *>(full + NST);   // last item loaded per stage
     int *done = reinterpret_cast<int *>(const_cast<long long *>(issued) + NST);         // warps finished per stage
     volatile int *abort_flag = done + NST;
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(ColW<N0>::THREADS, ColW<N0>::CTAS_PER_SM)
     const int64_t mine = nitems > blockIdx.x ? (nitems - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
     for (int i = tid; i < Cfg::NTW; i += blockDim.x) tw_s[i] = p.tw0w[i];
-    for (int i = tid; i < N0; i += blockDim.x) e0_s[i] = p.E0[i];
+    for (int i = tid; i < 2 * N0; i += blockDim.x) e0_s[i] = p.E0[i];
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) {
             mbar_init(full + s, 1);
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(ColW<N0>::THREADS, ColW<N0>::CTAS_PER_SM)
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int j = t + P * m;
-            x[m] = cmul(x[m], e0_s[j]);   // the factor's FP32 rounding, as in the row pass
+            x[m] = cmul_hilo(x[m], e0_s[j], e0_s[N0 + j]);
         }
         warp_ifft<N0, E>(x, t, xat, tw);
 #pragma unroll
