@@ -375,9 +375,9 @@ int xsde_integrate_plain(xsde_problem *prob, xsde_vector *psi, double dt, int64_
  * process exit: a 16 MiB scratch field (npaths x points x element size must
  * not exceed 16 MiB, e.g. 8 paths of 512x512 complex64, else XSDE_EINVAL) and
  * 192 KiB of tables, rewritten by every call.  The call resolves the arrays'
- * device addresses the first time it runs on a device, so make that first call
- * before any stream capture.  Every call copies its tables from a host buffer
- * with cudaMemcpyAsync and waits for `stream` before it launches.  All calls
+ * device addresses the first time it runs on a device.  Every call copies its
+ * tables from a host buffer with cudaMemcpyAsync and waits for `stream` before
+ * it launches.  All calls
  * in the process share the arrays: calls that overlap on the GPU (other
  * streams, other threads) race and must not be issued.  The caller still
  * provides psi and any sampling buffers; the problem was created (and its
