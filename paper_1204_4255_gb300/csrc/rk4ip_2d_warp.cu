@@ -90,7 +90,14 @@ __global__ void __launch_bounds__(ColW<N0>::THREADS, ColW<N0>::CTAS_PER_SM)
     const int64_t nitems = p.npaths * (int64_t)tiles_per_path * nvec;
     const int64_t mine = nitems > blockIdx.x ? (nitems - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
-    for (int i = tid; i < Cfg::NTW; i += blockDim.x) tw_s[i] = p.tw0w[i];
+    // columns of 128 and 256 points (shared-memory-bound at 16 points a lane)
+    // stage the paired twiddles as split (c, s) / (c eps, s eps) arrays, so the
+    // forward reads 8 bytes a lane at an 8-byte stride; 512 keeps float4 entries
+    constexpr bool SPLIT = N0 <= 256;
+    float2 *tw_hi = reinterpret_cast<float2 *>(tw_s), *tw_lo = tw_hi + Cfg::NTW;
+    if constexpr (SPLIT) stage_paired(tw_hi, tw_lo, p.tw0w, Cfg::NTW, tid, blockDim.x);
+    else
+        for (int i = tid; i < Cfg::NTW; i += blockDim.x) tw_s[i] = p.tw0w[i];
     for (int i = tid; i < 2 * N0; i += blockDim.x) e0_s[i] = p.E0[i];
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) {
@@ -170,7 +177,10 @@ __global__ void __launch_bounds__(ColW<N0>::THREADS, ColW<N0>::CTAS_PER_SM)
     // take lanes in blocks of 8 (each half-warp then holds two columns).
     const int c = CPW == 2 ? warp * 2 + (lane & 1) : warp * CPW + lane / P;
     const int t = CPW == 2 ? lane >> 1 : lane % P;
-    const TwiddleTable<TW> tw{tw_s};
+    const auto tw = [&] {
+        if constexpr (SPLIT) return PairedTwiddles{tw_hi, tw_lo};
+        else return TwiddleTable<TW>{tw_s};
+    }();
     const bool sample = p.sample_slot >= 0;
     for (int64_t k = 0; k < mine; ++k) {
         const int s = (int)(k % NST);
