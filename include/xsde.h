@@ -237,12 +237,14 @@ int xsde_set_noise_substeps(xsde_problem *prob, int32_t substeps);
  * k - npts); read during the call and copied to the device in the problem's
  * precision.  NULL removes the term.  The call synchronises the device first,
  * so no integration in flight sees a half-written kernel.  Energy moments add
- * the pair energy 1/2 V_nl |psi|^2 dV.  1D and 2D Fourier lattices
- * (XSDE_EUNSUPPORTED elsewhere); on 2D lattices khat is [n0][n1] and each N
- * evaluation takes a density convolution of its own (a row pass forming the
- * density's row transform, a column pass multiplying by khat, the evaluating
- * row pass finishing the inverse), three work fields of the field's size and
- * twelve passes a step.  Runs with RK4IP on one launch shape (xsde_kernel_variants
+ * the pair energy 1/2 V_nl |psi|^2 dV.  1D, 2D and 3D Fourier lattices
+ * (XSDE_EUNSUPPORTED on 0D lattices and cosine / sine lattices); on 2D
+ * lattices khat is [n0][n1] and each N evaluation takes a density convolution
+ * of its own (a row pass forming the density's row transform, a column pass
+ * multiplying by khat, the evaluating row pass finishing the inverse), three
+ * work fields of the field's size and twelve passes a step; on 3D lattices
+ * khat is [n0][n1][n2] and each convolution adds the dimension-1 transforms of
+ * the density (two more column passes).  Runs with RK4IP on one launch shape (xsde_kernel_variants
  * reports 1 while the term is set), and xsde_integrate with the semi-implicit scheme,
  * xsde_integrate_plain, xsde_integrate_adaptive and xsde_adjoint report
  * XSDE_EUNSUPPORTED while it is set.  Non-finite entries: XSDE_EINVAL. */

@@ -536,7 +536,7 @@ int col_maps(int kind, CUtensorMap *ma, CUtensorMap *mb, void *A, void *B, int64
 // dimension 0.
 // the scratch field B of the 2D/3D pass schedule (grown, never shrunk)
 // scratch fields of one 2D / 3D call: B, and C and D with the 2D non-local term
-int scratch_fields(const xsde_problem *p) { return p->nonlocal && p->grid.ndim == 2 ? 3 : 1; }
+int scratch_fields(const xsde_problem *p) { return p->nonlocal && p->grid.ndim >= 2 ? 3 : 1; }
 
 int ensure_scratch(xsde_problem *p, size_t need, cudaStream_t s) {
     if (p->scratch_bytes >= need) return XSDE_OK;
@@ -555,12 +555,90 @@ template <typename R>
 int run_si_3d(xsde_problem *p, Params2D<R> &qr, Params2D<R> &q1, Params2D<R> &q0, int64_t nsteps, int64_t npaths,
               uint64_t step0, cudaStream_t s);
 
+// RK4IP with the non-local pair potential on a 3D lattice (Example 5's term
+// on the 3D trap): the 2D schedule of run_nl_2d, each density convolution
+// taking three column passes over C -- dimension 1 forward, dimension 0 with
+// the kernel K(k0, k1, k2) (COL_CONV over [n0][n1 n2] columns), dimension 1
+// back -- and each propagation two (dimensions 1 and 0).  A sample at step n
+// is taken from the real-space field with its V_nl in C, by the row pass's
+// NL_FFT and the forward dimension-1 and spectral dimension-0 column passes of
+// the local 3D sample.  Generic passes in both precisions.
+template <typename R>
+int run_nl_3d(xsde_problem *p, Params2D<R> &qr, Params2D<R> &q1, Params2D<R> &q0, int64_t nsteps, uint64_t step0,
+              cudaStream_t s) {
+    const int S = qr.sm.every;
+    const bool sampling = S > 0;
+    Params2D<R> c1 = q1;   // the dimension-1 transforms of C (COL_FFT_FWD / COL_FFT_BWD act on B)
+    c1.B = q1.C;
+    auto row = [&](int op, uint64_t sg, int slot, int last = 0) -> cudaError_t {
+        qr.nl_op = op;
+        qr.nl_last = last;
+        qr.sg = sg;
+        qr.sample_slot = slot;
+        return timed(p, 9, s, [&] { return launch_row_pass<R>(ROW_NL, qr, s); });
+    };
+    auto col = [&](Params2D<R> &q, int mode, int slot) -> cudaError_t {
+        q.sample_slot = slot;
+        const int kind = (mode == COL_CONV || &q == &c1) ? 10 : mode == COL_SPECTRAL ? 8 : 7;
+        return timed(p, kind, s, [&] { return launch_col_pass<R>(mode, q, s); });
+    };
+    auto conv = [&]() -> cudaError_t {
+        cudaError_t e = col(c1, COL_FFT_FWD, -1);
+        if (e == cudaSuccess) e = col(q0, COL_CONV, -1);
+        if (e == cudaSuccess) e = col(c1, COL_FFT_BWD, -1);
+        return e;
+    };
+    auto propagate = [&]() -> cudaError_t {
+        cudaError_t e = col(q1, COL_PROPAGATE, -1);
+        if (e == cudaSuccess) e = col(q0, COL_PROPAGATE, -1);
+        return e;
+    };
+    // A holds the real-space field of step gs and C its F2 V_nl
+    auto sample = [&](int slot, uint64_t gs) -> cudaError_t {
+        cudaError_t e = row(NL_FFT, gs, slot);
+        if (e == cudaSuccess) e = col(q1, COL_FFT_FWD, -1);
+        if (e == cudaSuccess) e = col(q0, COL_SPECTRAL, slot);
+        return e;
+    };
+    if (nsteps > 0) {
+        XSDE_CUDA(row(NL_DENSITY, step0, -1), "row pass");
+        XSDE_CUDA(conv(), "col pass");
+        if (sampling) XSDE_CUDA(sample(0, step0), "sample");
+        XSDE_CUDA(row(NL_PROLOGUE, step0, -1), "row pass");
+        for (int64_t n = 0; n < nsteps; ++n) {
+            const uint64_t sg = step0 + n;
+            XSDE_CUDA(propagate(), "col pass");
+            XSDE_CUDA(row(NL_S2A, sg, -1), "row pass");
+            XSDE_CUDA(conv(), "col pass");
+            XSDE_CUDA(row(NL_S2B, sg, -1), "row pass");
+            XSDE_CUDA(conv(), "col pass");
+            XSDE_CUDA(row(NL_S2C, sg, -1), "row pass");
+            XSDE_CUDA(propagate(), "col pass");
+            XSDE_CUDA(row(NL_SDA, sg, -1), "row pass");
+            XSDE_CUDA(conv(), "col pass");
+            const bool last = n + 1 == nsteps;
+            XSDE_CUDA(row(NL_SDB, sg, -1, last ? 1 : 0), "row pass");
+            if (!last) {
+                XSDE_CUDA(conv(), "col pass");
+                if (sampling && (n + 1) % S == 0) XSDE_CUDA(sample((int)((n + 1) / S), sg + 1), "sample");
+                XSDE_CUDA(row(NL_PROLOGUE, sg + 1, -1), "row pass");
+            }
+        }
+    }
+    if (sampling && nsteps % S == 0) {
+        XSDE_CUDA(row(NL_DENSITY, step0 + nsteps, -1), "row pass");
+        XSDE_CUDA(conv(), "col pass");
+        XSDE_CUDA(sample((int)(nsteps / S), step0 + nsteps), "sample");
+    }
+    return XSDE_OK;
+}
+
 template <typename R>
 int run_3d(xsde_problem *p, void *psi, int64_t nsteps, int64_t npaths, uint64_t step0, const LocalTerm<R> &lt,
            const Sampling &sm, cudaStream_t s) {
     using V = cx<R>;
     const xsde_grid &g = p->grid;
-    int rc_s = ensure_scratch(p, (size_t)npaths * g.npts * sizeof(V), s);
+    int rc_s = ensure_scratch(p, (size_t)scratch_fields(p) * npaths * g.npts * sizeof(V), s);
     if (rc_s != XSDE_OK) return rc_s;
     Params2D<R> base;
     base.A = static_cast<V *>(psi);
@@ -592,6 +670,14 @@ int run_3d(xsde_problem *p, void *psi, int64_t nsteps, int64_t npaths, uint64_t 
     if (p->scheme == XSDE_SCHEME_SEMI_IMPLICIT) {
         if (!p->d_Ef[0] || !p->d_Ef[1] || !p->d_Ef[2]) return fail(XSDE_EINVAL, "semi-implicit 3D step: tables missing");
         return run_si_3d<R>(p, qr, q1, q0, nsteps, npaths, step0, s);
+    }
+    if (p->nonlocal) {
+        for (Params2D<R> *q : {&qr, &q1, &q0}) {
+            q->C = base.B + (size_t)npaths * g.npts;
+            q->D = q->C + (size_t)npaths * g.npts;
+            q->K2 = static_cast<const V *>(p->d_knl);
+        }
+        return run_nl_3d<R>(p, qr, q1, q0, nsteps, step0, s);
     }
     // complex64: the warp / TMA passes for the hot modes where they apply
     int rk = PASS_GENERIC, ck1 = PASS_GENERIC, ck0 = PASS_GENERIC;
@@ -1335,9 +1421,9 @@ int xsde_set_nonlocal(xsde_problem *p, const double *khat) {
         p->nonlocal = false;
         return XSDE_OK;
     }
-    if (p->grid.ndim < 1 || p->grid.ndim > 2 || any_basis(p->grid))
+    if (p->grid.ndim < 1 || any_basis(p->grid))
         return fail(XSDE_EUNSUPPORTED,
-                    "xsde_set_nonlocal: 1D and 2D Fourier lattices only (a circular convolution)");
+                    "xsde_set_nonlocal: 1D, 2D and 3D Fourier lattices only (a circular convolution)");
     int dev = -1;
     cudaGetDevice(&dev);
     if (dev != p->device)

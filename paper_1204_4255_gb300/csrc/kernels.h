@@ -128,7 +128,8 @@ enum ColMode {
     COL_SPECTRAL = 1,   // B: accumulate the kinetic energy only (no write)
     COL_FFT_FWD = 2,    // B <- F0 B (the middle transform of a 3D spectral sample)
     COL_SINGLE = 3,     // A -> F0^-1 E0 F0 A (the semi-implicit scheme's one field)
-    COL_CONV = 4        // C -> F0^-1 K2(k0, k1) F0 C (the non-local kernel, not separable)
+    COL_CONV = 4,       // C -> F0^-1 K2(k0, k1) F0 C (the non-local kernel, not separable)
+    COL_FFT_BWD = 5     // B <- F0^-1 B (3D non-local term: the density's dimension-1 transform back)
 };
 
 template <typename R> struct Params2D {

@@ -513,11 +513,11 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
 #pragma unroll
         for (int m = 0; m < E; ++m) store(p.A, t + m * T, y[0][m]);
         return;
-    } else if constexpr (MODE == COL_SPECTRAL || MODE == COL_FFT_FWD) {
+    } else if constexpr (MODE == COL_SPECTRAL || MODE == COL_FFT_FWD || MODE == COL_FFT_BWD) {
         V y[1][E];
 #pragma unroll
         for (int m = 0; m < E; ++m) y[0][m] = load(p.B, t + m * T);
-        fft<N0, E, -1, 1>(y, t, sm1, L, sync, tw);
+        fft<N0, E, MODE == COL_FFT_BWD ? +1 : -1, 1>(y, t, sm1, L, sync, tw);
         if constexpr (MODE == COL_SPECTRAL) {
             V yq[1][E];
             if constexpr (TRIG) partners(y, yq);
@@ -589,7 +589,7 @@ template <typename R, int N0, int MODE> cudaError_t col_launch(const Params2D<R>
     using Cfg = ColCfg<R, N0>;
     const size_t smem = (size_t)2 * N0 * Cfg::C * sizeof(cx<R>) + (Cfg::THREADS / 32 + 1) * sizeof(double);
     auto kern = col_pass_kernel<R, N0, MODE>;
-    if constexpr (MODE != COL_FFT_FWD && MODE != COL_SINGLE && MODE != COL_CONV)
+    if constexpr (MODE != COL_FFT_FWD && MODE != COL_FFT_BWD && MODE != COL_SINGLE && MODE != COL_CONV)
         if (p.basis0) kern = col_pass_kernel<R, N0, MODE, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -606,6 +606,7 @@ template <typename R, int N0> cudaError_t col_mode(int mode, const Params2D<R> &
         case COL_FFT_FWD: return col_launch<R, N0, COL_FFT_FWD>(p, s);
         case COL_SINGLE: return col_launch<R, N0, COL_SINGLE>(p, s);
         case COL_CONV: return col_launch<R, N0, COL_CONV>(p, s);
+        case COL_FFT_BWD: return col_launch<R, N0, COL_FFT_BWD>(p, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -628,7 +629,7 @@ template <typename R> cudaError_t launch_row_pass(int mode, const Params2D<R> &p
 }
 
 template <typename R> cudaError_t launch_col_pass(int mode, const Params2D<R> &p, cudaStream_t s) {
-    if (p.basis0 && (p.ndim != 2 || mode == COL_FFT_FWD)) return cudaErrorInvalidValue;
+    if (p.basis0 && (p.ndim != 2 || mode == COL_FFT_FWD || mode == COL_FFT_BWD)) return cudaErrorInvalidValue;
     switch (p.n0) {
         case 16: return col_mode<R, 16>(mode, p, s);
         case 32: return col_mode<R, 32>(mode, p, s);

@@ -2,7 +2,7 @@
 selected by XSDE_LIBRARY): every kernel family of the library on tiny lattices
 and ragged path counts -- the 1D whole-run kernel at 16..2048 points, 0D, the
 generic, TMA and warp 2D passes, 3D, the semi-implicit scheme, noise, tables,
-sampling, the non-local term in 1D and 2D, cosine lattices, the adjoint, the
+sampling, the non-local term in 1D, 2D and 3D, cosine lattices, the adjoint, the
 adaptive integrator, the plain step, the allocation-free entry, host fields and
 a batch.  Each case is compared with the FP64 oracle (or, where the case is
 another schedule of the same run, with xsde_integrate) and every call's device
@@ -81,13 +81,16 @@ got, _, _ = gpu_run(w, "c64", sample_every=2, scheme=1)
 grid, ops = O.from_workload(w)
 ops.scheme = 1
 case("2d_semi_implicit", got, O.rk4ip(w.psi0, grid, ops, w.dt, 5)[0])
-# non-local term, 1D and 2D
+# non-local term, 1D, 2D and 3D
 w = W.charged_bec(npaths=3, n=256, dt=1e-3, nsteps=10)
 got, _, _ = gpu_run(w, "c64", sample_every=5)
 case("1d_nonlocal", got, O.run_workload(w, sample_every=5)[0])
 w = W.charged_bec_2d(npaths=2, n=(32, 64), dt=1e-3, nsteps=6, box=8.0)
 got, _, _ = gpu_run(w, "c64", sample_every=3)
 case("2d_nonlocal", got, O.run_workload(w, sample_every=3)[0])
+w = W.charged_bec_3d(npaths=2, n=(16, 32, 16), dt=1e-3, nsteps=4)
+got, _, _ = gpu_run(w, "c64", sample_every=2)
+case("3d_nonlocal", got, O.run_workload(w, sample_every=2)[0])
 # cosine lattices: 1D and Example 3's 2D lattice (TMA column pass at 128)
 w = W.symmetric_gpe(npaths=3, n=64, nsteps=10)
 got, _, _ = gpu_run(w, "c64")

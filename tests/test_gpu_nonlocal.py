@@ -119,12 +119,12 @@ def test_calls_that_reject_the_term():
     P.integrate(psi, w.dt, 4)      # the old kernel is still in place
     P.synchronize()
     P.close()
-    w3 = W.gpe_3d(n=16, nsteps=2)
-    P3 = make_problem(w3, "c64")
+    w0 = W.ornstein_uhlenbeck(npaths=4, nsteps=2)
+    P0 = make_problem(w0, "c64")
     with pytest.raises(xsde.XsdeError) as e:
-        P3.set_nonlocal(np.ones(w3.npts, dtype=np.complex128))
+        P0.set_nonlocal(np.ones(1, dtype=np.complex128))
     assert e.value.status == xsde.XSDE_EUNSUPPORTED
-    P3.close()
+    P0.close()
 
 
 def test_batch_member_with_the_pair_potential():
@@ -251,3 +251,43 @@ def test_2d_batch_member_with_the_pair_potential():
         return out
     for a, b in zip(run(True), run(False)):
         assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------------------
+# 3D lattices: the density convolution over three dimensions
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(16, 16, 16), (16, 32, 16), (32, 16, 16)])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_3d_charged_condensate_matches_the_oracle(shape, dtype):
+    """State, norm, energy with the pair term and per-point moments, sampled
+    every 4 steps (the last sample at the end of the run) and every 3 (none at
+    the end)."""
+    for every in (4, 3):
+        w = W.charged_bec_3d(npaths=2, n=shape, dt=1e-3, nsteps=8)
+        got, pp, pq = gpu_run(w, dtype, sample_every=every)
+        ref, opp, opq = O.run_workload(w, sample_every=every)
+        tol = TOL[dtype]
+        assert np.max(rel_l2(got.reshape(2, -1), ref.reshape(2, -1), axis=1)) < tol
+        assert np.max(np.abs(pp - opp) / np.abs(opp)) < tol
+        assert np.linalg.norm(pq - opq) / np.linalg.norm(opq) < tol
+
+
+def test_3d_noisy_path_subset_with_the_pair_potential():
+    w = W.charged_bec_3d(npaths=4, n=(16, 16, 16), dt=1e-3, nsteps=6, noise_amp=0.02)
+    got, pp, _ = gpu_run(w, "c128", npaths=2, path0=2, sample_every=3)
+    ref, opp, _ = O.run_workload(w, npaths=2, path0=2, sample_every=3)
+    assert np.max(rel_l2(got.reshape(2, -1), ref.reshape(2, -1), axis=1)) < 1e-10
+    assert np.max(np.abs(pp - opp) / np.abs(opp)) < 1e-10
+
+
+def test_3d_constant_kernel_equals_the_contact_interaction():
+    """khat = c at every mode gives V_nl = c |psi|^2: the run equals the local
+    run with g + c (1e-12, complex128)."""
+    w = W.charged_bec_3d(npaths=2, n=(16, 16, 16), dt=1e-3, nsteps=6)
+    c = 0.7
+    w.knl = np.full(w.n, c, dtype=np.complex128)
+    got, _, _ = gpu_run(w, "c128")
+    w.knl, w.gnl = None, w.gnl + c
+    ref, _, _ = gpu_run(w, "c128")
+    assert rel_l2(got, ref) < 1e-12

@@ -2,8 +2,8 @@
 applied as a convolution through FFTs), against what mathematics fixes:
 
 * the FFT evaluation equals the circular convolution summed point by point
-  (an asymmetric pair function, so convolution and correlation differ), in 1D
-  and 2D;
+  (an asymmetric pair function, so convolution and correlation differ), in 1D,
+  2D and 3D;
 * a kernel that is the same at every k is a contact interaction: the run
   equals one with gnl raised by that constant (noise included);
 * on a uniform plane wave only the k = 0 entry acts, and the phase follows the
@@ -62,6 +62,28 @@ def test_fft_convolution_equals_the_point_sum_2d():
                     d1 = (o1 if o1 < n1 // 2 else o1 - n1) * dx1
                     s = s + f(d0, d1) * rho[:, m0, m1]
             want[:, i0, i1] = s * dx0 * dx1
+    assert np.max(np.abs(got - want)) < 1e-12 * np.max(np.abs(want))
+
+
+def test_fft_convolution_equals_the_point_sum_3d():
+    n = (4, 8, 8)
+    xmin, xmax = (-1.0, -2.0, -3.0), (1.0, 2.0, 3.0)
+    dx = [(xmax[d] - xmin[d]) / n[d] for d in range(3)]
+    rng = np.random.default_rng(3)
+    psi = rng.standard_normal((2,) + n) + 1j * rng.standard_normal((2,) + n)
+    f = lambda a, b, c: _pair(a) * np.exp(-0.3 * (b + 0.5) ** 2) * (1.0 + 0.2 * c)
+    khat = W.convolution_kernel(n, xmin, xmax, f)
+    got = O.nonlocal_potential(psi, O.Grid(n, xmin, xmax), O.Ops(knl=khat))
+    rho = np.abs(psi) ** 2
+    # minimum-image offsets along each dimension, then the sum over every source point
+    offs = []
+    for d in range(3):
+        o = (np.arange(n[d])[:, None] - np.arange(n[d])[None, :]) % n[d]
+        offs.append(np.where(o < n[d] // 2, o, o - n[d]) * dx[d])
+    want = np.zeros_like(got)
+    for i in np.ndindex(*n):
+        F = f(offs[0][i[0]][:, None, None], offs[1][i[1]][None, :, None], offs[2][i[2]][None, None, :])
+        want[(slice(None),) + i] = np.einsum("abc,pabc->p", F, rho) * dx[0] * dx[1] * dx[2]
     assert np.max(np.abs(got - want)) < 1e-12 * np.max(np.abs(want))
 
 

@@ -334,6 +334,32 @@ def charged_bec_2d(npaths: int = 16, n: tuple = (256, 256), dt: float = 1e-4, ns
                     knl=knl)
 
 
+def charged_bec_3d(npaths: int = 2, n: tuple = (32, 32, 32), dt: float = 1e-3, nsteps: int = 20, g: float = 10.0,
+                   charge: float = 1.0, soft: float = 0.5, box: float = 6.0, seed: int = 13,
+                   sample_every: int = 0, noise_amp: float = 0.0) -> Workload:
+    """Example 5 (Sec. 3.5) on a 3D harmonic trap: the dimensionless GPE with
+    V = r^2/2 and contact nonlinearity g, plus the softened Coulomb pair
+    potential charge / sqrt(|r - r'|^2 + soft^2) on [-box, box)^3.  Each path
+    starts from the 3D linear ground state (unit norm), displaced by a vector
+    uniform in [-1, 1]^3 and scaled in width by w uniform in [0.8, 1.25];
+    noise_amp > 0 adds complex additive Wiener noise."""
+    n = tuple(n)
+    ax = [-box + np.arange(k) * (2 * box / k) for k in n]
+    rng = np.random.default_rng(seed)
+    x0 = rng.uniform(-1.0, 1.0, (npaths, 3))
+    w = rng.uniform(0.8, 1.25, npaths)
+    X, Y, Z = np.meshgrid(ax[0], ax[1], ax[2], indexing="ij")
+    psi0 = np.stack([(np.pi * w[p] ** 2) ** -0.75 *
+                     np.exp(-((X - x0[p, 0]) ** 2 + (Y - x0[p, 1]) ** 2 + (Z - x0[p, 2]) ** 2) / (2 * w[p] ** 2))
+                     for p in range(npaths)])
+    knl = convolution_kernel(n, (-box,) * 3, (box,) * 3,
+                             lambda dx, dy, dz: charge / np.sqrt(dx * dx + dy * dy + dz * dz + soft * soft))
+    return Workload(f"charged_bec_3d_{n[0]}x{n[1]}x{n[2]}", n, (-box,) * 3, (box,) * 3, 0j, -0.5j, g, POT_HARMONIC,
+                    (1.0, 1.0, 1.0), None, NOISE_ADD_COMPLEX if noise_amp > 0 else NOISE_NONE, noise_amp, seed, dt,
+                    nsteps, psi0.astype(np.complex128), sample_every, extra={"charge": charge, "soft": soft},
+                    knl=knl)
+
+
 BASIS_FOURIER, BASIS_COS, BASIS_SIN = 0, 1, 2
 
 
