@@ -389,15 +389,29 @@ def nonlocal_cost(npaths: int = 4096, n: int = 1024, nsteps: int = 200) -> dict:
         P.close()
     # 2D: the charged condensate on the 2D trap, 16 paths x 256^2, 20 steps; the
     # term takes a density convolution (row, column, row pass) before each of
-    # the four N evaluations, on the generic passes
-    w2 = W.charged_bec_2d(npaths=16, n=(256, 256), nsteps=20)
-    out["2d"] = {"workload": "2D charged condensate 16 paths x 256^2, 20 RK4IP steps"}
+    # the four N evaluations, on the generic passes.  3D: 4 paths x 64^3, the
+    # convolution adding the density's dimension-1 transforms.
+    for key, w2, label in (("2d", W.charged_bec_2d(npaths=16, n=(256, 256), nsteps=20),
+                            "2D charged condensate 16 paths x 256^2, 20 RK4IP steps"),
+                           ("3d", W.charged_bec_3d(npaths=4, n=(64, 64, 64), dt=1e-3, nsteps=20),
+                            "3D charged condensate 4 paths x 64^3, 20 RK4IP steps")):
+        out[key] = _nonlocal_pair(w2, label, e0, e1)
+    torch.cuda.empty_cache()
+    return out
+
+
+def _nonlocal_pair(w2, label: str, e0, e1) -> dict:
+    """Device time of w2's run with its non-local term and without it, c64 and c128."""
+    import torch
+    from paper_1204_4255_gb300 import xsde
+    out = {"workload": label}
     for dtype in ("c64", "c128"):
         P = xsde.Problem(w2.n, w2.xmin, w2.xmax, dtype)
-        P.set_operators(c0=w2.c0, c2=w2.c2, g=w2.gnl, pot_kind=w2.pot_kind, omega=(1.0, 1.0, 0.0))
+        P.set_operators(c0=w2.c0, c2=w2.c2, g=w2.gnl, pot_kind=w2.pot_kind,
+                        omega=tuple(w2.omega) + (0.0,) * (3 - len(w2.omega)))
         src = torch.from_numpy(w2.psi0).to(torch.complex64 if dtype == "c64" else torch.complex128).cuda()
         res = {}
-        for label, khat in (("nonlocal", w2.knl), ("local_only", None)):
+        for kind, khat in (("nonlocal", w2.knl), ("local_only", None)):
             P.set_nonlocal(khat)
             psi = src.clone()
             P.integrate(psi, w2.dt, 2)
@@ -408,12 +422,11 @@ def nonlocal_cost(npaths: int = 4096, n: int = 1024, nsteps: int = 200) -> dict:
             torch.cuda.synchronize()
             P.synchronize()
             ms = e0.elapsed_time(e1)
-            res[label] = {"value": w2.npaths * w2.npts * w2.nsteps / (ms / 1e3), "ms": ms}
+            res[kind] = {"value": w2.npaths * w2.npts * w2.nsteps / (ms / 1e3), "ms": ms}
         res["cost_ratio"] = res["local_only"]["value"] / res["nonlocal"]["value"]
-        out["2d"][dtype] = res
+        out[dtype] = res
         P.close()
         del psi, src
-    torch.cuda.empty_cache()
     return out
 
 
