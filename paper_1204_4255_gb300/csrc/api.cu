@@ -80,6 +80,7 @@ struct xsde_problem {
     int scheme = XSDE_SCHEME_RK4IP;   // see xsde_set_scheme
     void *d_knl = nullptr;    // non-local kernel khat/npts in the problem's precision [npts]
     void *d_B = nullptr;      // cosine / sine dimension 0: the B table of its pair step
+    void *d_B1 = nullptr;     // cosine / sine dimension 1 of a 2D lattice: the B table of its pair step
     void *d_Ef[3] = {nullptr, nullptr, nullptr};   // whole-step factors exp(L dt) per dimension (2D/3D semi-implicit)
     bool nonlocal = false;    // see xsde_set_nonlocal
     uint64_t generation = 0;  // bumped by every call that changes what integrate launches
@@ -364,6 +365,12 @@ template <typename V> int ensure_tables(xsde_problem *p, double dt, cudaStream_t
             const double k = kval(g, 1, i);
             e1[i] = std::exp(c2 * (k * k) * (0.5 * dt));
         }
+        if (g.basis[1] != XSDE_BASIS_FOURIER) {
+            std::vector<std::complex<double>> A, B;
+            trig_pair_tables(g.basis[1], e1, A, B);
+            e1 = A;
+            if ((rc = upload<V>(B, &p->d_B1, s)) != XSDE_OK) return rc;
+        }
         if ((rc = upload<V>(e0, &p->d_E[0], s)) != XSDE_OK) return rc;
         if ((rc = upload<V>(e1, &p->d_E[1], s)) != XSDE_OK) return rc;
         if (p->scheme == XSDE_SCHEME_SEMI_IMPLICIT) {
@@ -506,7 +513,7 @@ bool tma_rows_ok(int n1, int64_t lines) { return tma_row_supported(n1) && lines 
 enum { PASS_GENERIC = 0, PASS_TMA = 1, PASS_WARP = 2 };
 int row_pass_kind(const xsde_problem *p, int n1, int64_t lines) {
     const int v = p->kernel_variant;
-    if (v == 1) return PASS_GENERIC;
+    if (v == 1 || p->grid.basis[p->grid.ndim - 1] != XSDE_BASIS_FOURIER) return PASS_GENERIC;
     return tma_rows_ok(n1, lines) ? PASS_TMA : PASS_GENERIC;
 }
 int col_pass_kind(const xsde_problem *p, int n0, int64_t n1, int basis0) {
@@ -1020,6 +1027,8 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
     q.status = p->d_status;
     q.basis0 = g.basis[0];
     q.B0 = static_cast<const V *>(p->d_B);
+    q.basis1 = g.basis[1];
+    q.B1 = static_cast<const V *>(p->d_B1);
     const int S = sm.every;
     if (p->scheme == XSDE_SCHEME_SEMI_IMPLICIT) {
         if (!p->d_Ef[0] || !p->d_Ef[1]) return fail(XSDE_EINVAL, "semi-implicit 2D step: tables missing");
@@ -1065,6 +1074,31 @@ int run_integrate(xsde_problem *p, void *psi, double dt, int64_t nsteps, int64_t
             return launch_col_pass<R>(mode, q, s);
         });
     };
+    if (g.basis[1] != XSDE_BASIS_FOURIER) {
+        // a cosine / sine dimension 1: the fused sample of the column pass needs
+        // the Fourier row spectrum, so samples are taken from the real-space
+        // field between chunks of steps (the 3D schedule): the row pass's
+        // cosine / sine spectrum and a spectral column pass
+        const int64_t chunk = S > 0 ? S : (nsteps > 0 ? nsteps : 1);
+        for (int64_t c0 = 0; c0 < nsteps || (S > 0 && c0 == nsteps); c0 += chunk) {
+            if (S > 0) {
+                XSDE_CUDA(row(ROW_FFT_ONLY, step0 + c0, (int)(c0 / S)), "row pass");
+                XSDE_CUDA(col(COL_SPECTRAL, (int)(c0 / S)), "col pass");
+            }
+            if (c0 == nsteps) break;
+            const int64_t len = (c0 + chunk <= nsteps) ? chunk : nsteps - c0;
+            XSDE_CUDA(row(ROW_PROLOGUE, step0 + c0, -1), "row pass");
+            for (int64_t n = 0; n < len; ++n) {
+                const uint64_t sg = step0 + c0 + n;
+                XSDE_CUDA(col(COL_PROPAGATE, -1), "col pass");
+                XSDE_CUDA(row(ROW_STAGE2, sg, -1), "row pass");
+                XSDE_CUDA(col(COL_PROPAGATE, -1), "col pass");
+                XSDE_CUDA(row(n + 1 < len ? ROW_STEADY : ROW_EPILOGUE, sg, -1), "row pass");
+            }
+            if (S > 0 && c0 + len == nsteps && nsteps % S != 0) break;
+        }
+        return XSDE_OK;
+    }
     if (nsteps > 0) {
         XSDE_CUDA(row(ROW_PROLOGUE, step0, sampling ? 0 : -1), "row pass");
         for (int64_t n = 0; n < nsteps; ++n) {
@@ -1126,8 +1160,6 @@ int check_integrate(const char *who, xsde_problem *p, const xsde_vector *psi, do
     if (any_basis(p->grid)) {
         const xsde_grid &g = p->grid;
         if (g.ndim == 3) return fail(XSDE_EUNSUPPORTED, "%s: cosine / sine bases on 1D and 2D lattices only", who);
-        if (g.ndim == 2 && g.basis[1] != XSDE_BASIS_FOURIER)
-            return fail(XSDE_EUNSUPPORTED, "%s: on a 2D lattice only dimension 0 may be cosine / sine", who);
         if (g.ndim == 2 && p->scheme != XSDE_SCHEME_RK4IP)
             return fail(XSDE_EUNSUPPORTED, "%s: the semi-implicit scheme on 2D Fourier lattices only", who);
     }
@@ -1300,6 +1332,7 @@ void xsde_problem_destroy(xsde_problem *p) {
     cudaFree(p->d_twp);
     cudaFree(p->d_knl);
     cudaFree(p->d_B);
+    cudaFree(p->d_B1);
     for (int d = 0; d < 3; ++d) cudaFree(p->d_Ef[d]);
     cudaFree(p->d_scratch);
     cudaFree(p->d_adj);

@@ -167,6 +167,10 @@ template <typename R> struct Params2D {
     // twiddles of the two-stage plan of dimension 0 (fft2.cuh), for the warp
     // column pass: entry (r-1) E + j holds w_n0^(r j), r < n0/E, j < E
     const tw_t<R> *tw0w = nullptr;
+    // a cosine / sine dimension 1 of a 2D lattice (1 / 2; 0 Fourier) and the B
+    // table of its pair step (hi[n1] | lo[n1]); E1 then holds the A table
+    int basis1 = 0;
+    const cx<R> *B1 = nullptr;
     // complex64 TMA row pass: the paired twiddles of fftp_fwd / fftp_bwd (fft.cuh)
     // for the row dimension
     const tw_t<R> *tw1p = nullptr;

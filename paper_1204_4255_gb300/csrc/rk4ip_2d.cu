@@ -55,7 +55,8 @@ template <int N1> struct RowCfg {
     static constexpr int THREADS = LINES * T;
 };
 
-template <typename R, int N1, int MODE>
+// TRIG1: dimension 1 is a cosine or sine dimension (p.basis1), see below
+template <typename R, int N1, int MODE, bool TRIG1 = false>
 __global__ void __launch_bounds__(RowCfg<N1>::THREADS) row_pass_kernel(const Params2D<R> p) {
     using V = cx<R>;
     using Cfg = RowCfg<N1>;
@@ -89,9 +90,26 @@ __global__ void __launch_bounds__(RowCfg<N1>::THREADS) row_pass_kernel(const Par
     const R sixth = R(1) / R(6), third = R(1) / R(3), half = R(0.5);
     const bool sample = p.sample_slot >= 0;
 
+    // A cosine / sine dimension 1 (TRIG1; XMDS2 Sec. 2.1) holds a line's points
+    // in the even-odd order of the DCT-II's evaluation by an N1-point FFT:
+    // register slot s holds point 2s below N1/2 and point 2 N1-1-2s above,
+    // negated (with its additive noise) for the sine basis.  Real-space loads
+    // and stores gather and scatter through that order; after the forward
+    // transform U_k = A_k V_k + B_k V_{N1-k} applies the dimension-1 factor of
+    // exp(L dt/2) in that basis (A in E1, B in p.B1; one exchange pairs k with
+    // N1-k), where a Fourier line multiplies by E1.
+    const int bas1 = TRIG1 ? p.basis1 : 0;
+    auto pt_of = [&](int sl) -> int { return !TRIG1 ? sl : (sl < N1 / 2 ? 2 * sl : 2 * N1 - 1 - 2 * sl); };
+    auto negated = [&](int sl) -> bool { return TRIG1 && bas1 == 2 && sl >= N1 / 2; };
+    auto load_real = [&](const V *f, int sl) -> V {
+        const V v = f[pt_of(sl)];
+        return negated(sl) ? mk<V>(-v.x, -v.y) : v;
+    };
+    auto store_real = [&](V *f, int sl, V v) { f[pt_of(sl)] = negated(sl) ? mk<V>(-v.x, -v.y) : v; };
+
     // raw potential of point (line, t + m T) at global step gs
     auto pot = [&](int m, uint64_t gs) -> R {
-        const int ic = t + m * T;
+        const int ic = pt_of(t + m * T);
         const int idx2[3] = {la, ic, 0};
         const int idx3[3] = {la, lb, ic};
         return potential(p.lt, p.ndim, p.ndim == 3 ? idx3 : idx2, (int64_t)i0 * N1 + ic, gs);
@@ -104,8 +122,10 @@ __global__ void __launch_bounds__(RowCfg<N1>::THREADS) row_pass_kernel(const Par
     for (int m = 0; m < E; ++m) Vst[m] = vtime ? R(0) : pot(m, 0);
     auto potv = [&](int m, uint64_t gs) -> R { return vtime ? pot(m, gs) : Vst[m]; };
     auto pterm = [&](int m, uint64_t gs) -> PointTerm<R> {
-        const int i1 = t + m * T;
-        return point_term(p.lt, potv(m, gs), (uint32_t)(i0 * N1 + i1), gp, (uint32_t)gs);
+        const int i1 = pt_of(t + m * T);
+        PointTerm<R> pt = point_term(p.lt, potv(m, gs), (uint32_t)(i0 * N1 + i1), gp, (uint32_t)gs);
+        if (negated(t + m * T)) pt.na = mk<V>(-pt.na.x, -pt.na.y);
+        return pt;
     };
     // local part of the sampling group for the real-space field f at global step gs
     // (vnl: the non-local potential of f, whose pair energy 1/2 V_nl |f|^2 the
@@ -119,7 +139,7 @@ __global__ void __launch_bounds__(RowCfg<N1>::THREADS) row_pass_kernel(const Par
             acc[1] += (double)potv(m, gs) * m2 + 0.5 * p.sm.g * m2 * m2;
             if (vnl) acc[1] += 0.5 * (double)vnl[m] * m2;
             if (active && (p.sm.which & (MOM_MOD2 | MOM_MOD4)) && p.sm.per_point) {
-                const int64_t ip = (int64_t)p.sample_slot * p.lt.npts + (int64_t)i0 * N1 + t + m * T;
+                const int64_t ip = (int64_t)p.sample_slot * p.lt.npts + (int64_t)i0 * N1 + pt_of(t + m * T);
                 if (!XSDE_IN(ip, p.sm.nsamp * p.lt.npts, p.status)) continue;
                 double *pp = p.sm.per_point + 2 * ip;
                 atomicAdd(pp, m2 * p.sm.inv_paths);
@@ -304,13 +324,33 @@ __global__ void __launch_bounds__(RowCfg<N1>::THREADS) row_pass_kernel(const Par
         }
     } else if constexpr (MODE == ROW_PROLOGUE || MODE == ROW_FFT_ONLY) {
 #pragma unroll
-        for (int m = 0; m < E; ++m) x[0][m] = Arow[t + m * T];
+        for (int m = 0; m < E; ++m) x[0][m] = load_real(Arow, t + m * T);
         if (sample) sample_local(x[0], p.sg);
         if constexpr (MODE == ROW_FFT_ONLY) {
             V y[1][E];
 #pragma unroll
             for (int m = 0; m < E; ++m) y[0][m] = x[0][m];
             fft<N1, E, -1, 1>(y, t, sm1, L, sync, tw);
+            if constexpr (TRIG1) {
+                // the cosine spectrum X_k = (w_k V_k + conj(w_k) V_{N1-k}) / 2,
+                // w_k = exp(-i pi k / 2 N1) (for the sine basis, mode N1-k at k)
+#pragma unroll
+                for (int m = 0; m < E; ++m) sm1[0][L(t + m * T)] = y[0][m];
+                sync();
+                V q[E];
+#pragma unroll
+                for (int m = 0; m < E; ++m) q[m] = sm1[0][L((N1 - t - m * T) & (N1 - 1))];
+                sync();
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    double sn, cs;
+                    sincospi(-(double)(t + m * T) / (2.0 * N1), &sn, &cs);
+                    const double yr = (double)y[0][m].x, yi = (double)y[0][m].y;
+                    const double qr = (double)q[m].x, qi = (double)q[m].y;
+                    y[0][m] = mk<V>((R)(0.5 * (cs * (yr + qr) - sn * (yi - qi))),
+                                    (R)(0.5 * (cs * (yi + qi) + sn * (yr - qr))));
+                }
+            }
             if (active)
 #pragma unroll
                 for (int m = 0; m < E; ++m) Brow[t + m * T] = y[0][m];
@@ -343,7 +383,7 @@ __global__ void __launch_bounds__(RowCfg<N1>::THREADS) row_pass_kernel(const Par
             if constexpr (MODE == ROW_EPILOGUE) {
                 if (active)
 #pragma unroll
-                    for (int m = 0; m < E; ++m) Arow[t + m * T] = x[0][m];
+                    for (int m = 0; m < E; ++m) store_real(Arow, t + m * T, x[0][m]);
                 return;
             } else {
                 if (sample) sample_local(x[0], p.sg + 1);
@@ -354,7 +394,28 @@ __global__ void __launch_bounds__(RowCfg<N1>::THREADS) row_pass_kernel(const Par
     }
     fft<N1, E, -1, 2>(x, t, sm2, L, sync, tw);
     // the dimension-1 factor of exp(L dt/2); the column pass applies the rest
-    if (active) {
+    if constexpr (TRIG1) {
+        V q[2][E];
+#pragma unroll
+        for (int m = 0; m < E; ++m)
+#pragma unroll
+            for (int iv = 0; iv < 2; ++iv) sm2[iv][L(t + m * T)] = x[iv][m];
+        sync();
+#pragma unroll
+        for (int m = 0; m < E; ++m)
+#pragma unroll
+            for (int iv = 0; iv < 2; ++iv) q[iv][m] = sm2[iv][L((N1 - t - m * T) & (N1 - 1))];
+        sync();
+        if (active)
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int j = t + m * T;
+                const V ah = __ldg(p.E1 + j), al = __ldg(p.E1 + N1 + j);
+                const V bh = __ldg(p.B1 + j), bl = __ldg(p.B1 + N1 + j);
+                Arow[j] = cadd(cmul_hilo(x[0][m], ah, al), cmul_hilo(q[0][m], bh, bl));
+                Brow[j] = cadd(cmul_hilo(x[1][m], ah, al), cmul_hilo(q[1][m], bh, bl));
+            }
+    } else if (active) {
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const V eh = __ldg(p.E1 + t + m * T), el = __ldg(p.E1 + N1 + t + m * T);
@@ -446,6 +507,11 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
             const double ka = p.sm.kscale[1] * (ia < nm / 2 ? ia : ia - nm);
             const double kb = p.sm.kscale[2] * (ib < p.kinner / 2 ? ib : ib - p.kinner);
             kc2 = ka * ka + kb * kb;
+        } else if (p.basis1) {
+            // cosine / sine dimension 1: B holds the cosine spectrum X_k1 (sine
+            // mode n1-k1 at k1); Parseval weight 2 for every mode but slot 0
+            const double k1 = p.sm.kscale[1] * (p.basis1 == 1 ? col : n1 - col);
+            kc2 = k1 * k1;
         } else {
             const double k1 = p.sm.kscale[1] * (col < n1 / 2 ? col : col - n1);
             kc2 = k1 * k1;
@@ -472,6 +538,7 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
             }
         }
         s *= w;
+        if (p.basis1 && p.kinner == 0 && col != 0) s *= 2.0;
         s = warp_sum(s);
         __syncthreads();
         if ((threadIdx.x & 31) == 0) scratch[threadIdx.x >> 5] = s;
@@ -564,6 +631,12 @@ template <typename R, int N1, int MODE> cudaError_t row_launch(const Params2D<R>
     const size_t smem = (size_t)Cfg::LINES * 2 * line_len<cx<R>, N1>() * sizeof(cx<R>) +
                         (size_t)Cfg::LINES * (Cfg::T / 32 + 1) * 2 * sizeof(double);
     auto kern = row_pass_kernel<R, N1, MODE>;
+    if constexpr (MODE == ROW_PROLOGUE || MODE == ROW_STAGE2 || MODE == ROW_STEADY || MODE == ROW_EPILOGUE ||
+                  MODE == ROW_FFT_ONLY) {
+        if (p.basis1) kern = row_pass_kernel<R, N1, MODE, true>;
+    } else if (p.basis1) {
+        return cudaErrorInvalidValue;   // the semi-implicit and non-local modes: Fourier lines only
+    }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t rows = p.npaths * (int64_t)p.n0;

@@ -2,7 +2,7 @@
 selected by XSDE_LIBRARY): every kernel family of the library on tiny lattices
 and ragged path counts -- the 1D whole-run kernel at 16..2048 points, 0D, the
 generic, TMA and warp 2D passes, 3D, the semi-implicit scheme, noise, tables,
-sampling, the non-local term in 1D, 2D and 3D, cosine lattices, the adjoint, the
+sampling, the non-local term in 1D, 2D and 3D, cosine / sine lattices (either 2D dimension), the adjoint, the
 adaptive integrator, the plain step, the allocation-free entry, host fields and
 a batch.  Each case is compared with the FP64 oracle (or, where the case is
 another schedule of the same run, with xsde_integrate) and every call's device
@@ -91,13 +91,23 @@ case("2d_nonlocal", got, O.run_workload(w, sample_every=3)[0])
 w = W.charged_bec_3d(npaths=2, n=(16, 32, 16), dt=1e-3, nsteps=4)
 got, _, _ = gpu_run(w, "c64", sample_every=2)
 case("3d_nonlocal", got, O.run_workload(w, sample_every=2)[0])
-# cosine lattices: 1D and Example 3's 2D lattice (TMA column pass at 128)
+# cosine / sine lattices: 1D and Example 3's 2D lattice (TMA column pass at 128)
 w = W.symmetric_gpe(npaths=3, n=64, nsteps=10)
 got, _, _ = gpu_run(w, "c64")
 case("1d_cosine", got, O.run_workload(w)[0])
 w = W.symmetric_gpe_2d(npaths=2, n0=128, n1=64, nsteps=4)
 got, _, _ = gpu_run(w, "c64")
 case("2d_cosine", got, O.run_workload(w)[0])
+# the same lattice with its axes swapped: a sine dimension 1 (the row passes'
+# pairing step, samples between chunks)
+w = W.symmetric_gpe_2d(npaths=2, n0=32, n1=64, L=6.0, dt=1e-3, nsteps=6)
+w.basis = (W.BASIS_SIN, W.BASIS_FOURIER)
+w.psi0 = w.psi0 * w.coords_of(0)[None, :, None]
+wt = W.Workload(w.name + "_t", (w.n[1], w.n[0]), (w.xmin[1], w.xmin[0]), (w.xmax[1], w.xmax[0]), w.c0, w.c2,
+                w.gnl, w.pot_kind, (w.omega[1], w.omega[0]), None, w.noise_kind, w.noise_amp, w.seed, w.dt,
+                w.nsteps, np.ascontiguousarray(w.psi0.transpose(0, 2, 1)), basis=(w.basis[1], w.basis[0]))
+got, _, _ = gpu_run(wt, "c64", sample_every=3)
+case("2d_sine_dimension_1", got, O.run_workload(wt, sample_every=3)[0])
 # adjoint (loss against the oracle adjoint's)
 w = W.adjoint_control(n=256, nsteps=20)
 P = make_problem(w, "c128")

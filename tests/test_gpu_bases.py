@@ -3,7 +3,9 @@ through the C-ABI against the FP64 oracle, whose transforms are the DCT-II /
 DST-II written out as sums: every 1D length, both precisions, ragged path
 counts, moments, noise, a time-dependent table, the semi-implicit scheme, the
 2D lattice of Example 3 (cosine or sine dimension 0, Fourier dimension 1) up
-to its full size, batches, and the calls that reject such lattices.
+to its full size, the same lattice with its axes swapped (a cosine or sine
+dimension 1) and with both dimensions cosine / sine, batches, and the calls
+that reject such lattices.
 
 Tolerances: complex128 within 1e-10 relative L2 of the oracle, complex64
 within 1e-4."""
@@ -120,6 +122,76 @@ def test_example3_full_size_on_a_sampled_path():
         assert rel_l2(got[p], ref[0]) < 1e-4, p
 
 
+def _transposed(w):
+    """The same problem with its axes swapped: the cosine / sine dimension last."""
+    return W.Workload(w.name + "_t", (w.n[1], w.n[0]), (w.xmin[1], w.xmin[0]), (w.xmax[1], w.xmax[0]), w.c0, w.c2,
+                      w.gnl, w.pot_kind, (w.omega[1], w.omega[0]), None, w.noise_kind, w.noise_amp, w.seed, w.dt,
+                      w.nsteps, np.ascontiguousarray(w.psi0.transpose(0, 2, 1)), w.sample_every,
+                      basis=(w.basis[1], w.basis[0]))
+
+
+@pytest.mark.parametrize("odd", [False, True])
+@pytest.mark.parametrize("shape", [(32, 16), (64, 128), (128, 64)])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_cosine_or_sine_dimension_1_matches_the_oracle(shape, dtype, odd):
+    """Example 3's lattice with the axes swapped: Fourier dimension 0 and a
+    cosine (sine) dimension 1 through the row passes' pairing step, sampled
+    every 7 steps (no sample at the end) and every 10 (one at the end)."""
+    w = W.symmetric_gpe_2d(npaths=3, n0=shape[1], n1=shape[0], L=6.0, dt=1e-3, nsteps=20)
+    if odd:
+        w.basis = (W.BASIS_SIN, W.BASIS_FOURIER)
+        w.psi0 = w.psi0 * w.coords_of(0)[None, :, None]
+    wt = _transposed(w)
+    for every in (7, 10):
+        got, pp, pq = gpu_run(wt, dtype, sample_every=every)
+        ref, opp, opq = O.run_workload(wt, sample_every=every)
+        _check(got, ref, pp, opp, pq, opq, TOL[dtype])
+
+
+@pytest.mark.parametrize("bases", [(W.BASIS_COS, W.BASIS_COS), (W.BASIS_SIN, W.BASIS_COS),
+                                   (W.BASIS_COS, W.BASIS_SIN)])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_both_dimensions_cosine_or_sine(bases, dtype):
+    """A quarter-domain trapped GPE, (0, L)^2 with a cosine or sine basis in
+    each dimension: the column pass's and the row pass's pairing steps
+    together, with the moments' Parseval weights in both dimensions."""
+    n0, n1, L = 32, 64, 6.0
+    x = (np.arange(n0) + 0.5) * (L / n0)
+    y = (np.arange(n1) + 0.5) * (L / n1)
+    fx = x if bases[0] == W.BASIS_SIN else np.ones_like(x)
+    fy = y if bases[1] == W.BASIS_SIN else np.ones_like(y)
+    rng = np.random.default_rng(21)
+    psi0 = np.stack([a * np.exp(-(x[:, None] ** 2 + y[None, :] ** 2) / 2) * fx[:, None] * fy[None, :]
+                     for a in rng.uniform(0.5, 1.5, 2)]).astype(np.complex128)
+    w = W.Workload("quarter_gpe", (n0, n1), (0.0, 0.0), (L, L), 0j, -0.5j, 10.0, W.POT_HARMONIC, (1.0, 1.0), None,
+                   W.NOISE_NONE, 0.0, 0, 1e-3, 16, psi0, basis=bases)
+    got, pp, pq = gpu_run(w, dtype, sample_every=8)
+    ref, opp, opq = O.run_workload(w, sample_every=8)
+    _check(got, ref, pp, opp, pq, opq, TOL[dtype])
+
+
+def test_noise_on_a_sine_dimension_1():
+    w = W.symmetric_gpe_2d(npaths=3, n0=64, n1=32, L=6.0, dt=1e-3, nsteps=12)
+    w.basis = (W.BASIS_SIN, W.BASIS_FOURIER)
+    w.psi0 = w.psi0 * w.coords_of(0)[None, :, None]
+    w.noise_kind, w.noise_amp, w.seed = W.NOISE_ADD_COMPLEX, 0.02, 5
+    wt = _transposed(w)
+    got, pp, pq = gpu_run(wt, "c128", sample_every=6, path0=1, npaths=2)
+    ref, opp, opq = O.run_workload(wt, sample_every=6, path0=1, npaths=2)
+    _check(got, ref, pp, opp, pq, opq, 1e-10)
+
+
+def test_cosine_dimension_1_with_the_fast_column_pass():
+    """complex64, Fourier dimension 0 of 256 points (the warp column pass) with
+    a cosine dimension 1 of 128 (generic rows): equals the generic passes."""
+    wt = _transposed(W.symmetric_gpe_2d(npaths=2, n0=128, n1=256, L=6.0, dt=1e-3, nsteps=8))
+    got, pp, pq = gpu_run(wt, "c64", sample_every=4)
+    ref, opp, opq = O.run_workload(wt, sample_every=4)
+    _check(got, ref, pp, opp, pq, opq, 1e-4)
+    gen, _, _ = gpu_run(wt, "c64", variant=1)
+    assert rel_l2(got.reshape(2, -1), gen.reshape(2, -1)) < 1e-5
+
+
 def test_batch_with_cosine_and_fourier_members():
     import torch
     from paper_1204_4255_gb300 import xsde
@@ -160,9 +232,13 @@ def test_lattices_and_calls_that_reject_the_bases():
     assert rejected(w1, lambda P, psi: P.integrate_plain(psi, 1e-3, 2))
     assert rejected(w1, lambda P, psi: P.integrate_adaptive(psi, 0.01, 1e-6, 1e-3))
     assert rejected(w1, lambda P, psi: P.set_nonlocal(np.ones(256, dtype=np.complex128)))
-    w3 = W.symmetric_gpe_2d(npaths=1, n0=32, n1=32, nsteps=2)
-    w3.basis = (W.BASIS_FOURIER, W.BASIS_COS)
-    assert rejected(w3, lambda P, psi: P.integrate(psi, 1e-3, 2))            # cosine dimension 1
+    w3 = _transposed(W.symmetric_gpe_2d(npaths=1, n0=32, n1=32, nsteps=2))
+    from paper_1204_4255_gb300 import xsde as X
+
+    def semi_implicit(P, psi):
+        X.xsde_set_scheme(P.prob, X.XSDE_SCHEME_SEMI_IMPLICIT)
+        P.integrate(psi, 1e-3, 2)
+    assert rejected(w3, semi_implicit)                                        # cosine dimension 1, SI
     w4 = W.gpe_3d(n=16, nsteps=2)
     w4.basis = (W.BASIS_COS, 0, 0)
     assert rejected(w4, lambda P, psi: P.integrate(psi, 1e-3, 2))

@@ -101,3 +101,26 @@ def test_example3_lattice_equals_the_extended_2d_run(odd):
     full, fpp, _ = O.run_workload(ext, sample_every=10)
     assert np.max(np.abs(full[:, n0:] - half)) < 1e-12
     assert np.allclose(hpp, fpp / 2, rtol=1e-12, atol=0)
+
+
+def test_swapping_the_axes_of_a_2d_cosine_or_sine_lattice():
+    """The oracle's transforms act along either dimension: Example 3's lattice
+    with its axes swapped (a cosine / sine dimension 1) gives the transposed
+    state and the same norm and energy samples."""
+    import numpy as np
+    import workloads as W
+    from oracle import oracle as O
+    for odd in (False, True):
+        w = W.symmetric_gpe_2d(npaths=2, n0=32, n1=16, L=6.0, dt=1e-3, nsteps=12)
+        if odd:
+            w.basis = (W.BASIS_SIN, W.BASIS_FOURIER)
+            w.psi0 = w.psi0 * w.coords_of(0)[None, :, None]
+        t = W.Workload(w.name + "_t", (w.n[1], w.n[0]), (w.xmin[1], w.xmin[0]), (w.xmax[1], w.xmax[0]), w.c0,
+                       w.c2, w.gnl, w.pot_kind, (w.omega[1], w.omega[0]), None, w.noise_kind, w.noise_amp, w.seed,
+                       w.dt, w.nsteps, np.ascontiguousarray(w.psi0.transpose(0, 2, 1)), basis=(w.basis[1], w.basis[0]))
+        a, pa, qa = O.run_workload(w, sample_every=6)
+        b, pb, qb = O.run_workload(t, sample_every=6)
+        assert np.max(np.abs(b - a.transpose(0, 2, 1))) < 1e-12 * np.max(np.abs(a))
+        assert np.allclose(pb, pa, rtol=1e-12, atol=0)
+        qt = qa.reshape(qa.shape[0], 32, 16, 2).transpose(0, 2, 1, 3).reshape(qb.shape)
+        assert np.max(np.abs(qb - qt)) < 1e-12 * np.max(np.abs(qt))   # tails ~1e-28: against the peak
