@@ -143,10 +143,11 @@ int64_t xsde_grid_points(const xsde_grid *grid);
  * of the points taken in even-odd order (Makhoul's algorithm) and one pairing
  * of mode k with n-k.  basis: ndim entries of XSDE_BASIS_*, read during the
  * call; the default is all Fourier.  Set it before creating problems, fields
- * or noise from the grid (they copy it).  Runs on 1D lattices and on either
- * or both dimensions of 2D lattices (RK4IP; a cosine / sine dimension 1 runs
- * the generic row passes and takes its samples between chunks of steps, from
- * the real-space field); 3D lattices, the semi-implicit scheme on 2D lattices,
+ * or noise from the grid (they copy it).  Runs on 1D lattices and on any
+ * dimensions of 2D and 3D lattices (RK4IP; a cosine / sine last dimension runs
+ * the generic row passes, and a 2D one takes its samples between chunks of
+ * steps from the real-space field; 3D cosine / sine columns run the generic
+ * column passes); the semi-implicit scheme on 2D and 3D lattices,
  * xsde_integrate_plain, xsde_integrate_adaptive, xsde_adjoint,
  * xsde_integrate_static_scratch and xsde_set_nonlocal report XSDE_EUNSUPPORTED
  * for such a problem.  A 1D cosine / sine problem has one launch shape

@@ -80,7 +80,8 @@ struct xsde_problem {
     int scheme = XSDE_SCHEME_RK4IP;   // see xsde_set_scheme
     void *d_knl = nullptr;    // non-local kernel khat/npts in the problem's precision [npts]
     void *d_B = nullptr;      // cosine / sine dimension 0: the B table of its pair step
-    void *d_B1 = nullptr;     // cosine / sine dimension 1 of a 2D lattice: the B table of its pair step
+    void *d_B1 = nullptr;     // cosine / sine dimension 1: the B table of its pair step
+    void *d_B2 = nullptr;     // cosine / sine dimension 2 of a 3D lattice: the B table of its pair step
     void *d_Ef[3] = {nullptr, nullptr, nullptr};   // whole-step factors exp(L dt) per dimension (2D/3D semi-implicit)
     bool nonlocal = false;    // see xsde_set_nonlocal
     uint64_t generation = 0;  // bumped by every call that changes what integrate launches
@@ -400,6 +401,13 @@ template <typename V> int ensure_tables(xsde_problem *p, double dt, cudaStream_t
                     e[i] = d == 0 ? std::exp((c0 + c2 * (k * k)) * tau) / ((double)g.n[0] * g.n[1] * g.n[2])
                                   : std::exp(c2 * (k * k) * tau);
                 }
+                if (h == 0 && g.basis[d] != XSDE_BASIS_FOURIER) {
+                    // a cosine / sine dimension: the A table in E[d], the B table beside it
+                    std::vector<std::complex<double>> A, B;
+                    trig_pair_tables(g.basis[d], e, A, B);
+                    e = A;
+                    if ((rc = upload<V>(B, d == 0 ? &p->d_B : d == 1 ? &p->d_B1 : &p->d_B2, s)) != XSDE_OK) return rc;
+                }
                 if ((rc = upload<V>(e, h == 0 ? &p->d_E[d] : &p->d_Ef[d], s)) != XSDE_OK) return rc;
             }
         }
@@ -518,6 +526,7 @@ int row_pass_kind(const xsde_problem *p, int n1, int64_t lines) {
 }
 int col_pass_kind(const xsde_problem *p, int n0, int64_t n1, int basis0) {
     const int v = p->kernel_variant;
+    if (basis0 && p->grid.ndim == 3) return PASS_GENERIC;   // 3D cosine / sine columns: the generic pass
     if (v == 0 && !basis0 && warp_col_supported(n0, n1)) return PASS_WARP;
     if ((v == 0 || v == 3) && tma_col_supported(n0) && n1 % COL_TMA_C == 0) return PASS_TMA;
     return PASS_GENERIC;
@@ -674,6 +683,16 @@ int run_3d(xsde_problem *p, void *psi, int64_t nsteps, int64_t npaths, uint64_t 
     q0.tw0 = static_cast<const tw_t<R> *>(p->d_tw[0]);
     q0.E0 = static_cast<const V *>(p->d_E[0]);
     q0.kinner = g.n[2];
+    // cosine / sine dimensions: each pass pairs along its own dimension; the
+    // spectral dimension-0 pass weighs the modes of dimensions 1 and 2
+    qr.basis1 = g.basis[2];
+    qr.B1 = static_cast<const V *>(p->d_B2);
+    q1.basis0 = g.basis[1];
+    q1.B0 = static_cast<const V *>(p->d_B1);
+    q0.basis0 = g.basis[0];
+    q0.B0 = static_cast<const V *>(p->d_B);
+    q0.basis1 = g.basis[1];
+    q0.basis2 = g.basis[2];
     if (p->scheme == XSDE_SCHEME_SEMI_IMPLICIT) {
         if (!p->d_Ef[0] || !p->d_Ef[1] || !p->d_Ef[2]) return fail(XSDE_EINVAL, "semi-implicit 3D step: tables missing");
         return run_si_3d<R>(p, qr, q1, q0, nsteps, npaths, step0, s);
@@ -693,9 +712,10 @@ int run_3d(xsde_problem *p, void *psi, int64_t nsteps, int64_t npaths, uint64_t 
         if ((uintptr_t)psi % 16 == 0 && (uintptr_t)p->d_scratch % 16 == 0) {
             rk = row_pass_kind(p, g.n[2], npaths * g.n[0] * g.n[1]);
             // dimension 1: [npaths n0 n1][n2]; dimension 0: [npaths n0][n1 n2]
-            ck1 = col_maps(col_pass_kind(p, g.n[1], g.n[2], 0), &map1A, &map1B, psi, p->d_scratch,
+            ck1 = col_maps(col_pass_kind(p, g.n[1], g.n[2], g.basis[1]), &map1A, &map1B, psi, p->d_scratch,
                            npaths * g.n[0] * g.n[1], g.n[2], g.n[1]);
-            ck0 = col_maps(col_pass_kind(p, g.n[0], (int64_t)g.n[1] * g.n[2], 0), &map0A, &map0B, psi, p->d_scratch,
+            ck0 = col_maps(col_pass_kind(p, g.n[0], (int64_t)g.n[1] * g.n[2], g.basis[0]), &map0A, &map0B, psi,
+                           p->d_scratch,
                            npaths * g.n[0], (int64_t)g.n[1] * g.n[2], g.n[0]);
             q1.tw0w = static_cast<const tw_t<R> *>(p->d_tw2[1]);
             q0.tw0w = static_cast<const tw_t<R> *>(p->d_tw2[0]);
@@ -1159,9 +1179,8 @@ int check_integrate(const char *who, xsde_problem *p, const xsde_vector *psi, do
         return fail(XSDE_EUNSUPPORTED, "%s: the non-local term runs with RK4IP only", who);
     if (any_basis(p->grid)) {
         const xsde_grid &g = p->grid;
-        if (g.ndim == 3) return fail(XSDE_EUNSUPPORTED, "%s: cosine / sine bases on 1D and 2D lattices only", who);
-        if (g.ndim == 2 && p->scheme != XSDE_SCHEME_RK4IP)
-            return fail(XSDE_EUNSUPPORTED, "%s: the semi-implicit scheme on 2D Fourier lattices only", who);
+        if (g.ndim >= 2 && p->scheme != XSDE_SCHEME_RK4IP)
+            return fail(XSDE_EUNSUPPORTED, "%s: the semi-implicit scheme on 2D / 3D Fourier lattices only", who);
     }
     int dev = -1;
     cudaGetDevice(&dev);
@@ -1333,6 +1352,7 @@ void xsde_problem_destroy(xsde_problem *p) {
     cudaFree(p->d_knl);
     cudaFree(p->d_B);
     cudaFree(p->d_B1);
+    cudaFree(p->d_B2);
     for (int d = 0; d < 3; ++d) cudaFree(p->d_Ef[d]);
     cudaFree(p->d_scratch);
     cudaFree(p->d_adj);

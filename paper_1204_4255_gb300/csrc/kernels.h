@@ -171,6 +171,9 @@ template <typename R> struct Params2D {
     // table of its pair step (hi[n1] | lo[n1]); E1 then holds the A table
     int basis1 = 0;
     const cx<R> *B1 = nullptr;
+    // 3D spectral pass along dimension 0: the basis of dimension 2 (that of
+    // dimension 1 in basis1); the column index splits as (k1, k2) by kinner
+    int basis2 = 0;
     // complex64 TMA row pass: the paired twiddles of fftp_fwd / fftp_bwd (fft.cuh)
     // for the row dimension
     const tw_t<R> *tw1p = nullptr;

@@ -502,10 +502,17 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
         // sum_k Re(i L(k)) |F psi|^2 dV / N, accumulated into the energy of this path.
         // The column index is k1 (2D) or the pair (k1, k2) = (col / kinner, col % kinner) (3D).
         double kc2;
+        double wc = 1.0;   // Parseval weights of cosine / sine dimensions 1 and 2
         if (p.kinner > 0) {
             const int ia = col / p.kinner, ib = col - ia * p.kinner, nm = n1 / p.kinner;
-            const double ka = p.sm.kscale[1] * (ia < nm / 2 ? ia : ia - nm);
-            const double kb = p.sm.kscale[2] * (ib < p.kinner / 2 ? ib : ib - p.kinner);
+            // a cosine / sine dimension holds its cosine spectrum (sine mode n-k
+            // at k), weight 2 for every mode but slot 0
+            const double ka = p.sm.kscale[1] * (p.basis1 == 1 ? ia : p.basis1 == 2 ? nm - ia
+                                                                   : (ia < nm / 2 ? ia : ia - nm));
+            const double kb = p.sm.kscale[2] * (p.basis2 == 1 ? ib : p.basis2 == 2 ? p.kinner - ib
+                                                                   : (ib < p.kinner / 2 ? ib : ib - p.kinner));
+            if (p.basis1 && ia != 0) wc *= 2.0;
+            if (p.basis2 && ib != 0) wc *= 2.0;
             kc2 = ka * ka + kb * kb;
         } else if (p.basis1) {
             // cosine / sine dimension 1: B holds the cosine spectrum X_k1 (sine
@@ -537,8 +544,8 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
                 s += (p.sm.h0 + p.sm.h2 * (k0 * k0 + kc2)) * (double)cabs2(f[m]);
             }
         }
-        s *= w;
-        if (p.basis1 && p.kinner == 0 && col != 0) s *= 2.0;
+        if (p.basis1 && p.kinner == 0 && col != 0) wc = 2.0;
+        s *= w * wc;
         s = warp_sum(s);
         __syncthreads();
         if ((threadIdx.x & 31) == 0) scratch[threadIdx.x >> 5] = s;
@@ -590,6 +597,21 @@ __global__ void __launch_bounds__(ColCfg<R, N0>::THREADS) col_pass_kernel(const 
             if constexpr (TRIG) partners(y, yq);
             kinetic(y[0], yq[0]);
         } else {
+            if constexpr (TRIG && MODE == COL_FFT_FWD) {
+                // a cosine / sine dimension 1 of a 3D sample: the cosine spectrum
+                // X_k = (w_k V_k + conj(w_k) V_{N0-k}) / 2, w_k = exp(-i pi k / 2 N0)
+                V yq[1][E];
+                partners(y, yq);
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    double sn, cs;
+                    sincospi(-(double)(t + m * T) / (2.0 * N0), &sn, &cs);
+                    const double yr = (double)y[0][m].x, yi = (double)y[0][m].y;
+                    const double qr = (double)yq[0][m].x, qi = (double)yq[0][m].y;
+                    y[0][m] = mk<V>((R)(0.5 * (cs * (yr + qr) - sn * (yi - qi))),
+                                    (R)(0.5 * (cs * (yi + qi) + sn * (yr - qr))));
+                }
+            }
 #pragma unroll
             for (int m = 0; m < E; ++m) p.B[base + (int64_t)(t + m * T) * n1] = y[0][m];   // 3D only
         }
@@ -662,7 +684,7 @@ template <typename R, int N0, int MODE> cudaError_t col_launch(const Params2D<R>
     using Cfg = ColCfg<R, N0>;
     const size_t smem = (size_t)2 * N0 * Cfg::C * sizeof(cx<R>) + (Cfg::THREADS / 32 + 1) * sizeof(double);
     auto kern = col_pass_kernel<R, N0, MODE>;
-    if constexpr (MODE != COL_FFT_FWD && MODE != COL_FFT_BWD && MODE != COL_SINGLE && MODE != COL_CONV)
+    if constexpr (MODE != COL_FFT_BWD && MODE != COL_SINGLE && MODE != COL_CONV)
         if (p.basis0) kern = col_pass_kernel<R, N0, MODE, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -702,7 +724,7 @@ template <typename R> cudaError_t launch_row_pass(int mode, const Params2D<R> &p
 }
 
 template <typename R> cudaError_t launch_col_pass(int mode, const Params2D<R> &p, cudaStream_t s) {
-    if (p.basis0 && (p.ndim != 2 || mode == COL_FFT_FWD || mode == COL_FFT_BWD)) return cudaErrorInvalidValue;
+    if (p.basis0 && (mode == COL_FFT_BWD || mode == COL_SINGLE || mode == COL_CONV)) return cudaErrorInvalidValue;
     switch (p.n0) {
         case 16: return col_mode<R, 16>(mode, p, s);
         case 32: return col_mode<R, 32>(mode, p, s);

@@ -108,6 +108,16 @@ wt = W.Workload(w.name + "_t", (w.n[1], w.n[0]), (w.xmin[1], w.xmin[0]), (w.xmax
                 w.nsteps, np.ascontiguousarray(w.psi0.transpose(0, 2, 1)), basis=(w.basis[1], w.basis[0]))
 got, _, _ = gpu_run(wt, "c64", sample_every=3)
 case("2d_sine_dimension_1", got, O.run_workload(wt, sample_every=3)[0])
+# a 3D lattice with a cosine dimension 1 and a sine dimension 2
+x1 = (np.arange(32) + 0.5) * (5.0 / 32)
+x2 = (np.arange(16) + 0.5) * (5.0 / 16)
+x0 = -5.0 + np.arange(16) * (10.0 / 16)
+g0 = np.exp(-(x0[:, None, None] ** 2 + x1[None, :, None] ** 2 + x2[None, None, :] ** 2) / 2) * x2[None, None, :]
+w = W.Workload("trap_3d", (16, 32, 16), (-5.0, 0.0, 0.0), (5.0, 5.0, 5.0), 0j, -0.5j, 10.0, W.POT_HARMONIC,
+               (1.0, 1.0, 1.0), None, W.NOISE_NONE, 0.0, 0, 1e-3, 4, np.stack([g0, 0.7 * g0]).astype(np.complex128),
+               basis=(W.BASIS_FOURIER, W.BASIS_COS, W.BASIS_SIN))
+got, _, _ = gpu_run(w, "c64", sample_every=2)
+case("3d_cosine_sine", got, O.run_workload(w, sample_every=2)[0])
 # adjoint (loss against the oracle adjoint's)
 w = W.adjoint_control(n=256, nsteps=20)
 P = make_problem(w, "c128")

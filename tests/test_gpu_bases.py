@@ -4,8 +4,9 @@ DST-II written out as sums: every 1D length, both precisions, ragged path
 counts, moments, noise, a time-dependent table, the semi-implicit scheme, the
 2D lattice of Example 3 (cosine or sine dimension 0, Fourier dimension 1) up
 to its full size, the same lattice with its axes swapped (a cosine or sine
-dimension 1) and with both dimensions cosine / sine, batches, and the calls
-that reject such lattices.
+dimension 1) and with both dimensions cosine / sine, 3D lattices with cosine /
+sine dimensions in every position, batches, and the calls that reject such
+lattices.
 
 Tolerances: complex128 within 1e-10 relative L2 of the oracle, complex64
 within 1e-4."""
@@ -192,6 +193,54 @@ def test_cosine_dimension_1_with_the_fast_column_pass():
     assert rel_l2(got.reshape(2, -1), gen.reshape(2, -1)) < 1e-5
 
 
+def _trap_3d(bases, n, nsteps=12, dt=1e-3, L=5.0, npaths=2, seed=31):
+    """The 3D trapped GPE with a cosine (sine) dimension on (0, L) cell-centred
+    and a Fourier dimension on [-L, L): each path a displaced, scaled Gaussian,
+    times x along a sine dimension (odd about 0)."""
+    axes, xmin, xmax = [], [], []
+    for d, b in enumerate(bases):
+        if b == W.BASIS_FOURIER:
+            axes.append(-L + np.arange(n[d]) * (2 * L / n[d]))
+            xmin.append(-L)
+        else:
+            axes.append((np.arange(n[d]) + 0.5) * (L / n[d]))
+            xmin.append(0.0)
+        xmax.append(L)
+    X = np.meshgrid(*axes, indexing="ij")
+    rng = np.random.default_rng(seed)
+    psi0 = []
+    for _ in range(npaths):
+        a, w = rng.uniform(0.5, 1.5), rng.uniform(0.8, 1.25)
+        f = a * np.exp(-sum(x * x for x in X) / (2 * w * w))
+        for d, b in enumerate(bases):
+            if b == W.BASIS_FOURIER:
+                f = f * np.exp(1j * rng.uniform(-0.5, 0.5) * X[d])
+            elif b == W.BASIS_SIN:
+                f = f * X[d]
+        psi0.append(f)
+    return W.Workload("trap_3d", tuple(n), tuple(xmin), tuple(xmax), 0j, -0.5j, 10.0, W.POT_HARMONIC,
+                      (1.0, 1.0, 1.0), None, W.NOISE_NONE, 0.0, 0, dt, nsteps,
+                      np.stack(psi0).astype(np.complex128), basis=tuple(bases))
+
+
+@pytest.mark.parametrize("bases", [(W.BASIS_COS, W.BASIS_FOURIER, W.BASIS_FOURIER),
+                                   (W.BASIS_FOURIER, W.BASIS_SIN, W.BASIS_FOURIER),
+                                   (W.BASIS_FOURIER, W.BASIS_FOURIER, W.BASIS_COS),
+                                   (W.BASIS_SIN, W.BASIS_COS, W.BASIS_SIN)])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_3d_cosine_and_sine_dimensions(bases, dtype):
+    """3D lattices with cosine / sine dimensions in every position: the column
+    passes' and the row pass's pairing steps, the cosine spectra of the 3D
+    sample (row pass, dimension-1 pass) and the Parseval weights of all three
+    dimensions; sampled every 4 steps (one sample at the end) and every 5
+    (none)."""
+    w = _trap_3d(bases, (16, 32, 16))
+    for every in (4, 5):
+        got, pp, pq = gpu_run(w, dtype, sample_every=every)
+        ref, opp, opq = O.run_workload(w, sample_every=every)
+        _check(got, ref, pp, opp, pq, opq, TOL[dtype])
+
+
 def test_batch_with_cosine_and_fourier_members():
     import torch
     from paper_1204_4255_gb300 import xsde
@@ -239,6 +288,5 @@ def test_lattices_and_calls_that_reject_the_bases():
         X.xsde_set_scheme(P.prob, X.XSDE_SCHEME_SEMI_IMPLICIT)
         P.integrate(psi, 1e-3, 2)
     assert rejected(w3, semi_implicit)                                        # cosine dimension 1, SI
-    w4 = W.gpe_3d(n=16, nsteps=2)
-    w4.basis = (W.BASIS_COS, 0, 0)
-    assert rejected(w4, lambda P, psi: P.integrate(psi, 1e-3, 2))
+    w4 = _trap_3d((W.BASIS_COS, W.BASIS_FOURIER, W.BASIS_FOURIER), (16, 16, 16), nsteps=2)
+    assert rejected(w4, semi_implicit)                                        # 3D cosine, SI
