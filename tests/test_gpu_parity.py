@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle on the
 same seeded inputs, plus closed forms the paper's problems fix.
 
-Tolerances (spec bar): raw Philox words bit-exact; C128 runs within
+Tolerances: raw Philox words bit-exact; C128 runs within
 1e-10 relative L2 of the oracle after the full run; C64 runs within 1e-4
 relative L2 of the FP64 oracle; ensemble moments within 3 standard errors.
 """
