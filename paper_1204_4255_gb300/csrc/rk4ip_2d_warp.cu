@@ -54,7 +54,9 @@ template <int N0> struct ColW {
     static constexpr int BOXR = N0 < 256 ? N0 : 256;           // tensor-copy box rows
     static constexpr size_t TILE = (size_t)N0 * C * sizeof(V); // 32 / 16 / 8 KB
     static constexpr int NTW = warp_fft_table_size<N0, E>();
-    static constexpr size_t SMEM = 1024 + NST * TILE + NTW * sizeof(TW) + 2 * N0 * sizeof(V) +
+    // (512 points: a compact (c, s) copy of the twiddles for the forward, NTW float2)
+    static constexpr size_t TWF = N0 > 256 ? NTW * sizeof(float2) : 0;
+    static constexpr size_t SMEM = 1024 + NST * TILE + NTW * sizeof(TW) + 2 * N0 * sizeof(V) + TWF +
                                    NST * (sizeof(uint64_t) + sizeof(long long) + sizeof(int)) + 16;
     static constexpr int CTAS_PER_SM = N0 == 512 ? 2 : N0 == 256 ? 3 : 6;
     static_assert(CTAS_PER_SM * (SMEM + 1024) <= 233472, "shared memory per SM");
@@ -78,7 +80,8 @@ __global__ void __launch_bounds__(ColW<N0>::THREADS, ColW<N0>::CTAS_PER_SM)
     unsigned char *tiles = base;
     TW *tw_s = reinterpret_cast<TW *>(base + NST * Cfg::TILE);
     V *e0_s = reinterpret_cast<V *>(tw_s + Cfg::NTW);
-    uint64_t *full = reinterpret_cast<uint64_t *>(e0_s + 2 * N0);   // e0_s: hi[N0] | lo[N0]
+    float2 *twf_s = reinterpret_cast<float2 *>(e0_s + 2 * N0);          // e0_s: hi[N0] | lo[N0]
+    uint64_t *full = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(twf_s) + Cfg::TWF);
     volatile long long *issued = reinterpret_cast<volatile long long *>(full + NST);   // last item loaded per stage
     int *done = reinterpret_cast<int *>(const_cast<long long *>(issued) + NST);         // warps finished per stage
     volatile int *abort_flag = done + NST;
@@ -93,11 +96,19 @@ __global__ void __launch_bounds__(ColW<N0>::THREADS, ColW<N0>::CTAS_PER_SM)
     // columns of 128 and 256 points (shared-memory-bound at 16 points a lane)
     // stage the paired twiddles as split (c, s) / (c eps, s eps) arrays, so the
     // forward reads 8 bytes a lane at an 8-byte stride; 512 keeps float4 entries
+    // for the backward (one 16-byte read a twiddle) and a compact (c, s) copy
+    // for the forward
     constexpr bool SPLIT = N0 <= 256;
     float2 *tw_hi = reinterpret_cast<float2 *>(tw_s), *tw_lo = tw_hi + Cfg::NTW;
-    if constexpr (SPLIT) stage_paired(tw_hi, tw_lo, p.tw0w, Cfg::NTW, tid, blockDim.x);
-    else
-        for (int i = tid; i < Cfg::NTW; i += blockDim.x) tw_s[i] = p.tw0w[i];
+    if constexpr (SPLIT) {
+        stage_paired(tw_hi, tw_lo, p.tw0w, Cfg::NTW, tid, blockDim.x);
+    } else {
+        for (int i = tid; i < Cfg::NTW; i += blockDim.x) {
+            const TW w = p.tw0w[i];
+            tw_s[i] = w;
+            twf_s[i] = make_float2(w.x, w.y);
+        }
+    }
     for (int i = tid; i < 2 * N0; i += blockDim.x) e0_s[i] = p.E0[i];
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) {
@@ -181,6 +192,11 @@ __global__ void __launch_bounds__(ColW<N0>::THREADS, ColW<N0>::CTAS_PER_SM)
         if constexpr (SPLIT) return PairedTwiddles{tw_hi, tw_lo};
         else return TwiddleTable<TW>{tw_s};
     }();
+    // the forward's twiddles: the (c, s) halves only (tw_fwd reads no more)
+    const auto twf = [&] {
+        if constexpr (SPLIT) return PairedTwiddles{tw_hi, tw_lo};
+        else return PairedTwiddles{twf_s, twf_s};
+    }();
     const bool sample = p.sample_slot >= 0;
     for (int64_t k = 0; k < mine; ++k) {
         const int s = (int)(k % NST);
@@ -202,7 +218,7 @@ __global__ void __launch_bounds__(ColW<N0>::THREADS, ColW<N0>::CTAS_PER_SM)
 #pragma unroll
         for (int m = 0; m < E; ++m) x[m] = *at(t + P * m);
         __syncwarp();
-        warp_fft<N0, E>(x, t, xat, tw);
+        warp_fft<N0, E>(x, t, xat, twf);
         if (sample && vec == 0) {
             // kinetic energy of a_n: sum_k Re(i L(k)) |F psi|^2 dV/(n0 n1); the
             // dimension-1 factor of exp(L dt/2) already applied is divided out
