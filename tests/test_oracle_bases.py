@@ -10,7 +10,9 @@ mathematics fixes:
 * a full RK4IP run on (0, L) with the cosine (sine) basis equals the Fourier
   run of the even (odd) extension on the doubled domain, in 1D and with a
   Fourier second dimension (Example 3's lattice), including a time-dependent
-  potential; norm and energy are half the extended run's.
+  potential, and in 3D with a cosine and a sine dimension extended together;
+  norm and energy are the extended run's divided by the number of copies;
+* swapping the axes of a 2D lattice transposes the run.
 """
 import numpy as np
 import pytest
@@ -107,9 +109,6 @@ def test_swapping_the_axes_of_a_2d_cosine_or_sine_lattice():
     """The oracle's transforms act along either dimension: Example 3's lattice
     with its axes swapped (a cosine / sine dimension 1) gives the transposed
     state and the same norm and energy samples."""
-    import numpy as np
-    import workloads as W
-    from oracle import oracle as O
     for odd in (False, True):
         w = W.symmetric_gpe_2d(npaths=2, n0=32, n1=16, L=6.0, dt=1e-3, nsteps=12)
         if odd:
@@ -124,3 +123,27 @@ def test_swapping_the_axes_of_a_2d_cosine_or_sine_lattice():
         assert np.allclose(pb, pa, rtol=1e-12, atol=0)
         qt = qa.reshape(qa.shape[0], 32, 16, 2).transpose(0, 2, 1, 3).reshape(qb.shape)
         assert np.max(np.abs(qb - qt)) < 1e-12 * np.max(np.abs(qt))   # tails ~1e-28: against the peak
+
+
+def test_3d_cosine_and_sine_dimensions_equal_the_extended_run():
+    """A 3D lattice with a cosine dimension 1 and a sine dimension 2 on (0, L)
+    equals the all-Fourier run of the state extended evenly along dimension 1
+    and oddly along dimension 2 (on [-L + dx/2, L + dx/2)), restricted to the
+    original octant; its norm and energy are a quarter of the extended run's."""
+    n0, n1, n2, L = 16, 8, 8, 4.0
+    x0 = -L + np.arange(n0) * (2 * L / n0)
+    x1 = (np.arange(n1) + 0.5) * (L / n1)
+    x2 = (np.arange(n2) + 0.5) * (L / n2)
+    g = np.exp(-(x0[:, None, None] ** 2 + x1[None, :, None] ** 2 + x2[None, None, :] ** 2) / 2)
+    psi0 = np.stack([g * x2[None, None, :] * np.exp(0.3j * x0[:, None, None]), 0.6 * g * x2[None, None, :]])
+    w = W.Workload("octant", (n0, n1, n2), (-L, 0.0, 0.0), (L, L, L), 0j, -0.5j, 10.0, W.POT_HARMONIC,
+                   (1.0, 1.0, 1.0), None, W.NOISE_NONE, 0.0, 0, 2e-3, 12, psi0.astype(np.complex128),
+                   basis=(W.BASIS_FOURIER, W.BASIS_COS, W.BASIS_SIN))
+    half, hpp, _ = O.run_workload(w, sample_every=6)
+    d1, d2 = L / n1, L / n2
+    ext0 = _extend(_extend(w.psi0, 2, False), 3, True)
+    ext = W.Workload("ext", (n0, 2 * n1, 2 * n2), (-L, -L + d1 / 2, -L + d2 / 2), (L, L + d1 / 2, L + d2 / 2),
+                     w.c0, w.c2, w.gnl, w.pot_kind, w.omega, None, W.NOISE_NONE, 0.0, 0, w.dt, w.nsteps, ext0)
+    full, fpp, _ = O.run_workload(ext, sample_every=6)
+    assert np.max(np.abs(full[:, :, n1:, n2:] - half)) < 1e-12 * np.max(np.abs(half))
+    assert np.allclose(hpp, fpp / 4, rtol=1e-12, atol=0)
