@@ -42,3 +42,19 @@ def test_convolution_kernel_is_the_dft_of_the_sampled_pair_function():
     khat = W.convolution_kernel((n,), (-L,), (L,), lambda d: 1.0 / np.sqrt(d * d + 0.25))
     assert np.max(np.abs(khat.imag)) < 1e-12
     assert np.allclose(khat[1:], khat[1:][::-1])
+
+
+def test_multidimensional_charged_condensates():
+    """The 2D and 3D charged condensates: deterministic, unit norm per path on
+    the lattice (to the sampling of the Gaussian), and a softened Coulomb
+    kernel that is real and even (the pair function is), so V_nl is real."""
+    for make, dims in ((lambda: W.charged_bec_2d(npaths=3, n=(32, 64), box=8.0), 2),
+                       (lambda: W.charged_bec_3d(npaths=3, n=(16, 32, 16)), 3)):
+        a, b = make(), make()
+        assert np.array_equal(a.psi0, b.psi0) and np.array_equal(a.knl, b.knl)
+        assert a.knl.shape == a.n and a.psi0.shape == (3,) + a.n
+        dV = np.prod([a.dx(d) for d in range(dims)])
+        assert np.allclose(np.sum(np.abs(a.psi0) ** 2, axis=tuple(range(1, dims + 1))) * dV, 1.0, rtol=1e-3)
+        assert np.max(np.abs(a.knl.imag)) < 1e-10 * np.max(np.abs(a.knl))
+        flipped = np.roll(np.flip(a.knl, axis=tuple(range(dims))), 1, axis=tuple(range(dims)))
+        assert np.allclose(a.knl, flipped, rtol=1e-12, atol=1e-12 * np.max(np.abs(a.knl)))
